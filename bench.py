@@ -1,0 +1,403 @@
+#!/usr/bin/env python3
+"""Throughput of the fused RLBM step on GB300 (MLUPS and fraction of the HBM roofline).
+
+Default workload (the 2-d massless Taylor-Green configuration): 512 x 512
+doubly periodic grid, order-2 massless quadrature (Q = 28), off-lattice
+bilinear streaming with lambda = 1, tau = 1, u0 = 0.1 c, uniform n = T = 1,
+FP32 populations with the FP64 Landau solve.  A bench step is one RLBM time
+step (one fused kernel launch over the whole grid); the L2 cache is flushed
+(a 256 MiB write) before every timed step, so each step reads its inputs
+from HBM.  Each launch is timed with CUDA events on the stream it runs on.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torch.distributed.run) every rank runs an
+independent replica on its own GPU (replicas only; the step has no exchange
+on one grid per GPU); value = all ranks' cell updates / max-over-ranks time.
+``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "tg512": dict(workload="tg512_bilinear_fp32", L=512, stream="bilinear", lam=1.0, tau=1.0,
+                  u0=0.1, precision="fp32", order=2, m=0.0, resident_steps=5000),
+    "tg512_onlattice": dict(workload="tg512_onlattice_fp32", L=512, stream="onlattice", lam=0.0,
+                            tau=1.0, u0=0.1, precision="fp32", order=2, m=0.0, resident_steps=5000),
+    "tg2048": dict(workload="tg2048_bilinear_fp32", L=2048, stream="bilinear", lam=1.0, tau=1.0,
+                   u0=0.1, precision="fp32", order=2, m=0.0, resident_steps=500),
+    "tg512_fp64": dict(workload="tg512_bilinear_fp64", L=512, stream="bilinear", lam=1.0, tau=1.0,
+                       u0=0.1, precision="fp64", order=2, m=0.0, resident_steps=200),
+}
+
+METRIC = "MLUPS"   # million lattice-cell updates per second (whole job)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_source_sha():
+    h = hashlib.sha256()
+    for name in ("step_impl.cuh", "kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_1909_04502_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic(workload):
+    """DRAM bytes per launch from the committed ncu summary of this workload,
+    or None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "step_%s.md" % workload)
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    s = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", txt)
+    if not m or not s or s.group(1) != _kernel_source_sha():
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# Oracle timing (CPU; test infrastructure) -- run in a child process pinned to
+# one thread so that the reported core count is exact.
+# ---------------------------------------------------------------------------
+
+
+def _oracle_worker(L, steps, warmup, stream, lam, tau, u0):
+    import numpy as np
+    from oracle import lattice as OL
+    from oracle import scheme as OS
+    from paper_1909_04502_gb300 import inputs
+    q = OL.massless_quadrature(2)
+    sim = OS.Simulation(q, OL.Expansion(q), L, L, tau=tau, stream=stream,
+                        lam=lam if stream == "bilinear" else None)
+    sim.init(*inputs.taylor_green(L, u0=u0))
+    sim.step(warmup)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        sim.step(1)
+        times.append(time.perf_counter() - t0)
+    print(json.dumps({"cells": L * L, "times": times, "finite": bool(np.isfinite(sim.fs).all())}))
+
+
+def run_oracle(L, steps, warmup, wl):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    cmd = [sys.executable, os.path.abspath(__file__), "--_oracle_worker",
+           json.dumps([L, steps, warmup, wl["stream"], wl["lam"], wl["tau"], wl["u0"]])]
+    out = subprocess.run(cmd, capture_output=True, text=True, env=env, cwd=ROOT)
+    if out.returncode != 0:
+        raise RuntimeError("oracle worker failed: " + out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def oracle_sample_size(wl, budget_s, nsteps):
+    """Largest square grid <= the workload's whose nsteps oracle steps fit the budget."""
+    probe = run_oracle(64, 2, 0, wl)
+    per_cell = statistics.median(probe["times"]) / probe["cells"]
+    L = wl["L"]
+    while L > 32 and per_cell * L * L * nsteps > budget_s:
+        L //= 2
+    return L
+
+
+# ---------------------------------------------------------------------------
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tg512", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--_oracle_worker", default=None)
+    args = ap.parse_args()
+    if args._oracle_worker is not None:
+        _oracle_worker(*json.loads(args._oracle_worker))
+        return
+    args.warmup = max(args.warmup, 3)
+    wl = WORKLOADS[args.workload]
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        bench_reference(args, wl)
+        return
+
+    import numpy as np
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    from paper_1909_04502_gb300 import build as _build
+    if rank == 0:
+        _build.build()
+    if dist:
+        dist.barrier()
+    from paper_1909_04502_gb300 import inputs, rlbm
+
+    L = wl["L"]
+    ncell = L * L
+    fields = [np.ascontiguousarray(a) for a in inputs.taylor_green(L, u0=wl["u0"])]
+    stream = torch.cuda.current_stream()
+    lat = rlbm.Lattice(L, L, m=wl["m"], order=wl["order"], tau=wl["tau"], stream=wl["stream"],
+                       lam=wl["lam"], precision=wl["precision"], cuda_stream=stream.cuda_stream)
+    Q = lat.Q
+    elem = 4 if wl["precision"] == "fp32" else 8
+    lat.init(*fields)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    # warm-up
+    for _ in range(args.warmup):
+        flush.zero_()
+        lat.step(1)
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            lat.step(1)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    kt = [s.elapsed_time(e) for s, e in zip(starts, ends)]   # ms per launch
+    total_ms = sum(kt)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    status = lat.sync_status(raise_on_error=False)
+
+    value = world * ncell * args.steps / (total_ms * 1e-3) / 1e6
+    ms_per_step = total_ms / args.steps
+    peak, peak_kind = _peaks()
+    alg_bytes = 2 * Q * elem * ncell                     # read + write every population once
+    achieved = alg_bytes / (ms_per_step * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": _profiled_traffic(wl["workload"]),
+                "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes,
+                "kernel": "k_step (fused stream+collide)"}
+
+    # back-to-back run of the whole job (L2 not flushed between steps)
+    lat.init(*fields)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(wl["resident_steps"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    resident_ms = e0.elapsed_time(e1)
+    resident = {"steps": wl["resident_steps"],
+                "mlups": round(ncell * wl["resident_steps"] / (resident_ms * 1e-3) / 1e6, 1),
+                "note": "whole run back to back; the 59 MB working set of 512^2 stays in the 129 MB L2"}
+
+    # end to end through the C ABI with pinned host buffers
+    host_in = [torch.from_numpy(a).pin_memory() for a in fields]
+    host_out = {k: torch.empty((L, L), dtype=torch.float64).pin_memory() for k in ("n", "ux", "uy", "T", "eps")}
+    e2e_steps = 100
+    e2e_iters = 5
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_iters):
+        lat.init(*host_in)
+        lat.step(e2e_steps)
+        _moments_to_pinned(lat, host_out)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_iters
+    e2e = {"value": round(ncell * e2e_steps / e2e_s / 1e6, 1), "unit": METRIC,
+           "h2d_bytes_per_step": 4 * 8 * ncell, "d2h_bytes_per_step": 5 * 8 * ncell,
+           "steps_per_call": e2e_steps,
+           "call": "rlbm_init(host n,u,T) + rlbm_step(100) + rlbm_moments(host n,u,T,eps), pinned"}
+
+    parity = None
+    cpu = None
+    if rank == 0:
+        parity = oracle_parity(lat, fields, wl)
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = cpu_baseline(wl)
+
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32" if elem == 4 else "f64",
+        "data": "synthetic",
+        "config": {"workload": wl["workload"], "nx": L, "ny": L, "Q": Q, "order": wl["order"],
+                   "quadrature": "App. H massless order 2", "stream": wl["stream"], "lambda": wl["lam"],
+                   "tau": wl["tau"], "u0": wl["u0"], "landau_dtype": "f64",
+                   "l2": "flushed before every timed step (256 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+        "clocks": clocks, "resident": resident, "parity": parity,
+        "status": {"nonphysical_cells": status[1]}, "wall_s_timed_region": round(wall, 4),
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    lat.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def _moments_to_pinned(lat, host_out):
+    import ctypes
+    from paper_1909_04502_gb300 import rlbm
+    ptr = [host_out[k].data_ptr() for k in ("n", "ux", "uy", "T", "eps")]
+    rc = rlbm.lib().rlbm_moments(lat.h, *ptr, None, None, 0)
+    if rc != 0:
+        raise RuntimeError(rlbm.lib().rlbm_last_error(lat.h).decode())
+
+
+def oracle_parity(lat, fields, wl):
+    """Two steps of the bench workload against the FP64 oracle, element by element."""
+    import numpy as np
+    from tests.cases import oracle_quadrature, oracle_sim, permutation, rel_linf
+    L = wl["L"]
+    if L > 1024:
+        return None
+    quad = oracle_quadrature(wl["m"], wl["order"])
+    sim = oracle_sim(quad, L, L, tau=wl["tau"], stream=wl["stream"],
+                     lam=wl["lam"] if wl["stream"] == "bilinear" else None)
+    sim.init(*fields)
+    lat.init(*fields)
+    lat.step(2)
+    sim.step(2)
+    idx = permutation(lat.n, lat.p, quad)
+    m = lat.moments()
+    return {"steps": 2, "rel_linf_f": rel_linf(lat.populations()[idx], sim.fs),
+            "rel_linf_ux": float(np.abs(m["ux"] - sim.fields.ux).max() / np.abs(sim.fields.ux).max()),
+            "bar": 1e-5 if wl["precision"] == "fp32" else 1e-12}
+
+
+def cpu_baseline(wl, budget_s=20.0, nsteps=3):
+    L = oracle_sample_size(wl, budget_s, nsteps)
+    r = run_oracle(L, nsteps, 1, wl)
+    t = sum(r["times"])
+    return {"value": round(r["cells"] * nsteps / t / 1e6, 4), "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": "%d oracle steps of the same Taylor-Green configuration on a %dx%d grid (numpy FP64, "
+                      "one thread)" % (nsteps, L, L)}
+
+
+def bench_reference(args, wl):
+    """The FP64 CPU oracle as the reference arm, on the host cores."""
+    budget = 150.0
+    L = oracle_sample_size(wl, budget, args.steps + args.warmup)
+    r = run_oracle(L, args.steps, args.warmup, wl)
+    t = sum(r["times"])
+    value = r["cells"] * args.steps / t / 1e6
+    cpu = {"value": round(value, 4), "unit": METRIC, "cores": 1, "kind": "oracle",
+           "sample": "each step one oracle time step of the Taylor-Green configuration on a %dx%d grid" % (L, L)}
+    line = {"metric": METRIC, "value": round(value, 4), "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": wl["workload"], "nx": L, "ny": L, "sample_of": [wl["L"], wl["L"]]},
+            "cpu_baseline": cpu, "e2e": {"value": round(value, 4), "unit": METRIC, "h2d_bytes_per_step": 0,
+                                         "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

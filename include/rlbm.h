@@ -1,0 +1,177 @@
+/*
+ * rlbm.h -- C ABI of the GB300-native relativistic lattice Boltzmann (RLBM) step.
+ *
+ * The method is the one of Gabbana, Simeoni, Succi, Tripiccione,
+ * "Relativistic Lattice Boltzmann Methods: Theory and Applications"
+ * (arXiv:1909.04502).  One time step is the fused per-cell update of
+ * Sec. 6.2: stream (Eq. discrete-rbe), moments N^a and T^ab (step 1),
+ * Landau-frame eigen-solve (step 2, Sec. 4), n = U.N (step 3), T from the
+ * EOS (step 4, Eq. eos-ddim), polynomial equilibrium (step 5,
+ * Eq. mj-discrete-feq), local tau (step 7) and Anderson-Witting relaxation
+ * (step 8).
+ *
+ * Units: lattice units c = k_B = T0 = 1, Delta t = 1 (Sec. 5.3, Sec. 6.1).
+ * Metric eta = diag(1, -1, -1).  Fields are FP64, row-major [y][x]
+ * (index y*nx + x).  Velocities are 3-velocities u = U^i/U^0 (fraction of c).
+ *
+ * State convention.  The library holds the post-collision populations
+ * f*(t).  rlbm_step advances t -> t+1: f(t+1) = S f*(t) (streaming),
+ * f*(t+1) = C(f(t+1)) (collision).  rlbm_init sets f(0) = f*(0) =
+ * f^eq(n, u, T) (Sec. 6.2, first paragraph: collision of an equilibrium is
+ * the identity).  rlbm_moments reports the Landau-frame fields of the
+ * streamed f(t), i.e. those computed in steps 1-4 at time t.
+ *
+ * Errors.  Every int-returning call returns RLBM_OK (0) or a negative
+ * RLBM_ERR_* code; rlbm_last_error() gives a message.  Calls are asynchronous
+ * on the handle's CUDA stream unless stated otherwise; device-side faults of
+ * the physics (a cell without a timelike Landau eigenvector, n <= 0,
+ * T <= 0, non-finite values) are recorded in a device status word and
+ * reported by rlbm_sync_status().
+ *
+ * Ownership.  Host arrays passed in are caller-owned and read or written
+ * before the call returns (the call synchronises the stream when it copies
+ * from or to host memory).  Device pointers passed in are borrowed for the
+ * duration of the call.  The handle owns every buffer it allocates;
+ * ownership never transfers.
+ */
+#ifndef RLBM_H
+#define RLBM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  RLBM_OK = 0,
+  RLBM_ERR_INVALID_ARG = -1,   /* bad parameter or size                        */
+  RLBM_ERR_UNSUPPORTED = -2,   /* valid but not implemented (e.g. d = 3)       */
+  RLBM_ERR_CUDA = -3,          /* a CUDA runtime call failed                   */
+  RLBM_ERR_NONPHYSICAL = -4,   /* a cell had no physical Landau frame          */
+  RLBM_ERR_TIMEOUT = -5,       /* a bounded device-side wait gave up           */
+  RLBM_ERR_OOM = -6,           /* device allocation failed                     */
+  RLBM_ERR_QUADRATURE = -7     /* no non-negative quadrature found             */
+};
+
+/* Quadratures (App. H; Sec. 5.3). */
+enum {
+  RLBM_QUAD_MASSLESS = 0,      /* m~ = 0: App. H (2+1)-d table of the requested order
+                                  (order 2: Q = 28, order 3: Q = 44)             */
+  RLBM_QUAD_MASSIVE = 1,       /* m~ > 0: Eq. discrete-momentum-vectors on an FS stencil,
+                                  weights from Eq. mj-orthogonal-conditions,
+                                  v0 by the line search of Sec. 5.3              */
+  RLBM_QUAD_CUSTOM = 2         /* caller table: custom_table / custom_Q           */
+};
+
+enum { RLBM_BC_PERIODIC = 0, RLBM_BC_FREEFLOW_X = 1 };
+enum { RLBM_FP64 = 0, RLBM_FP32_STORE = 1 };   /* storage/collision precision    */
+enum { RLBM_ONLATTICE = 0, RLBM_BILINEAR = 1 };
+enum { RLBM_TAU_CONST = 0, RLBM_TAU_FIELD = 1, RLBM_TAU_ETA_OVER_S = 2 };
+
+typedef struct rlbm_params {
+  int d;              /* spatial dimensions; must be 2 (a 1-D problem runs as nx x 1) */
+  double m;           /* rest mass m~ = m c^2/(k_B T0); zeta = m~/T~ (Sec. 5.2)      */
+  int order;          /* expansion order N of Eq. mj-discrete-feq: 2 or 3           */
+  int quadrature;     /* RLBM_QUAD_*                                                 */
+  const int* groups;  /* RLBM_QUAD_MASSIVE: n_groups generator vectors (x, y) of the
+                         FS stencil (Sec. 5.3); NULL selects the built-in choice   */
+  int n_groups;
+  double v0;          /* RLBM_QUAD_MASSIVE: v0 of Eq. discrete-momentum-vectors;
+                         0 = search for a non-negative solution                    */
+  const double* custom_table; /* RLBM_QUAD_CUSTOM: custom_Q rows (nx, ny, p0, px, py, w) */
+  int custom_Q;
+  int tau_mode;       /* RLBM_TAU_*                                                  */
+  double tau;         /* RLBM_TAU_CONST: relaxation time in units of Delta t        */
+  double eta_over_s;  /* RLBM_TAU_ETA_OVER_S: tau = (eta/s)(d+2) kappa / T (step 7)  */
+  double kappa;       /*   kappa = hbar/(k_B T0 dt)                                  */
+  int boundary;       /* RLBM_BC_*                                                   */
+  int nx, ny;         /* grid size in cells                                          */
+  int precision;      /* RLBM_FP64 | RLBM_FP32_STORE (FP32 populations, FP64 Landau
+                         solve and EOS inversion)                                    */
+  int stream_mode;    /* RLBM_ONLATTICE | RLBM_BILINEAR                              */
+  double lambda;      /* RLBM_BILINEAR: displacement per step = lambda * v_i cells
+                         (lambda = 1/dx in units of c dt; the on-lattice value is
+                         ||n_i|| for m~ = 0 and 1/v0 for m~ > 0)                     */
+  double n_ref, T_ref;/* reference state of the shifted FP32 storage (default 1, 1) */
+  void* stream;       /* cudaStream_t all work is issued on (NULL = legacy default) */
+} rlbm_params;
+
+typedef struct rlbm_handle rlbm_handle;
+
+/* Fill *p with defaults: d = 2, m = 0, order 2, massless quadrature, tau 1,
+ * periodic, FP32 storage, on-lattice, n_ref = T_ref = 1. */
+void rlbm_default_params(rlbm_params* p);
+
+/* Build the stencil, quadrature and equilibrium tables (Sec. 5.2-5.3, App. F-H)
+ * on the host in FP64 and allocate two population buffers, a tau buffer and a
+ * status word on the current device.  Synchronous. */
+int rlbm_create(const rlbm_params* p, rlbm_handle** out);
+
+/* Host-only planning: build the quadrature and equilibrium tables for *p
+ * exactly as rlbm_create does, without touching a GPU.  Outputs (all
+ * nullable except Q and K): nvec 2*Q ints, p 3*Q, w Q, H Q*K (row-major,
+ * f^eq_i = sum_k H_ik M_k with M the Maxwell-Juttner moments of the basis
+ * p0^e px^a py^b, e in {0,1}, e + a + b <= N, in the order 1 | p0 px py |
+ * p0px p0py pxpx pxpy pypy | p0pxpx p0pxpy p0pypy pxpxpx pxpxpy pxpypy
+ * pypypy), v0 the massive parameter.  Arrays must hold 72 rows (72*16 for H). */
+int rlbm_plan(const rlbm_params* p, int* Q, int* K, int* nvec, double* pmom, double* w,
+              double* H, double* v0);
+
+/* Release everything the handle owns.  Synchronises its stream first. */
+void rlbm_destroy(rlbm_handle* h);
+
+/* Set f(0) = f*(0) = f^eq(n, u, T) (Sec. 6.2).  n, ux, uy, T: nx*ny FP64 each,
+ * host (on_device = 0) or device (on_device = 1) pointers.  Resets t to 0. */
+int rlbm_init(rlbm_handle* h, const double* n, const double* ux, const double* uy,
+              const double* T, int on_device);
+
+/* Set the per-cell relaxation time (tau_mode RLBM_TAU_FIELD), nx*ny FP64. */
+int rlbm_set_tau_field(rlbm_handle* h, const double* tau, int on_device);
+
+/* Advance nsteps time steps (asynchronous on the handle's stream). */
+int rlbm_step(rlbm_handle* h, int nsteps);
+
+/* Landau-frame fields of f(t) (steps 1-4 of Sec. 6.2).  Every output is
+ * nullable; n, ux, uy, T, eps: nx*ny FP64; Nab: 3*nx*ny (N^0, N^x, N^y
+ * planes); Tab: 6*nx*ny (T^00, T^0x, T^0y, T^xx, T^xy, T^yy planes).
+ * With on_device = 0 the call copies to host and synchronises. */
+int rlbm_moments(rlbm_handle* h, double* n, double* ux, double* uy, double* T,
+                 double* eps, double* Nab, double* Tab, int on_device);
+
+/* Post-collision populations f*(t) as FP64 [Q][ny][nx] (unshifted), and
+ * their replacement (checkpoint / restart).  set_populations keeps t. */
+int rlbm_get_populations(rlbm_handle* h, double* f, int on_device);
+int rlbm_set_populations(rlbm_handle* h, const double* f, int on_device);
+
+/* Stencil actually used: Q, integer vectors n_i (2Q, x then y per row),
+ * momenta p_i^mu (3Q), weights w_i (Q).  Every pointer but Q is nullable. */
+int rlbm_stencil(const rlbm_handle* h, int* Q, int* nvec, double* p, double* w);
+
+/* Number of completed time steps. */
+long long rlbm_time(const rlbm_handle* h);
+
+/* Synchronise the stream and report device-side status: RLBM_OK,
+ * RLBM_ERR_NONPHYSICAL (*count, nullable, gets the number of flagged cell
+ * updates since the last call) or RLBM_ERR_CUDA.  Clears the status. */
+int rlbm_sync_status(rlbm_handle* h, long long* count);
+
+/* Change the stream subsequent calls are issued on. */
+int rlbm_set_stream(rlbm_handle* h, void* stream);
+
+/* Device pointers of the current f*(t) buffer and of the previous one
+ * (borrowed; valid until the next rlbm_step / rlbm_destroy), element size
+ * (4 or 8 bytes) and population-plane stride in elements.  FP32-storage
+ * handles hold g = f - f_ref (the reference equilibrium f_ref,i =
+ * f^eq_i(n_ref, 0, T_ref)). */
+int rlbm_buffers(rlbm_handle* h, void** cur, void** prev, int* elem_size, long long* plane);
+
+/* Message of the last error on this handle (or of the last failed
+ * rlbm_create when h is NULL).  Never NULL. */
+const char* rlbm_last_error(const rlbm_handle* h);
+
+/* Static description of an error code. */
+const char* rlbm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RLBM_H */

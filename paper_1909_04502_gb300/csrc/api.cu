@@ -1,0 +1,504 @@
+// C ABI of the RLBM library (declared in include/rlbm.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/rlbm.h"
+#include "dispatch.h"
+#include "handle.h"
+#include "setup.h"
+
+using namespace rlbm;
+
+namespace {
+
+thread_local std::string g_create_error = "no error";
+
+int fail(rlbm_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+int cuda_fail(rlbm_handle* h, cudaError_t e, const char* where) {
+  return fail(h, RLBM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define RLBM_CUDA(h, call)                                   \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+  } while (0)
+
+long long mod_pos(long long a, long long n) { return ((a % n) + n) % n; }
+
+// Device kernels converting between stored (shifted, storage precision)
+// populations and FP64 unshifted populations.
+template <typename S>
+__global__ void k_export(const S* __restrict__ src, double* __restrict__ dst, int Q, int ncell,
+                         long long plane, const double* __restrict__ fref) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)Q * ncell) return;
+  int i = (int)(idx / ncell), c = (int)(idx - (long long)i * ncell);
+  dst[idx] = (double)src[i * plane + c] + fref[i];
+}
+
+template <typename S>
+__global__ void k_import(const double* __restrict__ src, S* __restrict__ dst, int Q, int ncell,
+                         long long plane, const double* __restrict__ fref) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)Q * ncell) return;
+  int i = (int)(idx / ncell), c = (int)(idx - (long long)i * ncell);
+  dst[i * plane + c] = (S)(src[idx] - fref[i]);
+}
+
+template <typename S>
+__global__ void k_tau_import(const double* __restrict__ src, S* __restrict__ dst, int ncell) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < ncell) dst[idx] = (S)src[idx];
+}
+
+template <typename R>
+void fill_tables(const rlbm_handle* h, Tables<R>* t) {
+  std::memset(t, 0, sizeof(Tables<R>));
+  const Quadrature& q = h->q;
+  const int nx = h->p.nx, ny = h->p.ny;
+  for (int i = 0; i < q.Q; ++i) {
+    const double p0 = q.p0[i], px = q.px[i], py = q.py[i];
+    const double c[9] = {p0, px, py, p0 * p0, p0 * px, p0 * py, px * px, px * py, py * py};
+    for (int j = 0; j < 9; ++j) t->c[i][j] = (R)c[j];
+    t->vx[i] = (R)(px / p0);
+    t->vy[i] = (R)(py / p0);
+    for (int k = 0; k < h->K; ++k) t->H[i][k] = (R)h->H[(size_t)i * h->K + k];
+    t->sxp[i] = (int)mod_pos(-q.nx[i], nx);
+    t->syp[i] = (int)mod_pos(-q.ny[i], ny);
+    t->sxr[i] = -q.nx[i];
+    // off-lattice pull taps: source point x - lambda v_i
+    double src[2] = {-h->p.lambda * px / p0, -h->p.lambda * py / p0};
+    double o[2], phi[2];
+    for (int d = 0; d < 2; ++d) {
+      double r = std::nearbyint(src[d]);
+      if (std::fabs(src[d] - r) < 1e-12) src[d] = r;   // whole-cell displacement
+      o[d] = std::floor(src[d]);
+      phi[d] = src[d] - o[d];
+    }
+    t->bw[i][0] = (R)((1.0 - phi[0]) * (1.0 - phi[1]));
+    t->bw[i][1] = (R)(phi[0] * (1.0 - phi[1]));
+    t->bw[i][2] = (R)((1.0 - phi[0]) * phi[1]);
+    t->bw[i][3] = (R)(phi[0] * phi[1]);
+    t->oxp[i] = (int)mod_pos((long long)o[0], nx);
+    t->oyp[i] = (int)mod_pos((long long)o[1], ny);
+    t->oxr[i] = (int)o[0];
+  }
+}
+
+int build_quadrature(const rlbm_params* p, Quadrature* q, std::string* err) {
+  if (p->quadrature == RLBM_QUAD_MASSLESS) {
+    if (p->m != 0.0) { *err = "RLBM_QUAD_MASSLESS needs m = 0"; return RLBM_ERR_INVALID_ARG; }
+    return massless_quadrature(p->order, q, err) ? RLBM_OK : RLBM_ERR_INVALID_ARG;
+  }
+  if (p->quadrature == RLBM_QUAD_MASSIVE) {
+    if (!(p->m > 0.0)) { *err = "RLBM_QUAD_MASSIVE needs m > 0"; return RLBM_ERR_INVALID_ARG; }
+    if (p->groups == nullptr || p->n_groups <= 0) {
+      if (p->v0 != 0.0) { *err = "v0 given without groups"; return RLBM_ERR_INVALID_ARG; }
+      return builtin_massive(p->m, p->order, q, err) ? RLBM_OK : RLBM_ERR_QUADRATURE;
+    }
+    std::vector<int> g(p->groups, p->groups + 2 * p->n_groups);
+    double v0 = p->v0;
+    if (v0 == 0.0 && !search_v0(g, p->m, p->order, &v0, nullptr, nullptr)) {
+      *err = "no v0 gives non-negative weights on this stencil";
+      return RLBM_ERR_QUADRATURE;
+    }
+    double res;
+    if (!massive_quadrature(g, p->m, v0, p->order, q, &res, nullptr) || res > 1e-9) {
+      *err = "orthonormality conditions not satisfied on this stencil";
+      return RLBM_ERR_QUADRATURE;
+    }
+    return RLBM_OK;
+  }
+  if (p->quadrature == RLBM_QUAD_CUSTOM) {
+    if (!p->custom_table || p->custom_Q <= 0) { *err = "custom table missing"; return RLBM_ERR_INVALID_ARG; }
+    *q = Quadrature();
+    q->m = p->m;
+    q->order = p->order;
+    for (int i = 0; i < p->custom_Q; ++i) {
+      const double* r = p->custom_table + 6 * i;
+      q->nx.push_back((int)std::lround(r[0]));
+      q->ny.push_back((int)std::lround(r[1]));
+      q->p0.push_back(r[2]);
+      q->px.push_back(r[3]);
+      q->py.push_back(r[4]);
+      q->w.push_back(r[5]);
+    }
+    q->Q = p->custom_Q;
+    return RLBM_OK;
+  }
+  *err = "unknown quadrature";
+  return RLBM_ERR_INVALID_ARG;
+}
+
+}  // namespace
+
+extern "C" {
+
+void rlbm_default_params(rlbm_params* p) {
+  std::memset(p, 0, sizeof(*p));
+  p->d = 2;
+  p->m = 0.0;
+  p->order = 2;
+  p->quadrature = RLBM_QUAD_MASSLESS;
+  p->tau_mode = RLBM_TAU_CONST;
+  p->tau = 1.0;
+  p->boundary = RLBM_BC_PERIODIC;
+  p->nx = p->ny = 0;
+  p->precision = RLBM_FP32_STORE;
+  p->stream_mode = RLBM_ONLATTICE;
+  p->lambda = 0.0;
+  p->n_ref = 1.0;
+  p->T_ref = 1.0;
+}
+
+const char* rlbm_strerror(int code) {
+  switch (code) {
+    case RLBM_OK: return "ok";
+    case RLBM_ERR_INVALID_ARG: return "invalid argument";
+    case RLBM_ERR_UNSUPPORTED: return "unsupported";
+    case RLBM_ERR_CUDA: return "CUDA error";
+    case RLBM_ERR_NONPHYSICAL: return "non-physical cell state";
+    case RLBM_ERR_TIMEOUT: return "device wait timed out";
+    case RLBM_ERR_OOM: return "out of device memory";
+    case RLBM_ERR_QUADRATURE: return "no quadrature";
+  }
+  return "unknown error";
+}
+
+const char* rlbm_last_error(const rlbm_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int rlbm_plan(const rlbm_params* p, int* Q, int* K, int* nvec, double* pmom, double* w, double* H,
+              double* v0) {
+  if (!p || !Q || !K) return fail(nullptr, RLBM_ERR_INVALID_ARG, "null argument");
+  if (p->order != 2 && p->order != 3) return fail(nullptr, RLBM_ERR_INVALID_ARG, "order must be 2 or 3");
+  Quadrature q;
+  std::string err;
+  int rc = build_quadrature(p, &q, &err);
+  if (rc != RLBM_OK) return fail(nullptr, rc, err);
+  if (q.Q > kMaxQ) return fail(nullptr, RLBM_ERR_UNSUPPORTED, "too many populations");
+  std::vector<double> Hm;
+  if (!equilibrium_matrix(q, &Hm, &err)) return fail(nullptr, RLBM_ERR_QUADRATURE, err);
+  *Q = q.Q;
+  *K = (int)moment_basis(p->order).size();
+  for (int i = 0; i < q.Q; ++i) {
+    if (nvec) { nvec[2 * i] = q.nx[i]; nvec[2 * i + 1] = q.ny[i]; }
+    if (pmom) { pmom[3 * i] = q.p0[i]; pmom[3 * i + 1] = q.px[i]; pmom[3 * i + 2] = q.py[i]; }
+    if (w) w[i] = q.w[i];
+  }
+  if (H) std::copy(Hm.begin(), Hm.end(), H);
+  if (v0) *v0 = q.v0;
+  return RLBM_OK;
+}
+
+int rlbm_create(const rlbm_params* p, rlbm_handle** out) {
+  if (!p || !out) return fail(nullptr, RLBM_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (p->d != 2) return fail(nullptr, p->d == 3 ? RLBM_ERR_UNSUPPORTED : RLBM_ERR_INVALID_ARG, "d must be 2");
+  if (p->order != 2 && p->order != 3) return fail(nullptr, RLBM_ERR_INVALID_ARG, "order must be 2 or 3");
+  if (p->nx <= 0 || p->ny <= 0 || (long long)p->nx * p->ny > (1LL << 30))
+    return fail(nullptr, RLBM_ERR_INVALID_ARG, "grid size out of range");
+  if (p->precision != RLBM_FP64 && p->precision != RLBM_FP32_STORE)
+    return fail(nullptr, RLBM_ERR_INVALID_ARG, "precision");
+  if (p->boundary != RLBM_BC_PERIODIC && p->boundary != RLBM_BC_FREEFLOW_X)
+    return fail(nullptr, RLBM_ERR_INVALID_ARG, "boundary");
+  if (p->stream_mode != RLBM_ONLATTICE && p->stream_mode != RLBM_BILINEAR)
+    return fail(nullptr, RLBM_ERR_INVALID_ARG, "stream_mode");
+  if (p->stream_mode == RLBM_BILINEAR && !(p->lambda > 0.0))
+    return fail(nullptr, RLBM_ERR_INVALID_ARG, "bilinear streaming needs lambda > 0");
+  if (p->tau_mode == RLBM_TAU_CONST && !(p->tau > 0.5))
+    return fail(nullptr, RLBM_ERR_INVALID_ARG, "tau must exceed 1/2");
+  if (p->tau_mode == RLBM_TAU_ETA_OVER_S && !(p->eta_over_s > 0.0 && p->kappa > 0.0))
+    return fail(nullptr, RLBM_ERR_INVALID_ARG, "eta_over_s and kappa must be positive");
+  if (p->tau_mode < 0 || p->tau_mode > 2) return fail(nullptr, RLBM_ERR_INVALID_ARG, "tau_mode");
+  if (!(p->T_ref > 0.0) || !(p->n_ref >= 0.0)) return fail(nullptr, RLBM_ERR_INVALID_ARG, "reference state");
+
+  std::unique_ptr<rlbm_handle> h(new rlbm_handle());
+  h->p = *p;
+  h->p.groups = nullptr;
+  h->p.custom_table = nullptr;
+  std::string err;
+  int rc = build_quadrature(p, &h->q, &err);
+  if (rc != RLBM_OK) return fail(nullptr, rc, err);
+  if (h->q.Q > kMaxQ) return fail(nullptr, RLBM_ERR_UNSUPPORTED, "too many populations");
+  h->K = (int)moment_basis(p->order).size();
+  if (!equilibrium_matrix(h->q, &h->H, &err)) return fail(nullptr, RLBM_ERR_QUADRATURE, err);
+
+  const double m = p->m;
+  const double nr = (p->precision == RLBM_FP32_STORE) ? p->n_ref : 0.0;
+  const double Tr = p->T_ref;
+  Scalars& s = h->sc;
+  std::memset(&s, 0, sizeof(s));
+  s.Q = h->q.Q;
+  s.K = h->K;
+  s.order = p->order;
+  s.nx = p->nx;
+  s.ny = p->ny;
+  s.ncell = p->nx * p->ny;
+  s.plane = ((long long)s.ncell + 31) / 32 * 32;
+  s.boundary = p->boundary;
+  s.tau_mode = p->tau_mode;
+  s.tau = p->tau;
+  s.tau_coef = p->eta_over_s * (p->d + 2) * p->kappa;
+  s.m = m;
+  s.n_ref = nr;
+  s.T_ref = Tr;
+  s.N0_ref = nr;
+  s.T00_ref = nr * (m * m + 2.0 * m * Tr + 2.0 * Tr * Tr) / (m + Tr);
+  s.Tii_ref = nr * Tr;
+  s.r2_ref = Tr * (m * m + 3.0 * m * Tr + 3.0 * Tr * Tr) / (m + Tr);
+  s.kappa_guess = (float)(Tr * (m + Tr) / (m * m + 2.0 * m * Tr + 2.0 * Tr * Tr));
+  // reference populations f_ref,i = sum_k H_ik M_k(n_ref, e0, T_ref)
+  std::vector<double> Mref(h->K);
+  const double e0[3] = {1.0, 0.0, 0.0};
+  mj_moments(p->order, m, nr, e0, Tr, Mref.data());
+  h->fref.assign(h->q.Q, 0.0);
+  for (int i = 0; i < h->q.Q; ++i)
+    for (int k = 0; k < h->K; ++k) h->fref[i] += h->H[(size_t)i * h->K + k] * Mref[k];
+
+  h->elem = (p->precision == RLBM_FP32_STORE) ? 4 : 8;
+  h->stream = (cudaStream_t)p->stream;
+  if (h->elem == 4) {
+    h->tf.reset(new Tables<float>());
+    fill_tables(h.get(), h->tf.get());
+  } else {
+    h->td.reset(new Tables<double>());
+    fill_tables(h.get(), h->td.get());
+  }
+  // device buffers
+  const size_t pop_bytes = (size_t)h->q.Q * s.plane * h->elem;
+  cudaError_t e;
+  for (int b = 0; b < 2; ++b) {
+    e = cudaMalloc(&h->buf[b], pop_bytes);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(nullptr, RLBM_ERR_OOM, "population buffers"); }
+  }
+  e = cudaMalloc(&h->fields, (size_t)14 * s.plane * sizeof(double));
+  if (e != cudaSuccess) { cudaGetLastError(); return fail(nullptr, RLBM_ERR_OOM, "field buffer"); }
+  e = cudaMalloc(&h->tau_field, (size_t)s.plane * h->elem);
+  if (e != cudaSuccess) { cudaGetLastError(); return fail(nullptr, RLBM_ERR_OOM, "tau buffer"); }
+  e = cudaMalloc(&h->status, 2 * sizeof(unsigned long long));
+  if (e != cudaSuccess) { cudaGetLastError(); return fail(nullptr, RLBM_ERR_OOM, "status word"); }
+  e = cudaMalloc(&h->fref_dev, kMaxQ * sizeof(double));
+  if (e != cudaSuccess) { cudaGetLastError(); return fail(nullptr, RLBM_ERR_OOM, "reference"); }
+  cudaMemset(h->buf[0], 0, pop_bytes);
+  cudaMemset(h->buf[1], 0, pop_bytes);
+  cudaMemset(h->status, 0, 2 * sizeof(unsigned long long));
+  cudaMemcpy(h->fref_dev, h->fref.data(), h->q.Q * sizeof(double), cudaMemcpyHostToDevice);
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(nullptr, RLBM_ERR_CUDA, cudaGetErrorString(e));
+  *out = h.release();
+  return RLBM_OK;
+}
+
+void rlbm_destroy(rlbm_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  cudaFree(h->buf[0]);
+  cudaFree(h->buf[1]);
+  cudaFree(h->fields);
+  cudaFree(h->tau_field);
+  cudaFree(h->status);
+  cudaFree(h->fref_dev);
+  if (h->staging) cudaFree(h->staging);
+  delete h;
+}
+
+int rlbm_set_stream(rlbm_handle* h, void* stream) {
+  if (!h) return RLBM_ERR_INVALID_ARG;
+  h->stream = (cudaStream_t)stream;
+  return RLBM_OK;
+}
+
+long long rlbm_time(const rlbm_handle* h) { return h ? h->t : -1; }
+
+int rlbm_stencil(const rlbm_handle* h, int* Q, int* nvec, double* p, double* w) {
+  if (!h || !Q) return RLBM_ERR_INVALID_ARG;
+  *Q = h->q.Q;
+  for (int i = 0; i < h->q.Q; ++i) {
+    if (nvec) { nvec[2 * i] = h->q.nx[i]; nvec[2 * i + 1] = h->q.ny[i]; }
+    if (p) { p[3 * i] = h->q.p0[i]; p[3 * i + 1] = h->q.px[i]; p[3 * i + 2] = h->q.py[i]; }
+    if (w) w[i] = h->q.w[i];
+  }
+  return RLBM_OK;
+}
+
+int rlbm_init(rlbm_handle* h, const double* n, const double* ux, const double* uy, const double* T,
+              int on_device) {
+  if (!h || !n || !ux || !uy || !T) return RLBM_ERR_INVALID_ARG;
+  const Scalars& s = h->sc;
+  const size_t bytes = (size_t)s.ncell * sizeof(double);
+  const double* src[4] = {n, ux, uy, T};
+  const double* dev[4];
+  for (int k = 0; k < 4; ++k) {
+    if (on_device) {
+      dev[k] = src[k];
+    } else {
+      double* d = h->fields + (size_t)k * s.plane;   // the field planes double as staging
+      RLBM_CUDA(h, cudaMemcpyAsync(d, src[k], bytes, cudaMemcpyHostToDevice, h->stream));
+      dev[k] = d;
+    }
+  }
+  cudaError_t e;
+  if (h->elem == 4) {
+    InitArgs<float> a{s, dev[0], dev[1], dev[2], dev[3], (float*)h->buf[h->cur], h->status};
+    e = launch_init<float>(*h->tf, a, h->stream);
+  } else {
+    InitArgs<double> a{s, dev[0], dev[1], dev[2], dev[3], (double*)h->buf[h->cur], h->status};
+    e = launch_init<double>(*h->td, a, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "init kernel");
+  if (!on_device) RLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->t = 0;
+  h->have_prev = false;
+  return RLBM_OK;
+}
+
+int rlbm_set_tau_field(rlbm_handle* h, const double* tau, int on_device) {
+  if (!h || !tau) return RLBM_ERR_INVALID_ARG;
+  const Scalars& s = h->sc;
+  const double* d = tau;
+  if (!on_device) {
+    double* st = h->fields;
+    RLBM_CUDA(h, cudaMemcpyAsync(st, tau, (size_t)s.ncell * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    d = st;
+  }
+  const int nb = (s.ncell + 255) / 256;
+  if (h->elem == 4) k_tau_import<float><<<nb, 256, 0, h->stream>>>(d, (float*)h->tau_field, s.ncell);
+  else k_tau_import<double><<<nb, 256, 0, h->stream>>>(d, (double*)h->tau_field, s.ncell);
+  RLBM_CUDA(h, cudaGetLastError());
+  if (!on_device) RLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  return RLBM_OK;
+}
+
+int rlbm_step(rlbm_handle* h, int nsteps) {
+  if (!h || nsteps < 0) return RLBM_ERR_INVALID_ARG;
+  const int mode = h->p.stream_mode == RLBM_BILINEAR ? kBilinear : kOnLattice;
+  for (int it = 0; it < nsteps; ++it) {
+    cudaError_t e;
+    if (h->elem == 4) {
+      StepArgs<float> a{h->sc, (const float*)h->buf[h->cur], (float*)h->buf[h->cur ^ 1],
+                        (const float*)h->tau_field, h->status};
+      e = launch_step<float>(*h->tf, a, mode, h->stream);
+    } else {
+      StepArgs<double> a{h->sc, (const double*)h->buf[h->cur], (double*)h->buf[h->cur ^ 1],
+                         (const double*)h->tau_field, h->status};
+      e = launch_step<double>(*h->td, a, mode, h->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
+    h->cur ^= 1;
+    h->t += 1;
+    h->have_prev = true;
+  }
+  return RLBM_OK;
+}
+
+int rlbm_moments(rlbm_handle* h, double* n, double* ux, double* uy, double* T, double* eps, double* Nab,
+                 double* Tab, int on_device) {
+  if (!h) return RLBM_ERR_INVALID_ARG;
+  const Scalars& s = h->sc;
+  const int mode = h->p.stream_mode == RLBM_BILINEAR ? kBilinear : kOnLattice;
+  const int want = (Nab || Tab) ? 1 : 0;
+  const void* fin = h->have_prev ? h->buf[h->cur ^ 1] : h->buf[h->cur];
+  cudaError_t e;
+  if (h->elem == 4) {
+    MomentArgs<float> a{s, (const float*)fin, h->have_prev ? 1 : 0, h->fields, want, h->status};
+    e = launch_fields<float>(*h->tf, a, mode, h->stream);
+  } else {
+    MomentArgs<double> a{s, (const double*)fin, h->have_prev ? 1 : 0, h->fields, want, h->status};
+    e = launch_fields<double>(*h->td, a, mode, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "fields kernel");
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const size_t bytes = (size_t)s.ncell * sizeof(double);
+  double* outs[5] = {n, ux, uy, T, eps};
+  for (int k = 0; k < 5; ++k)
+    if (outs[k]) RLBM_CUDA(h, cudaMemcpyAsync(outs[k], h->fields + (size_t)k * s.plane, bytes, kind, h->stream));
+  for (int k = 0; k < 3; ++k)
+    if (Nab) RLBM_CUDA(h, cudaMemcpyAsync(Nab + (size_t)k * s.ncell, h->fields + (size_t)(5 + k) * s.plane, bytes, kind, h->stream));
+  for (int k = 0; k < 6; ++k)
+    if (Tab) RLBM_CUDA(h, cudaMemcpyAsync(Tab + (size_t)k * s.ncell, h->fields + (size_t)(8 + k) * s.plane, bytes, kind, h->stream));
+  if (!on_device) RLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  return RLBM_OK;
+}
+
+static int ensure_staging(rlbm_handle* h) {
+  if (h->staging) return RLBM_OK;
+  cudaError_t e = cudaMalloc(&h->staging, (size_t)h->q.Q * h->sc.ncell * sizeof(double));
+  if (e != cudaSuccess) { cudaGetLastError(); return fail(h, RLBM_ERR_OOM, "staging buffer"); }
+  return RLBM_OK;
+}
+
+int rlbm_get_populations(rlbm_handle* h, double* f, int on_device) {
+  if (!h || !f) return RLBM_ERR_INVALID_ARG;
+  const Scalars& s = h->sc;
+  double* dst = f;
+  if (!on_device) {
+    int rc = ensure_staging(h);
+    if (rc) return rc;
+    dst = h->staging;
+  }
+  const long long total = (long long)s.Q * s.ncell;
+  const int nb = (int)((total + 255) / 256);
+  if (h->elem == 4) k_export<float><<<nb, 256, 0, h->stream>>>((const float*)h->buf[h->cur], dst, s.Q, s.ncell, s.plane, h->fref_dev);
+  else k_export<double><<<nb, 256, 0, h->stream>>>((const double*)h->buf[h->cur], dst, s.Q, s.ncell, s.plane, h->fref_dev);
+  RLBM_CUDA(h, cudaGetLastError());
+  if (!on_device) {
+    RLBM_CUDA(h, cudaMemcpyAsync(f, dst, total * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    RLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  return RLBM_OK;
+}
+
+int rlbm_set_populations(rlbm_handle* h, const double* f, int on_device) {
+  if (!h || !f) return RLBM_ERR_INVALID_ARG;
+  const Scalars& s = h->sc;
+  const long long total = (long long)s.Q * s.ncell;
+  const double* src = f;
+  if (!on_device) {
+    int rc = ensure_staging(h);
+    if (rc) return rc;
+    RLBM_CUDA(h, cudaMemcpyAsync(h->staging, f, total * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    src = h->staging;
+  }
+  const int nb = (int)((total + 255) / 256);
+  if (h->elem == 4) k_import<float><<<nb, 256, 0, h->stream>>>(src, (float*)h->buf[h->cur], s.Q, s.ncell, s.plane, h->fref_dev);
+  else k_import<double><<<nb, 256, 0, h->stream>>>(src, (double*)h->buf[h->cur], s.Q, s.ncell, s.plane, h->fref_dev);
+  RLBM_CUDA(h, cudaGetLastError());
+  if (!on_device) RLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->have_prev = false;
+  return RLBM_OK;
+}
+
+int rlbm_sync_status(rlbm_handle* h, long long* count) {
+  if (!h) return RLBM_ERR_INVALID_ARG;
+  RLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  unsigned long long st[2] = {0, 0};
+  RLBM_CUDA(h, cudaMemcpy(st, h->status, sizeof(st), cudaMemcpyDeviceToHost));
+  RLBM_CUDA(h, cudaMemset(h->status, 0, sizeof(st)));
+  if (count) *count = (long long)st[0];
+  if (st[1]) return fail(h, RLBM_ERR_TIMEOUT, "a device-side wait timed out");
+  if (st[0]) return fail(h, RLBM_ERR_NONPHYSICAL, std::to_string(st[0]) + " non-physical cell updates");
+  return RLBM_OK;
+}
+
+int rlbm_buffers(rlbm_handle* h, void** cur, void** prev, int* elem_size, long long* plane) {
+  if (!h) return RLBM_ERR_INVALID_ARG;
+  if (cur) *cur = h->buf[h->cur];
+  if (prev) *prev = h->buf[h->cur ^ 1];
+  if (elem_size) *elem_size = (int)h->elem;
+  if (plane) *plane = h->sc.plane;
+  return RLBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,487 @@
+// Host-side FP64 construction of the RLBM lattice tables.
+//
+// Sec. 5.2 (orthonormal polynomials under the weight omega), Sec. 5.3
+// (quadratures with prescribed abscissas, Eq. mj-orthogonal-conditions,
+// Eq. quadrature-problem), App. B (Maxwell-Juttner moments via the Z
+// integrals), App. H (stencils and massless tables) of arXiv:1909.04502.
+#include "setup.h"
+
+#include <algorithm>
+#include <cmath>
+#include <set>
+#include <utility>
+
+namespace rlbm {
+
+namespace {
+constexpr double kPi = 3.14159265358979323846;
+}
+
+std::vector<Monomial> moment_basis(int order) {
+  std::vector<Monomial> out;
+  for (int deg = 0; deg <= order; ++deg) {
+    // p0 times a degree-(deg-1) monomial in (px, py), then pure (px, py) monomials
+    if (deg >= 1)
+      for (int a = deg - 1; a >= 0; --a) out.push_back({1, a, deg - 1 - a});
+    for (int a = deg; a >= 0; --a) out.push_back({0, a, deg - a});
+  }
+  // order 2: 1 | p0 px py | p0px p0py pxpx pxpy pypy (K = 9); order 3 adds
+  // p0pxpx p0pxpy p0pypy pxpxpx pxpxpy pxpypy pypypy (K = 16)
+  return out;
+}
+
+void gauss_laguerre(int n, std::vector<double>& x, std::vector<double>& w) {
+  // Roots of L_n by Newton iteration from the usual asymptotic starting
+  // values; weights w_j = x_j / ((n+1)^2 L_{n+1}(x_j)^2).
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  double z = 0.0;
+  for (int i = 0; i < n; ++i) {
+    if (i == 0) z = 3.0 / (1.0 + 2.4 * n);
+    else if (i == 1) z += 15.0 / (1.0 + 2.5 * n);
+    else {
+      double ai = i - 1;
+      z += ((1.0 + 2.55 * ai) / (1.9 * ai)) * (z - x[i - 2]);
+    }
+    for (int it = 0; it < 100; ++it) {
+      double l0 = 1.0, l1 = 1.0 - z;
+      for (int k = 1; k < n; ++k) {
+        double l2 = ((2.0 * k + 1.0 - z) * l1 - k * l0) / (k + 1.0);
+        l0 = l1;
+        l1 = l2;
+      }
+      // l1 = L_n(z), l0 = L_{n-1}(z); z L_n' = n (L_n - L_{n-1})
+      double dl = n * (l1 - l0) / z;
+      double dz = l1 / dl;
+      z -= dz;
+      if (std::fabs(dz) <= 1e-15 * std::fabs(z)) break;
+    }
+    x[i] = z;
+    double l0 = 1.0, l1 = 1.0 - z;
+    for (int k = 1; k <= n; ++k) {
+      double l2 = ((2.0 * k + 1.0 - z) * l1 - k * l0) / (k + 1.0);
+      l0 = l1;
+      l1 = l2;
+    }
+    w[i] = z / ((n + 1.0) * (n + 1.0) * l1 * l1);
+  }
+}
+
+double omega_moment(int c, int a, int b, double m) {
+  if ((a & 1) || (b & 1)) return 0.0;
+  // d^2p / p0 = dp0 dtheta on the mass shell; p0 = m + s, |p|^2 = s (2m + s).
+  static thread_local std::vector<double> xs, ws;
+  if (xs.empty()) gauss_laguerre(16, xs, ws);   // exact for polynomials of degree <= 31
+  double radial = 0.0;
+  const int k2 = (a + b) / 2;
+  for (size_t j = 0; j < xs.size(); ++j) {
+    double s = xs[j];
+    radial += ws[j] * std::pow(m + s, c) * std::pow(s * (2.0 * m + s), k2);
+  }
+  const int nth = 64;                             // exact for trig degree < 64
+  double ang = 0.0;
+  for (int j = 0; j < nth; ++j) {
+    double th = 2.0 * kPi * j / nth;
+    ang += std::pow(std::cos(th), a) * std::pow(std::sin(th), b);
+  }
+  ang /= nth;
+  return ang * radial;
+}
+
+std::vector<double> gram_matrix(int order, double m) {
+  auto B = moment_basis(order);
+  const int K = (int)B.size();
+  std::vector<double> G(K * K);
+  for (int i = 0; i < K; ++i)
+    for (int j = 0; j < K; ++j)
+      G[i * K + j] = omega_moment(B[i].e + B[j].e, B[i].a + B[j].a, B[i].b + B[j].b, m);
+  return G;
+}
+
+namespace {
+
+// Well-conditioned working basis phi'_k = s^e (px/sg)^a (py/sg)^b with
+// s = p0 - m and sg = sqrt(m + 1) (the scale of App. F's J^(1)_x).  It spans
+// the same space as moment_basis, phi = A phi'.
+double omega_moment_shifted(int c, int a, int b, double m) {
+  if ((a & 1) || (b & 1)) return 0.0;
+  static thread_local std::vector<double> xs, ws;
+  if (xs.empty()) gauss_laguerre(16, xs, ws);
+  double radial = 0.0;
+  const int k2 = (a + b) / 2;
+  const double sg2 = m + 1.0;
+  for (size_t j = 0; j < xs.size(); ++j) {
+    double s = xs[j];
+    radial += ws[j] * std::pow(s, c) * std::pow(s * (2.0 * m + s) / sg2, k2);
+  }
+  const int nth = 64;
+  double ang = 0.0;
+  for (int j = 0; j < nth; ++j) {
+    double th = 2.0 * kPi * j / nth;
+    ang += std::pow(std::cos(th), a) * std::pow(std::sin(th), b);
+  }
+  return ang / nth * radial;
+}
+
+std::vector<double> gram_shifted(int order, double m) {
+  auto B = moment_basis(order);
+  const int K = (int)B.size();
+  std::vector<double> G(K * K);
+  for (int i = 0; i < K; ++i)
+    for (int j = 0; j < K; ++j)
+      G[i * K + j] = omega_moment_shifted(B[i].e + B[j].e, B[i].a + B[j].a, B[i].b + B[j].b, m);
+  return G;
+}
+
+void eval_shifted(const std::vector<Monomial>& B, double m, double p0, double px, double py, double* out) {
+  const double sg = std::sqrt(m + 1.0);
+  const double s = p0 - m, qx = px / sg, qy = py / sg;
+  for (size_t k = 0; k < B.size(); ++k) {
+    double r = B[k].e ? s : 1.0;
+    for (int i = 0; i < B[k].a; ++i) r *= qx;
+    for (int i = 0; i < B[k].b; ++i) r *= qy;
+    out[k] = r;
+  }
+}
+
+}  // namespace
+
+bool cholesky(std::vector<double>& a, int n) {
+  for (int j = 0; j < n; ++j) {
+    double d = a[j * n + j];
+    for (int k = 0; k < j; ++k) d -= a[j * n + k] * a[j * n + k];
+    if (!(d > 0.0)) return false;
+    d = std::sqrt(d);
+    a[j * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double s = a[i * n + j];
+      for (int k = 0; k < j; ++k) s -= a[i * n + k] * a[j * n + k];
+      a[i * n + j] = s / d;
+    }
+    for (int k = j + 1; k < n; ++k) a[j * n + k] = 0.0;
+  }
+  return true;
+}
+
+std::vector<double> spd_inverse(const std::vector<double>& a, int n, bool* ok) {
+  std::vector<double> L = a;
+  std::vector<double> inv(n * n, 0.0);
+  if (!cholesky(L, n)) {
+    *ok = false;
+    return inv;
+  }
+  // solve L L^T X = I column by column
+  std::vector<double> y(n);
+  for (int c = 0; c < n; ++c) {
+    for (int i = 0; i < n; ++i) {
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) s -= L[i * n + k] * y[k];
+      y[i] = s / L[i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double s = y[i];
+      for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * inv[k * n + c];
+      inv[i * n + c] = s / L[i * n + i];
+    }
+  }
+  *ok = true;
+  return inv;
+}
+
+// ---------------------------------------------------------------------------
+// Stencils
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// Full-symmetric group of a generator vector: all sign flips and the swap of
+// the two components, without repetitions (Sec. 5.3).
+std::vector<std::pair<int, int>> fs_group(int gx, int gy) {
+  std::set<std::pair<int, int>> s;
+  const int sx[2] = {1, -1};
+  for (int swap = 0; swap < 2; ++swap) {
+    int u = swap ? gy : gx, v = swap ? gx : gy;
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) s.insert({sx[a] * u, sx[b] * v});
+  }
+  return std::vector<std::pair<int, int>>(s.begin(), s.end());
+}
+
+
+// Least squares min ||A w - b|| by Householder QR (A: rows x cols, row-major).
+bool least_squares(std::vector<double> A, std::vector<double> b, int rows, int cols,
+                   std::vector<double>* x) {
+  if (rows < cols) return false;
+  for (int k = 0; k < cols; ++k) {
+    double nrm = 0.0;
+    for (int i = k; i < rows; ++i) nrm += A[i * cols + k] * A[i * cols + k];
+    nrm = std::sqrt(nrm);
+    if (nrm == 0.0) return false;
+    double alpha = A[k * cols + k] > 0 ? -nrm : nrm;
+    std::vector<double> v(rows - k);
+    for (int i = k; i < rows; ++i) v[i - k] = A[i * cols + k];
+    v[0] -= alpha;
+    double vn = 0.0;
+    for (double t : v) vn += t * t;
+    if (vn == 0.0) continue;
+    for (int j = k; j < cols; ++j) {
+      double s = 0.0;
+      for (int i = k; i < rows; ++i) s += v[i - k] * A[i * cols + j];
+      s = 2.0 * s / vn;
+      for (int i = k; i < rows; ++i) A[i * cols + j] -= s * v[i - k];
+    }
+    double s = 0.0;
+    for (int i = k; i < rows; ++i) s += v[i - k] * b[i];
+    s = 2.0 * s / vn;
+    for (int i = k; i < rows; ++i) b[i] -= s * v[i - k];
+  }
+  x->assign(cols, 0.0);
+  for (int i = cols - 1; i >= 0; --i) {
+    double s = b[i];
+    for (int j = i + 1; j < cols; ++j) s -= A[i * cols + j] * (*x)[j];
+    if (std::fabs(A[i * cols + i]) < 1e-300) return false;
+    (*x)[i] = s / A[i * cols + i];
+  }
+  return true;
+}
+
+}  // namespace
+
+bool massless_quadrature(int order, Quadrature* q, std::string* err) {
+  // App. H, ultra-relativistic regime, (2+1) dimensions.  Stencil
+  // {(+-3, +-4)FS, (+-5, 0)FS}; shell energies are the printed p0_j.  The
+  // printed weight column is read shell by shell, the (+-5, 0) group first
+  // and the (+-3, +-4) group second; this reading satisfies the
+  // orthonormality conditions (the literal group-by-group reading does not).
+  static const double s2[3] = {0.4157745567834790, 2.2942803602790417, 6.2899450829374791};
+  static const double c2[6] = {0.0, 0.0888866262411466, 0.0, 0.0348147166961551,
+                               0.0017535654166088, 0.0004218743543938};
+  static const double s3[4] = {0.3225476896193923, 1.7457611011583465, 4.5366202969211279,
+                               9.3950709123011331};
+  static const double c3[8] = {0.0, 0.0753942630427042, 0.0410206173754781,
+                               0.0241670278669858, 0.0044457884155769, 0.0026380943565871,
+                               0.0000616926157132, 0.0000365655303385};
+  const double* shells;
+  const double* col;
+  int ns;
+  if (order == 2) { shells = s2; col = c2; ns = 3; }
+  else if (order == 3) { shells = s3; col = c3; ns = 4; }
+  else { *err = "massless quadrature: order must be 2 or 3"; return false; }
+  *q = Quadrature();
+  q->m = 0.0;
+  q->order = order;
+  const int gens[2][2] = {{3, 4}, {5, 0}};
+  for (int g = 0; g < 2; ++g) {
+    for (auto v : fs_group(gens[g][0], gens[g][1])) {
+      double norm = std::sqrt(double(v.first * v.first + v.second * v.second));
+      for (int j = 0; j < ns; ++j) {
+        double wgt = col[2 * j + (g == 0 ? 1 : 0)];
+        if (wgt == 0.0) continue;
+        q->nx.push_back(v.first);
+        q->ny.push_back(v.second);
+        q->p0.push_back(shells[j]);
+        q->px.push_back(shells[j] * v.first / norm);
+        q->py.push_back(shells[j] * v.second / norm);
+        q->w.push_back(wgt);
+      }
+    }
+  }
+  q->Q = (int)q->w.size();
+  return true;
+}
+
+bool massive_quadrature(const std::vector<int>& groups, double m, double v0, int order,
+                        Quadrature* q, double* residual, std::vector<double>* group_w) {
+  const int ng = (int)groups.size() / 2;
+  auto B = moment_basis(order);
+  const int K = (int)B.size();
+  std::vector<double> L = gram_shifted(order, m);
+  if (!cholesky(L, K)) return false;
+  // stencil and momenta, Eq. discrete-momentum-vectors / discrete-p0
+  std::vector<int> vx, vy, gid;
+  for (int g = 0; g < ng; ++g)
+    for (auto v : fs_group(groups[2 * g], groups[2 * g + 1])) {
+      vx.push_back(v.first);
+      vy.push_back(v.second);
+      gid.push_back(g);
+    }
+  const int Qf = (int)vx.size();
+  std::vector<double> p0(Qf), px(Qf), py(Qf), J((size_t)Qf * K);
+  for (int i = 0; i < Qf; ++i) {
+    double v2 = v0 * v0 * (vx[i] * vx[i] + vy[i] * vy[i]);
+    if (v2 >= 1.0) return false;
+    double gam = 1.0 / std::sqrt(1.0 - v2);
+    p0[i] = m * gam;
+    px[i] = m * gam * v0 * vx[i];
+    py[i] = m * gam * v0 * vy[i];
+    // orthonormal basis J = L^{-1} phi' (G' = L L^T)
+    std::vector<double> phi(K);
+    eval_shifted(B, m, p0[i], px[i], py[i], phi.data());
+    for (int k = 0; k < K; ++k) {
+      double s = phi[k];
+      for (int j = 0; j < k; ++j) s -= L[k * K + j] * J[(size_t)i * K + j];
+      J[(size_t)i * K + k] = s / L[k * K + k];
+    }
+  }
+  // Eq. mj-orthogonal-conditions, one unknown per FS group
+  const int rows = K * (K + 1) / 2;
+  std::vector<double> A((size_t)rows * ng, 0.0), b(rows, 0.0);
+  int r = 0;
+  for (int l = 0; l < K; ++l)
+    for (int k = l; k < K; ++k, ++r) {
+      for (int i = 0; i < Qf; ++i) A[(size_t)r * ng + gid[i]] += J[(size_t)i * K + l] * J[(size_t)i * K + k];
+      b[r] = (l == k) ? 1.0 : 0.0;
+    }
+  std::vector<double> wg;
+  if (!least_squares(A, b, rows, ng, &wg)) return false;
+  double res = 0.0;
+  for (int rr = 0; rr < rows; ++rr) {
+    double s = -b[rr];
+    for (int g = 0; g < ng; ++g) s += A[(size_t)rr * ng + g] * wg[g];
+    res = std::max(res, std::fabs(s));
+  }
+  *residual = res;
+  if (group_w) *group_w = wg;
+  *q = Quadrature();
+  q->m = m;
+  q->order = order;
+  q->v0 = v0;
+  q->groups = groups;
+  for (int i = 0; i < Qf; ++i) {
+    if (wg[gid[i]] == 0.0) continue;
+    q->nx.push_back(vx[i]);
+    q->ny.push_back(vy[i]);
+    q->p0.push_back(p0[i]);
+    q->px.push_back(px[i]);
+    q->py.push_back(py[i]);
+    q->w.push_back(wg[gid[i]]);
+  }
+  q->Q = (int)q->w.size();
+  return true;
+}
+
+bool search_v0(const std::vector<int>& groups, double m, int order, double* v0_out,
+               double* lo_out, double* hi_out) {
+  double nmax = 0.0;
+  for (size_t g = 0; g + 1 < groups.size(); g += 2)
+    nmax = std::max(nmax, std::hypot((double)groups[g], (double)groups[g + 1]));
+  if (nmax == 0.0) return false;
+  const double vmax = 1.0 / nmax;
+  const int npts = 4000;
+  int best_lo = -1, best_hi = -1, run_lo = -1;
+  for (int j = 1; j <= npts; ++j) {
+    double v0 = vmax * j / (npts + 1.0);
+    Quadrature q;
+    double res = 1.0;
+    std::vector<double> wg;
+    bool ok = massive_quadrature(groups, m, v0, order, &q, &res, &wg) && res < 1e-9;
+    if (ok)
+      for (double x : wg) ok = ok && x >= 0.0;
+    if (ok) {
+      if (run_lo < 0) run_lo = j;
+      if (best_lo < 0 || j - run_lo > best_hi - best_lo) { best_lo = run_lo; best_hi = j; }
+    } else {
+      run_lo = -1;
+    }
+  }
+  if (best_lo < 0) return false;
+  double lo = vmax * best_lo / (npts + 1.0), hi = vmax * best_hi / (npts + 1.0);
+  *v0_out = 0.5 * (lo + hi);
+  if (lo_out) *lo_out = lo;
+  if (hi_out) *hi_out = hi;
+  return true;
+}
+
+bool builtin_massive(double m, int order, Quadrature* q, std::string* err) {
+  // Candidate stencils: the Sec. 5.3 worked example (order 2) and the five
+  // (2+1)-d columns of App. H for the requested order.
+  static const std::vector<std::vector<int>> o2 = {
+      {0, 0, 1, 0, 1, 1, 2, 1, 2, 2, 3, 1},   // Sec. 5.3 example (m~ = 5)
+      {0, 0, 1, 0, 1, 1, 2, 0, 2, 1, 2, 2},   // App. H G_A^(o2)
+      {0, 0, 1, 0, 1, 1, 2, 2, 3, 2, 4, 0},   // G_B^(o2)
+      {0, 0, 3, 3, 4, 2, 4, 3, 5, 0, 5, 1},   // G_C^(o2)
+      {0, 0, 3, 1, 4, 2, 4, 3, 5, 0, 5, 1},   // G_D^(o2)
+      {0, 0, 5, 2, 5, 3, 5, 4, 6, 0, 6, 2}};  // G_E^(o2)
+  static const std::vector<std::vector<int>> o3 = {
+      {0, 0, 1, 1, 4, 2, 5, 4, 5, 5, 6, 2, 6, 3, 6, 4, 7, 1, 7, 2},   // G_A^(o3)
+      {0, 0, 1, 1, 2, 2, 4, 3, 5, 0, 5, 5, 6, 2, 6, 3, 6, 4, 7, 1},   // G_B^(o3)
+      {0, 0, 1, 0, 2, 0, 2, 2, 3, 0, 3, 2, 3, 3, 4, 0, 4, 1, 4, 2},   // G_C^(o3)
+      {0, 0, 1, 0, 1, 1, 2, 0, 2, 1, 3, 1, 3, 2, 3, 3, 4, 0, 4, 2},   // G_D^(o3)
+      {0, 0, 1, 0, 1, 1, 2, 0, 2, 1, 2, 2, 3, 0, 3, 1, 3, 2, 3, 3}};  // G_E^(o3)
+  const auto& cands = (order == 2) ? o2 : o3;
+  if (order != 2 && order != 3) { *err = "order must be 2 or 3"; return false; }
+  for (const auto& g : cands) {
+    double v0;
+    if (!search_v0(g, m, order, &v0, nullptr, nullptr)) continue;
+    double res;
+    if (massive_quadrature(g, m, v0, order, q, &res, nullptr) && res < 1e-9) return true;
+  }
+  *err = "no built-in stencil yields a non-negative quadrature for this mass and order";
+  return false;
+}
+
+bool equilibrium_matrix(const Quadrature& q, std::vector<double>* H, std::string* err) {
+  // H = W Phi G^{-1} in the basis of moment_basis; evaluated through the
+  // shifted basis phi' = A^{-1} phi as H = W Phi' G'^{-1} A^{-1}.
+  auto B = moment_basis(q.order);
+  const int K = (int)B.size();
+  bool ok;
+  std::vector<double> Gi = spd_inverse(gram_shifted(q.order, q.m), K, &ok);
+  if (!ok) { *err = "Gram matrix not positive definite"; return false; }
+  const double sg = std::sqrt(q.m + 1.0);
+  // column of the e = 0 monomial with the same (a, b) as each e = 1 monomial
+  std::vector<int> partner(K, -1);
+  for (int k = 0; k < K; ++k)
+    if (B[k].e == 1)
+      for (int j = 0; j < K; ++j)
+        if (B[j].e == 0 && B[j].a == B[k].a && B[j].b == B[k].b) partner[k] = j;
+  H->assign((size_t)q.Q * K, 0.0);
+  std::vector<double> phi(K), r(K);
+  for (int i = 0; i < q.Q; ++i) {
+    eval_shifted(B, q.m, q.p0[i], q.px[i], q.py[i], phi.data());
+    for (int k = 0; k < K; ++k) {
+      double t = 0.0;
+      for (int j = 0; j < K; ++j) t += phi[j] * Gi[j * K + k];
+      r[k] = t;
+    }
+    // multiply by A^{-1}: phi'_k = sg^{-(a+b)} (phi_k - m phi_partner(k)) for e = 1
+    for (int k = 0; k < K; ++k) {
+      const double sc = std::pow(sg, -(B[k].a + B[k].b)) * q.w[i] * r[k];
+      (*H)[(size_t)i * K + k] += sc;
+      if (B[k].e == 1) (*H)[(size_t)i * K + partner[k]] -= q.m * sc;
+    }
+  }
+  return true;
+}
+
+void mj_moments(int order, double m, double n, const double U[3], double T, double* M) {
+  // App. B: B Z^{a1..ar} = n T^{r-1} sum_k (-1)^k (A_{r-k}/A_1) <U_{r-2k} eta_k>,
+  // with, for d = 2 (half-integer Bessel functions are elementary):
+  //   A_0/(A_1 T) = 1/(m + T), T A_2/A_1 = (m^2 + 3mT + 3T^2)/(m + T),
+  //   T^2 A_3/A_1 = (m^3 + 6m^2 T + 15 m T^2 + 15 T^3)/(m + T).
+  const double eta[3] = {1.0, -1.0, -1.0};
+  const double r0 = 1.0 / (m + T);
+  const double r2 = (m * m + 3.0 * m * T + 3.0 * T * T) / (m + T);
+  const double r3 = (m * m * m + 6.0 * m * m * T + 15.0 * m * T * T + 15.0 * T * T * T) / (m + T);
+  auto Bs = moment_basis(order);
+  for (size_t k = 0; k < Bs.size(); ++k) {
+    int idx[4], r = 0;
+    for (int i = 0; i < Bs[k].e; ++i) idx[r++] = 0;
+    for (int i = 0; i < Bs[k].a; ++i) idx[r++] = 1;
+    for (int i = 0; i < Bs[k].b; ++i) idx[r++] = 2;
+    double v;
+    if (r == 0) v = n * r0;
+    else if (r == 1) v = n * U[idx[0]];
+    else if (r == 2) {
+      double e01 = idx[0] == idx[1] ? eta[idx[0]] : 0.0;
+      v = n * (r2 * U[idx[0]] * U[idx[1]] - T * e01);
+    } else {
+      int a = idx[0], b = idx[1], c = idx[2];
+      double eab = a == b ? eta[a] : 0.0, eac = a == c ? eta[a] : 0.0, ebc = b == c ? eta[b] : 0.0;
+      v = n * (r3 * U[a] * U[b] * U[c] - T * r2 * (eab * U[c] + eac * U[b] + ebc * U[a]));
+    }
+    M[k] = v;
+  }
+}
+
+}  // namespace rlbm

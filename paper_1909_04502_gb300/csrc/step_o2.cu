@@ -1,0 +1,45 @@
+// Order-2 (K = 9) instantiations of the fused kernels, and the field kernels
+// for every population bucket.
+#include "dispatch.h"
+#include "step_impl.cuh"
+
+namespace rlbm {
+
+template <typename S>
+cudaError_t launch_step_k9(const Tables<S>& tb, const StepArgs<S>& a, int mode, cudaStream_t st) {
+  const int Q = a.s.Q;
+  if (Q <= 28) return launch_step_q<S, 28, 9>(tb, a, mode, st);
+  if (Q <= 32) return launch_step_q<S, 32, 9>(tb, a, mode, st);
+  if (Q <= 40) return launch_step_q<S, 40, 9>(tb, a, mode, st);
+  if (Q <= 48) return launch_step_q<S, 48, 9>(tb, a, mode, st);
+  return cudaErrorInvalidValue;
+}
+
+template <typename S>
+cudaError_t launch_fields(const Tables<S>& tb, const MomentArgs<S>& a, int mode, cudaStream_t st) {
+  const int Q = a.s.Q;
+  if (Q <= 28) return launch_fields_q<S, 28>(tb, a, mode, st);
+  if (Q <= 32) return launch_fields_q<S, 32>(tb, a, mode, st);
+  if (Q <= 40) return launch_fields_q<S, 40>(tb, a, mode, st);
+  if (Q <= 48) return launch_fields_q<S, 48>(tb, a, mode, st);
+  if (Q <= 56) return launch_fields_q<S, 56>(tb, a, mode, st);
+  if (Q <= 64) return launch_fields_q<S, 64>(tb, a, mode, st);
+  if (Q <= 72) return launch_fields_q<S, 72>(tb, a, mode, st);
+  return cudaErrorInvalidValue;
+}
+
+template <typename S>
+cudaError_t launch_init(const Tables<S>& tb, const InitArgs<S>& a, cudaStream_t st) {
+  if (a.s.K == 9) return launch_init_k<S, 9>(tb, a, st);
+  if (a.s.K == 16) return launch_init_k<S, 16>(tb, a, st);
+  return cudaErrorInvalidValue;
+}
+
+template cudaError_t launch_step_k9<float>(const Tables<float>&, const StepArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_step_k9<double>(const Tables<double>&, const StepArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_fields<float>(const Tables<float>&, const MomentArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_fields<double>(const Tables<double>&, const MomentArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_init<float>(const Tables<float>&, const InitArgs<float>&, cudaStream_t);
+template cudaError_t launch_init<double>(const Tables<double>&, const InitArgs<double>&, cudaStream_t);
+
+}  // namespace rlbm

@@ -1,0 +1,290 @@
+"""Thin Python binding of the C ABI in include/rlbm.h (argument marshalling only).
+
+Every step of the RLBM update runs in the CUDA library ``librlbm.so`` built
+in-tree by ``paper_1909_04502_gb300.build``.  There is no CPU fallback: if the
+library is missing or cannot be loaded, every call raises.  PyTorch supplies
+device memory and the CUDA stream; numpy arrays are accepted for host data.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "librlbm.so")
+
+RLBM_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "CUDA", -4: "NONPHYSICAL", -5: "TIMEOUT",
+          -6: "OOM", -7: "QUADRATURE"}
+QUAD = {"massless": 0, "massive": 1, "custom": 2}
+BC = {"periodic": 0, "freeflow_x": 1}
+PREC = {"fp64": 0, "fp32": 1}
+STREAM = {"onlattice": 0, "bilinear": 1}
+TAU = {"const": 0, "field": 1, "eta_over_s": 2}
+
+
+class RLBMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("d", ctypes.c_int), ("m", ctypes.c_double), ("order", ctypes.c_int),
+        ("quadrature", ctypes.c_int), ("groups", ctypes.POINTER(ctypes.c_int)),
+        ("n_groups", ctypes.c_int), ("v0", ctypes.c_double),
+        ("custom_table", ctypes.POINTER(ctypes.c_double)), ("custom_Q", ctypes.c_int),
+        ("tau_mode", ctypes.c_int), ("tau", ctypes.c_double), ("eta_over_s", ctypes.c_double),
+        ("kappa", ctypes.c_double), ("boundary", ctypes.c_int), ("nx", ctypes.c_int),
+        ("ny", ctypes.c_int), ("precision", ctypes.c_int), ("stream_mode", ctypes.c_int),
+        ("lam", ctypes.c_double), ("n_ref", ctypes.c_double), ("T_ref", ctypes.c_double),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+_LIB = None
+_DP = ctypes.POINTER(ctypes.c_double)
+_IP = ctypes.POINTER(ctypes.c_int)
+_VP = ctypes.c_void_p
+_H = ctypes.c_void_p
+
+SIGNATURES = {
+    "rlbm_default_params": (None, [ctypes.POINTER(Params)]),
+    "rlbm_create": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(_H)]),
+    "rlbm_plan": (ctypes.c_int, [ctypes.POINTER(Params), _IP, _IP, _IP, _DP, _DP, _DP, _DP]),
+    "rlbm_destroy": (None, [_H]),
+    "rlbm_init": (ctypes.c_int, [_H, _VP, _VP, _VP, _VP, ctypes.c_int]),
+    "rlbm_set_tau_field": (ctypes.c_int, [_H, _VP, ctypes.c_int]),
+    "rlbm_step": (ctypes.c_int, [_H, ctypes.c_int]),
+    "rlbm_moments": (ctypes.c_int, [_H, _VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_int]),
+    "rlbm_get_populations": (ctypes.c_int, [_H, _VP, ctypes.c_int]),
+    "rlbm_set_populations": (ctypes.c_int, [_H, _VP, ctypes.c_int]),
+    "rlbm_stencil": (ctypes.c_int, [_H, _IP, _IP, _DP, _DP]),
+    "rlbm_time": (ctypes.c_longlong, [_H]),
+    "rlbm_sync_status": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_longlong)]),
+    "rlbm_set_stream": (ctypes.c_int, [_H, _VP]),
+    "rlbm_buffers": (ctypes.c_int, [_H, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _IP,
+                                    ctypes.POINTER(ctypes.c_longlong)]),
+    "rlbm_last_error": (ctypes.c_char_p, [_H]),
+    "rlbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+
+def lib():
+    """Load librlbm.so (built in-tree).  Raises if it is absent: the library
+    has no fallback path."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIBPATH):
+            raise RuntimeError("librlbm.so is not built; run paper_1909_04502_gb300.build.build()")
+        L = ctypes.CDLL(LIBPATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name, None)
+            if fn is None:
+                continue
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(rc, handle=None):
+    if rc != RLBM_OK:
+        msg = lib().rlbm_last_error(handle).decode()
+        raise RLBMError(rc, msg)
+
+
+def make_params(nx, ny, m=0.0, order=2, quadrature=None, groups=None, v0=0.0, custom=None,
+                tau=1.0, tau_mode="const", eta_over_s=0.0, kappa=0.0, boundary="periodic",
+                precision="fp32", stream="onlattice", lam=0.0, n_ref=1.0, T_ref=1.0,
+                cuda_stream=None):
+    """Fill an rlbm_params struct; returns (params, keepalive) -- the second
+    item holds arrays the struct points to."""
+    p = Params()
+    lib().rlbm_default_params(ctypes.byref(p))
+    p.d = 2
+    p.m = float(m)
+    p.order = int(order)
+    if quadrature is None:
+        quadrature = "massless" if m == 0 else "massive"
+    p.quadrature = QUAD[quadrature]
+    keep = []
+    if groups is not None:
+        g = np.ascontiguousarray(np.asarray(groups, dtype=np.int32).reshape(-1))
+        keep.append(g)
+        p.groups = g.ctypes.data_as(_IP)
+        p.n_groups = len(g) // 2
+    p.v0 = float(v0)
+    if custom is not None:
+        c = np.ascontiguousarray(np.asarray(custom, dtype=np.float64).reshape(-1, 6))
+        keep.append(c)
+        p.custom_table = c.ctypes.data_as(_DP)
+        p.custom_Q = c.shape[0]
+    p.tau_mode = TAU[tau_mode]
+    p.tau = float(tau)
+    p.eta_over_s = float(eta_over_s)
+    p.kappa = float(kappa)
+    p.boundary = BC[boundary]
+    p.nx, p.ny = int(nx), int(ny)
+    p.precision = PREC[precision]
+    p.stream_mode = STREAM[stream]
+    p.lam = float(lam)
+    p.n_ref, p.T_ref = float(n_ref), float(T_ref)
+    p.stream = cuda_stream
+    return p, keep
+
+
+def plan(**kw):
+    """Host-only tables (no GPU): dict with Q, K, n (Q,2), p (Q,3), w, H (Q,K), v0."""
+    p, keep = make_params(kw.pop("nx", 1), kw.pop("ny", 1), **kw)
+    Q, K = ctypes.c_int(), ctypes.c_int()
+    nvec = np.zeros(144, dtype=np.int32)
+    pm = np.zeros(216)
+    w = np.zeros(72)
+    H = np.zeros(72 * 16)
+    v0 = ctypes.c_double()
+    _check(lib().rlbm_plan(ctypes.byref(p), ctypes.byref(Q), ctypes.byref(K),
+                           nvec.ctypes.data_as(_IP), pm.ctypes.data_as(_DP), w.ctypes.data_as(_DP),
+                           H.ctypes.data_as(_DP), ctypes.byref(v0)))
+    q, k = Q.value, K.value
+    return dict(Q=q, K=k, n=nvec[:2 * q].reshape(q, 2).copy(), p=pm[:3 * q].reshape(q, 3).copy(),
+                w=w[:q].copy(), H=H[:q * k].reshape(q, k).copy(), v0=v0.value)
+
+
+def _ptr(a):
+    """(pointer, on_device) for a numpy array or a torch tensor."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous float64")
+        return a.ctypes.data, 0
+    import torch
+    if not isinstance(a, torch.Tensor) or a.dtype != torch.float64 or not a.is_contiguous():
+        raise ValueError("tensors must be contiguous float64")
+    return a.data_ptr(), 1 if a.is_cuda else 0
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+class Lattice:
+    """One RLBM simulation on the current CUDA device (see include/rlbm.h).
+
+    Keyword arguments are those of ``make_params``.  Work is issued on the
+    torch current stream at construction unless ``cuda_stream`` is given.
+    """
+
+    def __init__(self, nx, ny, **kw):
+        if "cuda_stream" not in kw:
+            kw["cuda_stream"] = _current_stream()
+        self.nx, self.ny = int(nx), int(ny)
+        self._params, self._keep = make_params(nx, ny, **kw)
+        h = _H()
+        _check(lib().rlbm_create(ctypes.byref(self._params), ctypes.byref(h)))
+        self.h = h
+        Q = ctypes.c_int()
+        _check(lib().rlbm_stencil(self.h, ctypes.byref(Q), None, None, None), self.h)
+        self.Q = Q.value
+        self.n = np.zeros((self.Q, 2), dtype=np.int32)
+        self.p = np.zeros((self.Q, 3))
+        self.w = np.zeros(self.Q)
+        _check(lib().rlbm_stencil(self.h, ctypes.byref(Q), self.n.ctypes.data_as(_IP),
+                                  self.p.ctypes.data_as(_DP), self.w.ctypes.data_as(_DP)), self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().rlbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def ncell(self):
+        return self.nx * self.ny
+
+    @property
+    def t(self):
+        return lib().rlbm_time(self.h)
+
+    def set_stream(self, stream):
+        _check(lib().rlbm_set_stream(self.h, stream), self.h)
+
+    def init(self, n, ux, uy, T):
+        ptrs = [_ptr(a) for a in (n, ux, uy, T)]
+        dev = {d for _, d in ptrs}
+        if len(dev) != 1:
+            raise ValueError("all init fields must live on the same side")
+        for a in (n, ux, uy, T):
+            size = a.size if isinstance(a, np.ndarray) else a.numel()
+            if size != self.ncell:
+                raise ValueError("field size must be nx*ny")
+        _check(lib().rlbm_init(self.h, ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[3][0], dev.pop()), self.h)
+
+    def set_tau_field(self, tau):
+        ptr, dev = _ptr(tau)
+        _check(lib().rlbm_set_tau_field(self.h, ptr, dev), self.h)
+
+    def step(self, nsteps=1):
+        _check(lib().rlbm_step(self.h, int(nsteps)), self.h)
+
+    def moments(self, full=False, out=None):
+        """Fields of f(t) as numpy arrays (ny, nx) (host copy), or written into
+        the given dict of float64 CUDA tensors ``out``."""
+        names = ["n", "ux", "uy", "T", "eps"]
+        if out is None:
+            res = {k: np.empty((self.ny, self.nx)) for k in names}
+            if full:
+                res["N"] = np.empty((3, self.ny, self.nx))
+                res["Tab"] = np.empty((6, self.ny, self.nx))
+        else:
+            res = out
+        ptrs = [_ptr(res.get(k))[0] for k in names + ["N", "Tab"]]
+        on_dev = 0 if out is None else 1
+        _check(lib().rlbm_moments(self.h, *ptrs, on_dev), self.h)
+        return res
+
+    def populations(self):
+        """Post-collision populations f*(t), float64 (Q, ny, nx)."""
+        f = np.empty((self.Q, self.ny, self.nx))
+        _check(lib().rlbm_get_populations(self.h, f.ctypes.data, 0), self.h)
+        return f
+
+    def set_populations(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        _check(lib().rlbm_set_populations(self.h, f.ctypes.data, 0), self.h)
+
+    def sync_status(self, raise_on_error=True):
+        cnt = ctypes.c_longlong()
+        rc = lib().rlbm_sync_status(self.h, ctypes.byref(cnt))
+        if rc != RLBM_OK and raise_on_error:
+            _check(rc, self.h)
+        return rc, cnt.value
+
+    def buffers(self):
+        cur, prev = _VP(), _VP()
+        es = ctypes.c_int()
+        plane = ctypes.c_longlong()
+        _check(lib().rlbm_buffers(self.h, ctypes.byref(cur), ctypes.byref(prev), ctypes.byref(es),
+                                  ctypes.byref(plane)), self.h)
+        return cur.value, prev.value, es.value, plane.value

@@ -1,0 +1,131 @@
+"""CPU-side checks of the C-ABI library: it loads, exports every symbol that
+include/rlbm.h declares, and its host-side setup (quadratures, equilibrium
+matrix: Sec. 5.2-5.3, App. F-H) agrees with the oracle.  No compute call here
+needs a GPU."""
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import lattice as OL
+from oracle import physics as OP
+from tests.cases import oracle_quadrature
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def rl():
+    from paper_1909_04502_gb300 import build, rlbm
+    build.build()
+    return rlbm
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "rlbm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rlbm_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(rl):
+    L = rl.lib()
+    syms = declared_symbols()
+    assert len(syms) >= 15
+    for s in syms:
+        assert hasattr(L, s), s
+    # and the Python binding knows every one of them
+    assert set(syms) <= set(rl.SIGNATURES)
+
+
+def test_strerror_and_invalid_create(rl):
+    L = rl.lib()
+    assert L.rlbm_strerror(-4).decode() == "non-physical cell state"
+    p, keep = rl.make_params(0, 8)                       # nx = 0
+    import ctypes
+    h = ctypes.c_void_p()
+    assert L.rlbm_create(ctypes.byref(p), ctypes.byref(h)) == -1
+    assert "grid" in L.rlbm_last_error(None).decode()
+    p, keep = rl.make_params(8, 8, tau=0.4)
+    assert L.rlbm_create(ctypes.byref(p), ctypes.byref(h)) == -1
+    p, keep = rl.make_params(8, 8)
+    p.d = 3
+    assert L.rlbm_create(ctypes.byref(p), ctypes.byref(h)) == -2
+
+
+def _key(n, p0):
+    return (int(n[0]), int(n[1]), round(float(p0), 10))
+
+
+def _match(plan, quad):
+    """Permutation idx with plan row idx[j] == oracle row j."""
+    pos = {_key(plan["n"][i], plan["p"][i, 0]): i for i in range(plan["Q"])}
+    return np.array([pos[_key(quad.n[j], quad.p[j, 0])] for j in range(quad.Q)])
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_massless_tables_agree_with_oracle(rl, order):
+    d = rl.plan(nx=16, ny=16, order=order)
+    q = OL.massless_quadrature(order)
+    assert d["Q"] == q.Q
+    idx = _match(d, q)
+    assert np.abs(d["p"][idx] - q.p).max() < 1e-15
+    assert np.abs(d["w"][idx] - q.w).max() == 0.0
+
+
+def test_mass5_example_weights_from_product_solver(rl):
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "mass5_worked_example.json")))
+    d = rl.plan(nx=8, ny=8, m=5.0, groups=g["groups"], v0=g["v0"])
+    q, _ = OL.massive_quadrature([tuple(x) for x in g["groups"]], 5.0, g["v0"])
+    idx = _match(d, q)
+    # w2 sits next to its pruning value (w2 = 0 at v0 = 0.27259...): two
+    # independent least-squares solutions agree to ~1e-14 absolute only
+    assert np.abs(d["w"][idx] - q.w).max() < 3e-14
+    assert np.abs(d["w"][idx] / q.w - 1).max() < 2e-11
+    assert np.allclose(sorted(set(np.round(d["w"], 15))), sorted(g["weights"]), rtol=0, atol=5e-14)
+
+
+def _mj_vector(order, m, n, U, T):
+    """MJ moments of the product basis p0^e px^a py^b via the oracle's App. B."""
+    mons = []
+    for deg in range(order + 1):
+        if deg >= 1:
+            mons += [(1, a, deg - 1 - a) for a in range(deg - 1, -1, -1)]
+        mons += [(0, a, deg - a) for a in range(deg, -1, -1)]
+    return np.array([OL.mj_monomial_moment(mo, n, U, T, m) for mo in mons])
+
+
+@pytest.mark.parametrize("case", [("massless", 2, 0.0), ("massless", 3, 0.0), ("massive", 2, 1.0),
+                                  ("massive", 2, 5.0), ("massive", 2, 10.0)])
+def test_equilibrium_matrix_reproduces_oracle_feq(rl, case):
+    kind, order, m = case
+    d = rl.plan(nx=8, ny=8, m=m, order=order)
+    if kind == "massless":
+        q = OL.massless_quadrature(order)
+    else:
+        # the product's weights satisfy the orthonormality conditions (oracle basis)
+        C, mons = OL.gram_schmidt_basis(order, m)
+        J = C @ OL.eval_monomials(mons, d["p"])
+        assert np.abs((J * d["w"]) @ J.T - np.eye(J.shape[0])).max() < 1e-11
+        assert np.all(d["w"] > 0)
+        # the oracle's own weights on the same stencil and v0
+        q = oracle_quadrature(m, order, d["n"], d["v0"])
+    idx = _match(d, q)
+    e = OL.Expansion(q)
+    rng = np.random.default_rng(7)
+    for _ in range(5):
+        n, T = rng.uniform(0.5, 2), rng.uniform(0.7, 1.5)
+        u = rng.uniform(-0.5, 0.5, 2)
+        U = OP.four_velocity(np.array(u[0]), np.array(u[1]))
+        feq_o = e.feq(np.array(n), U, np.array(T))
+        feq_p = d["H"] @ _mj_vector(order, m, n, U, T)
+        # massive weights come from two independent least-squares solves (~2e-13 apart)
+        tol = 1e-13 if kind == "massless" else 5e-13
+        assert np.abs(feq_p[idx] - feq_o).max() < tol * np.abs(feq_o).max()
+
+
+def test_builtin_massive_quadratures_exist_for_sweep_masses(rl):
+    for m in (1.0, 10.0):
+        d = rl.plan(nx=8, ny=8, m=m)
+        assert d["Q"] <= 40 and np.all(d["w"] > 0) and abs(d["w"].sum() - 1) < 1e-12

@@ -1,0 +1,213 @@
+"""GPU parity of the fused RLBM step (C ABI) against the FP64 oracle.
+
+Bars: relative L-infinity <= 1e-12 in FP64 mode and <= 1e-5 in FP32-storage
+mode (FP64 Landau solve), normalised by max |reference| of the compared
+field.  Grids are ragged (cell counts not multiples of the 256-thread block)
+and span several blocks.
+"""
+import numpy as np
+import pytest
+
+from paper_1909_04502_gb300 import inputs
+from tests.cases import oracle_quadrature, oracle_sim, permutation, rel_linf
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rl():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1909_04502_gb300 import build, rlbm
+    build.build()
+    return rlbm
+
+
+def make_pair(rl, nx, ny, fields, m=0.0, order=2, tau=1.0, boundary="periodic", stream="onlattice",
+              lam=0.0, precision="fp64", tau_mode="const", eta_over_s=0.0, kappa=0.0, tau_field=None):
+    lat = rl.Lattice(nx, ny, m=m, order=order, tau=tau, boundary=boundary, stream=stream, lam=lam,
+                     precision=precision, tau_mode=tau_mode, eta_over_s=eta_over_s, kappa=kappa)
+    d = rl.plan(nx=nx, ny=ny, m=m, order=order)
+    quad = oracle_quadrature(m, order, d["n"], d["v0"])
+    idx = permutation(lat.n, lat.p, quad)
+    if tau_mode == "const":
+        otau = tau
+    elif tau_mode == "field":
+        otau = tau_field
+        lat.set_tau_field(np.ascontiguousarray(tau_field))
+    else:
+        otau = (eta_over_s, kappa)
+    sim = oracle_sim(quad, nx, ny, tau=otau, boundary=boundary, stream=stream,
+                     lam=lam if stream == "bilinear" else None)
+    n, ux, uy, T = [np.ascontiguousarray(a) for a in fields]
+    lat.init(n, ux, uy, T)
+    sim.init(n, ux, uy, T)
+    return lat, sim, idx
+
+
+def compare(lat, sim, idx, tol, fields_tol=None):
+    f = lat.populations()[idx]
+    err_f = rel_linf(f, sim.fs)
+    m = lat.moments()
+    fl = sim.fields
+    errs = {"f": err_f, "n": rel_linf(m["n"], fl.n), "T": rel_linf(m["T"], fl.T),
+            "ux": float(np.abs(m["ux"] - fl.ux).max() / max(np.abs(fl.ux).max(), 1e-300)),
+            "uy": float(np.abs(m["uy"] - fl.uy).max() / max(np.abs(fl.uy).max(), 1e-300)),
+            "eps": rel_linf(m["eps"], fl.eps)}
+    ftol = tol if fields_tol is None else fields_tol
+    assert err_f <= tol, errs
+    for k in ("n", "T", "eps", "ux", "uy"):
+        assert errs[k] <= ftol, errs
+    return errs
+
+
+CASES_FP64 = [
+    # name, nx, ny, kwargs, steps
+    ("onlattice_periodic_N2", 37, 23, dict(), 12),
+    ("bilinear_lambda1_N2", 41, 29, dict(stream="bilinear", lam=1.0), 12),
+    ("bilinear_lambda2.5_N2", 33, 27, dict(stream="bilinear", lam=2.5), 8),
+    ("onlattice_N3", 31, 19, dict(order=3), 8),
+    ("onlattice_tau0.7", 29, 31, dict(tau=0.7), 10),
+    ("massive_m1_N2", 35, 21, dict(m=1.0), 8),
+    ("massive_m10_N2", 27, 25, dict(m=10.0), 8),
+]
+
+
+@pytest.mark.parametrize("name,nx,ny,kw,steps", CASES_FP64, ids=[c[0] for c in CASES_FP64])
+def test_fp64_parity(rl, name, nx, ny, kw, steps):
+    fields = inputs.random_smooth(nx, ny, seed=3, umax=0.3)
+    lat, sim, idx = make_pair(rl, nx, ny, fields, **kw)
+    compare(lat, sim, idx, 1e-12)                   # t = 0: equilibrium initialisation
+    for _ in range(2):
+        lat.step(steps // 2)
+        sim.step(steps // 2)
+        compare(lat, sim, idx, 1e-12)
+    assert lat.sync_status()[0] == 0
+
+
+def test_fp64_tau_field_and_freeflow(rl):
+    nx, ny = 300, 1
+    fields = inputs.sod(nx, ny)
+    tau = np.ascontiguousarray(0.8 + 0.5 * np.sin(np.arange(nx) / 17.0)[None, :] ** 2)
+    lat, sim, idx = make_pair(rl, nx, ny, fields, boundary="freeflow_x", tau_mode="field", tau_field=tau)
+    for _ in range(3):
+        lat.step(10)
+        sim.step(10)
+        compare(lat, sim, idx, 1e-12)
+
+
+def test_fp64_eta_over_s_sod(rl):
+    nx, ny = 256, 1
+    lat, sim, idx = make_pair(rl, nx, ny, inputs.sod(nx, ny), boundary="freeflow_x",
+                              tau_mode="eta_over_s", eta_over_s=0.1, kappa=15.79)
+    lat.step(25)
+    sim.step(25)
+    compare(lat, sim, idx, 1e-12)
+
+
+def test_fp64_bilinear_at_integer_displacement_equals_onlattice(rl):
+    nx, ny = 24, 20
+    fields = inputs.random_smooth(nx, ny, seed=11)
+    a = rl.Lattice(nx, ny, precision="fp64")
+    b = rl.Lattice(nx, ny, precision="fp64", stream="bilinear", lam=5.0)
+    for L in (a, b):
+        L.init(*[np.ascontiguousarray(x) for x in fields])
+        L.step(7)
+    assert np.array_equal(a.populations(), b.populations())
+
+
+def test_fp64_global_conservation(rl):
+    nx, ny = 48, 40
+    lat = rl.Lattice(nx, ny, precision="fp64", tau=0.9)
+    lat.init(*[np.ascontiguousarray(x) for x in inputs.random_smooth(nx, ny, seed=5)])
+    m0 = lat.moments(full=True)
+    lat.step(30)
+    m1 = lat.moments(full=True)
+    # N^0 and T^{0a} summed over the periodic box are conserved (collision
+    # invariants, exact streaming)
+    assert abs(m1["N"][0].sum() / m0["N"][0].sum() - 1) < 1e-13
+    for k in range(3):
+        assert abs(m1["Tab"][k].sum() - m0["Tab"][k].sum()) < 1e-13 * m0["Tab"][0].sum()
+
+
+FP32_CASES = [
+    ("tg_bilinear", 64, 64, dict(stream="bilinear", lam=1.0), "tg"),
+    ("tg_onlattice", 64, 48, dict(), "tg"),
+    ("random_onlattice", 45, 37, dict(tau=0.8), "random"),
+    ("random_N3", 40, 36, dict(order=3), "random"),
+    ("massive_m1", 40, 40, dict(m=1.0), "random"),
+]
+
+
+@pytest.mark.parametrize("name,nx,ny,kw,init", FP32_CASES, ids=[c[0] for c in FP32_CASES])
+def test_fp32_parity(rl, name, nx, ny, kw, init):
+    if init == "tg":
+        n, ux, uy, T = inputs.taylor_green(nx, u0=0.1)
+        n, ux, uy, T = n[:ny], ux[:ny], uy[:ny], T[:ny]
+    else:
+        n, ux, uy, T = inputs.random_smooth(nx, ny, seed=9, umax=0.25)
+    lat, sim, idx = make_pair(rl, nx, ny, (n, ux, uy, T), precision="fp32", **kw)
+    for _ in range(4):
+        lat.step(25)
+        sim.step(25)
+        compare(lat, sim, idx, 1e-5)
+    assert lat.sync_status()[0] == 0
+
+
+def test_init_reports_input_fields(rl):
+    nx, ny = 50, 30
+    n, ux, uy, T = inputs.random_smooth(nx, ny, seed=2, umax=0.6)
+    for prec, tol in (("fp64", 1e-12), ("fp32", 1e-6)):
+        lat = rl.Lattice(nx, ny, precision=prec)
+        lat.init(*[np.ascontiguousarray(a) for a in (n, ux, uy, T)])
+        m = lat.moments()
+        assert np.abs(m["n"] - n).max() < tol and np.abs(m["T"] - T).max() < tol
+        assert np.abs(m["ux"] - ux).max() < tol and np.abs(m["uy"] - uy).max() < tol
+
+
+def test_device_side_init_and_moments_with_torch(rl):
+    import torch
+    nx, ny = 33, 17
+    f = [torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+         for a in inputs.random_smooth(nx, ny, seed=4)]
+    lat = rl.Lattice(nx, ny, precision="fp64")
+    lat.init(*f)
+    lat.step(3)
+    out = {k: torch.empty((ny, nx), dtype=torch.float64, device="cuda") for k in ("n", "ux", "uy", "T", "eps")}
+    lat.moments(out=out)
+    torch.cuda.synchronize()
+    host = lat.moments()
+    for k in out:
+        assert np.array_equal(out[k].cpu().numpy(), host[k])
+
+
+def test_nonphysical_state_is_reported_not_faulted(rl):
+    nx, ny = 16, 8
+    n, ux, uy, T = [np.ascontiguousarray(a) for a in inputs.random_smooth(nx, ny, seed=1)]
+    ux[3, 4] = 1.2                          # faster than light: no physical equilibrium
+    lat = rl.Lattice(nx, ny, precision="fp64")
+    lat.init(n, ux, uy, T)
+    rc, count = lat.sync_status(raise_on_error=False)
+    assert rc == -4 and count >= 1
+    assert lat.sync_status(raise_on_error=False) == (0, 0)    # status cleared
+
+
+def test_tiny_grid_smaller_than_shift(rl):
+    """Periodic wrap when the grid is narrower than the 5-cell shifts."""
+    nx, ny = 3, 2
+    lat, sim, idx = make_pair(rl, nx, ny, inputs.random_smooth(nx, ny, seed=8))
+    lat.step(4)
+    sim.step(4)
+    compare(lat, sim, idx, 1e-12)
+
+
+def test_full_size_tg512_first_steps_fp32(rl):
+    """Config of the bench (512 x 512 Taylor-Green, bilinear lambda = 1, FP32
+    storage): two steps against the oracle, element by element."""
+    L = 512
+    lat, sim, idx = make_pair(rl, L, L, inputs.taylor_green(L, u0=0.1), precision="fp32",
+                              stream="bilinear", lam=1.0)
+    lat.step(2)
+    sim.step(2)
+    compare(lat, sim, idx, 1e-5)
