@@ -6,6 +6,8 @@
 // integrals), App. H (stencils and massless tables) of arXiv:1909.04502.
 #include "setup.h"
 
+#include "dd.h"
+
 #include <algorithm>
 #include <cmath>
 #include <set>
@@ -103,34 +105,84 @@ namespace {
 // Well-conditioned working basis phi'_k = s^e (px/sg)^a (py/sg)^b with
 // s = p0 - m and sg = sqrt(m + 1) (the scale of App. F's J^(1)_x).  It spans
 // the same space as moment_basis, phi = A phi'.
-double omega_moment_shifted(int c, int a, int b, double m) {
-  if ((a & 1) || (b & 1)) return 0.0;
-  static thread_local std::vector<double> xs, ws;
-  if (xs.empty()) gauss_laguerre(16, xs, ws);
-  double radial = 0.0;
+// E_omega[s^c (px/sg)^a (py/sg)^b] in double-double.  With p0 = m + s,
+// |p|^2 = s (2m + s) and d^2p/p0 = ds dtheta, the radial integrand expands
+// into positive terms s^q e^{-s} (int = q!), the angular factor is
+// (a-1)!!(b-1)!!/(a+b)!! for even a, b and zero otherwise.
+dd omega_moment_shifted_dd(int c, int a, int b, double m) {
+  if ((a & 1) || (b & 1)) return dd(0.0);
   const int k2 = (a + b) / 2;
-  const double sg2 = m + 1.0;
-  for (size_t j = 0; j < xs.size(); ++j) {
-    double s = xs[j];
-    radial += ws[j] * std::pow(s, c) * std::pow(s * (2.0 * m + s) / sg2, k2);
+  dd ang(1.0);
+  for (int k = a - 1; k > 0; k -= 2) ang = ang * dd((double)k);
+  for (int k = b - 1; k > 0; k -= 2) ang = ang * dd((double)k);
+  dd den(1.0);
+  for (int k = a + b; k > 0; k -= 2) den = den * dd((double)k);
+  ang = ang / den;
+  // (2m + s)^k2 = sum_j C(k2, j) (2m)^(k2-j) s^j
+  dd radial(0.0);
+  dd binom(1.0);
+  for (int j = 0; j <= k2; ++j) {
+    if (j > 0) binom = binom * dd((double)(k2 - j + 1)) / dd((double)j);
+    dd pw(1.0);
+    for (int t = 0; t < k2 - j; ++t) pw = pw * dd(2.0 * m);
+    dd fact(1.0);
+    for (int t = 2; t <= c + k2 + j; ++t) fact = fact * dd((double)t);
+    radial = radial + binom * pw * fact;
   }
-  const int nth = 64;
-  double ang = 0.0;
-  for (int j = 0; j < nth; ++j) {
-    double th = 2.0 * kPi * j / nth;
-    ang += std::pow(std::cos(th), a) * std::pow(std::sin(th), b);
-  }
-  return ang / nth * radial;
+  dd sg2 = dd(m) + dd(1.0);
+  dd scale(1.0);
+  for (int t = 0; t < k2; ++t) scale = scale * sg2;
+  return ang * radial / scale;
+}
+
+std::vector<dd> gram_shifted_dd(int order, double m) {
+  auto B = moment_basis(order);
+  const int K = (int)B.size();
+  std::vector<dd> G(K * K);
+  for (int i = 0; i < K; ++i)
+    for (int j = 0; j < K; ++j)
+      G[i * K + j] = omega_moment_shifted_dd(B[i].e + B[j].e, B[i].a + B[j].a, B[i].b + B[j].b, m);
+  return G;
 }
 
 std::vector<double> gram_shifted(int order, double m) {
-  auto B = moment_basis(order);
-  const int K = (int)B.size();
-  std::vector<double> G(K * K);
-  for (int i = 0; i < K; ++i)
-    for (int j = 0; j < K; ++j)
-      G[i * K + j] = omega_moment_shifted(B[i].e + B[j].e, B[i].a + B[j].a, B[i].b + B[j].b, m);
-  return G;
+  std::vector<dd> g = gram_shifted_dd(order, m);
+  std::vector<double> out(g.size());
+  for (size_t i = 0; i < g.size(); ++i) out[i] = g[i].to_double();
+  return out;
+}
+
+// Inverse of a symmetric positive definite matrix in double-double
+// (Cholesky, then forward and back substitution per column).
+bool spd_inverse_dd(const std::vector<dd>& a, int n, std::vector<dd>* inv) {
+  std::vector<dd> L = a;
+  for (int j = 0; j < n; ++j) {
+    dd d = L[j * n + j];
+    for (int k = 0; k < j; ++k) d = d - L[j * n + k] * L[j * n + k];
+    if (!(d.hi > 0.0)) return false;
+    d = dd_sqrt(d);
+    L[j * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      dd s = L[i * n + j];
+      for (int k = 0; k < j; ++k) s = s - L[i * n + k] * L[j * n + k];
+      L[i * n + j] = s / d;
+    }
+  }
+  inv->assign(n * n, dd(0.0));
+  std::vector<dd> y(n);
+  for (int c = 0; c < n; ++c) {
+    for (int i = 0; i < n; ++i) {
+      dd s((i == c) ? 1.0 : 0.0);
+      for (int k = 0; k < i; ++k) s = s - L[i * n + k] * y[k];
+      y[i] = s / L[i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      dd s = y[i];
+      for (int k = i + 1; k < n; ++k) s = s - L[k * n + i] * (*inv)[k * n + c];
+      (*inv)[i * n + c] = s / L[i * n + i];
+    }
+  }
+  return true;
 }
 
 void eval_shifted(const std::vector<Monomial>& B, double m, double p0, double px, double py, double* out) {
@@ -422,34 +474,45 @@ bool builtin_massive(double m, int order, Quadrature* q, std::string* err) {
 
 bool equilibrium_matrix(const Quadrature& q, std::vector<double>* H, std::string* err) {
   // H = W Phi G^{-1} in the basis of moment_basis; evaluated through the
-  // shifted basis phi' = A^{-1} phi as H = W Phi' G'^{-1} A^{-1}.
+  // shifted basis phi' = A^{-1} phi as H = W Phi' G'^{-1} A^{-1}, in
+  // double-double and rounded once at the end.
   auto B = moment_basis(q.order);
   const int K = (int)B.size();
-  bool ok;
-  std::vector<double> Gi = spd_inverse(gram_shifted(q.order, q.m), K, &ok);
-  if (!ok) { *err = "Gram matrix not positive definite"; return false; }
-  const double sg = std::sqrt(q.m + 1.0);
-  // column of the e = 0 monomial with the same (a, b) as each e = 1 monomial
+  std::vector<dd> Gi;
+  if (!spd_inverse_dd(gram_shifted_dd(q.order, q.m), K, &Gi)) {
+    *err = "Gram matrix not positive definite";
+    return false;
+  }
+  const dd sg = dd_sqrt(dd(q.m) + dd(1.0));
   std::vector<int> partner(K, -1);
   for (int k = 0; k < K; ++k)
     if (B[k].e == 1)
       for (int j = 0; j < K; ++j)
         if (B[j].e == 0 && B[j].a == B[k].a && B[j].b == B[k].b) partner[k] = j;
   H->assign((size_t)q.Q * K, 0.0);
-  std::vector<double> phi(K), r(K);
+  std::vector<dd> phi(K), r(K), row(K);
   for (int i = 0; i < q.Q; ++i) {
-    eval_shifted(B, q.m, q.p0[i], q.px[i], q.py[i], phi.data());
+    const dd s = dd(q.p0[i]) - dd(q.m), qx = dd(q.px[i]) / sg, qy = dd(q.py[i]) / sg;
     for (int k = 0; k < K; ++k) {
-      double t = 0.0;
-      for (int j = 0; j < K; ++j) t += phi[j] * Gi[j * K + k];
+      dd v = B[k].e ? s : dd(1.0);
+      for (int t = 0; t < B[k].a; ++t) v = v * qx;
+      for (int t = 0; t < B[k].b; ++t) v = v * qy;
+      phi[k] = v;
+    }
+    for (int k = 0; k < K; ++k) {
+      dd t(0.0);
+      for (int j = 0; j < K; ++j) t = t + phi[j] * Gi[j * K + k];
       r[k] = t;
     }
+    for (int k = 0; k < K; ++k) row[k] = dd(0.0);
     // multiply by A^{-1}: phi'_k = sg^{-(a+b)} (phi_k - m phi_partner(k)) for e = 1
     for (int k = 0; k < K; ++k) {
-      const double sc = std::pow(sg, -(B[k].a + B[k].b)) * q.w[i] * r[k];
-      (*H)[(size_t)i * K + k] += sc;
-      if (B[k].e == 1) (*H)[(size_t)i * K + partner[k]] -= q.m * sc;
+      dd sc = dd(q.w[i]) * r[k];
+      for (int t = 0; t < B[k].a + B[k].b; ++t) sc = sc / sg;
+      row[k] = row[k] + sc;
+      if (B[k].e == 1) row[partner[k]] = row[partner[k]] - dd(q.m) * sc;
     }
+    for (int k = 0; k < K; ++k) (*H)[(size_t)i * K + k] = row[k].to_double();
   }
   return true;
 }

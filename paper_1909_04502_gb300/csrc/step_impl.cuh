@@ -9,6 +9,9 @@ namespace rlbm {
 
 constexpr int kThreads = 256;
 
+// kernel parameters are limited to 32764 bytes
+static_assert(sizeof(Tables<double>) + sizeof(MomentArgs<double>) <= 32764, "kernel parameter space");
+
 // ---------------------------------------------------------------------------
 // Step 1 of the update: streaming by pull (Eq. discrete-rbe, left side).
 // On-lattice: f_i(x) = f*_i(x - n_i).  Bilinear: f_i(x) = sum_ab W_ab
