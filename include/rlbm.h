@@ -164,6 +164,38 @@ int rlbm_set_stream(rlbm_handle* h, void* stream);
  * f^eq_i(n_ref, 0, T_ref)). */
 int rlbm_buffers(rlbm_handle* h, void** cur, void** prev, int* elem_size, long long* plane);
 
+/* Allocation-free variant of the fused step, for callers that cannot
+ * allocate device memory: code that runs inside another runtime which owns
+ * the device memory (a plugin whose buffers come from the host application's
+ * pool), code that must not allocate while it records or replays work, or
+ * code that cannot afford the device-wide synchronisation of cudaMalloc /
+ * cudaFree.  The paper has no counterpart (it describes no API).
+ *
+ * f_a holds f*(t) on entry in the storage layout of a handle created with
+ * the same parameters (see rlbm_buffers): elements of 4 bytes (FP32 storage)
+ * or 8 bytes (FP64), population plane i at element offset i * plane with
+ * plane = nx*ny rounded up to a multiple of 32, cell (x, y) at y*nx + x
+ * inside a plane; FP32 storage holds f - f_ref (pass n_ref = 0 to store f).
+ * f_b is a second buffer of the same size.  The call runs nsteps steps,
+ * alternating f_a -> f_b -> f_a ...: the result is in f_b when nsteps is
+ * odd and in f_a when it is even.  tau_field (device, storage precision,
+ * nx*ny) is read when p->tau_mode is RLBM_TAU_FIELD.  Work is issued on
+ * p->stream.  If counts is non-NULL it receives, per step, the number of
+ * non-physical cell updates; the call then synchronises the stream and
+ * returns RLBM_ERR_NONPHYSICAL if any count is non-zero.
+ *
+ * Memory.  The call allocates no device memory: its only scratch is a
+ * file-scope device array of 1024 eight-byte counters (one per step), which
+ * every GPU that loads the library holds until the process exits.  nsteps
+ * above 1024 is rejected with RLBM_ERR_INVALID_ARG.  The first call on a
+ * device looks the array up (cudaGetSymbolAddress) for that device; make it
+ * before any stream capture.  All calls share the array and each clears its
+ * counters first, so calls that overlap on the GPU race on it.  The host
+ * side caches the tables of each parameter set in host memory.  Errors are
+ * reported through rlbm_last_error(NULL). */
+int rlbm_step_noalloc(const rlbm_params* p, void* f_a, void* f_b, const void* tau_field, int nsteps,
+                      long long* counts);
+
 /* Message of the last error on this handle (or of the last failed
  * rlbm_create when h is NULL).  Never NULL. */
 const char* rlbm_last_error(const rlbm_handle* h);

@@ -502,3 +502,66 @@ int rlbm_buffers(rlbm_handle* h, void** cur, void** prev, int* elem_size, long l
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Host-only helpers for the allocation-free entry point (noalloc.cu).
+// ---------------------------------------------------------------------------
+
+void rlbm_internal_set_error(const std::string& msg) { g_create_error = msg; }
+
+int rlbm_internal_prepare(const rlbm_params* p, Scalars* sc, Tables<float>* tf, Tables<double>* td,
+                          std::string* err) {
+  if (p->d != 2) { *err = "d must be 2"; return p->d == 3 ? RLBM_ERR_UNSUPPORTED : RLBM_ERR_INVALID_ARG; }
+  if (p->order != 2 && p->order != 3) { *err = "order must be 2 or 3"; return RLBM_ERR_INVALID_ARG; }
+  if (p->nx <= 0 || p->ny <= 0 || (long long)p->nx * p->ny > (1LL << 30)) {
+    *err = "grid size out of range";
+    return RLBM_ERR_INVALID_ARG;
+  }
+  if (p->precision != RLBM_FP64 && p->precision != RLBM_FP32_STORE) { *err = "precision"; return RLBM_ERR_INVALID_ARG; }
+  if (p->boundary != RLBM_BC_PERIODIC && p->boundary != RLBM_BC_FREEFLOW_X) { *err = "boundary"; return RLBM_ERR_INVALID_ARG; }
+  if (p->stream_mode != RLBM_ONLATTICE && p->stream_mode != RLBM_BILINEAR) { *err = "stream_mode"; return RLBM_ERR_INVALID_ARG; }
+  if (p->stream_mode == RLBM_BILINEAR && !(p->lambda > 0.0)) { *err = "bilinear streaming needs lambda > 0"; return RLBM_ERR_INVALID_ARG; }
+  if (p->tau_mode == RLBM_TAU_CONST && !(p->tau > 0.5)) { *err = "tau must exceed 1/2"; return RLBM_ERR_INVALID_ARG; }
+  if (p->tau_mode == RLBM_TAU_ETA_OVER_S && !(p->eta_over_s > 0.0 && p->kappa > 0.0)) {
+    *err = "eta_over_s and kappa must be positive";
+    return RLBM_ERR_INVALID_ARG;
+  }
+  if (p->tau_mode < 0 || p->tau_mode > 2) { *err = "tau_mode"; return RLBM_ERR_INVALID_ARG; }
+  if (!(p->T_ref > 0.0) || !(p->n_ref >= 0.0)) { *err = "reference state"; return RLBM_ERR_INVALID_ARG; }
+  rlbm_handle h;                      // host-side description only: no device buffers
+  h.p = *p;
+  h.p.groups = nullptr;
+  h.p.custom_table = nullptr;
+  int rc = build_quadrature(p, &h.q, err);
+  if (rc != RLBM_OK) return rc;
+  if (h.q.Q > kMaxQ) { *err = "too many populations"; return RLBM_ERR_UNSUPPORTED; }
+  h.K = (int)moment_basis(p->order).size();
+  if (!equilibrium_matrix(h.q, &h.H, err)) return RLBM_ERR_QUADRATURE;
+  const double m = p->m;
+  const double nr = (p->precision == RLBM_FP32_STORE) ? p->n_ref : 0.0;
+  const double Tr = p->T_ref;
+  Scalars& s = *sc;
+  std::memset(&s, 0, sizeof(s));
+  s.Q = h.q.Q;
+  s.K = h.K;
+  s.order = p->order;
+  s.nx = p->nx;
+  s.ny = p->ny;
+  s.ncell = p->nx * p->ny;
+  s.plane = ((long long)s.ncell + 31) / 32 * 32;
+  s.boundary = p->boundary;
+  s.tau_mode = p->tau_mode;
+  s.tau = p->tau;
+  s.tau_coef = p->eta_over_s * (p->d + 2) * p->kappa;
+  s.m = m;
+  s.n_ref = nr;
+  s.T_ref = Tr;
+  s.N0_ref = nr;
+  s.T00_ref = nr * (m * m + 2.0 * m * Tr + 2.0 * Tr * Tr) / (m + Tr);
+  s.Tii_ref = nr * Tr;
+  s.r2_ref = Tr * (m * m + 3.0 * m * Tr + 3.0 * Tr * Tr) / (m + Tr);
+  s.kappa_guess = (float)(Tr * (m + Tr) / (m * m + 2.0 * m * Tr + 2.0 * Tr * Tr));
+  if (p->precision == RLBM_FP32_STORE) fill_tables(&h, tf);
+  else fill_tables(&h, td);
+  return RLBM_OK;
+}

@@ -68,6 +68,8 @@ SIGNATURES = {
     "rlbm_set_stream": (ctypes.c_int, [_H, _VP]),
     "rlbm_buffers": (ctypes.c_int, [_H, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _IP,
                                     ctypes.POINTER(ctypes.c_longlong)]),
+    "rlbm_step_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), _VP, _VP, _VP, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_longlong)]),
     "rlbm_last_error": (ctypes.c_char_p, [_H]),
     "rlbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
