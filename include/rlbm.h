@@ -159,10 +159,15 @@ int rlbm_set_stream(rlbm_handle* h, void* stream);
 
 /* Device pointers of the current f*(t) buffer and of the previous one
  * (borrowed; valid until the next rlbm_step / rlbm_destroy), element size
- * (4 or 8 bytes) and population-plane stride in elements.  FP32-storage
- * handles hold g = f - f_ref (the reference equilibrium f_ref,i =
- * f^eq_i(n_ref, 0, T_ref)). */
-int rlbm_buffers(rlbm_handle* h, void** cur, void** prev, int* elem_size, long long* plane);
+ * (4 or 8 bytes), population-plane stride in elements, and the padded
+ * layout {pitch, hx, hy, px} (nullable, 4 ints).  Plane i starts at element
+ * i * plane; interior cell (x, y) is at (y + hy) * pitch + (x + px); the hx
+ * columns left and right and the hy rows above and below hold copies of
+ * cells (periodic images, or the first / last column for free-flow ends) so
+ * that streaming reads need no wrap-around.  FP32-storage handles hold
+ * g = f - f_ref (f_ref,i = f^eq_i(n_ref, 0, T_ref)); FP64 handles hold f. */
+int rlbm_buffers(rlbm_handle* h, void** cur, void** prev, int* elem_size, long long* plane,
+                 int* layout);
 
 /* Allocation-free variant of the fused step, for callers that cannot
  * allocate device memory: code that runs inside another runtime which owns
@@ -171,12 +176,11 @@ int rlbm_buffers(rlbm_handle* h, void** cur, void** prev, int* elem_size, long l
  * code that cannot afford the device-wide synchronisation of cudaMalloc /
  * cudaFree.  The paper has no counterpart (it describes no API).
  *
- * f_a holds f*(t) on entry in the storage layout of a handle created with
- * the same parameters (see rlbm_buffers): elements of 4 bytes (FP32 storage)
- * or 8 bytes (FP64), population plane i at element offset i * plane with
- * plane = nx*ny rounded up to a multiple of 32, cell (x, y) at y*nx + x
- * inside a plane; FP32 storage holds f - f_ref (pass n_ref = 0 to store f).
- * f_b is a second buffer of the same size.  The call runs nsteps steps,
+ * f_a holds f*(t) on entry, halo included, in the storage layout of a
+ * handle created with the same parameters (rlbm_buffers describes it; a
+ * copy of such a handle's buffer is a valid start).  f_b is a second buffer
+ * of the same size.  FP32 storage holds f - f_ref (pass n_ref = 0 to store
+ * f).  The call runs nsteps steps,
  * alternating f_a -> f_b -> f_a ...: the result is in f_b when nsteps is
  * odd and in f_a when it is even.  tau_field (device, storage precision,
  * nx*ny) is read when p->tau_mode is RLBM_TAU_FIELD.  Work is issued on

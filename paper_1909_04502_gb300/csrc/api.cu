@@ -11,6 +11,7 @@
 #include "../../include/rlbm.h"
 #include "dispatch.h"
 #include "handle.h"
+#include "step_impl.cuh"
 #include "setup.h"
 
 using namespace rlbm;
@@ -35,26 +36,43 @@ int cuda_fail(rlbm_handle* h, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
   } while (0)
 
-long long mod_pos(long long a, long long n) { return ((a % n) + n) % n; }
+// Off-lattice pull taps for velocity (vx, vy) and lambda: the departure point
+// is x - lambda v; o = floor of it, phi = its fractional part.  A displacement
+// within 1e-12 of a whole number of cells is that number.
+void bilinear_base(double lambda, double vx, double vy, int o[2], double phi[2]) {
+  double src[2] = {-lambda * vx, -lambda * vy};
+  for (int d = 0; d < 2; ++d) {
+    double r = std::nearbyint(src[d]);
+    if (std::fabs(src[d] - r) < 1e-12) src[d] = r;
+    double fl = std::floor(src[d]);
+    o[d] = (int)fl;
+    if (phi) phi[d] = src[d] - fl;
+  }
+}
 
-// Device kernels converting between stored (shifted, storage precision)
-// populations and FP64 unshifted populations.
+// Device kernels converting between stored (shifted, storage precision,
+// padded) populations and FP64 unshifted populations [Q][ny][nx].  The import
+// also fills the halo images.
 template <typename S>
-__global__ void k_export(const S* __restrict__ src, double* __restrict__ dst, int Q, int ncell,
-                         long long plane, const double* __restrict__ fref) {
+__global__ void k_export(const S* __restrict__ src, double* __restrict__ dst, const Scalars s,
+                         const double* __restrict__ fref) {
   long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= (long long)Q * ncell) return;
-  int i = (int)(idx / ncell), c = (int)(idx - (long long)i * ncell);
-  dst[idx] = (double)src[i * plane + c] + fref[i];
+  if (idx >= (long long)s.Q * s.ncell) return;
+  int i = (int)(idx / s.ncell), c = (int)(idx - (long long)i * s.ncell);
+  int y = c / s.nx, x = c - y * s.nx;
+  dst[idx] = (double)src[i * s.plane + sidx(s, x, y)] + fref[i];
 }
 
 template <typename S>
-__global__ void k_import(const double* __restrict__ src, S* __restrict__ dst, int Q, int ncell,
-                         long long plane, const double* __restrict__ fref) {
+__global__ void k_import(const double* __restrict__ src, S* __restrict__ dst, const Scalars s,
+                         const double* __restrict__ fref) {
   long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= (long long)Q * ncell) return;
-  int i = (int)(idx / ncell), c = (int)(idx - (long long)i * ncell);
-  dst[i * plane + c] = (S)(src[idx] - fref[i]);
+  if (idx >= (long long)s.Q * s.ncell) return;
+  int i = (int)(idx / s.ncell), c = (int)(idx - (long long)i * s.ncell);
+  int y = c / s.nx, x = c - y * s.nx;
+  const S v = (S)(src[idx] - fref[i]);
+  dst[i * s.plane + sidx(s, x, y)] = v;
+  for_each_halo_image(s, x, y, [&](long long hi) { dst[i * s.plane + hi] = v; });
 }
 
 template <typename S>
@@ -63,11 +81,46 @@ __global__ void k_tau_import(const double* __restrict__ src, S* __restrict__ dst
   if (idx < ncell) dst[idx] = (S)src[idx];
 }
 
+// Derived scalars: FP32 copies, flags, the int plane stride.
+void finish_scalars(Scalars* s) {
+  s->PE_ref = s->Tii_ref + s->T00_ref;
+  s->massless = (s->m == 0.0) ? 1 : 0;
+  s->iplane = (int)s->plane;
+  s->f_tau = (float)s->tau;
+  s->f_tau_coef = (float)s->tau_coef;
+  s->f_m = (float)s->m;
+  s->f_n_ref = (float)s->n_ref;
+  s->f_T_ref = (float)s->T_ref;
+  s->f_T00_ref = (float)s->T00_ref;
+  s->f_Tii_ref = (float)s->Tii_ref;
+}
+
+// Halo widths and padded layout of the population planes (kernels.cuh).
+void compute_layout(const Quadrature& q, const rlbm_params& p, size_t elem, Scalars* s) {
+  int hx = 0, hy = 0;
+  for (int i = 0; i < q.Q; ++i) {
+    if (p.stream_mode == RLBM_ONLATTICE) {
+      hx = std::max(hx, std::abs(q.nx[i]));
+      hy = std::max(hy, std::abs(q.ny[i]));
+    } else {
+      int o[2];
+      bilinear_base(p.lambda, q.px[i] / q.p0[i], q.py[i] / q.p0[i], o, nullptr);
+      hx = std::max(hx, std::max(-o[0], o[0] + 1));
+      hy = std::max(hy, std::max(-o[1], o[1] + 1));
+    }
+  }
+  const int align = (int)(32 / elem);                 // 32-byte row alignment
+  s->hx = hx;
+  s->hy = hy;
+  s->px = (hx + align - 1) / align * align;
+  s->pitch = (s->px + p.nx + hx + align - 1) / align * align;
+  s->plane = ((long long)(p.ny + 2 * hy) * s->pitch + 31) / 32 * 32;
+}
+
 template <typename R>
-void fill_tables(const rlbm_handle* h, Tables<R>* t) {
+void fill_tables(const rlbm_handle* h, const Scalars& s, Tables<R>* t) {
   std::memset(t, 0, sizeof(Tables<R>));
   const Quadrature& q = h->q;
-  const int nx = h->p.nx, ny = h->p.ny;
   for (int i = 0; i < q.Q; ++i) {
     const double p0 = q.p0[i], px = q.px[i], py = q.py[i];
     const double c[9] = {p0, px, py, p0 * p0, p0 * px, p0 * py, px * px, px * py, py * py};
@@ -75,25 +128,19 @@ void fill_tables(const rlbm_handle* h, Tables<R>* t) {
     t->vx[i] = (R)(px / p0);
     t->vy[i] = (R)(py / p0);
     for (int k = 0; k < h->K; ++k) t->H[i][k] = (R)h->H[(size_t)i * h->K + k];
-    t->sxp[i] = (int)mod_pos(-q.nx[i], nx);
-    t->syp[i] = (int)mod_pos(-q.ny[i], ny);
-    t->sxr[i] = -q.nx[i];
-    // off-lattice pull taps: source point x - lambda v_i
-    double src[2] = {-h->p.lambda * px / p0, -h->p.lambda * py / p0};
-    double o[2], phi[2];
-    for (int d = 0; d < 2; ++d) {
-      double r = std::nearbyint(src[d]);
-      if (std::fabs(src[d] - r) < 1e-12) src[d] = r;   // whole-cell displacement
-      o[d] = std::floor(src[d]);
-      phi[d] = src[d] - o[d];
+    if (h->p.stream_mode == RLBM_ONLATTICE) {
+      t->off[i] = -q.ny[i] * s.pitch - q.nx[i];
+      t->bw[i][0] = (R)1.0;
+    } else {
+      int o[2];
+      double phi[2];
+      bilinear_base(h->p.lambda, px / p0, py / p0, o, phi);
+      t->off[i] = o[1] * s.pitch + o[0];
+      t->bw[i][0] = (R)((1.0 - phi[0]) * (1.0 - phi[1]));
+      t->bw[i][1] = (R)(phi[0] * (1.0 - phi[1]));
+      t->bw[i][2] = (R)((1.0 - phi[0]) * phi[1]);
+      t->bw[i][3] = (R)(phi[0] * phi[1]);
     }
-    t->bw[i][0] = (R)((1.0 - phi[0]) * (1.0 - phi[1]));
-    t->bw[i][1] = (R)(phi[0] * (1.0 - phi[1]));
-    t->bw[i][2] = (R)((1.0 - phi[0]) * phi[1]);
-    t->bw[i][3] = (R)(phi[0] * phi[1]);
-    t->oxp[i] = (int)mod_pos((long long)o[0], nx);
-    t->oyp[i] = (int)mod_pos((long long)o[1], ny);
-    t->oxr[i] = (int)o[0];
   }
 }
 
@@ -246,7 +293,8 @@ int rlbm_create(const rlbm_params* p, rlbm_handle** out) {
   s.nx = p->nx;
   s.ny = p->ny;
   s.ncell = p->nx * p->ny;
-  s.plane = ((long long)s.ncell + 31) / 32 * 32;
+  h->elem = (p->precision == RLBM_FP32_STORE) ? 4 : 8;
+  compute_layout(h->q, *p, h->elem, &s);
   s.boundary = p->boundary;
   s.tau_mode = p->tau_mode;
   s.tau = p->tau;
@@ -257,8 +305,10 @@ int rlbm_create(const rlbm_params* p, rlbm_handle** out) {
   s.N0_ref = nr;
   s.T00_ref = nr * (m * m + 2.0 * m * Tr + 2.0 * Tr * Tr) / (m + Tr);
   s.Tii_ref = nr * Tr;
-  s.r2_ref = Tr * (m * m + 3.0 * m * Tr + 3.0 * Tr * Tr) / (m + Tr);
   s.kappa_guess = (float)(Tr * (m + Tr) / (m * m + 2.0 * m * Tr + 2.0 * Tr * Tr));
+  finish_scalars(&s);
+  if ((long long)h->q.Q * s.plane >= (1LL << 31))
+    return fail(nullptr, RLBM_ERR_UNSUPPORTED, "grid too large: Q * plane must stay below 2^31 elements");
   // reference populations f_ref,i = sum_k H_ik M_k(n_ref, e0, T_ref)
   std::vector<double> Mref(h->K);
   const double e0[3] = {1.0, 0.0, 0.0};
@@ -267,14 +317,13 @@ int rlbm_create(const rlbm_params* p, rlbm_handle** out) {
   for (int i = 0; i < h->q.Q; ++i)
     for (int k = 0; k < h->K; ++k) h->fref[i] += h->H[(size_t)i * h->K + k] * Mref[k];
 
-  h->elem = (p->precision == RLBM_FP32_STORE) ? 4 : 8;
   h->stream = (cudaStream_t)p->stream;
   if (h->elem == 4) {
     h->tf.reset(new Tables<float>());
-    fill_tables(h.get(), h->tf.get());
+    fill_tables(h.get(), s, h->tf.get());
   } else {
     h->td.reset(new Tables<double>());
-    fill_tables(h.get(), h->td.get());
+    fill_tables(h.get(), s, h->td.get());
   }
   // device buffers
   const size_t pop_bytes = (size_t)h->q.Q * s.plane * h->elem;
@@ -283,9 +332,9 @@ int rlbm_create(const rlbm_params* p, rlbm_handle** out) {
     e = cudaMalloc(&h->buf[b], pop_bytes);
     if (e != cudaSuccess) { cudaGetLastError(); return fail(nullptr, RLBM_ERR_OOM, "population buffers"); }
   }
-  e = cudaMalloc(&h->fields, (size_t)14 * s.plane * sizeof(double));
+  e = cudaMalloc(&h->fields, (size_t)14 * s.ncell * sizeof(double));
   if (e != cudaSuccess) { cudaGetLastError(); return fail(nullptr, RLBM_ERR_OOM, "field buffer"); }
-  e = cudaMalloc(&h->tau_field, (size_t)s.plane * h->elem);
+  e = cudaMalloc(&h->tau_field, (size_t)s.ncell * h->elem);
   if (e != cudaSuccess) { cudaGetLastError(); return fail(nullptr, RLBM_ERR_OOM, "tau buffer"); }
   e = cudaMalloc(&h->status, 2 * sizeof(unsigned long long));
   if (e != cudaSuccess) { cudaGetLastError(); return fail(nullptr, RLBM_ERR_OOM, "status word"); }
@@ -344,7 +393,7 @@ int rlbm_init(rlbm_handle* h, const double* n, const double* ux, const double* u
     if (on_device) {
       dev[k] = src[k];
     } else {
-      double* d = h->fields + (size_t)k * s.plane;   // the field planes double as staging
+      double* d = h->fields + (size_t)k * s.ncell;   // the field planes double as staging
       RLBM_CUDA(h, cudaMemcpyAsync(d, src[k], bytes, cudaMemcpyHostToDevice, h->stream));
       dev[k] = d;
     }
@@ -423,11 +472,11 @@ int rlbm_moments(rlbm_handle* h, double* n, double* ux, double* uy, double* T, d
   const size_t bytes = (size_t)s.ncell * sizeof(double);
   double* outs[5] = {n, ux, uy, T, eps};
   for (int k = 0; k < 5; ++k)
-    if (outs[k]) RLBM_CUDA(h, cudaMemcpyAsync(outs[k], h->fields + (size_t)k * s.plane, bytes, kind, h->stream));
+    if (outs[k]) RLBM_CUDA(h, cudaMemcpyAsync(outs[k], h->fields + (size_t)k * s.ncell, bytes, kind, h->stream));
   for (int k = 0; k < 3; ++k)
-    if (Nab) RLBM_CUDA(h, cudaMemcpyAsync(Nab + (size_t)k * s.ncell, h->fields + (size_t)(5 + k) * s.plane, bytes, kind, h->stream));
+    if (Nab) RLBM_CUDA(h, cudaMemcpyAsync(Nab + (size_t)k * s.ncell, h->fields + (size_t)(5 + k) * s.ncell, bytes, kind, h->stream));
   for (int k = 0; k < 6; ++k)
-    if (Tab) RLBM_CUDA(h, cudaMemcpyAsync(Tab + (size_t)k * s.ncell, h->fields + (size_t)(8 + k) * s.plane, bytes, kind, h->stream));
+    if (Tab) RLBM_CUDA(h, cudaMemcpyAsync(Tab + (size_t)k * s.ncell, h->fields + (size_t)(8 + k) * s.ncell, bytes, kind, h->stream));
   if (!on_device) RLBM_CUDA(h, cudaStreamSynchronize(h->stream));
   return RLBM_OK;
 }
@@ -450,8 +499,8 @@ int rlbm_get_populations(rlbm_handle* h, double* f, int on_device) {
   }
   const long long total = (long long)s.Q * s.ncell;
   const int nb = (int)((total + 255) / 256);
-  if (h->elem == 4) k_export<float><<<nb, 256, 0, h->stream>>>((const float*)h->buf[h->cur], dst, s.Q, s.ncell, s.plane, h->fref_dev);
-  else k_export<double><<<nb, 256, 0, h->stream>>>((const double*)h->buf[h->cur], dst, s.Q, s.ncell, s.plane, h->fref_dev);
+  if (h->elem == 4) k_export<float><<<nb, 256, 0, h->stream>>>((const float*)h->buf[h->cur], dst, s, h->fref_dev);
+  else k_export<double><<<nb, 256, 0, h->stream>>>((const double*)h->buf[h->cur], dst, s, h->fref_dev);
   RLBM_CUDA(h, cudaGetLastError());
   if (!on_device) {
     RLBM_CUDA(h, cudaMemcpyAsync(f, dst, total * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -472,8 +521,8 @@ int rlbm_set_populations(rlbm_handle* h, const double* f, int on_device) {
     src = h->staging;
   }
   const int nb = (int)((total + 255) / 256);
-  if (h->elem == 4) k_import<float><<<nb, 256, 0, h->stream>>>(src, (float*)h->buf[h->cur], s.Q, s.ncell, s.plane, h->fref_dev);
-  else k_import<double><<<nb, 256, 0, h->stream>>>(src, (double*)h->buf[h->cur], s.Q, s.ncell, s.plane, h->fref_dev);
+  if (h->elem == 4) k_import<float><<<nb, 256, 0, h->stream>>>(src, (float*)h->buf[h->cur], s, h->fref_dev);
+  else k_import<double><<<nb, 256, 0, h->stream>>>(src, (double*)h->buf[h->cur], s, h->fref_dev);
   RLBM_CUDA(h, cudaGetLastError());
   if (!on_device) RLBM_CUDA(h, cudaStreamSynchronize(h->stream));
   h->have_prev = false;
@@ -492,12 +541,18 @@ int rlbm_sync_status(rlbm_handle* h, long long* count) {
   return RLBM_OK;
 }
 
-int rlbm_buffers(rlbm_handle* h, void** cur, void** prev, int* elem_size, long long* plane) {
+int rlbm_buffers(rlbm_handle* h, void** cur, void** prev, int* elem_size, long long* plane, int* layout) {
   if (!h) return RLBM_ERR_INVALID_ARG;
   if (cur) *cur = h->buf[h->cur];
   if (prev) *prev = h->buf[h->cur ^ 1];
   if (elem_size) *elem_size = (int)h->elem;
   if (plane) *plane = h->sc.plane;
+  if (layout) {
+    layout[0] = h->sc.pitch;
+    layout[1] = h->sc.hx;
+    layout[2] = h->sc.hy;
+    layout[3] = h->sc.px;
+  }
   return RLBM_OK;
 }
 
@@ -548,7 +603,7 @@ int rlbm_internal_prepare(const rlbm_params* p, Scalars* sc, Tables<float>* tf, 
   s.nx = p->nx;
   s.ny = p->ny;
   s.ncell = p->nx * p->ny;
-  s.plane = ((long long)s.ncell + 31) / 32 * 32;
+  compute_layout(h.q, *p, p->precision == RLBM_FP32_STORE ? 4 : 8, &s);
   s.boundary = p->boundary;
   s.tau_mode = p->tau_mode;
   s.tau = p->tau;
@@ -559,9 +614,13 @@ int rlbm_internal_prepare(const rlbm_params* p, Scalars* sc, Tables<float>* tf, 
   s.N0_ref = nr;
   s.T00_ref = nr * (m * m + 2.0 * m * Tr + 2.0 * Tr * Tr) / (m + Tr);
   s.Tii_ref = nr * Tr;
-  s.r2_ref = Tr * (m * m + 3.0 * m * Tr + 3.0 * Tr * Tr) / (m + Tr);
   s.kappa_guess = (float)(Tr * (m + Tr) / (m * m + 2.0 * m * Tr + 2.0 * Tr * Tr));
-  if (p->precision == RLBM_FP32_STORE) fill_tables(&h, tf);
-  else fill_tables(&h, td);
+  finish_scalars(&s);
+  if ((long long)h.q.Q * s.plane >= (1LL << 31)) {
+    *err = "grid too large: Q * plane must stay below 2^31 elements";
+    return RLBM_ERR_UNSUPPORTED;
+  }
+  if (p->precision == RLBM_FP32_STORE) fill_tables(&h, s, tf);
+  else fill_tables(&h, s, td);
   return RLBM_OK;
 }

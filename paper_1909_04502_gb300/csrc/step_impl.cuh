@@ -7,56 +7,74 @@
 
 namespace rlbm {
 
-constexpr int kThreads = 256;
+// 2-d thread blocks: a warp covers 32 consecutive cells of one row.
+constexpr int kBX = 32;
+constexpr int kBY = 8;
+constexpr int kThreads = kBX * kBY;
 
 // kernel parameters are limited to 32764 bytes
 static_assert(sizeof(Tables<double>) + sizeof(MomentArgs<double>) <= 32764, "kernel parameter space");
 
 // ---------------------------------------------------------------------------
-// Step 1 of the update: streaming by pull (Eq. discrete-rbe, left side).
-// On-lattice: f_i(x) = f*_i(x - n_i).  Bilinear: f_i(x) = sum_ab W_ab
-// f*_i(x + o_i + (a, b)) (off-lattice reading; taps and weights per
-// population in the tables).  Periodic in y always; periodic or clamped
-// (free-flow) in x.
+// Exact FP32 -> FP64 and rounding FP64 -> FP32 conversions on the integer
+// pipe (IEEE-754 bit layouts), keeping the FP64 pipe for arithmetic (a
+// hardware conversion costs about as much as an FP64 multiply on this part).
+// Zero and FP32 denormals map to signed zero; infinities and NaNs keep their
+// class.
 // ---------------------------------------------------------------------------
-template <typename S, int QT, int MODE>
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned sgn = b & 0x80000000u;
+  const unsigned e = (b >> 23) & 0xFFu;
+  const unsigned man = b & 0x7FFFFFu;
+  unsigned hi = sgn | ((e + 896u) << 20) | (man >> 3);
+  unsigned lo = man << 29;
+  hi = (e == 0u) ? sgn : ((e == 0xFFu) ? (sgn | 0x7FF00000u | (man >> 3)) : hi);
+  lo = (e == 0u) ? 0u : lo;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ float d2f(double d) {
+  // round to nearest (ties away from zero) on the magnitude bits: adding half
+  // of the discarded 29-bit tail carries into mantissa and exponent as needed
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(d);
+  const unsigned sgn = (unsigned)(bits >> 32) & 0x80000000u;
+  const unsigned long long mag = (bits & 0x7FFFFFFFFFFFFFFFull);
+  const unsigned ed = (unsigned)(mag >> 52);
+  const unsigned long long r = mag + (1ull << 28);
+  const int e = (int)(r >> 52) - 1023 + 127;
+  const unsigned man = (unsigned)((r >> 29) & 0x7FFFFFull);
+  unsigned b = sgn | ((unsigned)e << 23) | man;
+  const bool is_nan = (ed == 0x7FFu) && ((mag & 0xFFFFFFFFFFFFFull) != 0ull);
+  const unsigned special = is_nan ? 0x7FC00000u : (sgn | 0x7F800000u);
+  b = (e <= 0) ? sgn : ((e >= 255 || ed == 0x7FFu) ? special : b);
+  return __uint_as_float(b);
+}
+
+// ---------------------------------------------------------------------------
+// Step 1 of the update: streaming by pull (Eq. discrete-rbe, left side) from
+// the padded layout: the halo already holds the periodic images / free-flow
+// copies, so every tap is base + constant offset.
+// On-lattice: f_i(x) = f*_i(x - n_i).  Bilinear: f_i(x) = sum_ab W_ab
+// f*_i(x + o_i + (a, b)).
+// ---------------------------------------------------------------------------
+template <typename S, int QT, bool EX, int MODE>
 __device__ __forceinline__ void gather(const Tables<S>& tb, const Scalars& s,
-                                       const S* __restrict__ fin, int x, int y, S (&g)[QT]) {
+                                       const S* __restrict__ fin, long long si, S (&g)[QT]) {
+  const S* __restrict__ base = fin + si;
+  const int Qn = EX ? QT : s.Q;
 #pragma unroll
   for (int i = 0; i < QT; ++i) {
     g[i] = S(0);
-    if (i < s.Q) {
-      const S* __restrict__ pl = fin + (long long)i * s.plane;
+    if (i < Qn) {
+      const int o = i * s.iplane + tb.off[i];
       if constexpr (MODE == kOnLattice) {
-        int ys = y + tb.syp[i];
-        ys -= (ys >= s.ny) ? s.ny : 0;
-        int xs;
-        if (s.boundary == 0) {
-          xs = x + tb.sxp[i];
-          xs -= (xs >= s.nx) ? s.nx : 0;
-        } else {
-          xs = min(max(x + tb.sxr[i], 0), s.nx - 1);
-        }
-        g[i] = __ldg(pl + ys * s.nx + xs);
+        g[i] = __ldg(base + o);
       } else {
-        int y0 = y + tb.oyp[i];
-        y0 -= (y0 >= s.ny) ? s.ny : 0;
-        int y1 = y0 + 1;
-        y1 -= (y1 >= s.ny) ? s.ny : 0;
-        int x0, x1;
-        if (s.boundary == 0) {
-          x0 = x + tb.oxp[i];
-          x0 -= (x0 >= s.nx) ? s.nx : 0;
-          x1 = x0 + 1;
-          x1 -= (x1 >= s.nx) ? s.nx : 0;
-        } else {
-          x0 = min(max(x + tb.oxr[i], 0), s.nx - 1);
-          x1 = min(max(x + tb.oxr[i] + 1, 0), s.nx - 1);
-        }
-        S v = tb.bw[i][0] * __ldg(pl + y0 * s.nx + x0);
-        v = fma(tb.bw[i][1], __ldg(pl + y0 * s.nx + x1), v);
-        v = fma(tb.bw[i][2], __ldg(pl + y1 * s.nx + x0), v);
-        v = fma(tb.bw[i][3], __ldg(pl + y1 * s.nx + x1), v);
+        S v = tb.bw[i][0] * __ldg(base + o);
+        v = fma(tb.bw[i][1], __ldg(base + o + 1), v);
+        v = fma(tb.bw[i][2], __ldg(base + o + s.pitch), v);
+        v = fma(tb.bw[i][3], __ldg(base + o + s.pitch + 1), v);
         g[i] = v;
       }
     }
@@ -65,91 +83,68 @@ __device__ __forceinline__ void gather(const Tables<S>& tb, const Scalars& s,
 
 // Step 1: N^a = sum_i f_i p_i^a, T^ab = sum_i f_i p_i^a p_i^b (of the
 // stored, possibly shifted, populations).
-template <typename S, int QT>
+template <typename S, int QT, bool EX>
 __device__ __forceinline__ void moments9(const Tables<S>& tb, int Q, const S (&g)[QT], S (&mm)[9]) {
+  const int Qn = EX ? QT : Q;
 #pragma unroll
   for (int j = 0; j < 9; ++j) mm[j] = S(0);
 #pragma unroll
   for (int i = 0; i < QT; ++i) {
-    if (i < Q) {
+    if (i < Qn) {
 #pragma unroll
       for (int j = 0; j < 9; ++j) mm[j] = fma(g[i], tb.c[i][j], mm[j]);
     }
   }
 }
 
-// Steps 2-4 in FP64: Landau frame eps U^a = T^ab U_b (largest eigenvalue of
-// the mixed tensor T^a_b, timelike eigenvector, Sec. 4), n = U_a N^a, T from
+// ---------------------------------------------------------------------------
+// Steps 2-4: Landau frame eps U^a = T^ab U_b (largest eigenvalue of the mixed
+// tensor T^a_b with a timelike eigenvector, Sec. 4), n = U_a N^a, T from
 // eps/n = T (G_2(m/T) - 1) (Eq. eos-ddim), inverted in closed form for d = 2.
 //
 // The eigenvalue is the largest root of p(l) = det(A - l I),
-//   p(l) = a D - s^2 c - t^2 b + 2 r s t,  a = T00 - l, b = Txx + l,
-//   c = Tyy + l, D = b c - r^2, s = T0x, t = T0y, r = Txy,
-// and its eigenvector is v = (D, s c - r t, t b - r s).  A first guess comes
-// from the ideal-fluid closed form (P = kappa eps) in FP32, refined by FP32
-// Newton steps; the root is then polished by Newton steps whose residual
-// p(l) is evaluated in FP64 (one step for FP32 storage, two in FP64 mode),
-// and v, its normalisation, n and T are evaluated in FP64.
-template <typename S>
-__device__ __forceinline__ Macro landau(const Scalars& sc, const S (&mm)[9]) {
-  constexpr bool F32 = sizeof(S) == 4;
-  const double N0 = sc.N0_ref + (double)mm[0];
-  const double Nx = (double)mm[1], Ny = (double)mm[2];
-  const double T00 = sc.T00_ref + (double)mm[3];
-  const double T0x = (double)mm[4], T0y = (double)mm[5];
-  const double Txx = sc.Tii_ref + (double)mm[6];
-  const double Txy = (double)mm[7];
-  const double Tyy = sc.Tii_ref + (double)mm[8];
+//   p(l) = a D - s vx - t vy,  a = T00 - l, b = Txx + l, c = Tyy + l,
+//   D = b c - r^2, vx = s c - r t, vy = t b - r s  (s = T0x, t = T0y, r = Txy),
+// and v = (D, vx, vy) is its eigenvector.  The first guess is the exact root
+// for an ideal fluid with P = kappa eps (kappa of the reference state),
+// refined by FP32 Newton steps.
+// ---------------------------------------------------------------------------
 
-  float fE, fs, ft, fr, fxx, fyy;
-  if constexpr (F32) {
-    fE = (float)sc.T00_ref + (float)mm[3];
-    fxx = (float)sc.Tii_ref + (float)mm[6];
-    fyy = (float)sc.Tii_ref + (float)mm[8];
-    fs = (float)mm[4]; ft = (float)mm[5]; fr = (float)mm[7];
-  } else {
-    fE = (float)T00; fxx = (float)Txx; fyy = (float)Tyy;
-    fs = (float)T0x; ft = (float)T0y; fr = (float)Txy;
-  }
+// FP64 mode: the whole solve in FP64 (two Newton steps from the FP32 root).
+__device__ __forceinline__ Macro landau_fp64(const Scalars& sc, const double (&mm)[9]) {
+  const double N0 = sc.N0_ref + mm[0], Nx = mm[1], Ny = mm[2];
+  const double T00 = sc.T00_ref + mm[3], T0x = mm[4], T0y = mm[5];
+  const double Txx = sc.Tii_ref + mm[6], Txy = mm[7], Tyy = sc.Tii_ref + mm[8];
+  const float fE = (float)T00, fxx = (float)Txx, fyy = (float)Tyy;
+  const float fs = (float)T0x, ft = (float)T0y, fr = (float)Txy;
   const float k = sc.kappa_guess;
   const float M2 = fs * fs + ft * ft;
   const float disc = (1.f - k) * (1.f - k) * fE * fE + 4.f * k * (fE * fE - M2);
   float lam = (-(1.f - k) * fE + sqrtf(fmaxf(disc, 0.f))) / (2.f * k);
-  float dpf = 1.f;
 #pragma unroll
   for (int it = 0; it < 3; ++it) {
     float a = fE - lam, b = fxx + lam, c = fyy + lam;
     float D = b * c - fr * fr;
-    float p = a * D - fs * fs * c - ft * ft * b + 2.f * fr * fs * ft;
-    dpf = -D + a * (b + c) - M2;
-    lam -= p / dpf;
+    float p = a * D - fs * (fs * c - fr * ft) - ft * (ft * b - fr * fs);
+    float dp = -D + a * (b + c) - M2;
+    lam -= p / dp;
   }
   double L = (double)lam;
 #pragma unroll
-  for (int it = 0; it < (F32 ? 1 : 2); ++it) {
+  for (int it = 0; it < 2; ++it) {
     double a = T00 - L, b = Txx + L, c = Tyy + L;
     double D = fma(b, c, -Txy * Txy);
-    double p = fma(a, D, fma(-T0x * T0x, c, fma(-T0y * T0y, b, 2.0 * Txy * T0x * T0y)));
-    if constexpr (F32) {
-      L -= (double)((float)p / dpf);
-    } else {
-      double dp = -D + a * (b + c) - T0x * T0x - T0y * T0y;
-      L -= p / dp;
-    }
+    double vx = fma(T0x, c, -Txy * T0y), vy = fma(T0y, b, -Txy * T0x);
+    double p = fma(a, D, -fma(T0x, vx, T0y * vy));
+    double dp = -D + a * (b + c) - T0x * T0x - T0y * T0y;
+    L -= p / dp;
   }
   const double b = Txx + L, c = Tyy + L;
   const double D = fma(b, c, -Txy * Txy);
   const double vx = fma(T0x, c, -Txy * T0y);
   const double vy = fma(T0y, b, -Txy * T0x);
   const double nrm2 = fma(D, D, -fma(vx, vx, vy * vy));
-  double inv;
-  if constexpr (F32) {
-    double y0 = (double)rsqrtf((float)nrm2);
-    double e = fma(-nrm2, y0 * y0, 1.0);
-    inv = fma(0.5 * y0, e, y0);
-  } else {
-    inv = rsqrt(nrm2);
-  }
+  const double inv = rsqrt(nrm2);
   Macro M;
   M.eps = L;
   M.U0 = D * inv;
@@ -158,32 +153,107 @@ __device__ __forceinline__ Macro landau(const Scalars& sc, const S (&mm)[9]) {
   M.n = fma(M.U0, N0, -fma(M.Ux, Nx, M.Uy * Ny));
   const double m = sc.m;
   if (m == 0.0) {
-    // eps = 2 P = 2 n T
-    if constexpr (F32) {
-      float rh = 0.5f / (float)M.n;
-      double T = L * (double)rh;
-      double e = fma(-2.0 * M.n, T, L);
-      M.T = fma((double)rh, e, T);
-    } else {
-      M.T = 0.5 * L / M.n;
-    }
+    M.T = 0.5 * L / M.n;   // eps = 2 P = 2 n T
   } else {
-    // n q(T) = 2 n T^2 + (2 m n - eps) T + m (m n - eps) = 0, positive root
-    if constexpr (F32) {
-      float fn = (float)M.n, fl = (float)L, fm = (float)m;
-      float e = fl / fn;
-      float T0 = 0.25f * ((e - 2.f * fm) + sqrtf(fmaxf(e * e + 4.f * e * fm - 4.f * fm * fm, 0.f)));
-      double Td = (double)T0;
-      double q = fma(fma(2.0 * M.n, Td, fma(2.0 * m, M.n, -L)), Td, m * fma(m, M.n, -L));
-      float dq = 4.f * fn * T0 + 2.f * fm * fn - fl;
-      M.T = Td - (double)((float)q / dq);
-    } else {
-      double e = L / M.n;
-      M.T = 0.25 * ((e - 2.0 * m) + sqrt(fma(e, e, 4.0 * m * (e - m))));
-    }
+    const double e = L / M.n;
+    M.T = 0.25 * ((e - 2.0 * m) + sqrt(fma(e, e, 4.0 * m * (e - m))));
   }
   M.ok = (D > 0.0) && (nrm2 > 0.0) && (M.n > 0.0) && (M.T > 0.0) && (L > 0.0) && isfinite(M.T) &&
          isfinite(M.U0);
+  return M;
+}
+
+// FP32 storage: the solve runs in FP32, then one Newton correction whose
+// residuals are evaluated in FP64 -- p(l), the eigenvector v, its Minkowski
+// norm, n = U.N and the EOS residual -- about thirty FP64 operations per
+// cell.  Corrections (differences of nearly equal FP64 numbers) are applied
+// in FP32.  The moments are reference + FP32 sums of g, and the eigenvalue is
+// written l = eps_ref + delta.
+__device__ __forceinline__ Macro landau_fp32(const Scalars& sc, const float (&mm)[9]) {
+  const float epsr = sc.f_T00_ref;
+  const float Pr = sc.f_Tii_ref;
+  const float fs = mm[4], ft = mm[5], fr = mm[7];
+  const float M2 = fs * fs + ft * ft;
+  // FP32 guess for delta = l - eps_ref
+  const float fE = epsr + mm[3];
+  const float k = sc.kappa_guess;
+  const float disc = (1.f - k) * (1.f - k) * fE * fE + 4.f * k * (fE * fE - M2);
+  const float lam0 = __fdividef(-(1.f - k) * fE + sqrtf(fmaxf(disc, 0.f)), 2.f * k);
+  float del = lam0 - epsr;
+  const float PE = Pr + epsr;
+  float b = 0.f, c = 0.f, dp = 1.f;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const float a = mm[3] - del;
+    b = PE + mm[6] + del;
+    c = PE + mm[8] + del;
+    const float D = b * c - fr * fr;
+    const float p = a * D - fs * (fs * c - fr * ft) - ft * (ft * b - fr * fs);
+    dp = -D + a * (b + c) - M2;
+    del -= __fdividef(p, dp);
+  }
+  // FP64 residual at l = eps_ref + del
+  const double dd = f2d(del);
+  const double s = f2d(fs), t = f2d(ft), r = f2d(fr);
+  const double base = sc.PE_ref + dd;
+  const double ad = f2d(mm[3]) - dd;
+  const double bd = base + f2d(mm[6]);
+  const double cd = base + f2d(mm[8]);
+  const double D = fma(bd, cd, -r * r);
+  double vx = fma(s, cd, -r * t);
+  double vy = fma(t, bd, -r * s);
+  const double p = fma(ad, D, -fma(s, vx, t * vy));
+  const float dl = -__fdividef(d2f(p), dp);          // Newton correction (FP32 is enough)
+  // eigenvector at the corrected root: v += dl * dv/dl, dv/dl = (b + c, s, t)
+  const double v0 = D + f2d(dl * (b + c));
+  vx += f2d(dl * fs);
+  vy += f2d(dl * ft);
+  const double eps = sc.T00_ref + (dd + f2d(dl));
+  // Minkowski norm of v; 1/sqrt refined once in FP64
+  const double nrm2 = fma(v0, v0, -fma(vx, vx, vy * vy));
+  const float yf = rsqrtf(d2f(nrm2));
+  const double yd = f2d(yf);
+  const float e = d2f(fma(-nrm2, yd * yd, 1.0));      // relative error of yf^2
+  const float yfc = yf * (1.f + 0.5f * e);
+  // n = U.N = (v.N) / |v|
+  const double N0 = sc.N0_ref + f2d(mm[0]);
+  const double w = fma(v0, N0, -fma(vx, f2d(mm[1]), vy * f2d(mm[2])));
+  double n = w * yd;
+  n = fma(n, f2d(0.5f * e), n);
+  Macro M;
+  M.fU0 = d2f(v0) * yfc;
+  M.fUx = d2f(vx) * yfc;
+  M.fUy = d2f(vy) * yfc;
+  M.fn = d2f(n);
+  M.fdn = d2f(n - sc.n_ref);
+  const float fn = M.fn, feps = d2f(eps), fm = sc.f_m, fTr = sc.f_T_ref;
+  float T, corr;
+  if (sc.massless) {
+    // eps = 2 n T: FP32 quotient, then the FP64 residual eps - n (2 T)
+    T = __fdividef(0.5f * feps, fn);
+    const double res = fma(-n, f2d(2.f * T), eps);
+    corr = __fdividef(0.5f * d2f(res), fn);
+  } else {
+    // n q(T) = 2 n T^2 + (2 m n - eps) T + m (m n - eps) = 0, positive root
+    const float ee = __fdividef(feps, fn);
+    T = 0.25f * ((ee - 2.f * fm) + sqrtf(fmaxf(ee * ee + 4.f * ee * fm - 4.f * fm * fm, 0.f)));
+    const double Td = f2d(T);
+    const double q = fma(fma(2.0 * n, Td, fma(2.0 * sc.m, n, -eps)), Td, sc.m * fma(sc.m, n, -eps));
+    const float dq = 4.f * fn * T + 2.f * fm * fn - feps;
+    corr = -__fdividef(d2f(q), dq);
+  }
+  M.fT = T + corr;
+  M.fdT = (T - fTr) + corr;
+  M.eps = eps;
+  M.n = n;
+  M.T = f2d(T) + f2d(corr);
+  M.U0 = f2d(M.fU0);
+  M.Ux = f2d(M.fUx);
+  M.Uy = f2d(M.fUy);
+  // positivity tests on the sign / exponent bits (integer pipe); FP32 tests
+  // catch non-finite values
+  M.ok = (__double2hiint(D) > 0) && (__double2hiint(nrm2) > 0) && (__double2hiint(n) > 0) &&
+         (__double2hiint(eps) > 0) && (M.fT > 0.f) && isfinite(M.fT) && isfinite(M.fU0) && isfinite(M.fn);
   return M;
 }
 
@@ -192,13 +262,11 @@ __device__ __forceinline__ Macro landau(const Scalars& sc, const S (&mm)[9]) {
 //   <1> = n/(m+T), <p^a> = n U^a, <p^a p^b> = n (r2 U^a U^b - T eta^ab),
 //   <p^a p^b p^c> = n (r3 U^a U^b U^c - T r2 (eta^ab U^c + eta^ac U^b + eta^bc U^a)),
 //   r2 = (m^2 + 3mT + 3T^2)/(m+T), r3 = (m^3 + 6m^2 T + 15 m T^2 + 15 T^3)/(m+T).
-// The differences from the reference are rearranged so that the FP32 result
-// is accurate relative to dM itself (only dn and dT are formed in FP64).
+// The differences from the reference are rearranged so that the result is
+// accurate relative to dM itself given accurate dn = n - n_ref and dT = T - T_ref.
 template <typename S, int KT>
-__device__ __forceinline__ void eq_moments(const Scalars& sc, const Macro& M, S (&dM)[KT]) {
-  const S dn = (S)(M.n - sc.n_ref), dT = (S)(M.T - sc.T_ref);
-  const S n = (S)M.n, T = (S)M.T, U0 = (S)M.U0, Ux = (S)M.Ux, Uy = (S)M.Uy;
-  const S m = (S)sc.m, nr = (S)sc.n_ref, Tr = (S)sc.T_ref;
+__device__ __forceinline__ void eq_moments(S dn, S dT, S n, S T, S U0, S Ux, S Uy, S m, S nr, S Tr,
+                                           S (&dM)[KT]) {
   const S U0m1 = (Ux * Ux + Uy * Uy) / (U0 + S(1));
   const S mT = m + T, mTr = m + Tr;
   const S r2 = (m * m + S(3) * m * T + S(3) * T * T) / mT;
@@ -233,68 +301,129 @@ __device__ __forceinline__ void eq_moments(const Scalars& sc, const Macro& M, S 
   }
 }
 
+template <typename S, int KT>
+__device__ __forceinline__ void eq_moments_of(const Scalars& sc, const Macro& M, S (&dM)[KT]) {
+  if constexpr (sizeof(S) == 4) {
+    eq_moments<S, KT>(M.fdn, M.fdT, M.fn, M.fT, M.fU0, M.fUx, M.fUy, sc.f_m, sc.f_n_ref, sc.f_T_ref, dM);
+  } else {
+    eq_moments<S, KT>(M.n - sc.n_ref, M.T - sc.T_ref, M.n, M.T, M.U0, M.Ux, M.Uy, sc.m, sc.n_ref,
+                      sc.T_ref, dM);
+  }
+}
+
+template <typename S>
+__device__ __forceinline__ Macro landau(const Scalars& sc, const S (&mm)[9]) {
+  if constexpr (sizeof(S) == 4) return landau_fp32(sc, mm);
+  else return landau_fp64(sc, mm);
+}
+
 template <typename S>
 __device__ __forceinline__ S local_tau(const Scalars& sc, const S* __restrict__ tau_field, int cell,
                                        const Macro& M) {
   if (sc.tau_mode == 1) return __ldg(tau_field + cell);
-  if (sc.tau_mode == 2) return (S)(sc.tau_coef / M.T);   // step 7, eta/s fixed
-  return (S)sc.tau;
+  if constexpr (sizeof(S) == 4) {
+    if (sc.tau_mode == 2) return __fdividef(sc.f_tau_coef, M.fT);   // step 7, eta/s fixed
+    return sc.f_tau;
+  } else {
+    if (sc.tau_mode == 2) return sc.tau_coef / M.T;   // step 7, eta/s fixed: tau = (eta/s)(d+2) kappa / T
+    return sc.tau;
+  }
+}
+
+// Halo images of interior cell (x, y): every padded position outside the
+// interior that shows this cell -- periodic images in y, and in x either
+// periodic images or, for free-flow ends, the halo columns beside the first
+// and last column.  Calls st(storage index) for each image.
+template <typename F>
+__device__ __forceinline__ void for_each_halo_image(const Scalars& s, int x, int y, F&& st) {
+  const bool xband = (s.boundary == 0) ? (x < s.hx || x >= s.nx - s.hx) : (x == 0 || x == s.nx - 1);
+  const bool yband = (y < s.hy || y >= s.ny - s.hy);
+  if (!xband && !yband) return;
+  int xlo, xhi, xstep;
+  if (s.boundary == 0) {
+    xlo = x - ((x + s.hx) / s.nx) * s.nx;       // smallest image >= -hx
+    xhi = s.nx + s.hx - 1;
+    xstep = s.nx;
+  } else {
+    xlo = (x == 0) ? -s.hx : x;
+    xhi = (x == s.nx - 1) ? s.nx - 1 + s.hx : x;
+    xstep = 1;
+  }
+  for (int yp = y - ((y + s.hy) / s.ny) * s.ny; yp < s.ny + s.hy; yp += s.ny) {
+    for (int xp = xlo; xp <= xhi; xp += xstep) {
+      if (xp == x && yp == y) continue;
+      st((long long)(yp + s.hy) * s.pitch + (xp + s.px));
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
-// Fused step kernel: one thread per cell.
+// Fused step kernel: one thread per cell, 32 x 8 cells per block.
 // ---------------------------------------------------------------------------
-template <typename S, int QT, int KT, int MODE>
+template <typename S, int QT, bool EX, int KT, int MODE>
 __global__ void __launch_bounds__(kThreads) k_step(const __grid_constant__ Tables<S> tb,
                                                    const __grid_constant__ StepArgs<S> a) {
-  const int cell = blockIdx.x * kThreads + threadIdx.x;
-  if (cell >= a.s.ncell) return;
-  const int y = cell / a.s.nx;
-  const int x = cell - y * a.s.nx;
+  const int x = blockIdx.x * kBX + threadIdx.x;
+  const int y = blockIdx.y * kBY + threadIdx.y;
+  if (x >= a.s.nx || y >= a.s.ny) return;
+  const long long si = sidx(a.s, x, y);
+  const int Qn = EX ? QT : a.s.Q;
   S g[QT];
-  gather<S, QT, MODE>(tb, a.s, a.fin, x, y, g);
+  gather<S, QT, EX, MODE>(tb, a.s, a.fin, si, g);
   S mm[9];
-  moments9<S, QT>(tb, a.s.Q, g, mm);
+  moments9<S, QT, EX>(tb, a.s.Q, g, mm);
   const Macro M = landau<S>(a.s, mm);
   if (!M.ok) atomicAdd(a.status, 1ULL);
   S dM[KT];
-  eq_moments<S, KT>(a.s, M, dM);
-  const S inv_tau = S(1) / local_tau<S>(a.s, a.tau_field, cell, M);
-  const S U0 = (S)M.U0, Ux = (S)M.Ux, Uy = (S)M.Uy;
+  eq_moments_of<S, KT>(a.s, M, dM);
+  const S inv_tau = S(1) / local_tau<S>(a.s, a.tau_field, y * a.s.nx + x, M);
+  S U0, Ux, Uy;
+  if constexpr (sizeof(S) == 4) { U0 = M.fU0; Ux = M.fUx; Uy = M.fUy; }
+  else { U0 = M.U0; Ux = M.Ux; Uy = M.Uy; }
   const S keep = M.ok ? S(1) : S(0);
+  S* __restrict__ obase = a.fout + si;
 #pragma unroll
   for (int i = 0; i < QT; ++i) {
-    if (i < a.s.Q) {
+    if (i < Qn) {
       S feq = S(0);
 #pragma unroll
       for (int k = 0; k < KT; ++k) feq = fma(tb.H[i][k], dM[k], feq);
       // step 8: Omega_i = p_i.U / (p_i^0 tau) = (U^0 - v_i . U) / tau
       const S om = keep * (U0 - Ux * tb.vx[i] - Uy * tb.vy[i]) * inv_tau;
-      a.fout[(long long)i * a.s.plane + cell] = fma(om, feq - g[i], g[i]);
+      g[i] = fma(om, feq - g[i], g[i]);
+      obase[i * a.s.iplane] = g[i];
     }
   }
+  for_each_halo_image(a.s, x, y, [&](long long hi) {
+    S* __restrict__ hb = a.fout + hi;
+#pragma unroll
+    for (int i = 0; i < QT; ++i)
+      if (i < Qn) hb[i * a.s.iplane] = g[i];
+  });
 }
 
-// Fields of f(t) (steps 1-4), optionally the raw moments.
-template <typename S, int QT, int MODE>
+// Fields of f(t) (steps 1-4), optionally the raw moments.  Output planes are
+// row-major [ny][nx].
+template <typename S, int QT, bool EX, int MODE>
 __global__ void __launch_bounds__(kThreads) k_fields(const __grid_constant__ Tables<S> tb,
                                                      const __grid_constant__ MomentArgs<S> a) {
-  const int cell = blockIdx.x * kThreads + threadIdx.x;
-  if (cell >= a.s.ncell) return;
-  const int y = cell / a.s.nx;
-  const int x = cell - y * a.s.nx;
+  const int x = blockIdx.x * kBX + threadIdx.x;
+  const int y = blockIdx.y * kBY + threadIdx.y;
+  if (x >= a.s.nx || y >= a.s.ny) return;
+  const long long si = sidx(a.s, x, y);
   S g[QT];
   if (a.gather) {
-    gather<S, QT, MODE>(tb, a.s, a.fin, x, y, g);
+    gather<S, QT, EX, MODE>(tb, a.s, a.fin, si, g);
   } else {
 #pragma unroll
-    for (int i = 0; i < QT; ++i) g[i] = (i < a.s.Q) ? a.fin[(long long)i * a.s.plane + cell] : S(0);
+    for (int i = 0; i < QT; ++i) g[i] = (i < a.s.Q) ? a.fin[i * a.s.plane + si] : S(0);
   }
   S mm[9];
-  moments9<S, QT>(tb, a.s.Q, g, mm);
+  moments9<S, QT, EX>(tb, a.s.Q, g, mm);
   const Macro M = landau<S>(a.s, mm);
   if (!M.ok) atomicAdd(a.status, 1ULL);
-  const long long P = a.s.plane;
+  const long long P = a.s.ncell;
+  const int cell = y * a.s.nx + x;
   double* o = a.out;
   o[0 * P + cell] = M.n;
   o[1 * P + cell] = M.Ux / M.U0;
@@ -314,57 +443,57 @@ __global__ void __launch_bounds__(kThreads) k_fields(const __grid_constant__ Tab
   }
 }
 
-// Initialisation f*(0) = f^eq(n, U, T) (Sec. 6.2), stored shifted.
+// Initialisation f*(0) = f^eq(n, U, T) (Sec. 6.2), stored shifted, with halo images.
 template <typename S, int KT>
 __global__ void __launch_bounds__(kThreads) k_init(const __grid_constant__ Tables<S> tb,
                                                    const __grid_constant__ InitArgs<S> a) {
-  const int cell = blockIdx.x * kThreads + threadIdx.x;
-  if (cell >= a.s.ncell) return;
+  const int x = blockIdx.x * kBX + threadIdx.x;
+  const int y = blockIdx.y * kBY + threadIdx.y;
+  if (x >= a.s.nx || y >= a.s.ny) return;
+  const int cell = y * a.s.nx + x;
   const double ux = a.ux[cell], uy = a.uy[cell];
   const double u2 = ux * ux + uy * uy;
-  Macro M;
-  M.n = a.n[cell];
-  M.T = a.T[cell];
-  M.ok = (u2 < 1.0) && (M.n > 0.0) && (M.T > 0.0);
-  const double gam = M.ok ? 1.0 / sqrt(1.0 - u2) : 1.0;
-  M.U0 = gam;
-  M.Ux = gam * ux;
-  M.Uy = gam * uy;
-  M.eps = 0.0;
-  if (!M.ok) atomicAdd(a.status, 1ULL);
+  const double n = a.n[cell], T = a.T[cell];
+  const bool ok = (u2 < 1.0) && (n > 0.0) && (T > 0.0);
+  if (!ok) atomicAdd(a.status, 1ULL);
+  const double gam = ok ? 1.0 / sqrt(1.0 - u2) : 1.0;
   S dM[KT];
-  eq_moments<S, KT>(a.s, M, dM);
+  eq_moments<S, KT>((S)(n - a.s.n_ref), (S)(T - a.s.T_ref), (S)n, (S)T, (S)gam, (S)(gam * ux),
+                    (S)(gam * uy), (S)a.s.m, (S)a.s.n_ref, (S)a.s.T_ref, dM);
+  const long long si = sidx(a.s, x, y);
   for (int i = 0; i < a.s.Q; ++i) {
     S feq = S(0);
 #pragma unroll
     for (int k = 0; k < KT; ++k) feq = fma(tb.H[i][k], dM[k], feq);
-    a.fout[(long long)i * a.s.plane + cell] = feq;
+    a.fout[i * a.s.plane + si] = feq;
+    for_each_halo_image(a.s, x, y, [&](long long hi) { a.fout[i * a.s.plane + hi] = feq; });
   }
 }
 
 // Dispatch helpers --------------------------------------------------------
 
-inline int blocks_for(int ncell) { return (ncell + kThreads - 1) / kThreads; }
+inline dim3 grid_for(const Scalars& s) { return dim3((s.nx + kBX - 1) / kBX, (s.ny + kBY - 1) / kBY); }
+inline dim3 block_dim() { return dim3(kBX, kBY); }
 
-template <typename S, int QT, int KT>
+// QT: population count of the instantiation; EX: the stencil has exactly QT
+// populations (no per-population bounds test), otherwise Q <= QT at run time.
+template <typename S, int QT, bool EX, int KT>
 cudaError_t launch_step_q(const Tables<S>& tb, const StepArgs<S>& a, int mode, cudaStream_t st) {
-  const int nb = blocks_for(a.s.ncell);
-  if (mode == kOnLattice) k_step<S, QT, KT, kOnLattice><<<nb, kThreads, 0, st>>>(tb, a);
-  else k_step<S, QT, KT, kBilinear><<<nb, kThreads, 0, st>>>(tb, a);
+  if (mode == kOnLattice) k_step<S, QT, EX, KT, kOnLattice><<<grid_for(a.s), block_dim(), 0, st>>>(tb, a);
+  else k_step<S, QT, EX, KT, kBilinear><<<grid_for(a.s), block_dim(), 0, st>>>(tb, a);
   return cudaGetLastError();
 }
 
-template <typename S, int QT>
+template <typename S, int QT, bool EX>
 cudaError_t launch_fields_q(const Tables<S>& tb, const MomentArgs<S>& a, int mode, cudaStream_t st) {
-  const int nb = blocks_for(a.s.ncell);
-  if (mode == kOnLattice) k_fields<S, QT, kOnLattice><<<nb, kThreads, 0, st>>>(tb, a);
-  else k_fields<S, QT, kBilinear><<<nb, kThreads, 0, st>>>(tb, a);
+  if (mode == kOnLattice) k_fields<S, QT, EX, kOnLattice><<<grid_for(a.s), block_dim(), 0, st>>>(tb, a);
+  else k_fields<S, QT, EX, kBilinear><<<grid_for(a.s), block_dim(), 0, st>>>(tb, a);
   return cudaGetLastError();
 }
 
 template <typename S, int KT>
 cudaError_t launch_init_k(const Tables<S>& tb, const InitArgs<S>& a, cudaStream_t st) {
-  k_init<S, KT><<<blocks_for(a.s.ncell), kThreads, 0, st>>>(tb, a);
+  k_init<S, KT><<<grid_for(a.s), block_dim(), 0, st>>>(tb, a);
   return cudaGetLastError();
 }
 

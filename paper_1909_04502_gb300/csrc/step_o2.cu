@@ -7,24 +7,28 @@ namespace rlbm {
 
 template <typename S>
 cudaError_t launch_step_k9(const Tables<S>& tb, const StepArgs<S>& a, int mode, cudaStream_t st) {
+  // exact instantiations for the built-in stencils (massless Q = 28; massive
+  // m~ = 10, 5, 1: Q = 25, 29, 33), bounded buckets otherwise
+  switch (a.s.Q) {
+    case 25: return launch_step_q<S, 25, true, 9>(tb, a, mode, st);
+    case 28: return launch_step_q<S, 28, true, 9>(tb, a, mode, st);
+    case 29: return launch_step_q<S, 29, true, 9>(tb, a, mode, st);
+    case 33: return launch_step_q<S, 33, true, 9>(tb, a, mode, st);
+    default: break;
+  }
   const int Q = a.s.Q;
-  if (Q <= 28) return launch_step_q<S, 28, 9>(tb, a, mode, st);
-  if (Q <= 32) return launch_step_q<S, 32, 9>(tb, a, mode, st);
-  if (Q <= 40) return launch_step_q<S, 40, 9>(tb, a, mode, st);
-  if (Q <= 48) return launch_step_q<S, 48, 9>(tb, a, mode, st);
+  if (Q <= 32) return launch_step_q<S, 32, false, 9>(tb, a, mode, st);
+  if (Q <= 40) return launch_step_q<S, 40, false, 9>(tb, a, mode, st);
+  if (Q <= 48) return launch_step_q<S, 48, false, 9>(tb, a, mode, st);
   return cudaErrorInvalidValue;
 }
 
 template <typename S>
 cudaError_t launch_fields(const Tables<S>& tb, const MomentArgs<S>& a, int mode, cudaStream_t st) {
   const int Q = a.s.Q;
-  if (Q <= 28) return launch_fields_q<S, 28>(tb, a, mode, st);
-  if (Q <= 32) return launch_fields_q<S, 32>(tb, a, mode, st);
-  if (Q <= 40) return launch_fields_q<S, 40>(tb, a, mode, st);
-  if (Q <= 48) return launch_fields_q<S, 48>(tb, a, mode, st);
-  if (Q <= 56) return launch_fields_q<S, 56>(tb, a, mode, st);
-  if (Q <= 64) return launch_fields_q<S, 64>(tb, a, mode, st);
-  if (Q <= 72) return launch_fields_q<S, 72>(tb, a, mode, st);
+  if (Q <= 32) return launch_fields_q<S, 32, false>(tb, a, mode, st);
+  if (Q <= 48) return launch_fields_q<S, 48, false>(tb, a, mode, st);
+  if (Q <= 72) return launch_fields_q<S, 72, false>(tb, a, mode, st);
   return cudaErrorInvalidValue;
 }
 

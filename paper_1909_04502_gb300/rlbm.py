@@ -67,7 +67,7 @@ SIGNATURES = {
     "rlbm_sync_status": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_longlong)]),
     "rlbm_set_stream": (ctypes.c_int, [_H, _VP]),
     "rlbm_buffers": (ctypes.c_int, [_H, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _IP,
-                                    ctypes.POINTER(ctypes.c_longlong)]),
+                                    ctypes.POINTER(ctypes.c_longlong), _IP]),
     "rlbm_step_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), _VP, _VP, _VP, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_longlong)]),
     "rlbm_last_error": (ctypes.c_char_p, [_H]),
@@ -284,9 +284,11 @@ class Lattice:
         return rc, cnt.value
 
     def buffers(self):
+        """(cur, prev, elem_size, plane, (pitch, hx, hy, px)) of the device buffers."""
         cur, prev = _VP(), _VP()
         es = ctypes.c_int()
         plane = ctypes.c_longlong()
+        lay = (ctypes.c_int * 4)()
         _check(lib().rlbm_buffers(self.h, ctypes.byref(cur), ctypes.byref(prev), ctypes.byref(es),
-                                  ctypes.byref(plane)), self.h)
-        return cur.value, prev.value, es.value, plane.value
+                                  ctypes.byref(plane), lay), self.h)
+        return cur.value, prev.value, es.value, plane.value, tuple(lay)
