@@ -200,6 +200,49 @@ int rlbm_buffers(rlbm_handle* h, void** cur, void** prev, int* elem_size, long l
 int rlbm_step_noalloc(const rlbm_params* p, void* f_a, void* f_b, const void* tau_field, int nsteps,
                       long long* counts);
 
+/* ------------------------------------------------------------------------
+ * Batched simulations: many independent grids (different sizes, tau and
+ * stencils; FP32 storage, order 2, built-in stencils, constant or eta/s tau)
+ * advanced together by one persistent cooperative kernel per call, replayed
+ * from a captured CUDA graph.  Not in the paper: it serves the paper's
+ * calibration of tau against transport coefficients (Sec. 7), which runs many
+ * independent simulations.  Each instance stays an ordinary handle
+ * (rlbm_batch_handle) for init / moments / populations; the batched step is
+ * bitwise identical to rlbm_step on every instance.
+ * ------------------------------------------------------------------------ */
+typedef struct rlbm_batch rlbm_batch;
+
+/* Create count handles from params[0..count) (all on params[0].stream) and
+ * the batch machinery.  RLBM_ERR_UNSUPPORTED for configurations outside the
+ * batched kernel (FP64, order 3, tau fields, stencils other than the massless
+ * Q = 28 (on-lattice or bilinear) and the built-in massive Q = 25, 29, 33;
+ * two instances of one stencil size must share the same stencil). */
+int rlbm_batch_create(const rlbm_params* params, int count, rlbm_batch** out);
+void rlbm_batch_destroy(rlbm_batch* b);
+int rlbm_batch_size(const rlbm_batch* b);
+/* The i-th instance (borrowed; owned by the batch). */
+rlbm_handle* rlbm_batch_handle(rlbm_batch* b, int i);
+/* Advance every instance by nsteps (one cooperative launch; asynchronous). */
+int rlbm_batch_step(rlbm_batch* b, int nsteps);
+/* Launch configuration: tile_shape 0 (32 x 8 cells per block) or 1 (32 x 4);
+ * grid = persistent blocks (at most the co-resident limit). */
+int rlbm_batch_config(rlbm_batch* b, int tile_shape, int grid);
+/* Autotuner: times trial_steps steps for each tile shape and three grid
+ * sizes and keeps the fastest.  It advances every instance by
+ * 12 * trial_steps steps; call it before rlbm_init of the instances.
+ * Outputs are nullable. */
+int rlbm_batch_tune(rlbm_batch* b, int trial_steps, int* tile_shape, int* grid, float* ms_per_step);
+/* Current configuration, co-resident limits {32x8, 32x4} and tile count. */
+int rlbm_batch_info(const rlbm_batch* b, int* tile_shape, int* grid, int* grid_max, long long* total_tiles);
+/* Iteration limit of the bounded grid-barrier wait (default 2^24 polls of
+ * about 64 ns).  A wait that runs out sets the batch error flag; every block
+ * leaves the kernel and rlbm_batch_sync_status returns RLBM_ERR_TIMEOUT. */
+int rlbm_batch_set_spin_limit(rlbm_batch* b, long long limit);
+/* Synchronise; report timeouts (RLBM_ERR_TIMEOUT, then clears them) or the
+ * first instance error; *nonphysical (nullable) gets the summed count. */
+int rlbm_batch_sync_status(rlbm_batch* b, long long* nonphysical);
+const char* rlbm_batch_last_error(const rlbm_batch* b);
+
 /* Message of the last error on this handle (or of the last failed
  * rlbm_create when h is NULL).  Never NULL. */
 const char* rlbm_last_error(const rlbm_handle* h);

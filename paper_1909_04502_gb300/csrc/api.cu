@@ -130,12 +130,16 @@ void fill_tables(const rlbm_handle* h, const Scalars& s, Tables<R>* t) {
     for (int k = 0; k < h->K; ++k) t->H[i][k] = (R)h->H[(size_t)i * h->K + k];
     if (h->p.stream_mode == RLBM_ONLATTICE) {
       t->off[i] = -q.ny[i] * s.pitch - q.nx[i];
+      t->dx[i] = (short)(-q.nx[i]);
+      t->dy[i] = (short)(-q.ny[i]);
       t->bw[i][0] = (R)1.0;
     } else {
       int o[2];
       double phi[2];
       bilinear_base(h->p.lambda, px / p0, py / p0, o, phi);
       t->off[i] = o[1] * s.pitch + o[0];
+      t->dx[i] = (short)o[0];
+      t->dy[i] = (short)o[1];
       t->bw[i][0] = (R)((1.0 - phi[0]) * (1.0 - phi[1]));
       t->bw[i][1] = (R)(phi[0] * (1.0 - phi[1]));
       t->bw[i][2] = (R)((1.0 - phi[0]) * phi[1]);

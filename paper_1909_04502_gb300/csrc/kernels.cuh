@@ -33,6 +33,7 @@ struct Tables {
   R bw[kMaxQ][4];          // bilinear weights of taps (0,0), (1,0), (0,1), (1,1)
   int off[kMaxQ];          // pull source offset in elements: on-lattice -n_iy*pitch - n_ix;
                            // bilinear o_iy*pitch + o_ix (tap (0,0))
+  short dx[kMaxQ], dy[kMaxQ];   // the same offset before the pitch is applied: off = dy*pitch + dx
 };
 
 struct Scalars {

@@ -37,15 +37,18 @@ __device__ __forceinline__ double f2d(float f) {
 __device__ __forceinline__ float d2f(double d) {
   // round to nearest (ties away from zero) on the magnitude bits: adding half
   // of the discarded 29-bit tail carries into mantissa and exponent as needed
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(d);
-  const unsigned sgn = (unsigned)(bits >> 32) & 0x80000000u;
-  const unsigned long long mag = (bits & 0x7FFFFFFFFFFFFFFFull);
-  const unsigned ed = (unsigned)(mag >> 52);
-  const unsigned long long r = mag + (1ull << 28);
-  const int e = (int)(r >> 52) - 1023 + 127;
-  const unsigned man = (unsigned)((r >> 29) & 0x7FFFFFull);
+  // (32-bit halves with an explicit carry keep this on the integer pipe)
+  const unsigned lo = (unsigned)__double2loint(d);
+  const unsigned hw = (unsigned)__double2hiint(d);
+  const unsigned sgn = hw & 0x80000000u;
+  unsigned hi = hw & 0x7FFFFFFFu;
+  const unsigned ed = hi >> 20;
+  const unsigned lo2 = lo + (1u << 28);
+  hi += (lo2 < lo) ? 1u : 0u;
+  const int e = (int)(hi >> 20) - 896;
+  const unsigned man = ((hi & 0xFFFFFu) << 3) | (lo2 >> 29);
   unsigned b = sgn | ((unsigned)e << 23) | man;
-  const bool is_nan = (ed == 0x7FFu) && ((mag & 0xFFFFFFFFFFFFFull) != 0ull);
+  const bool is_nan = (ed == 0x7FFu) && (((hw & 0xFFFFFu) | lo) != 0u);
   const unsigned special = is_nan ? 0x7FC00000u : (sgn | 0x7F800000u);
   b = (e <= 0) ? sgn : ((e >= 255 || ed == 0x7FFu) ? special : b);
   return __uint_as_float(b);
@@ -58,7 +61,18 @@ __device__ __forceinline__ float d2f(double d) {
 // On-lattice: f_i(x) = f*_i(x - n_i).  Bilinear: f_i(x) = sum_ab W_ab
 // f*_i(x + o_i + (a, b)).
 // ---------------------------------------------------------------------------
-template <typename S, int QT, bool EX, int MODE>
+// DYN: offsets computed from (dx, dy) and the run-time pitch (tables shared
+// by grids of different sizes), otherwise taken precomputed from tb.off.
+// NC: read through the non-coherent read-only path; only valid when the
+// source buffer is not written while the kernel runs (not in the persistent
+// batched kernel, which writes the buffer its next step reads).
+template <typename T, bool NC>
+__device__ __forceinline__ T ld(const T* p) {
+  if constexpr (NC) return __ldg(p);
+  else return *p;
+}
+
+template <typename S, int QT, bool EX, int MODE, bool DYN = false, bool NC = true>
 __device__ __forceinline__ void gather(const Tables<S>& tb, const Scalars& s,
                                        const S* __restrict__ fin, long long si, S (&g)[QT]) {
   const S* __restrict__ base = fin + si;
@@ -67,14 +81,14 @@ __device__ __forceinline__ void gather(const Tables<S>& tb, const Scalars& s,
   for (int i = 0; i < QT; ++i) {
     g[i] = S(0);
     if (i < Qn) {
-      const int o = i * s.iplane + tb.off[i];
+      const int o = i * s.iplane + (DYN ? (int)tb.dy[i] * s.pitch + (int)tb.dx[i] : tb.off[i]);
       if constexpr (MODE == kOnLattice) {
-        g[i] = __ldg(base + o);
+        g[i] = ld<S, NC>(base + o);
       } else {
-        S v = tb.bw[i][0] * __ldg(base + o);
-        v = fma(tb.bw[i][1], __ldg(base + o + 1), v);
-        v = fma(tb.bw[i][2], __ldg(base + o + s.pitch), v);
-        v = fma(tb.bw[i][3], __ldg(base + o + s.pitch + 1), v);
+        S v = tb.bw[i][0] * ld<S, NC>(base + o);
+        v = fma(tb.bw[i][1], ld<S, NC>(base + o + 1), v);
+        v = fma(tb.bw[i][2], ld<S, NC>(base + o + s.pitch), v);
+        v = fma(tb.bw[i][3], ld<S, NC>(base + o + s.pitch + 1), v);
         g[i] = v;
       }
     }
@@ -320,7 +334,7 @@ __device__ __forceinline__ Macro landau(const Scalars& sc, const S (&mm)[9]) {
 template <typename S>
 __device__ __forceinline__ S local_tau(const Scalars& sc, const S* __restrict__ tau_field, int cell,
                                        const Macro& M) {
-  if (sc.tau_mode == 1) return __ldg(tau_field + cell);
+  if (sc.tau_mode == 1) return tau_field[cell];
   if constexpr (sizeof(S) == 4) {
     if (sc.tau_mode == 2) return __fdividef(sc.f_tau_coef, M.fT);   // step 7, eta/s fixed
     return sc.f_tau;
@@ -360,28 +374,28 @@ __device__ __forceinline__ void for_each_halo_image(const Scalars& s, int x, int
 // ---------------------------------------------------------------------------
 // Fused step kernel: one thread per cell, 32 x 8 cells per block.
 // ---------------------------------------------------------------------------
-template <typename S, int QT, bool EX, int KT, int MODE>
-__global__ void __launch_bounds__(kThreads) k_step(const __grid_constant__ Tables<S> tb,
-                                                   const __grid_constant__ StepArgs<S> a) {
-  const int x = blockIdx.x * kBX + threadIdx.x;
-  const int y = blockIdx.y * kBY + threadIdx.y;
-  if (x >= a.s.nx || y >= a.s.ny) return;
-  const long long si = sidx(a.s, x, y);
-  const int Qn = EX ? QT : a.s.Q;
+// One cell of the fused step (Sec. 6.2, steps 1-8): pull-gather, moments,
+// Landau solve, equilibrium, relaxation, store (interior and halo images).
+template <typename S, int QT, bool EX, int KT, int MODE, bool DYN = false, bool NC = true>
+__device__ __forceinline__ void cell_update(const Tables<S>& tb, const Scalars& s, const S* __restrict__ fin,
+                                            S* __restrict__ fout, const S* __restrict__ tau_field,
+                                            unsigned long long* status, int x, int y) {
+  const long long si = sidx(s, x, y);
+  const int Qn = EX ? QT : s.Q;
   S g[QT];
-  gather<S, QT, EX, MODE>(tb, a.s, a.fin, si, g);
+  gather<S, QT, EX, MODE, DYN, NC>(tb, s, fin, si, g);
   S mm[9];
-  moments9<S, QT, EX>(tb, a.s.Q, g, mm);
-  const Macro M = landau<S>(a.s, mm);
-  if (!M.ok) atomicAdd(a.status, 1ULL);
+  moments9<S, QT, EX>(tb, s.Q, g, mm);
+  const Macro M = landau<S>(s, mm);
+  if (!M.ok) atomicAdd(status, 1ULL);
   S dM[KT];
-  eq_moments_of<S, KT>(a.s, M, dM);
-  const S inv_tau = S(1) / local_tau<S>(a.s, a.tau_field, y * a.s.nx + x, M);
+  eq_moments_of<S, KT>(s, M, dM);
+  const S inv_tau = S(1) / local_tau<S>(s, tau_field, y * s.nx + x, M);
   S U0, Ux, Uy;
   if constexpr (sizeof(S) == 4) { U0 = M.fU0; Ux = M.fUx; Uy = M.fUy; }
   else { U0 = M.U0; Ux = M.Ux; Uy = M.Uy; }
   const S keep = M.ok ? S(1) : S(0);
-  S* __restrict__ obase = a.fout + si;
+  S* __restrict__ obase = fout + si;
 #pragma unroll
   for (int i = 0; i < QT; ++i) {
     if (i < Qn) {
@@ -391,15 +405,26 @@ __global__ void __launch_bounds__(kThreads) k_step(const __grid_constant__ Table
       // step 8: Omega_i = p_i.U / (p_i^0 tau) = (U^0 - v_i . U) / tau
       const S om = keep * (U0 - Ux * tb.vx[i] - Uy * tb.vy[i]) * inv_tau;
       g[i] = fma(om, feq - g[i], g[i]);
-      obase[i * a.s.iplane] = g[i];
+      obase[i * s.iplane] = g[i];
     }
   }
-  for_each_halo_image(a.s, x, y, [&](long long hi) {
-    S* __restrict__ hb = a.fout + hi;
+  for_each_halo_image(s, x, y, [&](long long hi) {
+    S* __restrict__ hb = fout + hi;
 #pragma unroll
     for (int i = 0; i < QT; ++i)
-      if (i < Qn) hb[i * a.s.iplane] = g[i];
+      if (i < Qn) hb[i * s.iplane] = g[i];
   });
+}
+
+// FP32 storage: four 256-thread blocks per SM (at most 64 registers per
+// thread) -- the FP64 polish and the gather latency need the resident warps.
+template <typename S, int QT, bool EX, int KT, int MODE>
+__global__ void __launch_bounds__(kThreads, (sizeof(S) == 4 && QT <= 40) ? 4 : 2) k_step(const __grid_constant__ Tables<S> tb,
+                                                   const __grid_constant__ StepArgs<S> a) {
+  const int x = blockIdx.x * kBX + threadIdx.x;
+  const int y = blockIdx.y * kBY + threadIdx.y;
+  if (x >= a.s.nx || y >= a.s.ny) return;
+  cell_update<S, QT, EX, KT, MODE>(tb, a.s, a.fin, a.fout, a.tau_field, a.status, x, y);
 }
 
 // Fields of f(t) (steps 1-4), optionally the raw moments.  Output planes are

@@ -70,6 +70,17 @@ SIGNATURES = {
                                     ctypes.POINTER(ctypes.c_longlong), _IP]),
     "rlbm_step_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), _VP, _VP, _VP, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_longlong)]),
+    "rlbm_batch_create": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int, ctypes.POINTER(_VP)]),
+    "rlbm_batch_destroy": (None, [_VP]),
+    "rlbm_batch_size": (ctypes.c_int, [_VP]),
+    "rlbm_batch_handle": (_VP, [_VP, ctypes.c_int]),
+    "rlbm_batch_step": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "rlbm_batch_config": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
+    "rlbm_batch_tune": (ctypes.c_int, [_VP, ctypes.c_int, _IP, _IP, ctypes.POINTER(ctypes.c_float)]),
+    "rlbm_batch_info": (ctypes.c_int, [_VP, _IP, _IP, _IP, ctypes.POINTER(ctypes.c_longlong)]),
+    "rlbm_batch_set_spin_limit": (ctypes.c_int, [_VP, ctypes.c_longlong]),
+    "rlbm_batch_sync_status": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
+    "rlbm_batch_last_error": (ctypes.c_char_p, [_VP]),
     "rlbm_last_error": (ctypes.c_char_p, [_H]),
     "rlbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -292,3 +303,100 @@ class Lattice:
         _check(lib().rlbm_buffers(self.h, ctypes.byref(cur), ctypes.byref(prev), ctypes.byref(es),
                                   ctypes.byref(plane), lay), self.h)
         return cur.value, prev.value, es.value, plane.value, tuple(lay)
+
+
+class _BorrowedLattice(Lattice):
+    """A Lattice view of a handle owned by a Batch (never destroyed here)."""
+
+    def __init__(self, h, nx, ny):
+        self.h = h
+        self.nx, self.ny = nx, ny
+        Q = ctypes.c_int()
+        _check(lib().rlbm_stencil(self.h, ctypes.byref(Q), None, None, None), self.h)
+        self.Q = Q.value
+        self.n = np.zeros((self.Q, 2), dtype=np.int32)
+        self.p = np.zeros((self.Q, 3))
+        self.w = np.zeros(self.Q)
+        _check(lib().rlbm_stencil(self.h, ctypes.byref(Q), self.n.ctypes.data_as(_IP),
+                                  self.p.ctypes.data_as(_DP), self.w.ctypes.data_as(_DP)), self.h)
+
+    def close(self):
+        self.h = None
+
+
+class Batch:
+    """Many independent simulations stepped by one persistent kernel
+    (rlbm_batch_* in include/rlbm.h).  ``configs`` is a list of keyword dicts
+    for ``make_params`` (each with nx and ny)."""
+
+    def __init__(self, configs, cuda_stream=None):
+        if cuda_stream is None:
+            cuda_stream = _current_stream()
+        arr = (Params * len(configs))()
+        self._keep = []
+        dims = []
+        for i, c in enumerate(configs):
+            c = dict(c)
+            nx, ny = c.pop("nx"), c.pop("ny")
+            p, keep = make_params(nx, ny, cuda_stream=cuda_stream, **c)
+            arr[i] = p
+            self._keep.append(keep)
+            dims.append((nx, ny))
+        b = _VP()
+        rc = lib().rlbm_batch_create(arr, len(configs), ctypes.byref(b))
+        if rc != RLBM_OK:
+            raise RLBMError(rc, lib().rlbm_last_error(None).decode())
+        self.b = b
+        self.instances = [_BorrowedLattice(lib().rlbm_batch_handle(self.b, i), nx, ny)
+                          for i, (nx, ny) in enumerate(dims)]
+
+    def _chk(self, rc):
+        if rc != RLBM_OK:
+            raise RLBMError(rc, lib().rlbm_batch_last_error(self.b).decode())
+
+    def __len__(self):
+        return len(self.instances)
+
+    def __getitem__(self, i):
+        return self.instances[i]
+
+    def step(self, nsteps=1):
+        self._chk(lib().rlbm_batch_step(self.b, int(nsteps)))
+
+    def config(self, tile_shape, grid):
+        self._chk(lib().rlbm_batch_config(self.b, int(tile_shape), int(grid)))
+
+    def tune(self, trial_steps=3):
+        shape, grid = ctypes.c_int(), ctypes.c_int()
+        ms = ctypes.c_float()
+        self._chk(lib().rlbm_batch_tune(self.b, int(trial_steps), ctypes.byref(shape), ctypes.byref(grid),
+                                        ctypes.byref(ms)))
+        return shape.value, grid.value, ms.value
+
+    def info(self):
+        shape, grid = ctypes.c_int(), ctypes.c_int()
+        gmax = (ctypes.c_int * 2)()
+        tiles = ctypes.c_longlong()
+        self._chk(lib().rlbm_batch_info(self.b, ctypes.byref(shape), ctypes.byref(grid), gmax, ctypes.byref(tiles)))
+        return dict(tile_shape=shape.value, grid=grid.value, grid_max=tuple(gmax), tiles=tiles.value)
+
+    def set_spin_limit(self, limit):
+        self._chk(lib().rlbm_batch_set_spin_limit(self.b, int(limit)))
+
+    def sync_status(self, raise_on_error=True):
+        cnt = ctypes.c_longlong()
+        rc = lib().rlbm_batch_sync_status(self.b, ctypes.byref(cnt))
+        if rc != RLBM_OK and raise_on_error:
+            self._chk(rc)
+        return rc, cnt.value
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib().rlbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
