@@ -163,7 +163,8 @@ struct rlbm_batch {
   std::vector<int> kind;
   std::vector<int> tile_begin, tiles_x;
   int total_tiles = 0;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;          // the user's stream (graphs are launched on it)
+  cudaStream_t cap_stream = nullptr;      // private stream the graphs are captured on
   Tables<float>* tab_host = nullptr;     // pinned copy of the constant tables (graph memcpy source)
   BatchInst* inst_host = nullptr;        // pinned descriptor staging
   BatchInst* inst_dev = nullptr;
@@ -210,12 +211,12 @@ bool same_stencil(const rlbm_handle* a, const rlbm_handle* b) {
 }
 
 template <int BX, int BY>
-cudaError_t launch_batch(rlbm_batch* b, int nsteps, int grid) {
+cudaError_t launch_batch(rlbm_batch* b, int nsteps, int grid, cudaStream_t st) {
   BatchArgs a{b->inst_dev, b->tile_inst_dev, b->total_tiles, nsteps, b->bar, b->timeouts, b->spin_limit};
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(BX, BY);
-  cfg.stream = b->stream;
+  cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
@@ -224,13 +225,13 @@ cudaError_t launch_batch(rlbm_batch* b, int nsteps, int grid) {
   return cudaLaunchKernelEx(&cfg, k_batch<BX, BY>, a);
 }
 
-cudaError_t enqueue(rlbm_batch* b, int nsteps) {
+cudaError_t enqueue(rlbm_batch* b, int nsteps, cudaStream_t st) {
   cudaError_t e = cudaMemcpyToSymbolAsync(c_btab, b->tab_host, sizeof(Tables<float>) * kNumKinds, 0,
-                                          cudaMemcpyHostToDevice, b->stream);
+                                          cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return e;
-  e = (b->tile_shape == 0) ? launch_batch<32, 8>(b, nsteps, b->grid) : launch_batch<32, 4>(b, nsteps, b->grid);
+  e = (b->tile_shape == 0) ? launch_batch<32, 8>(b, nsteps, b->grid, st) : launch_batch<32, 4>(b, nsteps, b->grid, st);
   if (e != cudaSuccess) return e;
-  k_batch_flip<<<(int)((b->h.size() + 127) / 128), 128, 0, b->stream>>>(b->inst_dev, (int)b->h.size(), nsteps);
+  k_batch_flip<<<(int)((b->h.size() + 127) / 128), 128, 0, st>>>(b->inst_dev, (int)b->h.size(), nsteps);
   return cudaGetLastError();
 }
 
@@ -304,7 +305,8 @@ int rlbm_batch_create(const rlbm_params* params, int count, rlbm_batch** out) {
   }
   b->total_tiles = tiles;
   // constant tables (pinned host source for the graph's memcpy node)
-  e = cudaMallocHost(&b->tab_host, sizeof(Tables<float>) * kNumKinds);
+  e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMallocHost(&b->tab_host, sizeof(Tables<float>) * kNumKinds);
   if (e == cudaSuccess) e = cudaMallocHost(&b->inst_host, sizeof(BatchInst) * count);
   if (e == cudaSuccess) e = cudaMalloc(&b->inst_dev, sizeof(BatchInst) * count);
   if (e == cudaSuccess) e = cudaMalloc(&b->bar, sizeof(BarrierState));
@@ -377,6 +379,7 @@ void rlbm_batch_destroy(rlbm_batch* b) {
   cudaFree(b->tile_inst_dev);
   cudaFree(b->bar);
   cudaFree(b->timeouts);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   delete b;
 }
 
@@ -429,10 +432,10 @@ int rlbm_batch_step(rlbm_batch* b, int nsteps) {
     exec = it->second;
   } else {
     cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return batch_fail(b, RLBM_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
-    cudaError_t e2 = enqueue(b, nsteps);
-    e = cudaStreamEndCapture(b->stream, &g);
+    cudaError_t e2 = enqueue(b, nsteps, b->cap_stream);
+    e = cudaStreamEndCapture(b->cap_stream, &g);
     if (e2 != cudaSuccess || e != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
       return batch_fail(b, RLBM_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e2 != cudaSuccess ? e2 : e));
