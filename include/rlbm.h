@@ -243,6 +243,35 @@ int rlbm_batch_set_spin_limit(rlbm_batch* b, long long limit);
 int rlbm_batch_sync_status(rlbm_batch* b, long long* nonphysical);
 const char* rlbm_batch_last_error(const rlbm_batch* b);
 
+/* ------------------------------------------------------------------------
+ * Adjoint (reverse-mode gradient) of a run of the fused step.  Not in the
+ * paper: it serves the calibration of kinetic parameters against transport
+ * coefficients (Sec. 7) by gradients.  Loss on the run's final fields:
+ *   L = 1/2 sum_x |u(x, T) - u_target(x)|^2,  u = U^i/U^0 of f(T)
+ * (the fields rlbm_moments reports after T steps).  Gradients with respect
+ * to the per-cell relaxation time tau(x) (constant in time) and the initial
+ * velocity u0(x).  The backward pass recomputes the forward states segment
+ * by segment from checkpoints taken every checkpoint_every steps.
+ * Periodic boundaries, order 2, constant or per-cell tau; both precisions.
+ * ------------------------------------------------------------------------ */
+typedef struct rlbm_adjoint rlbm_adjoint;
+
+/* Allocate checkpoints (ceil(nsteps / checkpoint_every) population buffers),
+ * one segment of checkpoint_every buffers, two adjoint buffers and per-cell
+ * accumulators for a run of nsteps steps of handle h (borrowed). */
+int rlbm_adjoint_create(rlbm_handle* h, int nsteps, int checkpoint_every, rlbm_adjoint** out);
+void rlbm_adjoint_destroy(rlbm_adjoint* A);
+/* Forward pass: rlbm_init(n, u, T) then nsteps steps, saving checkpoints.
+ * Leaves the handle at t = nsteps. */
+int rlbm_adjoint_forward(rlbm_adjoint* A, const double* n, const double* ux, const double* uy, const double* T,
+                         int on_device);
+/* Backward pass for the targets (nx*ny each): loss (1 value), dL/dtau,
+ * dL/dux0, dL/duy0 (nx*ny each; all outputs nullable), on the host
+ * (out_on_device = 0) or the device.  Synchronous. */
+int rlbm_adjoint_backward(rlbm_adjoint* A, const double* ux_target, const double* uy_target, int on_device,
+                          double* loss, double* grad_tau, double* grad_ux0, double* grad_uy0, int out_on_device);
+const char* rlbm_adjoint_last_error(const rlbm_adjoint* A);
+
 /* Message of the last error on this handle (or of the last failed
  * rlbm_create when h is NULL).  Never NULL. */
 const char* rlbm_last_error(const rlbm_handle* h);

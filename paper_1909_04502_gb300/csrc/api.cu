@@ -132,6 +132,7 @@ void fill_tables(const rlbm_handle* h, const Scalars& s, Tables<R>* t) {
       t->off[i] = -q.ny[i] * s.pitch - q.nx[i];
       t->dx[i] = (short)(-q.nx[i]);
       t->dy[i] = (short)(-q.ny[i]);
+      t->roff[i] = q.ny[i] * s.pitch + q.nx[i];
       t->bw[i][0] = (R)1.0;
     } else {
       int o[2];
@@ -140,6 +141,7 @@ void fill_tables(const rlbm_handle* h, const Scalars& s, Tables<R>* t) {
       t->off[i] = o[1] * s.pitch + o[0];
       t->dx[i] = (short)o[0];
       t->dy[i] = (short)o[1];
+      t->roff[i] = (-o[1] - 1) * s.pitch + (-o[0] - 1);
       t->bw[i][0] = (R)((1.0 - phi[0]) * (1.0 - phi[1]));
       t->bw[i][1] = (R)(phi[0] * (1.0 - phi[1]));
       t->bw[i][2] = (R)((1.0 - phi[0]) * phi[1]);

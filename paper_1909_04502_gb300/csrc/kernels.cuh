@@ -34,6 +34,8 @@ struct Tables {
   int off[kMaxQ];          // pull source offset in elements: on-lattice -n_iy*pitch - n_ix;
                            // bilinear o_iy*pitch + o_ix (tap (0,0))
   short dx[kMaxQ], dy[kMaxQ];   // the same offset before the pitch is applied: off = dy*pitch + dx
+  int roff[kMaxQ];         // transposed streaming (adjoint pull): on-lattice +n_iy*pitch + n_ix;
+                           // bilinear (-o_iy-1)*pitch + (-o_ix-1), tap weights bw[i][3-k]
 };
 
 struct Scalars {

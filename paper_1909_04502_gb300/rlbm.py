@@ -81,6 +81,11 @@ SIGNATURES = {
     "rlbm_batch_set_spin_limit": (ctypes.c_int, [_VP, ctypes.c_longlong]),
     "rlbm_batch_sync_status": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
     "rlbm_batch_last_error": (ctypes.c_char_p, [_VP]),
+    "rlbm_adjoint_create": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_VP)]),
+    "rlbm_adjoint_destroy": (None, [_VP]),
+    "rlbm_adjoint_forward": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_int]),
+    "rlbm_adjoint_backward": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, ctypes.c_int]),
+    "rlbm_adjoint_last_error": (ctypes.c_char_p, [_VP]),
     "rlbm_last_error": (ctypes.c_char_p, [_H]),
     "rlbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -394,6 +399,62 @@ class Batch:
         if getattr(self, "b", None):
             lib().rlbm_batch_destroy(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Adjoint:
+    """Checkpointed forward run and hand-written adjoint (rlbm_adjoint_* in
+    include/rlbm.h) on a Lattice: gradients of L = 1/2 sum |u(T) - u_target|^2
+    with respect to the per-cell tau field and the initial velocity."""
+
+    def __init__(self, lattice, nsteps, checkpoint_every=100):
+        self.lat = lattice
+        self.nsteps = int(nsteps)
+        a = _VP()
+        rc = lib().rlbm_adjoint_create(lattice.h, self.nsteps, int(checkpoint_every), ctypes.byref(a))
+        if rc != RLBM_OK:
+            raise RLBMError(rc, "adjoint setup failed (periodic, order 2, constant or field tau)")
+        self.a = a
+
+    def _chk(self, rc):
+        if rc != RLBM_OK:
+            raise RLBMError(rc, lib().rlbm_adjoint_last_error(self.a).decode())
+
+    def forward(self, n, ux, uy, T):
+        ptrs = [_ptr(x) for x in (n, ux, uy, T)]
+        dev = {d for _, d in ptrs}
+        if len(dev) != 1:
+            raise ValueError("all fields must live on the same side")
+        self._chk(lib().rlbm_adjoint_forward(self.a, *[p for p, _ in ptrs], dev.pop()))
+
+    def backward(self, ux_target, uy_target, out=None):
+        """Returns (loss, grad_tau, grad_ux0, grad_uy0): numpy (host) or, with
+        ``out`` a dict of CUDA float64 tensors {'tau','ux0','uy0','loss'}, device."""
+        (pu, d1), (pv, d2) = _ptr(ux_target), _ptr(uy_target)
+        if d1 != d2:
+            raise ValueError("targets must live on the same side")
+        ny, nx = self.lat.ny, self.lat.nx
+        if out is None:
+            res = {"loss": np.zeros(1), "tau": np.zeros((ny, nx)), "ux0": np.zeros((ny, nx)),
+                   "uy0": np.zeros((ny, nx))}
+            od = 0
+        else:
+            res, od = out, 1
+        self._chk(lib().rlbm_adjoint_backward(self.a, pu, pv, d1, _ptr(res["loss"])[0], _ptr(res["tau"])[0],
+                                              _ptr(res["ux0"])[0], _ptr(res["uy0"])[0], od))
+        if out is None:
+            return float(res["loss"][0]), res["tau"], res["ux0"], res["uy0"]
+        return res
+
+    def close(self):
+        if getattr(self, "a", None):
+            lib().rlbm_adjoint_destroy(self.a)
+            self.a = None
 
     def __del__(self):
         try:

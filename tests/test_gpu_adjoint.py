@@ -1,0 +1,141 @@
+"""Hand-written adjoint of the RLBM step against central finite differences
+of the FP64 oracle, against itself across checkpoint intervals, FP32 against
+FP64, and through torch.autograd."""
+import numpy as np
+import pytest
+
+from paper_1909_04502_gb300 import inputs
+from oracle import lattice as OL
+from oracle import scheme as OS
+from oracle import physics as OP
+
+pytestmark = pytest.mark.gpu
+
+NX, NY, T = 16, 12, 6
+
+
+@pytest.fixture(scope="module")
+def rl():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1909_04502_gb300 import build, rlbm
+    build.build()
+    return rlbm
+
+
+def _setup(seed=31, nx=NX, ny=NY):
+    rng = np.random.default_rng(seed)
+    n, ux, uy, Tf = [np.ascontiguousarray(a) for a in inputs.random_smooth(nx, ny, seed=seed, umax=0.2)]
+    tau = np.ascontiguousarray(rng.uniform(0.7, 1.3, (ny, nx)))
+    uxt = np.ascontiguousarray(0.05 * rng.standard_normal((ny, nx)))
+    uyt = np.ascontiguousarray(0.05 * rng.standard_normal((ny, nx)))
+    return n, ux, uy, Tf, tau, uxt, uyt
+
+
+def _oracle_loss(n, ux, uy, Tf, tau, uxt, uyt, steps=T, stream="onlattice", lam=None):
+    q = OL.massless_quadrature(2)
+    sim = OS.Simulation(q, OL.Expansion(q), n.shape[1], n.shape[0], tau=tau, stream=stream, lam=lam)
+    sim.init(n, ux, uy, Tf)
+    sim.step(steps)
+    return 0.5 * np.sum((sim.fields.ux - uxt) ** 2 + (sim.fields.uy - uyt) ** 2)
+
+
+def _adjoint(rl, precision, K, data, stream="onlattice", lam=0.0, steps=T):
+    n, ux, uy, Tf, tau, uxt, uyt = data
+    lat = rl.Lattice(n.shape[1], n.shape[0], tau_mode="field", precision=precision, stream=stream, lam=lam)
+    lat.set_tau_field(tau)
+    adj = rl.Adjoint(lat, steps, K)
+    adj.forward(n, ux, uy, Tf)
+    res = adj.backward(uxt, uyt)
+    assert lat.sync_status()[0] == 0
+    adj.close()
+    lat.close()
+    return res
+
+
+@pytest.mark.parametrize("stream,lam", [("onlattice", 0.0), ("bilinear", 1.0)])
+def test_fp64_adjoint_matches_oracle_central_differences(rl, stream, lam):
+    data = _setup()
+    n, ux, uy, Tf, tau, uxt, uyt = data
+    loss, gtau, gux, guy = _adjoint(rl, "fp64", 4, data, stream, lam)
+    olam = lam if stream == "bilinear" else None
+    L0 = _oracle_loss(n, ux, uy, Tf, tau, uxt, uyt, stream=stream, lam=olam)
+    assert abs(loss - L0) < 1e-12 * abs(L0)
+    rng = np.random.default_rng(5)
+    h = 1e-4
+    # directional derivative along a random tau perturbation
+    d = rng.standard_normal(tau.shape)
+    fd = (_oracle_loss(n, ux, uy, Tf, tau + h * d, uxt, uyt, stream=stream, lam=olam)
+          - _oracle_loss(n, ux, uy, Tf, tau - h * d, uxt, uyt, stream=stream, lam=olam)) / (2 * h)
+    ad = float(np.sum(gtau * d))
+    assert abs(ad - fd) < 1e-6 * abs(fd), (ad, fd)
+    # and along a random initial-velocity perturbation
+    dx, dy = 0.1 * rng.standard_normal(ux.shape), 0.1 * rng.standard_normal(uy.shape)
+    fd = (_oracle_loss(n, ux + h * dx, uy + h * dy, Tf, tau, uxt, uyt, stream=stream, lam=olam)
+          - _oracle_loss(n, ux - h * dx, uy - h * dy, Tf, tau, uxt, uyt, stream=stream, lam=olam)) / (2 * h)
+    ad = float(np.sum(gux * dx + guy * dy))
+    assert abs(ad - fd) < 1e-6 * abs(fd), (ad, fd)
+
+
+def test_fp64_adjoint_single_cell_sensitivities(rl):
+    data = _setup(seed=44)
+    n, ux, uy, Tf, tau, uxt, uyt = data
+    _, gtau, gux, _ = _adjoint(rl, "fp64", 2, data)
+    h = 1e-4
+    for (j, i) in [(0, 0), (5, 9), (11, 15)]:
+        tp, tm = tau.copy(), tau.copy()
+        tp[j, i] += h
+        tm[j, i] -= h
+        fd = (_oracle_loss(n, ux, uy, Tf, tp, uxt, uyt) - _oracle_loss(n, ux, uy, Tf, tm, uxt, uyt)) / (2 * h)
+        assert abs(gtau[j, i] - fd) < 1e-6 * np.abs(gtau).max(), (j, i, gtau[j, i], fd)
+        up, um = ux.copy(), ux.copy()
+        up[j, i] += h
+        um[j, i] -= h
+        fd = (_oracle_loss(n, up, uy, Tf, tau, uxt, uyt) - _oracle_loss(n, um, uy, Tf, tau, uxt, uyt)) / (2 * h)
+        assert abs(gux[j, i] - fd) < 1e-6 * np.abs(gux).max(), (j, i, gux[j, i], fd)
+
+
+def test_checkpoint_interval_does_not_change_the_gradient(rl):
+    data = _setup(seed=8)
+    a = _adjoint(rl, "fp64", 1, data, steps=9)
+    b = _adjoint(rl, "fp64", 4, data, steps=9)
+    c = _adjoint(rl, "fp64", 9, data, steps=9)
+    for x, y in ((a, b), (a, c)):
+        assert x[0] == y[0]
+        for k in (1, 2, 3):
+            assert np.array_equal(x[k], y[k])
+
+
+def test_fp32_adjoint_against_fp64_and_differences(rl):
+    data = _setup(seed=12, nx=40, ny=32)
+    n, ux, uy, Tf, tau, uxt, uyt = data
+    l32, g32, gx32, gy32 = _adjoint(rl, "fp32", 3, data, steps=20)
+    l64, g64, gx64, gy64 = _adjoint(rl, "fp64", 3, data, steps=20)
+    assert abs(l32 - l64) < 1e-5 * l64
+    assert np.abs(g32 - g64).max() < 1e-4 * np.abs(g64).max()
+    assert np.abs(gx32 - gx64).max() < 1e-4 * np.abs(gx64).max()
+    rng = np.random.default_rng(2)
+    d = rng.standard_normal(tau.shape)
+    h = 1e-4
+    fd = (_oracle_loss(n, ux, uy, Tf, tau + h * d, uxt, uyt, steps=20)
+          - _oracle_loss(n, ux, uy, Tf, tau - h * d, uxt, uyt, steps=20)) / (2 * h)
+    assert abs(float(np.sum(g32 * d)) - fd) < 1e-4 * abs(fd)
+
+
+def test_torch_autograd_function(rl):
+    import torch
+    from paper_1909_04502_gb300.autograd import CalibrationRun, shear_loss
+    data = _setup(seed=3)
+    n, ux, uy, Tf, tau, uxt, uyt = [torch.tensor(a, dtype=torch.float64, device="cuda") for a in data]
+    run = CalibrationRun(NX, NY, T, checkpoint_every=3, precision="fp64")
+    tau_p = tau.clone().requires_grad_(True)
+    ux_p = ux.clone().requires_grad_(True)
+    uy_p = uy.clone().requires_grad_(True)
+    loss = shear_loss(run, tau_p, ux_p, uy_p, n, Tf, uxt, uyt)
+    loss.backward()
+    L_ref, g_ref, gx_ref, gy_ref = _adjoint(rl, "fp64", 3, data)
+    assert abs(loss.item() - L_ref) < 1e-12 * L_ref
+    assert np.array_equal(tau_p.grad.cpu().numpy(), g_ref)
+    assert np.array_equal(ux_p.grad.cpu().numpy(), gx_ref)
+    run.close()
