@@ -192,6 +192,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tg512", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint measurements")
     ap.add_argument("--_oracle_worker", default=None)
     args = ap.parse_args()
     if args._oracle_worker is not None:
@@ -314,10 +315,14 @@ def main():
 
     parity = None
     cpu = None
+    extras = {}
     if rank == 0:
         parity = oracle_parity(lat, fields, wl)
         if world == 1 and not args.no_cpu_baseline:
             cpu = cpu_baseline(wl)
+    if not args.no_extras:
+        extras["batched"] = bench_batched(torch, rlbm, inputs, stream)
+        extras["adjoint"] = bench_adjoint(torch, rlbm, inputs, stream)
 
     clocks = clk.summary()
     line = {
@@ -331,7 +336,7 @@ def main():
                    "l2": "flushed before every timed step (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
-        "clocks": clocks, "resident": resident, "parity": parity,
+        "clocks": clocks, "resident": resident, "parity": parity, **extras,
         "status": {"nonphysical_cells": status[1]}, "wall_s_timed_region": round(wall, 4),
     }
     if rank == 0:
@@ -378,6 +383,92 @@ def cpu_baseline(wl, budget_s=20.0, nsteps=3):
     return {"value": round(r["cells"] * nsteps / t / 1e6, 4), "unit": METRIC, "cores": 1, "kind": "oracle",
             "sample": "%d oracle steps of the same Taylor-Green configuration on a %dx%d grid (numpy FP64, "
                       "one thread)" % (nsteps, L, L)}
+
+
+def bench_batched(torch, rlbm, inputs, stream, steps=10, count=64, seed=1909):
+    """Batched tau-sweep: `count` shear-wave runs, side ~ U{64..1024}, tau ~
+    U[0.6, 2.0], zeta round-robin over {0, 1, 10}, amplitude 0.05 c, FP32
+    storage with the FP64 Landau solve, on-lattice order-2 stencils.  One
+    persistent cooperative launch per call (CUDA graph) against the same
+    instances stepped one handle at a time (back-to-back launches)."""
+    import numpy as np
+    runs = inputs.sweep(count=count, seed=seed)
+    cfgs = [dict(nx=r["side"], ny=r["side"], tau=r["tau"], m=r["zeta"], precision="fp32") for r in runs]
+    batch = rlbm.Batch(cfgs, cuda_stream=stream.cuda_stream)
+    shape, grid, _ = batch.tune(trial_steps=2)
+    cells = 0
+    for i, r in enumerate(runs):
+        f = [np.ascontiguousarray(a) for a in inputs.shear_wave(r["side"], r["side"], amp=0.05)]
+        batch[i].init(*f)
+        cells += r["side"] ** 2
+    Qs = [batch[i].Q for i in range(len(batch))]
+    alg_bytes = sum(2 * Q * 4 * r["side"] ** 2 for Q, r in zip(Qs, runs))
+    batch.step(steps)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    batch.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tb = e0.elapsed_time(e1) / steps
+    # the same instances, one handle at a time (each call launches `steps` kernels)
+    for lat in batch.instances:
+        lat.step(1)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for lat in batch.instances:
+        lat.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tp = e0.elapsed_time(e1) / steps
+    rc, nonphys = batch.sync_status(raise_on_error=False)
+    peak, _ = _peaks()
+    out = {"workload": "tau_sweep_64_shear_waves", "instances": count, "cells": cells, "seed": seed,
+           "steps_timed": steps, "ms_per_step_batched": round(tb, 4), "ms_per_step_plain_loop": round(tp, 4),
+           "mlups_batched": round(cells / (tb * 1e-3) / 1e6, 1), "mlups_plain_loop": round(cells / (tp * 1e-3) / 1e6, 1),
+           "speedup_vs_plain_loop": round(tp / tb, 3),
+           "roofline": {"bound": "hbm", "achieved": round(alg_bytes / (tb * 1e-3) / 1e9, 1), "peak": peak,
+                        "unit": "GB/s", "frac": round(alg_bytes / (tb * 1e-3) / 1e9 / peak, 4)},
+           "tuned": {"tile_shape": ["32x8", "32x4"][shape], "grid": grid}, "status": rc,
+           "nonphysical": nonphys}
+    batch.close()
+    return out
+
+
+def bench_adjoint(torch, rlbm, inputs, stream, L=512, nsteps=2000, K=100):
+    """Differentiable calibration run: L x L massless shear flow u_y = 0.05
+    sin(2 pi x / L), hidden tau field, nsteps steps; forward with checkpoints
+    every K steps, then the adjoint backward pass with recomputation."""
+    import numpy as np
+    n, ux, uy, T = [np.ascontiguousarray(a) for a in inputs.shear_wave(L, L, amp=0.05)]
+    tau = np.ascontiguousarray(inputs.smooth_tau(L, L))
+    lat = rlbm.Lattice(L, L, tau_mode="field", precision="fp32", cuda_stream=stream.cuda_stream)
+    lat.set_tau_field(tau)
+    adj = rlbm.Adjoint(lat, nsteps, K)
+    dev = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
+    n_d, ux_d, uy_d, T_d = dev(n), dev(ux), dev(uy), dev(T)
+    tgt_x, tgt_y = dev(np.zeros_like(ux)), dev(0.9 * uy)
+    out = {"loss": torch.zeros(1, dtype=torch.float64, device="cuda"), "tau": torch.empty_like(n_d),
+           "ux0": torch.empty_like(n_d), "uy0": torch.empty_like(n_d)}
+    adj.forward(n_d, ux_d, uy_d, T_d)                 # warm-up
+    adj.backward(tgt_x, tgt_y, out=out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    adj.forward(n_d, ux_d, uy_d, T_d)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    adj.backward(tgt_x, tgt_y, out=out)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    cells = L * L * nsteps
+    res = {"workload": "calibration_shear_%d_%dsteps_ckpt%d" % (L, nsteps, K), "forward_s": round(t1 - t0, 4),
+           "backward_s": round(t2 - t1, 4), "backward_over_forward": round((t2 - t1) / (t1 - t0), 3),
+           "mlups_forward": round(cells / (t1 - t0) / 1e6, 1),
+           "mlups_adjoint_incl_recompute": round(cells / (t2 - t1) / 1e6, 1),
+           "loss": float(out["loss"].item()), "grad_tau_norm": float(out["tau"].norm().item())}
+    adj.close()
+    lat.close()
+    return res
 
 
 def bench_reference(args, wl):

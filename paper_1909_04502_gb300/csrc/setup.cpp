@@ -10,6 +10,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <set>
 #include <utility>
 
@@ -445,6 +447,26 @@ bool search_v0(const std::vector<int>& groups, double m, int order, double* v0_o
 }
 
 bool builtin_massive(double m, int order, Quadrature* q, std::string* err) {
+  // the v0 scan is the expensive part: remember results per (m, order)
+  static std::mutex mtx;
+  static std::map<std::pair<double, int>, Quadrature> memo;
+  {
+    std::lock_guard<std::mutex> lock(mtx);
+    auto it = memo.find({m, order});
+    if (it != memo.end()) {
+      *q = it->second;
+      return true;
+    }
+  }
+  const bool ok = builtin_massive_search(m, order, q, err);
+  if (ok) {
+    std::lock_guard<std::mutex> lock(mtx);
+    memo[{m, order}] = *q;
+  }
+  return ok;
+}
+
+bool builtin_massive_search(double m, int order, Quadrature* q, std::string* err) {
   // Candidate stencils: the Sec. 5.3 worked example (order 2) and the five
   // (2+1)-d columns of App. H for the requested order.
   static const std::vector<std::vector<int>> o2 = {

@@ -58,6 +58,7 @@ bool search_v0(const std::vector<int>& groups, double m, int order, double* v0_o
 // Built-in stencil choice for a mass and order (tries a fixed candidate list
 // of App. H stencils and the Sec. 5.3 example).
 bool builtin_massive(double m, int order, Quadrature* q, std::string* err);
+bool builtin_massive_search(double m, int order, Quadrature* q, std::string* err);   // uncached
 
 // Equilibrium matrix H (Q x K, row-major) with f^eq_i = sum_k H_ik M_k(n, U, T),
 // M the Maxwell-Juttner moments of moment_basis(order):
