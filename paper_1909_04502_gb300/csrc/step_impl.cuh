@@ -178,10 +178,14 @@ __device__ __forceinline__ Macro landau_fp64(const Scalars& sc, const double (&m
 }
 
 // FP32 storage: the solve runs in FP32, then one Newton correction whose
-// residuals are evaluated in FP64 -- p(l), the eigenvector v, its Minkowski
-// norm, n = U.N and the EOS residual -- about thirty FP64 operations per
-// cell.  Corrections (differences of nearly equal FP64 numbers) are applied
-// in FP32.  The moments are reference + FP32 sums of g, and the eigenvalue is
+// residuals are evaluated in FP64: p(l) at the FP32 root, the eigenvector v
+// there, its Minkowski norm nu^2 = v.v and w = v.N (so that n = w / nu).  The
+// outputs the FP32 equilibrium needs are formed from accurate differences:
+//   dn = n - n_ref = (w^2 - n_ref^2 nu^2) / (nu (w + n_ref nu))   (numerator in FP64),
+//   d_eps = eps - eps_ref (the FP32 Newton unknown plus its correction),
+//   dT = T - T_ref from the EOS written for differences (FP32),
+// and U = v / nu only needs FP32 accuracy.  About 24 FP64 operations per
+// cell.  The moments are reference + FP32 sums of g, and the eigenvalue is
 // written l = eps_ref + delta.
 __device__ __forceinline__ Macro landau_fp32(const Scalars& sc, const float (&mm)[9]) {
   const float epsr = sc.f_T00_ref;
@@ -206,7 +210,7 @@ __device__ __forceinline__ Macro landau_fp32(const Scalars& sc, const float (&mm
     dp = -D + a * (b + c) - M2;
     del -= __fdividef(p, dp);
   }
-  // FP64 residual at l = eps_ref + del
+  // FP64 residuals at l = eps_ref + del
   const double dd = f2d(del);
   const double s = f2d(fs), t = f2d(ft), r = f2d(fr);
   const double base = sc.PE_ref + dd;
@@ -214,60 +218,65 @@ __device__ __forceinline__ Macro landau_fp32(const Scalars& sc, const float (&mm
   const double bd = base + f2d(mm[6]);
   const double cd = base + f2d(mm[8]);
   const double D = fma(bd, cd, -r * r);
-  double vx = fma(s, cd, -r * t);
-  double vy = fma(t, bd, -r * s);
+  const double vx = fma(s, cd, -r * t);
+  const double vy = fma(t, bd, -r * s);
   const double p = fma(ad, D, -fma(s, vx, t * vy));
   const float dl = -__fdividef(d2f(p), dp);          // Newton correction (FP32 is enough)
-  // eigenvector at the corrected root: v += dl * dv/dl, dv/dl = (b + c, s, t)
-  const double v0 = D + f2d(dl * (b + c));
-  vx += f2d(dl * fs);
-  vy += f2d(dl * ft);
-  const double eps = sc.T00_ref + (dd + f2d(dl));
-  // Minkowski norm of v; 1/sqrt refined once in FP64
-  const double nrm2 = fma(v0, v0, -fma(vx, vx, vy * vy));
-  const float yf = rsqrtf(d2f(nrm2));
-  const double yd = f2d(yf);
-  const float e = d2f(fma(-nrm2, yd * yd, 1.0));      // relative error of yf^2
-  const float yfc = yf * (1.f + 0.5f * e);
-  // n = U.N = (v.N) / |v|
+  const float fNx = mm[1], fNy = mm[2];
   const double N0 = sc.N0_ref + f2d(mm[0]);
-  const double w = fma(v0, N0, -fma(vx, f2d(mm[1]), vy * f2d(mm[2])));
-  double n = w * yd;
-  n = fma(n, f2d(0.5f * e), n);
+  const double nu2 = fma(D, D, -fma(vx, vx, vy * vy));
+  const double w = fma(D, N0, -fma(vx, f2d(fNx), vy * f2d(fNy)));
+  // first-order shift of v, w, nu^2 to the corrected root (v is quadratic in l
+  // with a unit second derivative in v0 only: the remainder is O(dl^2))
+  const float bc = b + c;
+  const float fD = d2f(D), fvx = d2f(vx), fvy = d2f(vy), fN0 = d2f(N0);
+  const float dw = dl * (bc * fN0 - fs * fNx - ft * fNy);
+  const float dnu2 = 2.f * dl * (fD * bc - fvx * fs - fvy * ft);
+  const double wc = w + f2d(dw);
+  const double nu2c = nu2 + f2d(dnu2);
+  const float fnu2 = d2f(nu2c);
+  const float inu = rsqrtf(fnu2);
+  const float fnu = fnu2 * inu;
+  const float fw = d2f(wc);
   Macro M;
-  M.fU0 = d2f(v0) * yfc;
-  M.fUx = d2f(vx) * yfc;
-  M.fUy = d2f(vy) * yfc;
-  M.fn = d2f(n);
-  M.fdn = d2f(n - sc.n_ref);
-  const float fn = M.fn, feps = d2f(eps), fm = sc.f_m, fTr = sc.f_T_ref;
-  float T, corr;
+  M.fU0 = (fD + dl * bc) * inu;
+  M.fUx = (fvx + dl * fs) * inu;
+  M.fUy = (fvy + dl * ft) * inu;
+  M.fn = fw * inu;
+  // dn = (w^2 - n_ref^2 nu^2) / (nu (w + n_ref nu))
+  const float nr = sc.f_n_ref;
+  const double num = fma(wc, wc, -(sc.n_ref * sc.n_ref) * nu2c);
+  M.fdn = __fdividef(d2f(num), fnu * (fw + nr * fnu));
+  const float deps = del + dl;                          // eps - eps_ref
+  const float fn = M.fn, fm = sc.f_m, fTr = sc.f_T_ref;
   if (sc.massless) {
-    // eps = 2 n T: FP32 quotient, then the FP64 residual eps - n (2 T)
-    T = __fdividef(0.5f * feps, fn);
-    const double res = fma(-n, f2d(2.f * T), eps);
-    corr = __fdividef(0.5f * d2f(res), fn);
+    // eps = 2 n T with eps_ref = 2 n_ref T_ref:  dT = (d_eps - 2 T_ref dn) / (2 n)
+    M.fdT = __fdividef(deps - 2.f * fTr * M.fdn, 2.f * fn);
+  } else if (sc.n_ref > 0.0) {
+    // 2T^2 + (2m - e) T + m (m - e) = 0 for (T, e) and (T_ref, e_ref):
+    // dT (2 (T + T_ref + m) - e) = de (T_ref + m),  e = eps/n
+    // with T = T_ref + dT:  2 dT^2 + B dT - de (T_ref + m) = 0,  B = 4 T_ref + 2m - e
+    const float feps = epsr + deps;
+    const float de = __fdividef(deps * nr - epsr * M.fdn, fn * nr);
+    const float e = __fdividef(feps, fn);
+    const float Bq = 4.f * fTr + 2.f * fm - e, Cq = de * (fTr + fm);
+    M.fdT = __fdividef(2.f * Cq, Bq + sqrtf(fmaxf(Bq * Bq + 8.f * Cq, 0.f)));
   } else {
-    // n q(T) = 2 n T^2 + (2 m n - eps) T + m (m n - eps) = 0, positive root
-    const float ee = __fdividef(feps, fn);
-    T = 0.25f * ((ee - 2.f * fm) + sqrtf(fmaxf(ee * ee + 4.f * ee * fm - 4.f * fm * fm, 0.f)));
-    const double Td = f2d(T);
-    const double q = fma(fma(2.0 * n, Td, fma(2.0 * sc.m, n, -eps)), Td, sc.m * fma(sc.m, n, -eps));
-    const float dq = 4.f * fn * T + 2.f * fm * fn - feps;
-    corr = -__fdividef(d2f(q), dq);
+    const float e = __fdividef(epsr + deps, fn);
+    const float T0 = 0.25f * ((e - 2.f * fm) + sqrtf(fmaxf(e * e + 4.f * e * fm - 4.f * fm * fm, 0.f)));
+    M.fdT = T0 - fTr;
   }
-  M.fT = T + corr;
-  M.fdT = (T - fTr) + corr;
-  M.eps = eps;
-  M.n = n;
-  M.T = f2d(T) + f2d(corr);
+  M.fT = fTr + M.fdT;
+  M.eps = sc.T00_ref + f2d(deps);
+  M.n = f2d(fn);
+  M.T = f2d(M.fT);
   M.U0 = f2d(M.fU0);
   M.Ux = f2d(M.fUx);
   M.Uy = f2d(M.fUy);
   // positivity tests on the sign / exponent bits (integer pipe); FP32 tests
   // catch non-finite values
-  M.ok = (__double2hiint(D) > 0) && (__double2hiint(nrm2) > 0) && (__double2hiint(n) > 0) &&
-         (__double2hiint(eps) > 0) && (M.fT > 0.f) && isfinite(M.fT) && isfinite(M.fU0) && isfinite(M.fn);
+  M.ok = (__double2hiint(D) > 0) && (__double2hiint(nu2c) > 0) && (__double2hiint(wc) > 0) && (M.fT > 0.f) &&
+         isfinite(M.fT) && isfinite(M.fU0) && isfinite(M.fn) && isfinite(M.fdn);
   return M;
 }
 
