@@ -385,14 +385,15 @@ def cpu_baseline(wl, budget_s=20.0, nsteps=3):
                       "one thread)" % (nsteps, L, L)}
 
 
-def bench_batched(torch, rlbm, inputs, stream, steps=10, count=64, seed=1909):
+def bench_batched(torch, rlbm, inputs, stream, steps=10, count=64, seed=1909, side_lo=64, side_hi=1024,
+                  zetas=(0.0, 1.0, 10.0)):
     """Batched tau-sweep: `count` shear-wave runs, side ~ U{64..1024}, tau ~
     U[0.6, 2.0], zeta round-robin over {0, 1, 10}, amplitude 0.05 c, FP32
     storage with the FP64 Landau solve, on-lattice order-2 stencils.  One
     persistent cooperative launch per call (CUDA graph) against the same
     instances stepped one handle at a time (back-to-back launches)."""
     import numpy as np
-    runs = inputs.sweep(count=count, seed=seed)
+    runs = inputs.sweep(count=count, seed=seed, side_lo=side_lo, side_hi=side_hi, zetas=zetas)
     cfgs = [dict(nx=r["side"], ny=r["side"], tau=r["tau"], m=r["zeta"], precision="fp32") for r in runs]
     batch = rlbm.Batch(cfgs, cuda_stream=stream.cuda_stream)
     shape, grid, _ = batch.tune(trial_steps=2)
@@ -423,7 +424,8 @@ def bench_batched(torch, rlbm, inputs, stream, steps=10, count=64, seed=1909):
     tp = e0.elapsed_time(e1) / steps
     rc, nonphys = batch.sync_status(raise_on_error=False)
     peak, _ = _peaks()
-    out = {"workload": "tau_sweep_64_shear_waves", "instances": count, "cells": cells, "seed": seed,
+    out = {"workload": "tau_sweep_%d_shear_waves_side_%d_%d" % (count, side_lo, side_hi), "instances": count,
+           "cells": cells, "seed": seed, "zetas": list(zetas),
            "steps_timed": steps, "ms_per_step_batched": round(tb, 4), "ms_per_step_plain_loop": round(tp, 4),
            "mlups_batched": round(cells / (tb * 1e-3) / 1e6, 1), "mlups_plain_loop": round(cells / (tp * 1e-3) / 1e6, 1),
            "speedup_vs_plain_loop": round(tp / tb, 3),

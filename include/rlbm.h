@@ -203,8 +203,9 @@ int rlbm_step_noalloc(const rlbm_params* p, void* f_a, void* f_b, const void* ta
 /* ------------------------------------------------------------------------
  * Batched simulations: many independent grids (different sizes, tau and
  * stencils; FP32 storage, order 2, built-in stencils, constant or eta/s tau)
- * advanced together by one persistent cooperative kernel per call, replayed
- * from a captured CUDA graph.  Not in the paper: it serves the paper's
+ * advanced together by persistent cooperative kernels replayed from one
+ * captured CUDA graph per call: one kernel per stencil kind present (the
+ * kinds run one after another, each over all its instances' tiles).  Not in the paper: it serves the paper's
  * calibration of tau against transport coefficients (Sec. 7), which runs many
  * independent simulations.  Each instance stays an ordinary handle
  * (rlbm_batch_handle) for init / moments / populations; the batched step is
@@ -222,17 +223,20 @@ void rlbm_batch_destroy(rlbm_batch* b);
 int rlbm_batch_size(const rlbm_batch* b);
 /* The i-th instance (borrowed; owned by the batch). */
 rlbm_handle* rlbm_batch_handle(rlbm_batch* b, int i);
-/* Advance every instance by nsteps (one cooperative launch; asynchronous). */
+/* Advance every instance by nsteps (one graph launch holding one cooperative
+ * kernel per stencil kind; asynchronous). */
 int rlbm_batch_step(rlbm_batch* b, int nsteps);
 /* Launch configuration: tile_shape 0 (32 x 8 cells per block) or 1 (32 x 4);
- * grid = persistent blocks (at most the co-resident limit). */
+ * grid = persistent blocks (at most the co-resident limit; a kind with fewer
+ * tiles runs with one block per tile). */
 int rlbm_batch_config(rlbm_batch* b, int tile_shape, int grid);
 /* Autotuner: times trial_steps steps for each tile shape and three grid
  * sizes and keeps the fastest.  It advances every instance by
  * 12 * trial_steps steps; call it before rlbm_init of the instances.
  * Outputs are nullable. */
 int rlbm_batch_tune(rlbm_batch* b, int trial_steps, int* tile_shape, int* grid, float* ms_per_step);
-/* Current configuration, co-resident limits {32x8, 32x4} and tile count. */
+/* Current configuration, co-resident limits {32x8, 32x4} (the smallest over
+ * the kinds present) and tile count. */
 int rlbm_batch_info(const rlbm_batch* b, int* tile_shape, int* grid, int* grid_max, long long* total_tiles);
 /* Iteration limit of the bounded grid-barrier wait (default 2^24 polls of
  * about 64 ns).  A wait that runs out sets the batch error flag; every block

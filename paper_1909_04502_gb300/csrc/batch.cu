@@ -1,11 +1,13 @@
 // Batched RLBM: many independent simulations (different grid sizes, tau and
-// stencils) advanced by one persistent cooperative kernel per call, captured
-// in a CUDA graph.  The per-cell update is the fused step of step_impl.cuh.
+// stencils) advanced by persistent cooperative kernels, one per stencil kind
+// present, captured together in one CUDA graph.  The per-cell update is the
+// fused step of step_impl.cuh.
 //
 // Work decomposition: every instance's grid is cut into tiles of BX x BY
-// cells, numbered consecutively over all instances; block b of the
-// persistent grid takes tiles b, b + G, b + 2G, ... of each time step, then
-// waits at a grid-wide barrier before the next step.  The barrier spins a
+// cells, numbered consecutively over all instances with the tiles of each
+// kind contiguous; block b of a kind's persistent grid takes that kind's
+// tiles b, b + G, b + 2G, ... of each time step, then waits at a grid-wide
+// barrier before the next step.  The barrier spins a
 // bounded number of times; on timeout it records RLBM_ERR_TIMEOUT and every
 // block leaves.
 #include <cuda_runtime.h>
@@ -51,7 +53,7 @@ struct BarrierState {
 struct BatchArgs {
   BatchInst* inst;
   const int* tile_inst;  // instance of each tile
-  int total_tiles;
+  int tile_lo, tile_hi;  // tiles of this launch's kind
   int nsteps;
   BarrierState* bar;
   unsigned long long* timeouts;
@@ -94,7 +96,7 @@ __device__ __forceinline__ bool grid_barrier(BarrierState* bar, unsigned long lo
   return s_ok != 0;
 }
 
-template <int BX, int BY>
+template <int BX, int BY, int KIND>
 __device__ __forceinline__ void batch_tile(const BatchInst& I, int tile, int step) {
   const int lt = tile - I.tile_begin;
   const int ty = lt / I.tiles_x, tx = lt - ty * I.tiles_x;
@@ -104,32 +106,29 @@ __device__ __forceinline__ void batch_tile(const BatchInst& I, int tile, int ste
   const int c = (I.cur + step) & 1;
   const float* fin = I.buf[c];
   float* fout = I.buf[c ^ 1];
-  switch (I.kind) {
-    case kKindMassless:
-      cell_update<float, 28, true, 9, kOnLattice, true, false>(c_btab[kKindMassless], I.s, fin, fout, I.tau_field, I.status, x, y);
-      break;
-    case kKindQ33:
-      cell_update<float, 33, true, 9, kOnLattice, true, false>(c_btab[kKindQ33], I.s, fin, fout, I.tau_field, I.status, x, y);
-      break;
-    case kKindQ25:
-      cell_update<float, 25, true, 9, kOnLattice, true, false>(c_btab[kKindQ25], I.s, fin, fout, I.tau_field, I.status, x, y);
-      break;
-    case kKindQ29:
-      cell_update<float, 29, true, 9, kOnLattice, true, false>(c_btab[kKindQ29], I.s, fin, fout, I.tau_field, I.status, x, y);
-      break;
-    default:
-      cell_update<float, 28, true, 9, kBilinear, true, false>(c_btab[kKindMasslessBilinear], I.s, fin, fout, I.tau_field, I.status, x, y);
-      break;
-  }
+  if constexpr (KIND == kKindMassless)
+    cell_update<float, 28, true, 9, kOnLattice, true, false>(c_btab[KIND], I.s, fin, fout, I.tau_field, I.status, x, y);
+  else if constexpr (KIND == kKindQ33)
+    cell_update<float, 33, true, 9, kOnLattice, true, false>(c_btab[KIND], I.s, fin, fout, I.tau_field, I.status, x, y);
+  else if constexpr (KIND == kKindQ25)
+    cell_update<float, 25, true, 9, kOnLattice, true, false>(c_btab[KIND], I.s, fin, fout, I.tau_field, I.status, x, y);
+  else if constexpr (KIND == kKindQ29)
+    cell_update<float, 29, true, 9, kOnLattice, true, false>(c_btab[KIND], I.s, fin, fout, I.tau_field, I.status, x, y);
+  else
+    cell_update<float, 28, true, 9, kBilinear, true, false>(c_btab[KIND], I.s, fin, fout, I.tau_field, I.status, x, y);
 }
 
-template <int BX, int BY>
+// One persistent kernel per stencil kind: a kernel compiled for a single
+// population count keeps the per-kind register budget of the single-grid
+// kernel (a kernel holding every kind's cell update spills).  The tiles of
+// the kind's instances are the contiguous range [tile_lo, tile_hi).
+template <int BX, int BY, int KIND>
 __global__ void __launch_bounds__(BX * BY, (BX * BY == 256) ? 4 : 8) k_batch(const __grid_constant__ BatchArgs a) {
   __shared__ BatchInst s_inst;
   __shared__ int s_idx;
   if (threadIdx.x == 0 && threadIdx.y == 0) s_idx = -1;
   for (int step = 0; step < a.nsteps; ++step) {
-    for (int t = blockIdx.x; t < a.total_tiles; t += gridDim.x) {
+    for (int t = a.tile_lo + blockIdx.x; t < a.tile_hi; t += gridDim.x) {
       const int idx = __ldg(a.tile_inst + t);
       __syncthreads();                // previous tile done; s_idx stable
       const int have = s_idx;
@@ -141,7 +140,7 @@ __global__ void __launch_bounds__(BX * BY, (BX * BY == 256) ? 4 : 8) k_batch(con
         }
         __syncthreads();
       }
-      batch_tile<BX, BY>(s_inst, t, step);
+      batch_tile<BX, BY, KIND>(s_inst, t, step);
     }
     if (!grid_barrier(a.bar, a.timeouts, a.spin_limit)) return;
   }
@@ -163,6 +162,7 @@ struct rlbm_batch {
   std::vector<int> kind;
   std::vector<int> tile_begin, tiles_x;
   int total_tiles = 0;
+  int kind_lo[kNumKinds] = {}, kind_hi[kNumKinds] = {};   // tile range of each kind (grouped by kind)
   cudaStream_t stream = nullptr;          // the user's stream (graphs are launched on it)
   cudaStream_t cap_stream = nullptr;      // private stream the graphs are captured on
   Tables<float>* tab_host = nullptr;     // pinned copy of the constant tables (graph memcpy source)
@@ -174,7 +174,7 @@ struct rlbm_batch {
   long long spin_limit = 1LL << 24;
   int tile_shape = 0;                     // 0: 32 x 8, 1: 32 x 4 (autotuned)
   int grid = 0;                           // persistent grid size (autotuned)
-  int grid_max[2] = {0, 0};               // co-resident limit per tile shape
+  int grid_max[2] = {0, 0};               // co-resident limit per tile shape (smallest over the kinds present)
   std::map<long long, cudaGraphExec_t> graphs;
   std::string err = "no error";
 };
@@ -210,9 +210,10 @@ bool same_stencil(const rlbm_handle* a, const rlbm_handle* b) {
   return true;
 }
 
-template <int BX, int BY>
-cudaError_t launch_batch(rlbm_batch* b, int nsteps, int grid, cudaStream_t st) {
-  BatchArgs a{b->inst_dev, b->tile_inst_dev, b->total_tiles, nsteps, b->bar, b->timeouts, b->spin_limit};
+template <int BX, int BY, int KIND>
+cudaError_t launch_kind(rlbm_batch* b, int nsteps, int grid, cudaStream_t st) {
+  BatchArgs a{b->inst_dev, b->tile_inst_dev, b->kind_lo[KIND], b->kind_hi[KIND], nsteps, b->bar, b->timeouts,
+              b->spin_limit};
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(BX, BY);
@@ -222,17 +223,71 @@ cudaError_t launch_batch(rlbm_batch* b, int nsteps, int grid, cudaStream_t st) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_batch<BX, BY>, a);
+  return cudaLaunchKernelEx(&cfg, k_batch<BX, BY, KIND>, a);
 }
 
+template <int BX, int BY>
+cudaError_t launch_batch(rlbm_batch* b, int kind, int nsteps, int grid, cudaStream_t st) {
+  switch (kind) {
+    case kKindMassless: return launch_kind<BX, BY, kKindMassless>(b, nsteps, grid, st);
+    case kKindQ33: return launch_kind<BX, BY, kKindQ33>(b, nsteps, grid, st);
+    case kKindQ25: return launch_kind<BX, BY, kKindQ25>(b, nsteps, grid, st);
+    case kKindQ29: return launch_kind<BX, BY, kKindQ29>(b, nsteps, grid, st);
+    default: return launch_kind<BX, BY, kKindMasslessBilinear>(b, nsteps, grid, st);
+  }
+}
+
+template <int BX, int BY>
+int blocks_per_sm(int kind) {
+  int nb = 0;
+  const int threads = BX * BY;
+  switch (kind) {
+    case kKindMassless: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<BX, BY, kKindMassless>, threads, 0); break;
+    case kKindQ33: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<BX, BY, kKindQ33>, threads, 0); break;
+    case kKindQ25: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<BX, BY, kKindQ25>, threads, 0); break;
+    case kKindQ29: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<BX, BY, kKindQ29>, threads, 0); break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<BX, BY, kKindMasslessBilinear>, threads, 0); break;
+  }
+  return nb;
+}
+
+// The kinds run one after another (each a cooperative launch of its own
+// tiles); a kind with fewer tiles than the grid gets a grid of its tile count.
 cudaError_t enqueue(rlbm_batch* b, int nsteps, cudaStream_t st) {
   cudaError_t e = cudaMemcpyToSymbolAsync(c_btab, b->tab_host, sizeof(Tables<float>) * kNumKinds, 0,
                                           cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return e;
-  e = (b->tile_shape == 0) ? launch_batch<32, 8>(b, nsteps, b->grid, st) : launch_batch<32, 4>(b, nsteps, b->grid, st);
-  if (e != cudaSuccess) return e;
+  for (int k = 0; k < kNumKinds; ++k) {
+    const int tiles = b->kind_hi[k] - b->kind_lo[k];
+    if (tiles <= 0) continue;
+    const int grid = std::min(b->grid, tiles);
+    e = (b->tile_shape == 0) ? launch_batch<32, 8>(b, k, nsteps, grid, st) : launch_batch<32, 4>(b, k, nsteps, grid, st);
+    if (e != cudaSuccess) return e;
+  }
   k_batch_flip<<<(int)((b->h.size() + 127) / 128), 128, 0, st>>>(b->inst_dev, (int)b->h.size(), nsteps);
   return cudaGetLastError();
+}
+
+// Tile map for tile height by: the tiles of each kind form one contiguous
+// range (kinds in enum order, instances in batch order inside a kind).
+std::vector<int> build_tile_map(rlbm_batch* b, int by) {
+  std::vector<int> tile_inst;
+  int tiles = 0;
+  for (int k = 0; k < kNumKinds; ++k) {
+    b->kind_lo[k] = tiles;
+    for (size_t i = 0; i < b->h.size(); ++i) {
+      if (b->kind[i] != k) continue;
+      const rlbm_handle* h = b->h[i];
+      const int nt = ((h->p.nx + 31) / 32) * ((h->p.ny + by - 1) / by);
+      b->tile_begin[i] = tiles;
+      b->inst_host[i].tile_begin = tiles;
+      for (int t = 0; t < nt; ++t) tile_inst.push_back((int)i);
+      tiles += nt;
+    }
+    b->kind_hi[k] = tiles;
+  }
+  b->total_tiles = tiles;
+  return tile_inst;
 }
 
 // Upload descriptors (instance buffers, current-buffer index) when the
@@ -297,13 +352,7 @@ int rlbm_batch_create(const rlbm_params* params, int count, rlbm_batch** out) {
     kind_owner[kind] = h;
     b->kind.push_back(kind);
   }
-  // tiles
-  int tiles = 0;
-  for (auto* h : b->h) {
-    b->tile_begin.push_back(tiles);
-    tiles += ((h->p.nx + 31) / 32) * ((h->p.ny + 7) / 8);
-  }
-  b->total_tiles = tiles;
+  b->tile_begin.assign(count, 0);
   // constant tables (pinned host source for the graph's memcpy node)
   e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMallocHost(&b->tab_host, sizeof(Tables<float>) * kNumKinds);
@@ -329,17 +378,13 @@ int rlbm_batch_create(const rlbm_params* params, int count, rlbm_batch** out) {
     I.status = h->status;
     I.kind = b->kind[i];
     I.tiles_x = (h->p.nx + 31) / 32;     // tiles are 32 wide for both shapes
-    I.tile_begin = b->tile_begin[i];
     I.cur = h->cur;
   }
-  // the tile -> instance map is built for the 32 x 8 shape; the 32 x 4 shape
-  // uses its own map (rebuilt by set_shape)
+  // the tile -> instance map starts with the 32 x 8 shape; rlbm_batch_config
+  // rebuilds it for the 32 x 4 shape
   b->tile_shape = 0;
-  std::vector<int> tile_inst(tiles);
-  for (int i = 0; i < count; ++i) {
-    const int nt = ((b->h[i]->p.nx + 31) / 32) * ((b->h[i]->p.ny + 7) / 8);
-    for (int t = 0; t < nt; ++t) tile_inst[b->tile_begin[i] + t] = i;
-  }
+  std::vector<int> tile_inst = build_tile_map(b.get(), 8);
+  const int tiles = b->total_tiles;
   // room for the 32 x 4 map (twice the tiles at most)
   e = cudaMalloc(&b->tile_inst_dev, sizeof(int) * (size_t)tiles * 2 + 64);
   if (e != cudaSuccess) {
@@ -351,11 +396,14 @@ int rlbm_batch_create(const rlbm_params* params, int count, rlbm_batch** out) {
   cudaMemset(b->bar, 0, sizeof(BarrierState));
   cudaMemset(b->timeouts, 0, sizeof(unsigned long long));
   // co-resident grid limits for the cooperative launch
-  int dev = 0, sms = 0, nb8 = 0, nb4 = 0;
+  int dev = 0, sms = 0, nb8 = 1 << 30, nb4 = 1 << 30;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb8, k_batch<32, 8>, 256, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb4, k_batch<32, 4>, 128, 0);
+  for (int k = 0; k < kNumKinds; ++k) {
+    if (!kind_owner[k]) continue;
+    nb8 = std::min(nb8, blocks_per_sm<32, 8>(k));
+    nb4 = std::min(nb4, blocks_per_sm<32, 4>(k));
+  }
   b->grid_max[0] = nb8 * sms;
   b->grid_max[1] = nb4 * sms;
   b->grid = b->grid_max[0];
@@ -396,18 +444,8 @@ int rlbm_batch_config(rlbm_batch* b, int tile_shape, int grid) {
   if (grid <= 0 || grid > gmax) return batch_fail(b, RLBM_ERR_INVALID_ARG, "grid exceeds co-resident blocks");
   if (tile_shape != b->tile_shape) {
     // rebuild the tile -> instance map and tile counts for the new shape
-    const int by = tile_shape == 0 ? 8 : 4;
-    std::vector<int> tile_inst;
-    int tiles = 0;
-    for (size_t i = 0; i < b->h.size(); ++i) {
-      const rlbm_handle* h = b->h[i];
-      const int nt = ((h->p.nx + 31) / 32) * ((h->p.ny + by - 1) / by);
-      b->tile_begin[i] = tiles;
-      b->inst_host[i].tile_begin = tiles;
-      for (int t = 0; t < nt; ++t) tile_inst.push_back((int)i);
-      tiles += nt;
-    }
-    b->total_tiles = tiles;
+    std::vector<int> tile_inst = build_tile_map(b, tile_shape == 0 ? 8 : 4);
+    const int tiles = b->total_tiles;
     cudaError_t e = cudaMemcpyAsync(b->tile_inst_dev, tile_inst.data(), sizeof(int) * tiles, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(b->inst_dev, b->inst_host, sizeof(BatchInst) * b->h.size(), cudaMemcpyHostToDevice, b->stream);

@@ -330,8 +330,8 @@ class _BorrowedLattice(Lattice):
 
 
 class Batch:
-    """Many independent simulations stepped by one persistent kernel
-    (rlbm_batch_* in include/rlbm.h).  ``configs`` is a list of keyword dicts
+    """Many independent simulations stepped by persistent kernels (one per
+    stencil kind) replayed from a CUDA graph (rlbm_batch_* in include/rlbm.h).  ``configs`` is a list of keyword dicts
     for ``make_params`` (each with nx and ny)."""
 
     def __init__(self, configs, cuda_stream=None):

@@ -26,6 +26,8 @@ CONFIGS = [
     dict(nx=33, ny=33, tau=1.1, m=1.0),
     dict(nx=70, ny=21, tau=0.65, m=10.0),
     dict(nx=1, ny=40, tau=1.0),
+    dict(nx=45, ny=30, tau=0.8, stream="bilinear", lam=1.0),
+    dict(nx=20, ny=52, tau=1.2, stream="bilinear", lam=1.0),
 ]
 
 
