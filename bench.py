@@ -172,13 +172,14 @@ def run_oracle(L, steps, warmup, wl):
 
 
 def oracle_sample_size(wl, budget_s, nsteps):
-    """Largest square grid <= the workload's whose nsteps oracle steps fit the budget."""
+    """Largest square grid <= the workload's whose nsteps oracle steps fit the
+    budget, and the probed oracle time per cell update."""
     probe = run_oracle(64, 2, 0, wl)
     per_cell = statistics.median(probe["times"]) / probe["cells"]
     L = wl["L"]
     while L > 32 and per_cell * L * L * nsteps > budget_s:
         L //= 2
-    return L
+    return L, per_cell
 
 
 # ---------------------------------------------------------------------------
@@ -193,6 +194,8 @@ def main():
     ap.add_argument("--workload", default="tg512", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint measurements")
+    ap.add_argument("--only", default=None, choices=["batched", "adjoint"],
+                    help="run only this extra measurement and print its JSON object")
     ap.add_argument("--_oracle_worker", default=None)
     args = ap.parse_args()
     if args._oracle_worker is not None:
@@ -229,6 +232,17 @@ def main():
     if dist:
         dist.barrier()
     from paper_1909_04502_gb300 import inputs, rlbm
+
+    if args.only:
+        stream = torch.cuda.current_stream()
+        if args.only == "batched":
+            res = {"batched": bench_batched(torch, rlbm, inputs, stream),
+                   "batched_small": bench_batched(torch, rlbm, inputs, stream, steps=50, side_hi=256)}
+        else:
+            res = {"adjoint": bench_adjoint(torch, rlbm, inputs, stream)}
+        if rank == 0:
+            print(json.dumps(res))
+        return
 
     L = wl["L"]
     ncell = L * L
@@ -322,6 +336,7 @@ def main():
             cpu = cpu_baseline(wl)
     if not args.no_extras:
         extras["batched"] = bench_batched(torch, rlbm, inputs, stream)
+        extras["batched_small"] = bench_batched(torch, rlbm, inputs, stream, steps=50, side_hi=256)
         extras["adjoint"] = bench_adjoint(torch, rlbm, inputs, stream)
 
     clocks = clk.summary()
@@ -376,8 +391,11 @@ def oracle_parity(lat, fields, wl):
             "bar": 1e-5 if wl["precision"] == "fp32" else 1e-12}
 
 
-def cpu_baseline(wl, budget_s=20.0, nsteps=3):
-    L = oracle_sample_size(wl, budget_s, nsteps)
+def cpu_baseline(wl, budget_s=20.0):
+    """The oracle on one host core: the workload's grid (halved until three
+    steps fit the budget) for as many steps as fill about budget_s seconds."""
+    L, per_cell = oracle_sample_size(wl, budget_s, 3)
+    nsteps = int(max(3, min(200, budget_s / (per_cell * L * L))))
     r = run_oracle(L, nsteps, 1, wl)
     t = sum(r["times"])
     return {"value": round(r["cells"] * nsteps / t / 1e6, 4), "unit": METRIC, "cores": 1, "kind": "oracle",
@@ -387,11 +405,13 @@ def cpu_baseline(wl, budget_s=20.0, nsteps=3):
 
 def bench_batched(torch, rlbm, inputs, stream, steps=10, count=64, seed=1909, side_lo=64, side_hi=1024,
                   zetas=(0.0, 1.0, 10.0)):
-    """Batched tau-sweep: `count` shear-wave runs, side ~ U{64..1024}, tau ~
-    U[0.6, 2.0], zeta round-robin over {0, 1, 10}, amplitude 0.05 c, FP32
-    storage with the FP64 Landau solve, on-lattice order-2 stencils.  One
-    persistent cooperative launch per call (CUDA graph) against the same
-    instances stepped one handle at a time (back-to-back launches)."""
+    """Batched tau-sweep: `count` shear-wave runs, side ~ U{side_lo..side_hi},
+    tau ~ U[0.6, 2.0], zeta round-robin over {0, 1, 10}, amplitude 0.05 c,
+    FP32 storage with the FP64 Landau solve, on-lattice order-2 stencils.  One
+    graph launch per call (one persistent cooperative kernel per stencil
+    kind) against the same instances stepped one handle at a time
+    (back-to-back launches).  The working set of all instances exceeds L2 for
+    both sweeps the bench runs (about 5 GB and 0.4 GB), so L2 is not flushed."""
     import numpy as np
     runs = inputs.sweep(count=count, seed=seed, side_lo=side_lo, side_hi=side_hi, zetas=zetas)
     cfgs = [dict(nx=r["side"], ny=r["side"], tau=r["tau"], m=r["zeta"], precision="fp32") for r in runs]
@@ -476,7 +496,7 @@ def bench_adjoint(torch, rlbm, inputs, stream, L=512, nsteps=2000, K=100):
 def bench_reference(args, wl):
     """The FP64 CPU oracle as the reference arm, on the host cores."""
     budget = 150.0
-    L = oracle_sample_size(wl, budget, args.steps + args.warmup)
+    L, _ = oracle_sample_size(wl, budget, args.steps + args.warmup)
     r = run_oracle(L, args.steps, args.warmup, wl)
     t = sum(r["times"])
     value = r["cells"] * args.steps / t / 1e6
