@@ -182,6 +182,22 @@ def oracle_sample_size(wl, budget_s, nsteps):
     return L, per_cell
 
 
+def reduce_timed_ms(local_ms, dist=None, device="cuda"):
+    """Job time of a replica run: the slowest rank's timed interval (MAX over
+    ranks; the identity on one rank)."""
+    if dist is None:
+        return float(local_ms)
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(total_cells, steps, job_ms):
+    """Whole-job throughput: cell updates of all ranks over the job time."""
+    return total_cells * steps / (job_ms * 1e-3) / 1e6
+
+
 # ---------------------------------------------------------------------------
 
 
@@ -279,14 +295,10 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     kt = [s.elapsed_time(e) for s, e in zip(starts, ends)]   # ms per launch
-    total_ms = sum(kt)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_timed_ms(sum(kt), dist, "cuda")
     status = lat.sync_status(raise_on_error=False)
 
-    value = world * ncell * args.steps / (total_ms * 1e-3) / 1e6
+    value = job_mlups(world * ncell, args.steps, total_ms)
     ms_per_step = total_ms / args.steps
     peak, peak_kind = _peaks()
     alg_bytes = 2 * Q * elem * ncell                     # read + write every population once
