@@ -99,3 +99,74 @@ def ce_shear_viscosity_coeff(zeta, d=2):
     zz = np.where(z > 0, z, 1.0)
     tail = np.where(z > 0, z ** 4 * special.hyperu(1.0, 1.0, zz) / (z + 1.0), 0.0)
     return (2.0 * g - z * z + tail) / 8.0
+
+
+def riemann_ur(nL, PL, nR, PR, d=2, c=1.0):
+    """Inviscid ultra-relativistic Riemann problem with the fluid at rest on
+    both sides of a membrane at x = 0 and PL > PR (App. D): a rarefaction
+    moving left, a contact discontinuity and a shock moving right.
+
+    The EOS is eps = d P, P = n T, so the sound speed is c/sqrt(d) and the
+    adiabatic index (d+1)/d.  Along the left-moving rarefaction the Riemann
+    invariants P R^a and n R^b are those of the left state, with
+    R = (1+beta)/(1-beta), a = (d+1)/(2 sqrt d), b = sqrt(d)/2.  Across the
+    shock the Rankine-Hugoniot conditions in the shock frame give the shock
+    speed, the post-shock velocity and n_II.  P_C is the root (by bisection
+    on (PR, PL)) of: the velocity reached at the tail of the rarefaction at
+    pressure P_C equals the post-shock velocity at P_C.
+
+    Returns a dict with P_C, beta_C, beta_s, n_I, n_II and the self-similar
+    speeds of the head, tail, contact and shock (in units of c)."""
+    sd = np.sqrt(d)
+    cs = 1.0 / sd
+
+    def beta_shock(P):
+        return np.sqrt(d * (P - PR) ** 2 / ((PR + d * P) * (P + d * PR)))
+
+    def beta_rare(P):
+        # (1 - beta)/(1 + beta) = (P/PL)^(1/a) on the fan
+        q = (P / PL) ** (2.0 * sd / (d + 1))
+        return (1.0 - q) / (1.0 + q)
+
+    lo, hi = PR, PL
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if beta_rare(mid) - beta_shock(mid) > 0.0:
+            lo = mid            # rarefaction still faster: P_C is higher
+        else:
+            hi = mid
+    PC = 0.5 * (lo + hi)
+    bC = beta_shock(PC)
+    bs = np.sqrt((PR + d * PC) / (d * (PC + d * PR)))
+    nII = nR * np.sqrt(PC * (PR + d * PC) / (PR * (PC + d * PR)))
+    nI = nL * (PC / PL) ** (d / (d + 1.0))
+    return {"P_C": PC, "beta_C": bC, "beta_s": bs, "n_I": nI, "n_II": nII,
+            "w_H": -cs * c, "w_T": c * (bC - cs) / (1.0 - bC * cs), "w_C": bC * c, "w_S": bs * c,
+            "nL": nL, "PL": PL, "nR": nR, "PR": PR, "d": d, "c": c}
+
+
+def riemann_ur_profile(sol, w):
+    """n, P, beta of the App. D solution at self-similar coordinates w = x/t."""
+    w = np.asarray(w, dtype=np.float64)
+    d, c = sol["d"], sol["c"]
+    sd = np.sqrt(d)
+    n = np.empty_like(w)
+    P = np.empty_like(w)
+    beta = np.zeros_like(w)
+    L = w < sol["w_H"]
+    fan = (w >= sol["w_H"]) & (w < sol["w_T"])
+    I = (w >= sol["w_T"]) & (w < sol["w_C"])
+    II = (w >= sol["w_C"]) & (w < sol["w_S"])
+    R = w >= sol["w_S"]
+    n[L], P[L] = sol["nL"], sol["PL"]
+    # on the fan the characteristic (beta - cs)/(1 - beta cs) equals w/c
+    x = w[fan] / c
+    b = (x + 1.0 / sd) / (1.0 + x / sd)
+    beta[fan] = b
+    ratio = (1.0 - b) / (1.0 + b)
+    n[fan] = sol["nL"] * ratio ** (sd / 2.0)
+    P[fan] = sol["PL"] * ratio ** ((d + 1) / (2.0 * sd))
+    n[I], P[I], beta[I] = sol["n_I"], sol["P_C"], sol["beta_C"]
+    n[II], P[II], beta[II] = sol["n_II"], sol["P_C"], sol["beta_C"]
+    n[R], P[R] = sol["nR"], sol["PR"]
+    return n, P, beta

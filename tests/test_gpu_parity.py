@@ -111,6 +111,20 @@ def test_fp64_eta_over_s_sod(rl):
     compare(lat, sim, idx, 1e-12)
 
 
+def test_fp64_sod_full_run(rl):
+    """The 1024-cell shock tube (eta/s = 0.1, free-flow ends) for its full
+    2000 steps against the oracle (which is itself pinned to the App. D
+    solution at 100 steps).  The waves leave through the free-flow ends after
+    about 140 steps, so the run also covers the outflow."""
+    nx, ny = 1024, 1
+    lat, sim, idx = make_pair(rl, nx, ny, inputs.sod(nx, ny), boundary="freeflow_x",
+                              tau_mode="eta_over_s", eta_over_s=0.1, kappa=15.79)
+    for _ in range(4):
+        lat.step(500)
+        sim.step(500)
+    compare(lat, sim, idx, 1e-12)
+
+
 def test_fp64_bilinear_at_integer_displacement_equals_onlattice(rl):
     nx, ny = 24, 20
     fields = inputs.random_smooth(nx, ny, seed=11)

@@ -479,3 +479,93 @@ def test_order3_shear_wave_viscosity_matches_chapman_enskog(tau):
     value of App. C with the second-order lattice shift of tau by half a step."""
     eta = _shear_wave_eta(3, 200, tau)
     assert abs(eta / (0.75 * (tau - 0.5)) - 1.0) < 0.01
+
+
+# ------------------------------------------------------- App. D Riemann problem
+
+
+def _ur_conserved(n, P, beta, d=2):
+    """(N^0, T^00, T^0x) and their x-fluxes (N^x, T^0x, T^xx) of an ideal
+    ultra-relativistic fluid, eps = d P (definitions of Sec. 3)."""
+    g2 = 1.0 / (1.0 - beta ** 2)
+    h = (d + 1) * P                      # eps + P
+    N0, Nx = n * np.sqrt(g2), n * np.sqrt(g2) * beta
+    T00, T0x, Txx = h * g2 - P, h * g2 * beta, h * g2 * beta ** 2 + P
+    return np.array([N0, T00, T0x]), np.array([Nx, T0x, Txx])
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_riemann_ur_satisfies_jump_conditions_from_the_definitions(d):
+    """Across the shock (speed beta_s) the lab-frame fluxes of N and T jump as
+    beta_s times the jump of the densities; across the contact P and beta are
+    continuous; the fan ends on the plateau."""
+    s = P.riemann_ur(1.0, 1.0, 0.5, 0.4, d=d)
+    q2, f2 = _ur_conserved(s["n_II"], s["P_C"], s["beta_C"], d)
+    qR, fR = _ur_conserved(s["nR"], s["PR"], 0.0, d)
+    assert np.abs(s["beta_s"] * (q2 - qR) - (f2 - fR)).max() < 1e-14
+    # tail of the fan: the profile just inside reaches (P_C, beta_C, n_I)
+    w = np.array([s["w_T"] - 1e-12])
+    n, Pw, b = P.riemann_ur_profile(s, w)
+    assert abs(Pw[0] - s["P_C"]) < 1e-10 and abs(b[0] - s["beta_C"]) < 1e-10
+    assert abs(n[0] - s["n_I"]) < 1e-10
+    # head of the fan: the left state
+    n, Pw, b = P.riemann_ur_profile(s, np.array([s["w_H"] + 1e-12]))
+    assert abs(Pw[0] - 1.0) < 1e-10 and abs(b[0]) < 1e-10 and abs(n[0] - 1.0) < 1e-10
+
+
+def test_riemann_ur_fan_is_a_self_similar_solution_of_the_conservation_laws():
+    """On the fan, d/dt Q + d/dx F = 0 with Q(w), F(w), w = x/t, reads
+    -w Q'(w) + F'(w) = 0 for N^0, T^00 and T^0x (central differences)."""
+    s = P.riemann_ur(1.0, 1.0, 0.5, 0.4)
+    h = 1e-5
+    for w in np.linspace(s["w_H"] + 0.01, s["w_T"] - 0.01, 7):
+        qa, fa = _ur_conserved(*P.riemann_ur_profile(s, np.array([w - h])))
+        qb, fb = _ur_conserved(*P.riemann_ur_profile(s, np.array([w + h])))
+        dq, df = (qb - qa) / (2 * h), (fb - fa) / (2 * h)
+        assert np.abs(-w * dq + df).max() < 1e-8 * np.abs(df).max()
+
+
+def test_riemann_ur_weak_shock_limit():
+    """P_R -> P_L: no flow, and the shock and the rarefaction head move at
+    the sound speed c/sqrt(d)."""
+    s = P.riemann_ur(1.0, 1.0, 1.0 - 1e-9, 1.0 - 1e-9)
+    assert abs(s["beta_C"]) < 1e-8
+    assert abs(s["beta_s"] - 1 / np.sqrt(2)) < 1e-8
+    assert abs(s["w_T"] - s["w_H"]) < 1e-8
+
+
+def test_oracle_sod_matches_app_d_solution():
+    """Config-1 shock tube (1024 x 1, eta/s = 0.1, free-flow ends) after 100
+    steps, before any wave reaches an end, against the inviscid App. D
+    solution: plateau pressure and velocity within 0.5 %, the densities on
+    either side of the contact within 1 % / 2.5 % (the contact is diffused by
+    the viscosity), the shock and the middle of the fan within 2 % in w."""
+    q = L.massless_quadrature(2)
+    nx, t = 1024, 100
+    sim = S.Simulation(q, L.Expansion(q), nx, 1, tau=(0.1, 15.79), boundary="freeflow_x")
+    left = np.arange(nx) < nx // 2
+    n0 = np.where(left, 1.0, 0.5)[None, :]
+    T0 = np.where(left, 1.0, 0.8)[None, :]
+    z = np.zeros((1, nx))
+    sim.init(n0, z, z.copy(), T0)
+    sim.step(t)
+    fl = sim.fields
+    Pn, b, n = (fl.n * fl.T)[0], fl.ux[0], fl.n[0]
+    s = P.riemann_ur(1.0, 1.0, 0.5, 0.4)
+    w = (np.arange(nx) - (nx // 2 - 0.5)) / (5.0 * t)       # c = 5 cells per step
+    plateau = (w > -0.1) & (w < 0.5)
+    assert abs(Pn[plateau].mean() / s["P_C"] - 1) < 5e-3
+    assert abs(b[plateau].mean() / s["beta_C"] - 1) < 5e-3
+    assert abs(n[np.argmin(abs(w + 0.25))] / s["n_I"] - 1) < 1e-2
+    assert abs(n[np.argmin(abs(w - 0.45))] / s["n_II"] - 1) < 2.5e-2
+
+    def crossing(level, lo, hi):
+        i = np.where((w > lo) & (w < hi) & (Pn < level))[0][0]
+        return w[i - 1] + (w[i] - w[i - 1]) * (Pn[i - 1] - level) / (Pn[i - 1] - Pn[i])
+
+    ws = crossing(0.5 * (s["P_C"] + 0.4), 0.5, 1.0)
+    assert abs(ws - s["w_S"]) < 0.02
+    Pmid = 0.5 * (1.0 + s["P_C"])
+    _, Pa, _ = P.riemann_ur_profile(s, w)
+    i = np.where((w > s["w_H"]) & (Pa < Pmid))[0][0]
+    assert abs(crossing(Pmid, -1.0, 0.0) - w[i]) < 0.02
