@@ -117,6 +117,29 @@ void compute_layout(const Quadrature& q, const rlbm_params& p, size_t elem, Scal
   s->plane = ((long long)(p.ny + 2 * hy) * s->pitch + 31) / 32 * 32;
 }
 
+// Bilinear weights in the storage type whose exact sum is one: each weight
+// becomes a multiple of 2^-b (b = 24 for float, 52 for double; every such
+// value in [0, 1] is exact in R) and the largest takes the remainder.
+// Rounding each weight on its own leaves the sum off by up to a few units in
+// the last place, which multiplies the streamed populations by that factor
+// every step and drifts the global sums of N^0 and T^{0a}.
+template <typename R>
+void quantize_unit_sum(const double (&w)[4], R (&out)[4]) {
+  const int bits = sizeof(R) == 4 ? 24 : 52;
+  const long long one = 1LL << bits;
+  long long k[4];
+  int big = 0;
+  for (int j = 0; j < 4; ++j) {
+    k[j] = std::llround(std::ldexp(w[j], bits));
+    if (w[j] > w[big]) big = j;
+  }
+  long long rest = one;
+  for (int j = 0; j < 4; ++j)
+    if (j != big) rest -= k[j];
+  k[big] = rest;
+  for (int j = 0; j < 4; ++j) out[j] = (R)std::ldexp((double)k[j], -bits);
+}
+
 template <typename R>
 void fill_tables(const rlbm_handle* h, const Scalars& s, Tables<R>* t) {
   std::memset(t, 0, sizeof(Tables<R>));
@@ -142,10 +165,9 @@ void fill_tables(const rlbm_handle* h, const Scalars& s, Tables<R>* t) {
       t->dx[i] = (short)o[0];
       t->dy[i] = (short)o[1];
       t->roff[i] = (-o[1] - 1) * s.pitch + (-o[0] - 1);
-      t->bw[i][0] = (R)((1.0 - phi[0]) * (1.0 - phi[1]));
-      t->bw[i][1] = (R)(phi[0] * (1.0 - phi[1]));
-      t->bw[i][2] = (R)((1.0 - phi[0]) * phi[1]);
-      t->bw[i][3] = (R)(phi[0] * phi[1]);
+      const double w[4] = {(1.0 - phi[0]) * (1.0 - phi[1]), phi[0] * (1.0 - phi[1]), (1.0 - phi[0]) * phi[1],
+                           phi[0] * phi[1]};
+      quantize_unit_sum<R>(w, t->bw[i]);
     }
   }
 }

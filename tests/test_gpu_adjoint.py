@@ -139,3 +139,60 @@ def test_torch_autograd_function(rl):
     assert np.array_equal(tau_p.grad.cpu().numpy(), g_ref)
     assert np.array_equal(ux_p.grad.cpu().numpy(), gx_ref)
     run.close()
+
+
+def test_calibration_full_size_gradient(rl):
+    """The 512^2 calibration run (massless shear flow u_y = 0.05 sin(2 pi x/L),
+    2000 steps, checkpoints every 100, hidden smooth tau): the FP32 adjoint's
+    tau gradient within 1e-4 of the FP64 adjoint's, and the FP64 directional
+    derivative within 1e-4 of central differences (h = 1e-4, relative on
+    tau) of the FP64 forward run (the forward and adjoint kernels share no
+    derivative code; the oracle is too slow for 5e8 cell updates)."""
+    L, nsteps, K = 512, 2000, 100
+    n, ux, uy, Tf = [np.ascontiguousarray(a) for a in inputs.shear_wave(L, L, amp=0.05)]
+    hidden = np.ascontiguousarray(inputs.smooth_tau(L, L))
+    tau = np.ones((L, L))
+
+    def run(precision, tau_field, target=None):
+        lat = rl.Lattice(L, L, tau_mode="field", precision=precision)
+        lat.set_tau_field(np.ascontiguousarray(tau_field))
+        if target is None:
+            lat.init(n, ux, uy, Tf)
+            lat.step(nsteps)
+            m = lat.moments()
+            assert lat.sync_status()[0] == 0
+            lat.close()
+            return m
+        adj = rl.Adjoint(lat, nsteps, K)
+        adj.forward(n, ux, uy, Tf)
+        res = adj.backward(*target)
+        assert lat.sync_status()[0] == 0
+        adj.close()
+        lat.close()
+        return res
+
+    mt = run("fp64", hidden)
+    target = (np.ascontiguousarray(mt["ux"]), np.ascontiguousarray(mt["uy"]))
+    l64, g64, _, _ = run("fp64", tau, target)
+    l32, g32, _, _ = run("fp32", tau, target)
+    # the loss is a residual: with |du| <= 1e-5 * 0.05 per cell (the FP32
+    # forward's parity bar on velocities), |l32 - l64| <= 2 sqrt(2 l64 N) |du|
+    bound = 2 * np.sqrt(2 * l64 * L * L) * 1e-5 * 0.05
+    assert abs(l32 - l64) < bound, (l32, l64, bound)
+    g_err = float(np.abs(g32 - g64).max() / np.abs(g64).max())
+    rng = np.random.default_rng(7)
+    d = np.ascontiguousarray(np.cos(2 * np.pi * rng.integers(1, 4) * np.arange(L) / L)[None, :]
+                             * np.ones((L, 1)) * tau)
+    h = 1e-4
+
+    def loss(tf):
+        m = run("fp64", tf)
+        return 0.5 * np.sum((m["ux"] - target[0]) ** 2 + (m["uy"] - target[1]) ** 2)
+
+    fd = (loss(tau + h * d) - loss(tau - h * d)) / (2 * h)
+    ad = float(np.sum(g64 * d))
+    ad32 = float(np.sum(g32 * d))
+    info = dict(fd=fd, ad64=ad, ad32=ad32, g32_vs_g64=g_err, l32=l32, l64=l64)
+    assert abs(ad - fd) < 1e-4 * abs(fd), info
+    assert abs(ad32 - fd) < 1e-4 * abs(fd), info
+    assert g_err < 1e-3, info

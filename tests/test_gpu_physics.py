@@ -1,0 +1,116 @@
+"""Whole-scheme checks of the CUDA path at full size, where the oracle is too
+slow to run alongside: the Chapman-Enskog shear viscosity from the decay of
+the 512^2 Taylor-Green vortex (App. C with the lattice shift of tau by half a
+step, the rate of Sec. 7.1 for a vortex), global conservation of N^0 and
+T^{0a} over the 5000-step Taylor-Green run, and 5000-step parity against the
+oracle on a small grid of the same configuration."""
+import numpy as np
+import pytest
+
+from paper_1909_04502_gb300 import inputs
+from tests.cases import oracle_quadrature, oracle_sim, permutation, rel_linf
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rl():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1909_04502_gb300 import build, rlbm
+    build.build()
+    return rlbm
+
+
+def _tg_amplitude(m, px, py):
+    return float(np.sum(m["ux"] * px + m["uy"] * py) / np.sum(px * px + py * py))
+
+
+def _tg_decay_rate(rl, L, order, stream, lam, tau, u0, t_lo, t_hi, every=50):
+    n, ux, uy, T = [np.ascontiguousarray(a) for a in inputs.taylor_green(L, u0=u0)]
+    px, py = ux / u0, uy / u0
+    lat = rl.Lattice(L, L, order=order, tau=tau, stream=stream, lam=lam, precision="fp32")
+    lat.init(n, ux, uy, T)
+    ts, amps = [], []
+    t = 0
+    while t < t_hi:
+        lat.step(every)
+        t += every
+        if t >= t_lo:
+            ts.append(t)
+            amps.append(_tg_amplitude(lat.moments(), px, py))
+    assert lat.sync_status()[0] == 0
+    lat.close()
+    return -np.polyfit(ts, np.log(amps), 1)[0]
+
+
+@pytest.mark.parametrize("tau", [0.8, 1.0])
+def test_tg512_order3_viscosity_matches_chapman_enskog(rl, tau):
+    """Order-3 massless stencil, on-lattice (delta x = 1/5, k = 10 pi / L):
+    a vortex decays at 2 eta k^2 / (eps + P) with eps + P = 3 P, so
+    eta / P = 3 rate / (2 k^2) must equal (3/4)(tau - 1/2) within 2 %."""
+    L = 512
+    k = 10 * np.pi / L
+    guess = (tau - 0.5) * k * k / 2
+    rate = _tg_decay_rate(rl, L, 3, "onlattice", 0.0, tau, 0.1, int(0.15 / guess), int(1.5 / guess))
+    eta = 3 * rate / (2 * k * k)
+    assert abs(eta / (0.75 * (tau - 0.5)) - 1) < 0.02, eta
+
+
+def test_tg512_bilinear_5000_steps_conserve_N0_and_T0a(rl):
+    """The full config-2 run (FP32 storage, bilinear lambda = 1, tau = 1).
+    The bilinear weights sum to one exactly and the collision conserves N^0
+    and T^{0a} per cell, so the global sums move only by rounding: each step
+    rounds every stored g_i = f_i - f_ref,i to FP32 (relative 2^-24) and
+    forms f^eq from an FP32 H, so a sum of c_i g_i over cells and
+    populations moves by at most 2 * 2^-24 * sum |c_i g_i| per step.  The
+    drift over 5000 steps must stay under that bound (g only decays in this
+    run, so the t = 0 sums bound every step)."""
+    L, steps = 512, 5000
+    fields = [np.ascontiguousarray(a) for a in inputs.taylor_green(L, u0=0.1)]
+    lat = rl.Lattice(L, L, stream="bilinear", lam=1.0, tau=1.0, precision="fp32")
+    lat.init(*fields)
+    d = rl.plan(nx=L, ny=L)
+    p0, w = d["p"][:, 0], d["w"]
+    g = lat.populations() - w[:, None, None]          # f_ref,i = n_ref w_i (rest frame, T_ref = 1)
+    gN = float(np.sum(np.abs(p0[:, None, None] * g)))
+    gT = float(np.sum(np.abs(p0[:, None, None] ** 2 * g)))
+    m0 = lat.moments(full=True)
+    lat.step(steps)
+    m1 = lat.moments(full=True)
+    assert lat.sync_status()[0] == 0
+    dN = abs(m1["N"][0].sum() - m0["N"][0].sum())
+    dT = np.abs(m1["Tab"][:3].sum(axis=(1, 2)) - m0["Tab"][:3].sum(axis=(1, 2)))
+    eps = 2.0 ** -24
+    info = dict(dN0=dN, dT0a=dT.tolist(), N0=m0["N"][0].sum(), T00=m0["Tab"][0].sum(), gN=gN, gT=gT)
+    assert dN <= 2 * steps * eps * gN, info
+    assert dT.max() <= 2 * steps * eps * gT, info
+    # and the drift is far below the FP32 parity bar
+    assert dN <= 1e-6 * m0["N"][0].sum() and dT.max() <= 1e-5 * m0["Tab"][0].sum(), info
+    lat.close()
+
+
+def test_tg_bilinear_fp32_5000_step_parity_small_grid(rl):
+    """The config-2 configuration (bilinear lambda = 1, tau = 1, u0 = 0.1,
+    FP32 storage with the FP64 Landau polish) on a 40 x 40 grid (two tiles
+    wide with a ragged tail) for the full 5000 steps against the FP64 oracle:
+    populations within 1e-5 relative, velocities within 1e-5 of the initial
+    speed."""
+    L = 40
+    fields = [np.ascontiguousarray(a) for a in inputs.taylor_green(L, u0=0.1)]
+    lat = rl.Lattice(L, L, stream="bilinear", lam=1.0, tau=1.0, precision="fp32")
+    d = rl.plan(nx=L, ny=L)
+    quad = oracle_quadrature(0.0, 2, d["n"], d["v0"])
+    idx = permutation(lat.n, lat.p, quad)
+    sim = oracle_sim(quad, L, L, tau=1.0, stream="bilinear", lam=1.0)
+    lat.init(*fields)
+    sim.init(*fields)
+    lat.step(5000)
+    sim.step(5000)
+    assert rel_linf(lat.populations()[idx], sim.fs) <= 1e-5
+    m = lat.moments()
+    for k in ("ux", "uy"):
+        assert np.abs(m[k] - getattr(sim.fields, k)).max() <= 1e-5 * 0.1
+    assert rel_linf(m["n"], sim.fields.n) <= 1e-5 and rel_linf(m["T"], sim.fields.T) <= 1e-5
+    lat.close()
