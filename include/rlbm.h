@@ -65,6 +65,12 @@ enum {
 enum { RLBM_BC_PERIODIC = 0, RLBM_BC_FREEFLOW_X = 1 };
 enum { RLBM_FP64 = 0, RLBM_FP32_STORE = 1 };   /* storage/collision precision    */
 enum { RLBM_ONLATTICE = 0, RLBM_BILINEAR = 1 };
+/* Step kernels (rlbm_set_step_kernel).  Both compute the same update (Sec.
+ * 6.2); they differ in how the pull reads f*: DIRECT loads every tap from
+ * global memory, one cell per thread; TMA_32X8 / TMA_32X4 are persistent
+ * kernels that stage each tile's source rectangles of all populations in
+ * shared memory with tensor copies, two tiles ahead of the arithmetic. */
+enum { RLBM_KERNEL_AUTO = 0, RLBM_KERNEL_DIRECT = 1, RLBM_KERNEL_TMA_32X8 = 2, RLBM_KERNEL_TMA_32X4 = 3 };
 enum { RLBM_TAU_CONST = 0, RLBM_TAU_FIELD = 1, RLBM_TAU_ETA_OVER_S = 2 };
 
 typedef struct rlbm_params {
@@ -129,6 +135,17 @@ int rlbm_set_tau_field(rlbm_handle* h, const double* tau, int on_device);
 
 /* Advance nsteps time steps (asynchronous on the handle's stream). */
 int rlbm_step(rlbm_handle* h, int nsteps);
+
+/* Choose the step kernel (RLBM_KERNEL_*); the TMA-staged kernels need FP32
+ * storage, the massless Q = 28 order-2 stencil and padded rows of at least
+ * 36 elements (RLBM_ERR_UNSUPPORTED otherwise).  AUTO (the default) is
+ * DIRECT, the faster kernel at every grid size measured on GB300.  The kernels evaluate the same
+ * expressions in the same order, so their results are bitwise identical.
+ * No counterpart in the paper. */
+int rlbm_set_step_kernel(rlbm_handle* h, int kernel);
+/* The kernel rlbm_step launches for this handle (RLBM_KERNEL_DIRECT,
+ * _TMA_32X8 or _TMA_32X4), or RLBM_ERR_INVALID_ARG. */
+int rlbm_step_kernel(const rlbm_handle* h);
 
 /* Landau-frame fields of f(t) (steps 1-4 of Sec. 6.2).  Every output is
  * nullable; n, ux, uy, T, eps: nx*ny FP64; Nab: 3*nx*ny (N^0, N^x, N^y

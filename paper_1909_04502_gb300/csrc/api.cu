@@ -123,6 +123,54 @@ void compute_layout(const Quadrature& q, const rlbm_params& p, size_t elem, Scal
 // Rounding each weight on its own leaves the sum off by up to a few units in
 // the last place, which multiplies the streamed populations by that factor
 // every step and drifts the global sums of N^0 and T^{0a}.
+// True when the kernels' orbit-symmetric evaluation applies: the built-in
+// massless stencil (Q = 28 or 44) in orbit order (setup.cpp), every member's
+// momentum the signed / swapped image of its orbit's first member, and every
+// row of H exactly the first row with the matching column signs and (for a
+// swapped member) swapped columns; the (p, 0) rows without py-odd entries.
+bool orbit_symmetric(const rlbm_handle* h) {
+  const Quadrature& q = h->q;
+  if (h->p.quadrature != RLBM_QUAD_MASSLESS || q.m != 0.0) return false;
+  int n8, n4;
+  if (q.Q == 28 && h->K == 9) { n8 = 3; n4 = 1; }
+  else if (q.Q == 44 && h->K == 16) { n8 = 4; n4 = 3; }
+  else return false;
+  const int K = h->K;
+  auto row = [&](int i, int k) { return h->H[(size_t)i * K + k]; };
+  auto check = [&](int i0, int i, int sx, int sy, bool swap) {
+    const double bx = swap ? q.py[i0] : q.px[i0], by = swap ? q.px[i0] : q.py[i0];
+    if (q.p0[i] != q.p0[i0] || q.px[i] != sx * bx || q.py[i] != sy * by || q.w[i] != q.w[i0]) return false;
+    for (int k = 0; k < K; ++k) {
+      const double sgn = (mono_ax(k) && sx < 0 ? -1.0 : 1.0) * (mono_ay(k) && sy < 0 ? -1.0 : 1.0);
+      if (row(i, k) != sgn * row(i0, swap ? mono_swap(k) : k)) return false;
+    }
+    return true;
+  };
+  const int sg[4][2] = {{1, 1}, {-1, 1}, {1, -1}, {-1, -1}};
+  for (int o = 0; o < n8; ++o)
+    for (int m = 0; m < 8; ++m)
+      if (!check(8 * o, 8 * o + m, sg[m & 3][0], sg[m & 3][1], m >= 4)) return false;
+  for (int o = 0; o < n4; ++o) {
+    const int i0 = 8 * n8 + 4 * o;
+    if (q.py[i0] != 0.0) return false;
+    for (int k = 0; k < K; ++k)
+      if (mono_ay(k) && row(i0, k) != 0.0) return false;
+    const int sgn4[4][3] = {{1, 1, 0}, {-1, 1, 0}, {1, 1, 1}, {1, -1, 1}};   // (sx, sy, swap)
+    for (int m = 0; m < 4; ++m)
+      if (!check(i0, i0 + m, sgn4[m][0], sgn4[m][1], sgn4[m][2] != 0)) return false;
+  }
+  return true;
+}
+
+// Step kernel a handle uses: the caller's choice, else the direct-load
+// kernel (on GB300 the TMA-staged kernels are slower at every grid size: the
+// shared-memory stages cut residency from 32 to 16-24 warps per SM, and the
+// collision's FP64 chains need those warps more than the pull needs staging).
+int effective_step_kernel(const rlbm_handle* h) {
+  if (h->step_kernel != RLBM_KERNEL_AUTO) return h->step_kernel;
+  return RLBM_KERNEL_DIRECT;
+}
+
 template <typename R>
 void quantize_unit_sum(const double (&w)[4], R (&out)[4]) {
   const int bits = sizeof(R) == 4 ? 24 : 52;
@@ -335,6 +383,7 @@ int rlbm_create(const rlbm_params* p, rlbm_handle** out) {
   s.Tii_ref = nr * Tr;
   s.kappa_guess = (float)(Tr * (m + Tr) / (m * m + 2.0 * m * Tr + 2.0 * Tr * Tr));
   finish_scalars(&s);
+  s.sym = orbit_symmetric(h.get()) ? 1 : 0;
   if ((long long)h->q.Q * s.plane >= (1LL << 31))
     return fail(nullptr, RLBM_ERR_UNSUPPORTED, "grid too large: Q * plane must stay below 2^31 elements");
   // reference populations f_ref,i = sum_k H_ik M_k(n_ref, e0, T_ref)
@@ -372,6 +421,17 @@ int rlbm_create(const rlbm_params* p, rlbm_handle** out) {
   cudaMemset(h->buf[1], 0, pop_bytes);
   cudaMemset(h->status, 0, 2 * sizeof(unsigned long long));
   cudaMemcpy(h->fref_dev, h->fref.data(), h->q.Q * sizeof(double), cudaMemcpyHostToDevice);
+  // tensor maps for the TMA-staged step kernel (where it applies)
+  if (tma_supported(h.get())) {
+    std::unique_ptr<TmaMaps> maps(new TmaMaps());
+    const int mode = p->stream_mode == RLBM_BILINEAR ? kBilinear : kOnLattice;
+    bool ok = true;
+    std::string why;
+    for (int b = 0; b < 2 && ok; ++b)
+      for (int v = 0; v < 2 && ok; ++v)
+        ok = tma_encode(h.get(), h->buf[b], tma_box_rows(mode, v == 0 ? 8 : 4), &maps->m[b][v], &why);
+    if (ok) h->tma = std::move(maps);
+  }
   e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return fail(nullptr, RLBM_ERR_CUDA, cudaGetErrorString(e));
   *out = h.release();
@@ -458,6 +518,17 @@ int rlbm_set_tau_field(rlbm_handle* h, const double* tau, int on_device) {
   return RLBM_OK;
 }
 
+int rlbm_set_step_kernel(rlbm_handle* h, int kernel) {
+  if (!h || kernel < RLBM_KERNEL_AUTO || kernel > RLBM_KERNEL_TMA_32X4) return RLBM_ERR_INVALID_ARG;
+  if ((kernel == RLBM_KERNEL_TMA_32X8 || kernel == RLBM_KERNEL_TMA_32X4) && !h->tma)
+    return fail(h, RLBM_ERR_UNSUPPORTED, "the TMA-staged kernel needs FP32 storage, the massless Q = 28 order-2 "
+                                         "stencil and a padded row of at least 36 elements");
+  h->step_kernel = kernel;
+  return RLBM_OK;
+}
+
+int rlbm_step_kernel(const rlbm_handle* h) { return h ? effective_step_kernel(h) : RLBM_ERR_INVALID_ARG; }
+
 int rlbm_step(rlbm_handle* h, int nsteps) {
   if (!h || nsteps < 0) return RLBM_ERR_INVALID_ARG;
   const int mode = h->p.stream_mode == RLBM_BILINEAR ? kBilinear : kOnLattice;
@@ -466,7 +537,12 @@ int rlbm_step(rlbm_handle* h, int nsteps) {
     if (h->elem == 4) {
       StepArgs<float> a{h->sc, (const float*)h->buf[h->cur], (float*)h->buf[h->cur ^ 1],
                         (const float*)h->tau_field, h->status};
-      e = launch_step<float>(*h->tf, a, mode, h->stream);
+      const int k = effective_step_kernel(h);
+      if (k == RLBM_KERNEL_TMA_32X8 || k == RLBM_KERNEL_TMA_32X4)
+        e = launch_step_tma(*h->tf, a, mode, k == RLBM_KERNEL_TMA_32X8 ? 8 : 4,
+                            h->tma->m[h->cur][k == RLBM_KERNEL_TMA_32X8 ? 0 : 1], h->stream);
+      else
+        e = launch_step<float>(*h->tf, a, mode, h->stream);
     } else {
       StepArgs<double> a{h->sc, (const double*)h->buf[h->cur], (double*)h->buf[h->cur ^ 1],
                          (const double*)h->tau_field, h->status};
@@ -644,6 +720,7 @@ int rlbm_internal_prepare(const rlbm_params* p, Scalars* sc, Tables<float>* tf, 
   s.Tii_ref = nr * Tr;
   s.kappa_guess = (float)(Tr * (m + Tr) / (m * m + 2.0 * m * Tr + 2.0 * Tr * Tr));
   finish_scalars(&s);
+  s.sym = orbit_symmetric(&h) ? 1 : 0;
   if ((long long)h.q.Q * s.plane >= (1LL << 31)) {
     *err = "grid too large: Q * plane must stay below 2^31 elements";
     return RLBM_ERR_UNSUPPORTED;

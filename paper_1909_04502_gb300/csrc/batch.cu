@@ -107,7 +107,7 @@ __device__ __forceinline__ void batch_tile(const BatchInst& I, int tile, int ste
   const float* fin = I.buf[c];
   float* fout = I.buf[c ^ 1];
   if constexpr (KIND == kKindMassless)
-    cell_update<float, 28, true, 9, kOnLattice, true, false>(c_btab[KIND], I.s, fin, fout, I.tau_field, I.status, x, y);
+    cell_update<float, 28, true, 9, kOnLattice, true, false, true>(c_btab[KIND], I.s, fin, fout, I.tau_field, I.status, x, y);
   else if constexpr (KIND == kKindQ33)
     cell_update<float, 33, true, 9, kOnLattice, true, false>(c_btab[KIND], I.s, fin, fout, I.tau_field, I.status, x, y);
   else if constexpr (KIND == kKindQ25)
@@ -115,7 +115,7 @@ __device__ __forceinline__ void batch_tile(const BatchInst& I, int tile, int ste
   else if constexpr (KIND == kKindQ29)
     cell_update<float, 29, true, 9, kOnLattice, true, false>(c_btab[KIND], I.s, fin, fout, I.tau_field, I.status, x, y);
   else
-    cell_update<float, 28, true, 9, kBilinear, true, false>(c_btab[KIND], I.s, fin, fout, I.tau_field, I.status, x, y);
+    cell_update<float, 28, true, 9, kBilinear, true, false, true>(c_btab[KIND], I.s, fin, fout, I.tau_field, I.status, x, y);
 }
 
 // One persistent kernel per stencil kind: a kernel compiled for a single
@@ -189,10 +189,10 @@ int batch_fail(rlbm_batch* b, int code, const std::string& msg) {
 int kind_of(const rlbm_handle* h, int* kind) {
   if (h->p.precision != RLBM_FP32_STORE || h->p.order != 2 || h->p.tau_mode == RLBM_TAU_FIELD) return -1;
   if (h->p.stream_mode == RLBM_BILINEAR) {
-    if (h->q.Q == 28 && h->p.m == 0.0) { *kind = kKindMasslessBilinear; return 0; }
+    if (h->q.Q == 28 && h->sc.sym) { *kind = kKindMasslessBilinear; return 0; }
     return -1;
   }
-  if (h->p.m == 0.0 && h->q.Q == 28) { *kind = kKindMassless; return 0; }
+  if (h->q.Q == 28 && h->sc.sym) { *kind = kKindMassless; return 0; }
   if (h->q.Q == 33) { *kind = kKindQ33; return 0; }
   if (h->q.Q == 25) { *kind = kKindQ25; return 0; }
   if (h->q.Q == 29) { *kind = kKindQ29; return 0; }

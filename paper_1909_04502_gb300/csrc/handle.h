@@ -9,6 +9,7 @@
 #include "../../include/rlbm.h"
 #include "kernels.cuh"
 #include "setup.h"
+#include "step_tma.h"
 
 struct rlbm_handle {
   rlbm_params p;                 // copy of the creation parameters (pointers cleared)
@@ -29,6 +30,8 @@ struct rlbm_handle {
   double* fref_dev = nullptr;    // fref on the device
   double* staging = nullptr;     // Q x ncell FP64 staging (lazy)
   cudaStream_t stream = nullptr;
+  std::unique_ptr<rlbm::TmaMaps> tma;   // tensor maps of buf[0], buf[1] (TMA-staged kernel), or null
+  int step_kernel = 0;           // RLBM_KERNEL_* requested by the caller (0: automatic)
   long long t = 0;
   std::string err = "no error";
 };

@@ -55,10 +55,25 @@ struct Scalars {
   double PE_ref;           // P_ref + eps_ref
   float kappa_guess;       // P/eps of the reference EOS, for the FP32 first guess
   int massless;            // m == 0
+  int sym;                 // built-in massless stencil in orbit order with exactly symmetric H
   int iplane;              // plane as int (Q * plane < 2^31 is checked at creation)
   // FP32 copies of the scalars used by the FP32-storage kernels
   float f_tau, f_tau_coef, f_m, f_n_ref, f_T_ref, f_T00_ref, f_Tii_ref;
 };
+
+// Parity of the px and py exponents of basis monomial k of setup.h
+// (1 | p0 px py | p0px p0py pxpx pxpy pypy | p0pxpx p0pxpy p0pypy pxpxpx
+// pxpxpy pxpypy pypypy), and the monomial with the two exponents exchanged.
+__host__ __device__ constexpr int mono_ax(int k) {
+  return (k == 2 || k == 4 || k == 7 || k == 10 || k == 12 || k == 14) ? 1 : 0;
+}
+__host__ __device__ constexpr int mono_ay(int k) {
+  return (k == 3 || k == 5 || k == 7 || k == 10 || k == 13 || k == 15) ? 1 : 0;
+}
+__host__ __device__ constexpr int mono_swap(int k) {
+  return k == 2 ? 3 : k == 3 ? 2 : k == 4 ? 5 : k == 5 ? 4 : k == 6 ? 8 : k == 8 ? 6 : k == 9 ? 11 : k == 11 ? 9
+       : k == 12 ? 15 : k == 15 ? 12 : k == 13 ? 14 : k == 14 ? 13 : k;
+}
 
 // Storage index of interior cell (x, y).
 __host__ __device__ __forceinline__ long long sidx(const Scalars& s, int x, int y) {

@@ -324,22 +324,27 @@ bool massless_quadrature(int order, Quadrature* q, std::string* err) {
   *q = Quadrature();
   q->m = 0.0;
   q->order = order;
-  const int gens[2][2] = {{3, 4}, {5, 0}};
-  for (int g = 0; g < 2; ++g) {
-    for (auto v : fs_group(gens[g][0], gens[g][1])) {
-      double norm = std::sqrt(double(v.first * v.first + v.second * v.second));
-      for (int j = 0; j < ns; ++j) {
-        double wgt = col[2 * j + (g == 0 ? 1 : 0)];
-        if (wgt == 0.0) continue;
-        q->nx.push_back(v.first);
-        q->ny.push_back(v.second);
-        q->p0.push_back(shells[j]);
-        q->px.push_back(shells[j] * v.first / norm);
-        q->py.push_back(shells[j] * v.second / norm);
-        q->w.push_back(wgt);
-      }
-    }
-  }
+  // Orbit order (the kernels' symmetric evaluation relies on it): for each
+  // shell with weight, the eight images of (3, 4) as two sign quartets
+  // (a, b), (-a, b), (a, -b), (-a, -b) of (3, 4) and of its swap (4, 3);
+  // then for each shell with weight the four images of (5, 0):
+  // (5, 0), (-5, 0), (0, 5), (0, -5).
+  static const int fam8[8][2] = {{3, 4}, {-3, 4}, {3, -4}, {-3, -4}, {4, 3}, {-4, 3}, {4, -3}, {-4, -3}};
+  static const int fam4[4][2] = {{5, 0}, {-5, 0}, {0, 5}, {0, -5}};
+  auto push = [&](int vx, int vy, int j, double wgt) {
+    q->nx.push_back(vx);
+    q->ny.push_back(vy);
+    q->p0.push_back(shells[j]);
+    q->px.push_back(shells[j] * vx / 5.0);
+    q->py.push_back(shells[j] * vy / 5.0);
+    q->w.push_back(wgt);
+  };
+  for (int j = 0; j < ns; ++j)
+    if (col[2 * j + 1] != 0.0)
+      for (auto& v : fam8) push(v[0], v[1], j, col[2 * j + 1]);
+  for (int j = 0; j < ns; ++j)
+    if (col[2 * j] != 0.0)
+      for (auto& v : fam4) push(v[0], v[1], j, col[2 * j]);
   q->Q = (int)q->w.size();
   return true;
 }

@@ -383,18 +383,121 @@ __device__ __forceinline__ void for_each_halo_image(const Scalars& s, int x, int
 // ---------------------------------------------------------------------------
 // Fused step kernel: one thread per cell, 32 x 8 cells per block.
 // ---------------------------------------------------------------------------
-// One cell of the fused step (Sec. 6.2, steps 1-8): pull-gather, moments,
-// Landau solve, equilibrium, relaxation, store (interior and halo images).
-template <typename S, int QT, bool EX, int KT, int MODE, bool DYN = false, bool NC = true>
-__device__ __forceinline__ void cell_update(const Tables<S>& tb, const Scalars& s, const S* __restrict__ fin,
-                                            S* __restrict__ fout, const S* __restrict__ tau_field,
-                                            unsigned long long* status, int x, int y) {
+// ---------------------------------------------------------------------------
+// Orbit-symmetric evaluation for the built-in massless stencils.  Their
+// populations come in orbit order (setup.cpp): per shell of the (3, 4) family
+// two sign quartets, (a, b), (-a, b), (a, -b), (-a, -b) and the same for the
+// swap (b, a); per shell of the (5, 0) family (p, 0), (-p, 0), (0, p), (0, -p).
+// Under a sign flip of px (py) the monomials of odd px (py) degree change sign,
+// and the swap px <-> py permutes them, so
+//   * the moments need per quartet only its sum and its x-, y- and
+//     xy-antisymmetric combinations (butterflies), and
+//   * the equilibrium row of every member is its orbit's first row with
+//     signs and (for the swapped quartet) permuted columns: per quartet the
+//     four parity classes of H_k dM_k are summed once and combined.
+// The host enables this only after checking these identities on H exactly.
+// ---------------------------------------------------------------------------
+template <int QT>
+struct Orbits {
+  static constexpr int n8 = 0, n4 = 0;
+};
+template <>
+struct Orbits<28> {   // order 2: 3 shells x 8 + 1 shell x 4
+  static constexpr int n8 = 3, n4 = 1;
+};
+template <>
+struct Orbits<44> {   // order 3: 4 shells x 8 + 3 shells x 4
+  static constexpr int n8 = 4, n4 = 3;
+};
+
+template <typename S, int QT>
+__device__ __forceinline__ void moments_sym(const Tables<S>& tb, const S (&g)[QT], S (&mm)[9]) {
+  using O = Orbits<QT>;
+#pragma unroll
+  for (int j = 0; j < 9; ++j) mm[j] = S(0);
+#pragma unroll
+  for (int o = 0; o < O::n8; ++o) {
+    const int i = 8 * o;
+    const S u0 = g[i] + g[i + 1], u1 = g[i] - g[i + 1], u2 = g[i + 2] + g[i + 3], u3 = g[i + 2] - g[i + 3];
+    const S v0 = g[i + 4] + g[i + 5], v1 = g[i + 4] - g[i + 5], v2 = g[i + 6] + g[i + 7], v3 = g[i + 6] - g[i + 7];
+    const S SA = u0 + u2, YA = u0 - u2, XA = u1 + u3, XYA = u1 - u3;
+    const S SB = v0 + v2, YB = v0 - v2, XB = v1 + v3, XYB = v1 - v3;
+    const S Sab = SA + SB;
+    // c = p0, a, b, p0^2, p0 a, p0 b, a^2, a b, b^2 of the quartet-A base (a, b)
+    mm[0] = fma(tb.c[i][0], Sab, mm[0]);
+    mm[1] = fma(tb.c[i][1], XA, fma(tb.c[i][2], XB, mm[1]));
+    mm[2] = fma(tb.c[i][2], YA, fma(tb.c[i][1], YB, mm[2]));
+    mm[3] = fma(tb.c[i][3], Sab, mm[3]);
+    mm[4] = fma(tb.c[i][4], XA, fma(tb.c[i][5], XB, mm[4]));
+    mm[5] = fma(tb.c[i][5], YA, fma(tb.c[i][4], YB, mm[5]));
+    mm[6] = fma(tb.c[i][6], SA, fma(tb.c[i][8], SB, mm[6]));
+    mm[7] = fma(tb.c[i][7], XYA + XYB, mm[7]);
+    mm[8] = fma(tb.c[i][8], SA, fma(tb.c[i][6], SB, mm[8]));
+  }
+#pragma unroll
+  for (int o = 0; o < O::n4; ++o) {
+    const int i = 8 * O::n8 + 4 * o;
+    const S S1 = g[i] + g[i + 1], D1 = g[i] - g[i + 1], S2 = g[i + 2] + g[i + 3], D2 = g[i + 2] - g[i + 3];
+    const S Sab = S1 + S2;
+    // c = p0, p, 0, p0^2, p0 p, 0, p^2, 0, 0 of the base (p, 0)
+    mm[0] = fma(tb.c[i][0], Sab, mm[0]);
+    mm[1] = fma(tb.c[i][1], D1, mm[1]);
+    mm[2] = fma(tb.c[i][1], D2, mm[2]);
+    mm[3] = fma(tb.c[i][3], Sab, mm[3]);
+    mm[4] = fma(tb.c[i][4], D1, mm[4]);
+    mm[5] = fma(tb.c[i][4], D2, mm[5]);
+    mm[6] = fma(tb.c[i][6], S1, mm[6]);
+    mm[8] = fma(tb.c[i][6], S2, mm[8]);
+  }
+}
+
+// f^eq - f_ref of the eight members of the (a, b) orbit whose first row is h.
+template <typename S, int KT>
+__device__ __forceinline__ void feq_orbit8(const S (&h)[kMaxK], const S (&dM)[KT], S (&f)[8]) {
+  S E = S(0), OX = S(0), OY = S(0), OXY = S(0), Eb = S(0), OXb = S(0), OYb = S(0), OXYb = S(0);
+#pragma unroll
+  for (int k = 0; k < KT; ++k) {
+    const int ax = mono_ax(k), ay = mono_ay(k);
+    const S t = dM[mono_swap(k)];
+    if (!ax && !ay) { E = fma(h[k], dM[k], E); Eb = fma(h[k], t, Eb); }
+    else if (ax && !ay) { OX = fma(h[k], dM[k], OX); OYb = fma(h[k], t, OYb); }
+    else if (!ax && ay) { OY = fma(h[k], dM[k], OY); OXb = fma(h[k], t, OXb); }
+    else { OXY = fma(h[k], dM[k], OXY); OXYb = fma(h[k], t, OXYb); }
+  }
+  // member (sx, sy): E + sx OX + sy OY + sx sy OXY, order (+,+), (-,+), (+,-), (-,-)
+  const S A = E + OXY, B = E - OXY, C = OX + OY, D = OX - OY;
+  f[0] = A + C; f[1] = B - D; f[2] = B + D; f[3] = A - C;
+  const S Ab = Eb + OXYb, Bb = Eb - OXYb, Cb = OXb + OYb, Db = OXb - OYb;
+  f[4] = Ab + Cb; f[5] = Bb - Db; f[6] = Bb + Db; f[7] = Ab - Cb;
+}
+
+// ... and of the four members (p, 0), (-p, 0), (0, p), (0, -p) (the row of
+// (p, 0) has no py-odd entries).
+template <typename S, int KT>
+__device__ __forceinline__ void feq_orbit4(const S (&h)[kMaxK], const S (&dM)[KT], S (&f)[4]) {
+  S E = S(0), OX = S(0), Eb = S(0), OYb = S(0);
+#pragma unroll
+  for (int k = 0; k < KT; ++k) {
+    const int ax = mono_ax(k), ay = mono_ay(k);
+    if (ay) continue;
+    const S t = dM[mono_swap(k)];
+    if (!ax) { E = fma(h[k], dM[k], E); Eb = fma(h[k], t, Eb); }
+    else { OX = fma(h[k], dM[k], OX); OYb = fma(h[k], t, OYb); }
+  }
+  f[0] = E + OX; f[1] = E - OX; f[2] = Eb + OYb; f[3] = Eb - OYb;
+}
+
+// Steps 2-8 of one cell from its streamed populations g: moments, Landau
+// solve, equilibrium, relaxation, store (interior and halo images).
+template <typename S, int QT, bool EX, int KT, bool SYM = false>
+__device__ __forceinline__ void collide_store(const Tables<S>& tb, const Scalars& s, S (&g)[QT],
+                                              S* __restrict__ fout, const S* __restrict__ tau_field,
+                                              unsigned long long* status, int x, int y) {
   const long long si = sidx(s, x, y);
   const int Qn = EX ? QT : s.Q;
-  S g[QT];
-  gather<S, QT, EX, MODE, DYN, NC>(tb, s, fin, si, g);
   S mm[9];
-  moments9<S, QT, EX>(tb, s.Q, g, mm);
+  if constexpr (SYM) moments_sym<S, QT>(tb, g, mm);
+  else moments9<S, QT, EX>(tb, s.Q, g, mm);
   const Macro M = landau<S>(s, mm);
   if (!M.ok) atomicAdd(status, 1ULL);
   S dM[KT];
@@ -405,16 +508,37 @@ __device__ __forceinline__ void cell_update(const Tables<S>& tb, const Scalars& 
   else { U0 = M.U0; Ux = M.Ux; Uy = M.Uy; }
   const S keep = M.ok ? S(1) : S(0);
   S* __restrict__ obase = fout + si;
+  // step 8: Omega_i = p_i.U / (p_i^0 tau) = (U^0 - v_i . U) / tau
+  auto relax = [&](int i, S feq) {
+    const S om = keep * (U0 - Ux * tb.vx[i] - Uy * tb.vy[i]) * inv_tau;
+    g[i] = fma(om, feq - g[i], g[i]);
+    obase[i * s.iplane] = g[i];
+  };
+  if constexpr (SYM) {
+    using O = Orbits<QT>;
 #pragma unroll
-  for (int i = 0; i < QT; ++i) {
-    if (i < Qn) {
-      S feq = S(0);
+    for (int o = 0; o < O::n8; ++o) {
+      S f[8];
+      feq_orbit8<S, KT>(tb.H[8 * o], dM, f);
 #pragma unroll
-      for (int k = 0; k < KT; ++k) feq = fma(tb.H[i][k], dM[k], feq);
-      // step 8: Omega_i = p_i.U / (p_i^0 tau) = (U^0 - v_i . U) / tau
-      const S om = keep * (U0 - Ux * tb.vx[i] - Uy * tb.vy[i]) * inv_tau;
-      g[i] = fma(om, feq - g[i], g[i]);
-      obase[i * s.iplane] = g[i];
+      for (int m = 0; m < 8; ++m) relax(8 * o + m, f[m]);
+    }
+#pragma unroll
+    for (int o = 0; o < O::n4; ++o) {
+      S f[4];
+      feq_orbit4<S, KT>(tb.H[8 * O::n8 + 4 * o], dM, f);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) relax(8 * O::n8 + 4 * o + m, f[m]);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < QT; ++i) {
+      if (i < Qn) {
+        S feq = S(0);
+#pragma unroll
+        for (int k = 0; k < KT; ++k) feq = fma(tb.H[i][k], dM[k], feq);
+        relax(i, feq);
+      }
     }
   }
   for_each_halo_image(s, x, y, [&](long long hi) {
@@ -425,15 +549,27 @@ __device__ __forceinline__ void cell_update(const Tables<S>& tb, const Scalars& 
   });
 }
 
+// One cell of the fused step (Sec. 6.2, steps 1-8): pull-gather from global
+// memory, then collide_store.
+template <typename S, int QT, bool EX, int KT, int MODE, bool DYN = false, bool NC = true, bool SYM = false>
+__device__ __forceinline__ void cell_update(const Tables<S>& tb, const Scalars& s, const S* __restrict__ fin,
+                                            S* __restrict__ fout, const S* __restrict__ tau_field,
+                                            unsigned long long* status, int x, int y) {
+  S g[QT];
+  gather<S, QT, EX, MODE, DYN, NC>(tb, s, fin, sidx(s, x, y), g);
+  collide_store<S, QT, EX, KT, SYM>(tb, s, g, fout, tau_field, status, x, y);
+}
+
 // FP32 storage: four 256-thread blocks per SM (at most 64 registers per
 // thread) -- the FP64 polish and the gather latency need the resident warps.
-template <typename S, int QT, bool EX, int KT, int MODE>
+// SYM: orbit-symmetric moments and equilibrium (built-in massless stencils).
+template <typename S, int QT, bool EX, int KT, int MODE, bool SYM>
 __global__ void __launch_bounds__(kThreads, (sizeof(S) == 4 && QT <= 40) ? 4 : 2) k_step(const __grid_constant__ Tables<S> tb,
                                                    const __grid_constant__ StepArgs<S> a) {
   const int x = blockIdx.x * kBX + threadIdx.x;
   const int y = blockIdx.y * kBY + threadIdx.y;
   if (x >= a.s.nx || y >= a.s.ny) return;
-  cell_update<S, QT, EX, KT, MODE>(tb, a.s, a.fin, a.fout, a.tau_field, a.status, x, y);
+  cell_update<S, QT, EX, KT, MODE, false, true, SYM>(tb, a.s, a.fin, a.fout, a.tau_field, a.status, x, y);
 }
 
 // Fields of f(t) (steps 1-4), optionally the raw moments.  Output planes are
@@ -511,10 +647,10 @@ inline dim3 block_dim() { return dim3(kBX, kBY); }
 
 // QT: population count of the instantiation; EX: the stencil has exactly QT
 // populations (no per-population bounds test), otherwise Q <= QT at run time.
-template <typename S, int QT, bool EX, int KT>
+template <typename S, int QT, bool EX, int KT, bool SYM = false>
 cudaError_t launch_step_q(const Tables<S>& tb, const StepArgs<S>& a, int mode, cudaStream_t st) {
-  if (mode == kOnLattice) k_step<S, QT, EX, KT, kOnLattice><<<grid_for(a.s), block_dim(), 0, st>>>(tb, a);
-  else k_step<S, QT, EX, KT, kBilinear><<<grid_for(a.s), block_dim(), 0, st>>>(tb, a);
+  if (mode == kOnLattice) k_step<S, QT, EX, KT, kOnLattice, SYM><<<grid_for(a.s), block_dim(), 0, st>>>(tb, a);
+  else k_step<S, QT, EX, KT, kBilinear, SYM><<<grid_for(a.s), block_dim(), 0, st>>>(tb, a);
   return cudaGetLastError();
 }
 

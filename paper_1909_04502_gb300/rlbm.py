@@ -59,6 +59,8 @@ SIGNATURES = {
     "rlbm_init": (ctypes.c_int, [_H, _VP, _VP, _VP, _VP, ctypes.c_int]),
     "rlbm_set_tau_field": (ctypes.c_int, [_H, _VP, ctypes.c_int]),
     "rlbm_step": (ctypes.c_int, [_H, ctypes.c_int]),
+    "rlbm_set_step_kernel": (ctypes.c_int, [_H, ctypes.c_int]),
+    "rlbm_step_kernel": (ctypes.c_int, [_H]),
     "rlbm_moments": (ctypes.c_int, [_H, _VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_int]),
     "rlbm_get_populations": (ctypes.c_int, [_H, _VP, ctypes.c_int]),
     "rlbm_set_populations": (ctypes.c_int, [_H, _VP, ctypes.c_int]),
@@ -265,6 +267,17 @@ class Lattice:
 
     def step(self, nsteps=1):
         _check(lib().rlbm_step(self.h, int(nsteps)), self.h)
+
+    KERNELS = {"auto": 0, "direct": 1, "tma_32x8": 2, "tma_32x4": 3}
+
+    def set_step_kernel(self, kernel):
+        """'auto', 'direct', 'tma_32x8' or 'tma_32x4' (rlbm_set_step_kernel)."""
+        _check(lib().rlbm_set_step_kernel(self.h, self.KERNELS[kernel]), self.h)
+
+    @property
+    def step_kernel(self):
+        k = lib().rlbm_step_kernel(self.h)
+        return {v: n for n, v in self.KERNELS.items()}[k]
 
     def moments(self, full=False, out=None):
         """Fields of f(t) as numpy arrays (ny, nx) (host copy), or written into

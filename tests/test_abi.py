@@ -129,3 +129,37 @@ def test_builtin_massive_quadratures_exist_for_sweep_masses(rl):
     for m in (1.0, 10.0):
         d = rl.plan(nx=8, ny=8, m=m)
         assert d["Q"] <= 40 and np.all(d["w"] > 0) and abs(d["w"].sum() - 1) < 1e-12
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_massless_tables_are_in_orbit_order_with_exactly_symmetric_H(rl, order):
+    """The built-in massless stencil comes in orbit order: per (3, 4) shell the
+    sign quartets of (a, b) and of (b, a), per (5, 0) shell (p, 0), (-p, 0),
+    (0, p), (0, -p); every H row equals its orbit's first row with the column
+    signs of the flips and, for the swapped members, px <-> py exchanged
+    columns -- exactly (the kernels evaluate moments and equilibrium from the
+    first rows only)."""
+    d = rl.plan(nx=16, ny=16, order=order)
+    Q, K, p, H = d["Q"], d["K"], d["p"], d["H"]
+    basis = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, 0, 1), (0, 2, 0), (0, 1, 1), (0, 0, 2),
+             (1, 2, 0), (1, 1, 1), (1, 0, 2), (0, 3, 0), (0, 2, 1), (0, 1, 2), (0, 0, 3)][:K]
+    swap = [basis.index((e, b, a)) for (e, a, b) in basis]
+    n8, n4 = (3, 1) if order == 2 else (4, 3)
+    assert Q == 8 * n8 + 4 * n4
+
+    def image(i0, sx, sy, sw):
+        bx, by = (p[i0, 2], p[i0, 1]) if sw else (p[i0, 1], p[i0, 2])
+        sgn = np.array([sx ** a * sy ** b for (_, a, b) in basis], dtype=float)
+        row = H[i0][swap] if sw else H[i0]
+        return np.array([p[i0, 0], sx * bx, sy * by]), sgn * row
+
+    members8 = [(1, 1, 0), (-1, 1, 0), (1, -1, 0), (-1, -1, 0), (1, 1, 1), (-1, 1, 1), (1, -1, 1), (-1, -1, 1)]
+    members4 = [(1, 1, 0), (-1, 1, 0), (1, 1, 1), (1, -1, 1)]
+    for o in range(n8 + n4):
+        i0 = 8 * o if o < n8 else 8 * n8 + 4 * (o - n8)
+        for m, (sx, sy, sw) in enumerate(members8 if o < n8 else members4):
+            pm, row = image(i0, sx, sy, sw)
+            assert np.array_equal(p[i0 + m], pm), (o, m)
+            assert np.array_equal(H[i0 + m], row), (o, m)
+        if o >= n8:
+            assert p[i0, 2] == 0.0 and all(H[i0][k] == 0.0 for k, (_, a, b) in enumerate(basis) if b % 2)
