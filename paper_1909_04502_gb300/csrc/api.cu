@@ -217,6 +217,9 @@ void fill_tables(const rlbm_handle* h, const Scalars& s, Tables<R>* t) {
                            phi[0] * phi[1]};
       quantize_unit_sum<R>(w, t->bw[i]);
     }
+    t->pl[i] = i * (int)s.plane;
+    t->offp[i] = t->pl[i] + t->off[i];
+    t->offr[i] = t->offp[i] + s.pitch;
   }
 }
 

@@ -81,14 +81,15 @@ __device__ __forceinline__ void gather(const Tables<S>& tb, const Scalars& s,
   for (int i = 0; i < QT; ++i) {
     g[i] = S(0);
     if (i < Qn) {
-      const int o = i * s.iplane + (DYN ? (int)tb.dy[i] * s.pitch + (int)tb.dx[i] : tb.off[i]);
+      const int o = DYN ? i * s.iplane + (int)tb.dy[i] * s.pitch + (int)tb.dx[i] : tb.offp[i];
       if constexpr (MODE == kOnLattice) {
         g[i] = ld<S, NC>(base + o);
       } else {
+        const int o2 = DYN ? o + s.pitch : tb.offr[i];
         S v = tb.bw[i][0] * ld<S, NC>(base + o);
         v = fma(tb.bw[i][1], ld<S, NC>(base + o + 1), v);
-        v = fma(tb.bw[i][2], ld<S, NC>(base + o + s.pitch), v);
-        v = fma(tb.bw[i][3], ld<S, NC>(base + o + s.pitch + 1), v);
+        v = fma(tb.bw[i][2], ld<S, NC>(base + o2), v);
+        v = fma(tb.bw[i][3], ld<S, NC>(base + o2 + 1), v);
         g[i] = v;
       }
     }
@@ -187,6 +188,8 @@ __device__ __forceinline__ Macro landau_fp64(const Scalars& sc, const double (&m
 // and U = v / nu only needs FP32 accuracy.  About 24 FP64 operations per
 // cell.  The moments are reference + FP32 sums of g, and the eigenvalue is
 // written l = eps_ref + delta.
+// ML: 1 massless (known at compile time), -1 decided by sc.massless.
+template <int ML = -1>
 __device__ __forceinline__ Macro landau_fp32(const Scalars& sc, const float (&mm)[9]) {
   const float epsr = sc.f_T00_ref;
   const float Pr = sc.f_Tii_ref;
@@ -229,7 +232,11 @@ __device__ __forceinline__ Macro landau_fp32(const Scalars& sc, const float (&mm
   // first-order shift of v, w, nu^2 to the corrected root (v is quadratic in l
   // with a unit second derivative in v0 only: the remainder is O(dl^2))
   const float bc = b + c;
-  const float fD = d2f(D), fvx = d2f(vx), fvy = d2f(vy), fN0 = d2f(N0);
+  // FP32 copies of v and N^0 for the FP32 outputs, evaluated in FP32 at the
+  // same root (D ~ (P + eps)^2 and the leading terms of vx, vy do not cancel)
+  const float fb = PE + mm[6] + del, fc = PE + mm[8] + del;
+  const float fD = fb * fc - fr * fr, fvx = fs * fc - fr * ft, fvy = ft * fb - fr * fs;
+  const float fN0 = sc.f_n_ref + mm[0];
   const float dw = dl * (bc * fN0 - fs * fNx - ft * fNy);
   const float dnu2 = 2.f * dl * (fD * bc - fvx * fs - fvy * ft);
   const double wc = w + f2d(dw);
@@ -249,7 +256,7 @@ __device__ __forceinline__ Macro landau_fp32(const Scalars& sc, const float (&mm
   M.fdn = __fdividef(d2f(num), fnu * (fw + nr * fnu));
   const float deps = del + dl;                          // eps - eps_ref
   const float fn = M.fn, fm = sc.f_m, fTr = sc.f_T_ref;
-  if (sc.massless) {
+  if (ML == 1 || (ML == -1 && sc.massless)) {
     // eps = 2 n T with eps_ref = 2 n_ref T_ref:  dT = (d_eps - 2 T_ref dn) / (2 n)
     M.fdT = __fdividef(deps - 2.f * fTr * M.fdn, 2.f * fn);
   } else if (sc.n_ref > 0.0) {
@@ -287,13 +294,21 @@ __device__ __forceinline__ Macro landau_fp32(const Scalars& sc, const float (&mm
 //   r2 = (m^2 + 3mT + 3T^2)/(m+T), r3 = (m^3 + 6m^2 T + 15 m T^2 + 15 T^3)/(m+T).
 // The differences from the reference are rearranged so that the result is
 // accurate relative to dM itself given accurate dn = n - n_ref and dT = T - T_ref.
+// Quotient: the FP32 path uses the fast reciprocal-based division (2 ulp,
+// no special-case branches), the FP64 path the IEEE one.
+template <typename S>
+__device__ __forceinline__ S qdiv(S a, S b) {
+  if constexpr (sizeof(S) == 4) return __fdividef(a, b);
+  else return a / b;
+}
+
 template <typename S, int KT>
 __device__ __forceinline__ void eq_moments(S dn, S dT, S n, S T, S U0, S Ux, S Uy, S m, S nr, S Tr,
                                            S (&dM)[KT]) {
-  const S U0m1 = (Ux * Ux + Uy * Uy) / (U0 + S(1));
+  const S U0m1 = qdiv(Ux * Ux + Uy * Uy, U0 + S(1));
   const S mT = m + T, mTr = m + Tr;
-  const S r2 = (m * m + S(3) * m * T + S(3) * T * T) / mT;
-  const S D1 = (dn * mTr - nr * dT) / (mT * mTr);
+  const S r2 = qdiv(m * m + S(3) * m * T + S(3) * T * T, mT);
+  const S D1 = qdiv(dn * mTr - nr * dT, mT * mTr);
   const S D2 = dn * U0 + nr * U0m1;
   const S D3 = dn * T + nr * dT;
   const S nr2 = n * r2;
@@ -308,10 +323,10 @@ __device__ __forceinline__ void eq_moments(S dn, S dT, S n, S T, S U0, S Ux, S U
   dM[8] = nr2 * Uy * Uy + D3;
   if constexpr (KT == 16) {
     const S q2 = T * r2;
-    const S r3 = (m * m * m + S(6) * m * m * T + S(15) * m * T * T + S(15) * T * T * T) / mT;
+    const S r3 = qdiv(m * m * m + S(6) * m * m * T + S(15) * m * T * T + S(15) * T * T * T, mT);
     const S Nh = dT * (m * (m * m + S(3) * m * (T + Tr) + S(3) * (T * T + T * Tr + Tr * Tr)) +
                        S(3) * T * Tr * (m + T + Tr));
-    const S dh = Nh / (mT * mTr);
+    const S dh = qdiv(Nh, mT * mTr);
     const S D4 = dn * q2 * U0 + nr * (q2 * U0m1 + dh);
     const S nr3 = n * r3, nq2 = n * q2;
     dM[9] = nr3 * U0 * Ux * Ux + D4;
@@ -334,9 +349,9 @@ __device__ __forceinline__ void eq_moments_of(const Scalars& sc, const Macro& M,
   }
 }
 
-template <typename S>
+template <typename S, int ML = -1>
 __device__ __forceinline__ Macro landau(const Scalars& sc, const S (&mm)[9]) {
-  if constexpr (sizeof(S) == 4) return landau_fp32(sc, mm);
+  if constexpr (sizeof(S) == 4) return landau_fp32<ML>(sc, mm);
   else return landau_fp64(sc, mm);
 }
 
@@ -489,7 +504,9 @@ __device__ __forceinline__ void feq_orbit4(const S (&h)[kMaxK], const S (&dM)[KT
 
 // Steps 2-8 of one cell from its streamed populations g: moments, Landau
 // solve, equilibrium, relaxation, store (interior and halo images).
-template <typename S, int QT, bool EX, int KT, bool SYM = false>
+// DYN: plane offsets from the run-time plane size (tables shared by grids
+// of different sizes), otherwise from the per-handle table tb.pl.
+template <typename S, int QT, bool EX, int KT, bool SYM = false, bool DYN = false>
 __device__ __forceinline__ void collide_store(const Tables<S>& tb, const Scalars& s, S (&g)[QT],
                                               S* __restrict__ fout, const S* __restrict__ tau_field,
                                               unsigned long long* status, int x, int y) {
@@ -498,37 +515,53 @@ __device__ __forceinline__ void collide_store(const Tables<S>& tb, const Scalars
   S mm[9];
   if constexpr (SYM) moments_sym<S, QT>(tb, g, mm);
   else moments9<S, QT, EX>(tb, s.Q, g, mm);
-  const Macro M = landau<S>(s, mm);
+  const Macro M = landau<S, SYM ? 1 : -1>(s, mm);
   if (!M.ok) atomicAdd(status, 1ULL);
   S dM[KT];
   eq_moments_of<S, KT>(s, M, dM);
-  const S inv_tau = S(1) / local_tau<S>(s, tau_field, y * s.nx + x, M);
+  const S inv_tau = qdiv(S(1), local_tau<S>(s, tau_field, y * s.nx + x, M));
   S U0, Ux, Uy;
   if constexpr (sizeof(S) == 4) { U0 = M.fU0; Ux = M.fUx; Uy = M.fUy; }
   else { U0 = M.U0; Ux = M.Ux; Uy = M.Uy; }
-  const S keep = M.ok ? S(1) : S(0);
+  const S kt = M.ok ? inv_tau : S(0);
   S* __restrict__ obase = fout + si;
-  // step 8: Omega_i = p_i.U / (p_i^0 tau) = (U^0 - v_i . U) / tau
-  auto relax = [&](int i, S feq) {
-    const S om = keep * (U0 - Ux * tb.vx[i] - Uy * tb.vy[i]) * inv_tau;
+  auto plane_of = [&](int i) { return DYN ? i * s.iplane : tb.pl[i]; };
+  // step 8: f* = f + Omega_i (f^eq - f), Omega_i = p_i.U / (p_i^0 tau) = (U^0 - v_i . U) / tau
+  auto relax = [&](int i, S feq, S om) {
     g[i] = fma(om, feq - g[i], g[i]);
-    obase[i * s.iplane] = g[i];
+    obase[plane_of(i)] = g[i];
   };
   if constexpr (SYM) {
     using O = Orbits<QT>;
+    const S U0k = U0 * kt, Uxk = Ux * kt, Uyk = Uy * kt;
+    // Omega of a sign quartet with base velocity (va, vb), members (+,+), (-,+), (+,-), (-,-)
+    auto quartet_om = [&](S va, S vb, S (&om)[4]) {
+      const S X = Uxk * va, Y = Uyk * vb;
+      const S M1 = U0k - Y, M2 = U0k + Y;
+      om[0] = M1 - X; om[1] = M1 + X; om[2] = M2 - X; om[3] = M2 + X;
+    };
 #pragma unroll
     for (int o = 0; o < O::n8; ++o) {
-      S f[8];
-      feq_orbit8<S, KT>(tb.H[8 * o], dM, f);
+      const int i0 = 8 * o;
+      S f[8], oa[4], ob[4];
+      feq_orbit8<S, KT>(tb.H[i0], dM, f);
+      quartet_om(tb.vx[i0], tb.vy[i0], oa);
+      quartet_om(tb.vx[i0 + 4], tb.vy[i0 + 4], ob);
 #pragma unroll
-      for (int m = 0; m < 8; ++m) relax(8 * o + m, f[m]);
+      for (int m = 0; m < 4; ++m) relax(i0 + m, f[m], oa[m]);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) relax(i0 + 4 + m, f[4 + m], ob[m]);
     }
 #pragma unroll
     for (int o = 0; o < O::n4; ++o) {
+      const int i0 = 8 * O::n8 + 4 * o;
       S f[4];
-      feq_orbit4<S, KT>(tb.H[8 * O::n8 + 4 * o], dM, f);
-#pragma unroll
-      for (int m = 0; m < 4; ++m) relax(8 * O::n8 + 4 * o + m, f[m]);
+      feq_orbit4<S, KT>(tb.H[i0], dM, f);
+      const S X = Uxk * tb.vx[i0], Y = Uyk * tb.vx[i0];   // members (v,0), (-v,0), (0,v), (0,-v)
+      relax(i0, f[0], U0k - X);
+      relax(i0 + 1, f[1], U0k + X);
+      relax(i0 + 2, f[2], U0k - Y);
+      relax(i0 + 3, f[3], U0k + Y);
     }
   } else {
 #pragma unroll
@@ -537,7 +570,7 @@ __device__ __forceinline__ void collide_store(const Tables<S>& tb, const Scalars
         S feq = S(0);
 #pragma unroll
         for (int k = 0; k < KT; ++k) feq = fma(tb.H[i][k], dM[k], feq);
-        relax(i, feq);
+        relax(i, feq, kt * (U0 - Ux * tb.vx[i] - Uy * tb.vy[i]));
       }
     }
   }
@@ -545,7 +578,7 @@ __device__ __forceinline__ void collide_store(const Tables<S>& tb, const Scalars
     S* __restrict__ hb = fout + hi;
 #pragma unroll
     for (int i = 0; i < QT; ++i)
-      if (i < Qn) hb[i * s.iplane] = g[i];
+      if (i < Qn) hb[plane_of(i)] = g[i];
   });
 }
 
@@ -557,7 +590,7 @@ __device__ __forceinline__ void cell_update(const Tables<S>& tb, const Scalars& 
                                             unsigned long long* status, int x, int y) {
   S g[QT];
   gather<S, QT, EX, MODE, DYN, NC>(tb, s, fin, sidx(s, x, y), g);
-  collide_store<S, QT, EX, KT, SYM>(tb, s, g, fout, tau_field, status, x, y);
+  collide_store<S, QT, EX, KT, SYM, DYN>(tb, s, g, fout, tau_field, status, x, y);
 }
 
 // FP32 storage: four 256-thread blocks per SM (at most 64 registers per
