@@ -84,6 +84,7 @@ __global__ void k_tau_import(const double* __restrict__ src, S* __restrict__ dst
 // Derived scalars: FP32 copies, flags, the int plane stride.
 void finish_scalars(Scalars* s) {
   s->PE_ref = s->Tii_ref + s->T00_ref;
+  s->n_ref2 = s->n_ref * s->n_ref;
   s->massless = (s->m == 0.0) ? 1 : 0;
   s->iplane = (int)s->plane;
   s->f_tau = (float)s->tau;

@@ -56,6 +56,7 @@ struct Scalars {
   double T00_ref;          // eps_ref = n_ref (m^2 + 2 m T_ref + 2 T_ref^2)/(m + T_ref)
   double Tii_ref;          // P_ref = n_ref T_ref
   double PE_ref;           // P_ref + eps_ref
+  double n_ref2;           // n_ref^2
   float kappa_guess;       // P/eps of the reference EOS, for the FP32 first guess
   int massless;            // m == 0
   int sym;                 // built-in massless stencil in orbit order with exactly symmetric H

@@ -178,6 +178,14 @@ __device__ __forceinline__ Macro landau_fp64(const Scalars& sc, const double (&m
   return M;
 }
 
+// Approximate FP32 square root (PTX sqrt.approx.f32, a few ulp): used only
+// for the first guess, which the Newton steps refine.
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // FP32 storage: the solve runs in FP32, then one Newton correction whose
 // residuals are evaluated in FP64: p(l) at the FP32 root, the eigenvector v
 // there, its Minkowski norm nu^2 = v.v and w = v.N (so that n = w / nu).  The
@@ -199,7 +207,7 @@ __device__ __forceinline__ Macro landau_fp32(const Scalars& sc, const float (&mm
   const float fE = epsr + mm[3];
   const float k = sc.kappa_guess;
   const float disc = (1.f - k) * (1.f - k) * fE * fE + 4.f * k * (fE * fE - M2);
-  const float lam0 = __fdividef(-(1.f - k) * fE + sqrtf(fmaxf(disc, 0.f)), 2.f * k);
+  const float lam0 = __fdividef(-(1.f - k) * fE + sqrt_approx(fmaxf(disc, 0.f)), 2.f * k);
   float del = lam0 - epsr;
   const float PE = Pr + epsr;
   float b = 0.f, c = 0.f, dp = 1.f;
@@ -252,7 +260,7 @@ __device__ __forceinline__ Macro landau_fp32(const Scalars& sc, const float (&mm
   M.fn = fw * inu;
   // dn = (w^2 - n_ref^2 nu^2) / (nu (w + n_ref nu))
   const float nr = sc.f_n_ref;
-  const double num = fma(wc, wc, -(sc.n_ref * sc.n_ref) * nu2c);
+  const double num = fma(wc, wc, -sc.n_ref2 * nu2c);
   M.fdn = __fdividef(d2f(num), fnu * (fw + nr * fnu));
   const float deps = del + dl;                          // eps - eps_ref
   const float fn = M.fn, fm = sc.f_m, fTr = sc.f_T_ref;
