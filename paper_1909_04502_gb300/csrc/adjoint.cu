@@ -98,16 +98,75 @@ __device__ __forceinline__ void landau_vjp(const Scalars& sc, const S (&mm)[9], 
   gm[5] = -r * gvx + b * gvy - k * (S(2) * (r * s - t * b));                   // T0y
 }
 
+// Orbit-symmetric transposes for the built-in massless stencils (member
+// order of moments_sym / feq_orbit8 in step_impl.cuh).
+// h += sum over the eight members m of r_m * (row of member m), the rows being
+// the first row h0 with the members' column signs and swaps.
+template <typename S>
+__device__ __forceinline__ void hrow_accum8(const S (&h0)[kMaxK], const S (&r)[8], S (&h)[9]) {
+  const S u0 = r[0] + r[1], u1 = r[0] - r[1], u2 = r[2] + r[3], u3 = r[2] - r[3];
+  const S v0 = r[4] + r[5], v1 = r[4] - r[5], v2 = r[6] + r[7], v3 = r[6] - r[7];
+  // sums weighted by 1, sx, sy, sx sy over each sign quartet
+  const S A[4] = {u0 + u2, u1 + u3, u0 - u2, u1 - u3};
+  const S B[4] = {v0 + v2, v1 + v3, v0 - v2, v1 - v3};
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const int cls = mono_ax(k) + 2 * mono_ay(k);
+    h[k] = fma(h0[k], A[cls], h[k]);
+    h[k] = fma(h0[mono_swap(k)], B[cls], h[k]);
+  }
+}
+
+template <typename S>
+__device__ __forceinline__ void hrow_accum4(const S (&h0)[kMaxK], const S (&r)[4], S (&h)[9]) {
+  // members (p,0), (-p,0), (0,p), (0,-p); the row of (p,0) has no py-odd entries
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    if (!mono_ay(k)) h[k] = fma(h0[k], mono_ax(k) ? r[0] - r[1] : r[0] + r[1], h[k]);
+    if (!mono_ax(k)) h[k] = fma(h0[mono_swap(k)], mono_ay(k) ? r[2] - r[3] : r[2] + r[3], h[k]);
+  }
+}
+
+// a_i += sum_k gm_k c_ik for the members of the orbits (transposed moments).
+template <typename S, int QT>
+__device__ __forceinline__ void moments_sym_transpose(const Tables<S>& tb, const S (&gm)[9], S (&a)[QT]) {
+  using O = Orbits<QT>;
+#pragma unroll
+  for (int o = 0; o < O::n8; ++o) {
+    const int i = 8 * o;
+    const S (&c)[9] = tb.c[i];   // p0, a, b, p0^2, p0 a, p0 b, a^2, a b, b^2 of the base (a, b)
+    const S E = fma(gm[0], c[0], fma(gm[3], c[3], fma(gm[6], c[6], gm[8] * c[8])));
+    const S X = fma(gm[1], c[1], gm[4] * c[4]), Y = fma(gm[2], c[2], gm[5] * c[5]), XY = gm[7] * c[7];
+    const S Eb = fma(gm[0], c[0], fma(gm[3], c[3], fma(gm[6], c[8], gm[8] * c[6])));
+    const S Xb = fma(gm[1], c[2], gm[4] * c[5]), Yb = fma(gm[2], c[1], gm[5] * c[4]);
+    const S A = E + XY, B = E - XY, C = X + Y, D = X - Y;
+    a[i] += A + C; a[i + 1] += B - D; a[i + 2] += B + D; a[i + 3] += A - C;
+    const S Ab = Eb + XY, Bb = Eb - XY, Cb = Xb + Yb, Db = Xb - Yb;
+    a[i + 4] += Ab + Cb; a[i + 5] += Bb - Db; a[i + 6] += Bb + Db; a[i + 7] += Ab - Cb;
+  }
+#pragma unroll
+  for (int o = 0; o < O::n4; ++o) {
+    const int i = 8 * O::n8 + 4 * o;
+    const S (&c)[9] = tb.c[i];   // p0, p, 0, p0^2, p0 p, 0, p^2, 0, 0
+    const S E = fma(gm[0], c[0], fma(gm[3], c[3], gm[6] * c[6]));
+    const S Eb = fma(gm[0], c[0], fma(gm[3], c[3], gm[8] * c[6]));
+    const S X = fma(gm[1], c[1], gm[4] * c[4]), Y = fma(gm[2], c[1], gm[5] * c[4]);
+    a[i] += E + X; a[i + 1] += E - X; a[i + 2] += Eb + Y; a[i + 3] += Eb - Y;
+  }
+}
+
 // Per-cell VJP of one collision.  g: f(t) (stored precision, shifted),
 // lam: dL/dx(t).  Outputs a = dL/df(t) and the tau sensitivity.
-template <typename S, int QT, bool EX>
+// SYM: orbit-symmetric moments, equilibrium and their transposes.
+template <typename S, int QT, bool EX, bool SYM = false>
 __device__ __forceinline__ void collide_vjp(const Tables<S>& tb, const Scalars& sc, const S (&g)[QT],
                                             const S (&lam)[QT], S tau, S (&a)[QT], S& gtau,
                                             unsigned long long* status) {
   const int Qn = EX ? QT : sc.Q;
   S mm[9];
-  moments9<S, QT, EX>(tb, sc.Q, g, mm);
-  const Macro M = landau<S>(sc, mm);
+  if constexpr (SYM) moments_sym<S, QT>(tb, g, mm);
+  else moments9<S, QT, EX>(tb, sc.Q, g, mm);
+  const Macro M = landau<S, SYM ? 1 : -1>(sc, mm);
   if (!M.ok) atomicAdd(status, 1ULL);
   S dM[9];
   eq_moments_of<S, 9>(sc, M, dM);
@@ -119,23 +178,50 @@ __device__ __forceinline__ void collide_vjp(const Tables<S>& tb, const Scalars& 
 #pragma unroll
   for (int k = 0; k < 9; ++k) h[k] = S(0);
   S q0 = 0, qx = 0, qy = 0, sr = 0;
+  // one population: returns ds/dfeq_i, accumulates the Omega and tau parts
+  auto pop = [&](int i, S feq) {
+    const S om = (U0 - Ux * tb.vx[i] - Uy * tb.vy[i]) * inv_tau;
+    const S diff = feq - g[i];
+    const S r = lam[i] * om;                 // ds/dfeq_i
+    const S q = lam[i] * diff * inv_tau;     // ds/d(tau Omega_i)
+    q0 += q;
+    qx = fma(-q, tb.vx[i], qx);
+    qy = fma(-q, tb.vy[i], qy);
+    sr = fma(r, diff, sr);
+    a[i] = lam[i] * (S(1) - om);
+    return r;
+  };
+  if constexpr (SYM) {
+    using O = Orbits<QT>;
 #pragma unroll
-  for (int i = 0; i < QT; ++i) {
-    if (i < Qn) {
-      S feq = S(0);
+    for (int o = 0; o < O::n8; ++o) {
+      const int i0 = 8 * o;
+      S f[8], r[8];
+      feq_orbit8<S, 9>(tb.H[i0], dM, f);
 #pragma unroll
-      for (int k = 0; k < 9; ++k) feq = fma(tb.H[i][k], dM[k], feq);
-      const S om = (U0 - Ux * tb.vx[i] - Uy * tb.vy[i]) * inv_tau;
-      const S diff = feq - g[i];
-      const S r = lam[i] * om;                 // ds/dfeq_i
-      const S q = lam[i] * diff * inv_tau;     // ds/d(tau Omega_i)
+      for (int m = 0; m < 8; ++m) r[m] = pop(i0 + m, f[m]);
+      hrow_accum8<S>(tb.H[i0], r, h);
+    }
 #pragma unroll
-      for (int k = 0; k < 9; ++k) h[k] = fma(r, tb.H[i][k], h[k]);
-      q0 += q;
-      qx = fma(-q, tb.vx[i], qx);
-      qy = fma(-q, tb.vy[i], qy);
-      sr = fma(r, diff, sr);
-      a[i] = lam[i] * (S(1) - om);
+    for (int o = 0; o < O::n4; ++o) {
+      const int i0 = 8 * O::n8 + 4 * o;
+      S f[4], r[4];
+      feq_orbit4<S, 9>(tb.H[i0], dM, f);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) r[m] = pop(i0 + m, f[m]);
+      hrow_accum4<S>(tb.H[i0], r, h);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < QT; ++i) {
+      if (i < Qn) {
+        S feq = S(0);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) feq = fma(tb.H[i][k], dM[k], feq);
+        const S r = pop(i, feq);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) h[k] = fma(r, tb.H[i][k], h[k]);
+      }
     }
   }
   gtau = -sr * inv_tau;
@@ -163,13 +249,17 @@ __device__ __forceinline__ void collide_vjp(const Tables<S>& tb, const Scalars& 
   gm[1] = -gn * Ux;
   gm[2] = -gn * Uy;
   landau_vjp<S>(sc, mm, M.eps, gE, gU0, gUx, gUy, gm);
+  if constexpr (SYM) {
+    moments_sym_transpose<S, QT>(tb, gm, a);
+  } else {
 #pragma unroll
-  for (int i = 0; i < QT; ++i) {
-    if (i < Qn) {
-      S acc = a[i];
+    for (int i = 0; i < QT; ++i) {
+      if (i < Qn) {
+        S acc = a[i];
 #pragma unroll
-      for (int k = 0; k < 9; ++k) acc = fma(gm[k], tb.c[i][k], acc);
-      a[i] = acc;
+        for (int k = 0; k < 9; ++k) acc = fma(gm[k], tb.c[i][k], acc);
+        a[i] = acc;
+      }
     }
   }
 }
@@ -185,8 +275,8 @@ struct AdjArgs {
   unsigned long long* status;
 };
 
-template <typename S, int QT, bool EX, int MODE>
-__global__ void __launch_bounds__(kThreads) k_adj_step(const __grid_constant__ Tables<S> tb,
+template <typename S, int QT, bool EX, int MODE, bool SYM>
+__global__ void __launch_bounds__(kThreads, sizeof(S) == 4 ? 2 : 1) k_adj_step(const __grid_constant__ Tables<S> tb,
                                                        const __grid_constant__ AdjArgs<S> a) {
   const int x = blockIdx.x * kBX + threadIdx.x;
   const int y = blockIdx.y * kBY + threadIdx.y;
@@ -199,7 +289,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_step(const __grid_constant__ T
   gather_rev<S, QT, EX, MODE>(tb, a.s, a.anext, si, lam);
   const S tau = (a.s.tau_mode == 1) ? a.tau_field[cell] : (S)a.s.tau;
   S gt;
-  collide_vjp<S, QT, EX>(tb, a.s, g, lam, tau, out, gt, a.status);
+  collide_vjp<S, QT, EX, SYM>(tb, a.s, g, lam, tau, out, gt, a.status);
   a.gtau[cell] += (double)gt;
   S* __restrict__ ob = a.aout + si;
 #pragma unroll
@@ -329,17 +419,19 @@ __global__ void __launch_bounds__(kThreads) k_adj_init(const __grid_constant__ T
 
 // ---------------------------------------------------------------------------
 
-template <typename S, int QT, bool EX>
+template <typename S, int QT, bool EX, bool SYM>
 cudaError_t adj_step_q(const Tables<S>& tb, const AdjArgs<S>& a, int mode, cudaStream_t st) {
-  if (mode == kOnLattice) k_adj_step<S, QT, EX, kOnLattice><<<grid_for(a.s), block_dim(), 0, st>>>(tb, a);
-  else k_adj_step<S, QT, EX, kBilinear><<<grid_for(a.s), block_dim(), 0, st>>>(tb, a);
+  if (mode == kOnLattice) k_adj_step<S, QT, EX, kOnLattice, SYM><<<grid_for(a.s), block_dim(), 0, st>>>(tb, a);
+  else k_adj_step<S, QT, EX, kBilinear, SYM><<<grid_for(a.s), block_dim(), 0, st>>>(tb, a);
   return cudaGetLastError();
 }
 
+// the built-in massless stencil (orbit order, exactly symmetric H) takes the
+// orbit-symmetric VJP; any other order-2 stencil the bounded generic one
 template <typename S>
 cudaError_t adj_step(const Tables<S>& tb, const AdjArgs<S>& a, int mode, cudaStream_t st) {
-  if (a.s.Q == 28) return adj_step_q<S, 28, true>(tb, a, mode, st);
-  if (a.s.Q <= 40) return adj_step_q<S, 40, false>(tb, a, mode, st);
+  if (a.s.Q == 28 && a.s.sym) return adj_step_q<S, 28, true, true>(tb, a, mode, st);
+  if (a.s.Q <= 40) return adj_step_q<S, 40, false, false>(tb, a, mode, st);
   return cudaErrorInvalidValue;
 }
 
