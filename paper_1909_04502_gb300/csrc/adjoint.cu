@@ -158,16 +158,41 @@ __device__ __forceinline__ void moments_sym_transpose(const Tables<S>& tb, const
 // Per-cell VJP of one collision.  g: f(t) (stored precision, shifted),
 // lam: dL/dx(t).  Outputs a = dL/df(t) and the tau sensitivity.
 // SYM: orbit-symmetric moments, equilibrium and their transposes.
-template <typename S, int QT, bool EX, bool SYM = false>
+// MIN (FP32 storage): the macroscopic state of the cell is read from mac
+// (planes written by the recomputing forward step) instead of re-solving the
+// Landau problem; a cell the forward step left unrelaxed (non-physical,
+// n stored as NaN) has the identity as its collision, so a = lam there.
+template <typename S, int QT, bool EX, bool SYM = false, bool MIN = false>
 __device__ __forceinline__ void collide_vjp(const Tables<S>& tb, const Scalars& sc, const S (&g)[QT],
                                             const S (&lam)[QT], S tau, S (&a)[QT], S& gtau,
-                                            unsigned long long* status) {
+                                            unsigned long long* status, const float* __restrict__ mac = nullptr,
+                                            int cell = 0) {
   const int Qn = EX ? QT : sc.Q;
   S mm[9];
   if constexpr (SYM) moments_sym<S, QT>(tb, g, mm);
   else moments9<S, QT, EX>(tb, sc.Q, g, mm);
-  const Macro M = landau<S, SYM ? 1 : -1>(sc, mm);
-  if (!M.ok) atomicAdd(status, 1ULL);
+  Macro M;
+  if constexpr (MIN && sizeof(S) == 4) {
+    const int nc = sc.ncell;
+    M.fn = __ldg(mac + cell);
+    M.fT = __ldg(mac + nc + cell);
+    M.fU0 = __ldg(mac + 2 * nc + cell);
+    M.fUx = __ldg(mac + 3 * nc + cell);
+    M.fUy = __ldg(mac + 4 * nc + cell);
+    M.fdn = __ldg(mac + 5 * nc + cell);
+    M.fdT = __ldg(mac + 6 * nc + cell);
+    M.eps = (double)__ldg(mac + 7 * nc + cell);
+    M.ok = !isnan(M.fn);
+    if (!M.ok) {
+#pragma unroll
+      for (int i = 0; i < QT; ++i) a[i] = lam[i];
+      gtau = S(0);
+      return;
+    }
+  } else {
+    M = landau<S, SYM ? 1 : -1>(sc, mm);
+    if (!M.ok) atomicAdd(status, 1ULL);
+  }
   S dM[9];
   eq_moments_of<S, 9>(sc, M, dM);
   S n, T, U0, Ux, Uy;
@@ -273,9 +298,10 @@ struct AdjArgs {
   const S* tau_field;    // per-cell tau (tau_mode 1) or null
   double* gtau;          // accumulated dL/dtau per cell [ny][nx]
   unsigned long long* status;
+  const float* macro = nullptr;   // macroscopic state of f(t) (FP32 storage), or null: recompute
 };
 
-template <typename S, int QT, bool EX, int MODE, bool SYM>
+template <typename S, int QT, bool EX, int MODE, bool SYM, bool MIN>
 __global__ void __launch_bounds__(kThreads, sizeof(S) == 4 ? 2 : 1) k_adj_step(const __grid_constant__ Tables<S> tb,
                                                        const __grid_constant__ AdjArgs<S> a) {
   const int x = blockIdx.x * kBX + threadIdx.x;
@@ -289,7 +315,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(S) == 4 ? 2 : 1) k_adj_step(c
   gather_rev<S, QT, EX, MODE>(tb, a.s, a.anext, si, lam);
   const S tau = (a.s.tau_mode == 1) ? a.tau_field[cell] : (S)a.s.tau;
   S gt;
-  collide_vjp<S, QT, EX, SYM>(tb, a.s, g, lam, tau, out, gt, a.status);
+  collide_vjp<S, QT, EX, SYM, MIN>(tb, a.s, g, lam, tau, out, gt, a.status, a.macro, cell);
   a.gtau[cell] += (double)gt;
   S* __restrict__ ob = a.aout + si;
 #pragma unroll
@@ -421,8 +447,16 @@ __global__ void __launch_bounds__(kThreads) k_adj_init(const __grid_constant__ T
 
 template <typename S, int QT, bool EX, bool SYM>
 cudaError_t adj_step_q(const Tables<S>& tb, const AdjArgs<S>& a, int mode, cudaStream_t st) {
-  if (mode == kOnLattice) k_adj_step<S, QT, EX, kOnLattice, SYM><<<grid_for(a.s), block_dim(), 0, st>>>(tb, a);
-  else k_adj_step<S, QT, EX, kBilinear, SYM><<<grid_for(a.s), block_dim(), 0, st>>>(tb, a);
+  if constexpr (SYM && sizeof(S) == 4) {
+    if (a.macro) {
+      if (mode == kOnLattice) k_adj_step<S, QT, EX, kOnLattice, SYM, true><<<grid_for(a.s), block_dim(), 0, st>>>(tb, a);
+      else k_adj_step<S, QT, EX, kBilinear, SYM, true><<<grid_for(a.s), block_dim(), 0, st>>>(tb, a);
+      return cudaGetLastError();
+    }
+  }
+  if (a.macro) return cudaErrorInvalidValue;
+  if (mode == kOnLattice) k_adj_step<S, QT, EX, kOnLattice, SYM, false><<<grid_for(a.s), block_dim(), 0, st>>>(tb, a);
+  else k_adj_step<S, QT, EX, kBilinear, SYM, false><<<grid_for(a.s), block_dim(), 0, st>>>(tb, a);
   return cudaGetLastError();
 }
 
@@ -476,7 +510,8 @@ struct rlbm_adjoint {
   int T = 0;                              // forward steps of the run
   int K = 0;                              // checkpoint interval
   void* ckpt = nullptr;                   // checkpoints x(0), x(K), x(2K), ...
-  void* seg = nullptr;                    // recomputed states of one segment (K buffers)
+  void* seg = nullptr;                    // recomputed states of one segment (K + 1 buffers)
+  float* macro = nullptr;                 // FP32 storage: macroscopic states of the segment [K + 1][planes][ncell]
   void* adj[2] = {nullptr, nullptr};      // adjoint populations (ping-pong)
   double* gtau = nullptr;                 // dL/dtau per cell
   double* init_fields = nullptr;          // n0, ux0, uy0, T0 of the run [4][ncell]
@@ -496,11 +531,16 @@ int adj_fail(rlbm_adjoint* A, int code, const std::string& msg) {
 
 void* state_ptr(void* base, size_t bytes, int k) { return (char*)base + bytes * (size_t)k; }
 
-// One forward step from src into dst using the handle's tables.
-cudaError_t fwd_step(rlbm_handle* h, const void* src, void* dst) {
+float* macro_ptr(rlbm_adjoint* A, int j) {
+  return A->macro + (size_t)j * kMacroPlanes * (size_t)A->h->sc.ncell;
+}
+
+// One forward step from src into dst using the handle's tables; with macro
+// (FP32 storage) the step also writes the macroscopic state of its cells.
+cudaError_t fwd_step(rlbm_handle* h, const void* src, void* dst, float* macro = nullptr) {
   const int mode = h->p.stream_mode == RLBM_BILINEAR ? kBilinear : kOnLattice;
   if (h->elem == 4) {
-    StepArgs<float> a{h->sc, (const float*)src, (float*)dst, (const float*)h->tau_field, h->status};
+    StepArgs<float> a{h->sc, (const float*)src, (float*)dst, (const float*)h->tau_field, h->status, macro};
     return launch_step<float>(*h->tf, a, mode, h->stream);
   }
   StepArgs<double> a{h->sc, (const double*)src, (double*)dst, (const double*)h->tau_field, h->status};
@@ -525,7 +565,9 @@ int rlbm_adjoint_create(rlbm_handle* h, int nsteps, int checkpoint_every, rlbm_a
   A->nckpt = (nsteps + A->K - 1) / A->K;
   const size_t nc = (size_t)h->sc.ncell;
   cudaError_t e = cudaMalloc(&A->ckpt, A->buf_bytes * A->nckpt);
-  if (e == cudaSuccess) e = cudaMalloc(&A->seg, A->buf_bytes * A->K);
+  if (e == cudaSuccess) e = cudaMalloc(&A->seg, A->buf_bytes * (A->K + 1));
+  if (e == cudaSuccess && h->elem == 4 && h->sc.sym && h->q.Q == 28)
+    e = cudaMalloc(&A->macro, sizeof(float) * kMacroPlanes * nc * (A->K + 1));
   if (e == cudaSuccess) e = cudaMalloc(&A->adj[0], A->buf_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&A->adj[1], A->buf_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&A->gtau, nc * sizeof(double));
@@ -533,7 +575,7 @@ int rlbm_adjoint_create(rlbm_handle* h, int nsteps, int checkpoint_every, rlbm_a
   if (e == cudaSuccess) e = cudaMalloc(&A->loss, sizeof(double));
   if (e != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(A->ckpt); cudaFree(A->seg); cudaFree(A->adj[0]); cudaFree(A->adj[1]);
+    cudaFree(A->ckpt); cudaFree(A->seg); cudaFree(A->macro); cudaFree(A->adj[0]); cudaFree(A->adj[1]);
     cudaFree(A->gtau); cudaFree(A->init_fields); cudaFree(A->loss);
     return RLBM_ERR_OOM;
   }
@@ -548,6 +590,7 @@ void rlbm_adjoint_destroy(rlbm_adjoint* A) {
   cudaStreamSynchronize(A->h->stream);
   cudaFree(A->ckpt);
   cudaFree(A->seg);
+  cudaFree(A->macro);
   cudaFree(A->adj[0]);
   cudaFree(A->adj[1]);
   cudaFree(A->gtau);
@@ -610,12 +653,19 @@ int rlbm_adjoint_backward(rlbm_adjoint* A, const double* ux_target, const double
   for (int sgi = A->nckpt - 1; sgi >= 0; --sgi) {
     const int c = sgi * A->K;
     const int last = std::min(c + A->K, A->T) - 1;        // states x(c) .. x(last) of this segment
-    // recompute the segment: seg[j] = x(c + j)
+    // adjoint steps t whose x(t-1) lies in this segment: t = last+1 .. c+1
+    // (t >= 1), except that t = T is the loss (done first) -- t runs below T
+    const int t_hi = std::min(last + 1, A->T - 1);
+    // recompute the segment: seg[j] = x(c + j).  With stored macroscopic
+    // states, macro[j] is that of f(c + j), which adjoint step t = c + j
+    // needs, so the recompute runs up to j = t_hi - c (<= K)
     e = cudaMemcpyAsync(state_ptr(A->seg, A->buf_bytes, 0), state_ptr(A->ckpt, A->buf_bytes, sgi), A->buf_bytes,
                         cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return adj_fail(A, RLBM_ERR_CUDA, cudaGetErrorString(e));
-    for (int j = 1; j <= last - c; ++j) {
-      e = fwd_step(h, state_ptr(A->seg, A->buf_bytes, j - 1), state_ptr(A->seg, A->buf_bytes, j));
+    const int jmax = A->macro ? std::max(t_hi - c, last - c) : last - c;
+    for (int j = 1; j <= jmax; ++j) {
+      e = fwd_step(h, state_ptr(A->seg, A->buf_bytes, j - 1), state_ptr(A->seg, A->buf_bytes, j),
+                   A->macro ? macro_ptr(A, j) : nullptr);
       if (e != cudaSuccess) return adj_fail(A, RLBM_ERR_CUDA, cudaGetErrorString(e));
     }
     if (!have_a) {
@@ -632,14 +682,12 @@ int rlbm_adjoint_backward(rlbm_adjoint* A, const double* ux_target, const double
       if (e != cudaSuccess) return adj_fail(A, RLBM_ERR_CUDA, cudaGetErrorString(e));
       have_a = true;
     }
-    // adjoint steps t whose x(t-1) lies in this segment: t = last .. c+1 (t >= 1),
-    // except that t = T is the loss (already done) -- t runs below T
-    const int t_hi = std::min(last + 1, A->T - 1);
     for (int t = t_hi; t >= c + 1; --t) {
       const void* xprev = state_ptr(A->seg, A->buf_bytes, t - 1 - c);
       if (h->elem == 4) {
         AdjArgs<float> aa{s, (const float*)xprev, (const float*)A->adj[an], (float*)A->adj[an ^ 1],
-                          (const float*)h->tau_field, A->gtau, h->status};
+                          (const float*)h->tau_field, A->gtau, h->status,
+                          A->macro ? macro_ptr(A, t - c) : nullptr};
         e = adj_step<float>(*h->tf, aa, mode, st);
       } else {
         AdjArgs<double> aa{s, (const double*)xprev, (const double*)A->adj[an], (double*)A->adj[an ^ 1],

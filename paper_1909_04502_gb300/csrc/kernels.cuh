@@ -84,6 +84,10 @@ __host__ __device__ __forceinline__ long long sidx(const Scalars& s, int x, int 
   return (long long)(y + s.hy) * s.pitch + (x + s.px);
 }
 
+// Macroscopic state of f(t+1)'s cells as the FP32-storage step leaves it:
+// planes n, T, U^0, U^x, U^y, n - n_ref, T - T_ref, eps ([kMacroPlanes][ncell]).
+constexpr int kMacroPlanes = 8;
+
 template <typename S>
 struct StepArgs {
   Scalars s;
@@ -91,6 +95,7 @@ struct StepArgs {
   S* fout;               // f*(t+1)
   const S* tau_field;    // per-cell tau, row-major [ny][nx] (tau_mode 1)
   unsigned long long* status;   // count of non-physical cell updates
+  float* macro = nullptr;       // optional macroscopic-state output (FP32 storage)
 };
 
 template <typename S>

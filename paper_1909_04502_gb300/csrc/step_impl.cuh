@@ -514,10 +514,13 @@ __device__ __forceinline__ void feq_orbit4(const S (&h)[kMaxK], const S (&dM)[KT
 // solve, equilibrium, relaxation, store (interior and halo images).
 // DYN: plane offsets from the run-time plane size (tables shared by grids
 // of different sizes), otherwise from the per-handle table tb.pl.
-template <typename S, int QT, bool EX, int KT, bool SYM = false, bool DYN = false>
+// MOUT (FP32 storage): also write the cell's macroscopic state to macro
+// (planes of kMacroPlanes; n is NaN where the update was non-physical).
+template <typename S, int QT, bool EX, int KT, bool SYM = false, bool DYN = false, bool MOUT = false>
 __device__ __forceinline__ void collide_store(const Tables<S>& tb, const Scalars& s, S (&g)[QT],
                                               S* __restrict__ fout, const S* __restrict__ tau_field,
-                                              unsigned long long* status, int x, int y) {
+                                              unsigned long long* status, int x, int y,
+                                              float* __restrict__ macro = nullptr) {
   const long long si = sidx(s, x, y);
   const int Qn = EX ? QT : s.Q;
   S mm[9];
@@ -525,6 +528,18 @@ __device__ __forceinline__ void collide_store(const Tables<S>& tb, const Scalars
   else moments9<S, QT, EX>(tb, s.Q, g, mm);
   const Macro M = landau<S, SYM ? 1 : -1>(s, mm);
   if (!M.ok) atomicAdd(status, 1ULL);
+  if constexpr (MOUT && sizeof(S) == 4) {
+    const int cell = y * s.nx + x;
+    const int nc = s.ncell;
+    macro[cell] = M.ok ? M.fn : __int_as_float(0x7fc00000);
+    macro[nc + cell] = M.fT;
+    macro[2 * nc + cell] = M.fU0;
+    macro[3 * nc + cell] = M.fUx;
+    macro[4 * nc + cell] = M.fUy;
+    macro[5 * nc + cell] = M.fdn;
+    macro[6 * nc + cell] = M.fdT;
+    macro[7 * nc + cell] = (float)M.eps;
+  }
   S dM[KT];
   eq_moments_of<S, KT>(s, M, dM);
   const S inv_tau = qdiv(S(1), local_tau<S>(s, tau_field, y * s.nx + x, M));
@@ -604,13 +619,20 @@ __device__ __forceinline__ void cell_update(const Tables<S>& tb, const Scalars& 
 // FP32 storage: four 256-thread blocks per SM (at most 64 registers per
 // thread) -- the FP64 polish and the gather latency need the resident warps.
 // SYM: orbit-symmetric moments and equilibrium (built-in massless stencils).
-template <typename S, int QT, bool EX, int KT, int MODE, bool SYM>
+// MOUT: also write the macroscopic state (a.macro).
+template <typename S, int QT, bool EX, int KT, int MODE, bool SYM, bool MOUT = false>
 __global__ void __launch_bounds__(kThreads, (sizeof(S) == 4 && QT <= 40) ? 4 : 2) k_step(const __grid_constant__ Tables<S> tb,
                                                    const __grid_constant__ StepArgs<S> a) {
   const int x = blockIdx.x * kBX + threadIdx.x;
   const int y = blockIdx.y * kBY + threadIdx.y;
   if (x >= a.s.nx || y >= a.s.ny) return;
-  cell_update<S, QT, EX, KT, MODE, false, true, SYM>(tb, a.s, a.fin, a.fout, a.tau_field, a.status, x, y);
+  if constexpr (MOUT) {
+    S g[QT];
+    gather<S, QT, EX, MODE>(tb, a.s, a.fin, sidx(a.s, x, y), g);
+    collide_store<S, QT, EX, KT, SYM, false, true>(tb, a.s, g, a.fout, a.tau_field, a.status, x, y, a.macro);
+  } else {
+    cell_update<S, QT, EX, KT, MODE, false, true, SYM>(tb, a.s, a.fin, a.fout, a.tau_field, a.status, x, y);
+  }
 }
 
 // Fields of f(t) (steps 1-4), optionally the raw moments.  Output planes are
@@ -688,10 +710,10 @@ inline dim3 block_dim() { return dim3(kBX, kBY); }
 
 // QT: population count of the instantiation; EX: the stencil has exactly QT
 // populations (no per-population bounds test), otherwise Q <= QT at run time.
-template <typename S, int QT, bool EX, int KT, bool SYM = false>
+template <typename S, int QT, bool EX, int KT, bool SYM = false, bool MOUT = false>
 cudaError_t launch_step_q(const Tables<S>& tb, const StepArgs<S>& a, int mode, cudaStream_t st) {
-  if (mode == kOnLattice) k_step<S, QT, EX, KT, kOnLattice, SYM><<<grid_for(a.s), block_dim(), 0, st>>>(tb, a);
-  else k_step<S, QT, EX, KT, kBilinear, SYM><<<grid_for(a.s), block_dim(), 0, st>>>(tb, a);
+  if (mode == kOnLattice) k_step<S, QT, EX, KT, kOnLattice, SYM, MOUT><<<grid_for(a.s), block_dim(), 0, st>>>(tb, a);
+  else k_step<S, QT, EX, KT, kBilinear, SYM, MOUT><<<grid_for(a.s), block_dim(), 0, st>>>(tb, a);
   return cudaGetLastError();
 }
 

@@ -96,11 +96,15 @@ def test_fp64_adjoint_single_cell_sensitivities(rl):
         assert abs(gux[j, i] - fd) < 1e-6 * np.abs(gux).max(), (j, i, gux[j, i], fd)
 
 
-def test_checkpoint_interval_does_not_change_the_gradient(rl):
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_checkpoint_interval_does_not_change_the_gradient(rl, precision):
+    """Recomputation is deterministic, so the gradient is bitwise the same for
+    any checkpoint interval (FP32: the recompute also stores the cells'
+    macroscopic states, which the adjoint steps read)."""
     data = _setup(seed=8)
-    a = _adjoint(rl, "fp64", 1, data, steps=9)
-    b = _adjoint(rl, "fp64", 4, data, steps=9)
-    c = _adjoint(rl, "fp64", 9, data, steps=9)
+    a = _adjoint(rl, precision, 1, data, steps=9)
+    b = _adjoint(rl, precision, 4, data, steps=9)
+    c = _adjoint(rl, precision, 9, data, steps=9)
     for x, y in ((a, b), (a, c)):
         assert x[0] == y[0]
         for k in (1, 2, 3):
