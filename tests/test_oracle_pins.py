@@ -451,6 +451,27 @@ def test_ce_shear_viscosity_limits():
     assert np.all(np.diff(P.ce_shear_viscosity_coeff(z)) > 0)
 
 
+@pytest.mark.parametrize("zeta", [0.0, 0.5, 1.0, 2.0, 5.0, 10.0, 50.0])
+def test_ce_shear_viscosity_matches_the_chapman_enskog_integral(zeta):
+    """App. C closed form against the first-order CE integral it comes from,
+    evaluated by quadrature: in a shear flow u_x(y) the Anderson-Witting
+    correction is df = -(tau / p0) f_eq p^x p^y du_x/dy / T (rest frame), so
+    eta = (tau / T) int d^2p (p^x p^y)^2 f_eq / p0^2 and, with n = int d^2p f_eq
+    and P = n T, eta / (P tau) = (pi/4) int p^5 e^{-p0/T}/p0^2 dp /
+    (2 pi T^2 int p e^{-p0/T} dp).  Independent of the Gamma(0, zeta) form."""
+    from scipy import integrate
+    T = 1.0
+    m = zeta * T
+
+    def w(p, k):
+        return p ** k * np.exp(-(np.sqrt(m * m + p * p) - m) / T)
+
+    num = (np.pi / 4) * integrate.quad(lambda p: w(p, 5) / (m * m + p * p), 0, np.inf, epsabs=0,
+                                       epsrel=1e-13, limit=500)[0]
+    den = T * T * 2 * np.pi * integrate.quad(lambda p: w(p, 1), 0, np.inf, epsabs=0, epsrel=1e-13, limit=500)[0]
+    assert abs(float(P.ce_shear_viscosity_coeff(np.array(zeta))) - num / den) < 1e-8
+
+
 def _shear_wave_eta(order, Lx, tau, amp=0.01):
     q = L.massless_quadrature(order)
     e = L.Expansion(q)
