@@ -233,7 +233,8 @@ typedef struct rlbm_batch rlbm_batch;
 /* Create count handles from params[0..count) (all on params[0].stream) and
  * the batch machinery.  RLBM_ERR_UNSUPPORTED for configurations outside the
  * batched kernel (FP64, order 3, tau fields, stencils other than the massless
- * Q = 28 (on-lattice or bilinear) and the built-in massive Q = 25, 29, 33;
+ * Q = 28 (on-lattice or bilinear) and the built-in massive Q = 25, 29, 33,
+ * each in orbit order with an exactly symmetric equilibrium matrix;
  * two instances of one stencil size must share the same stencil). */
 int rlbm_batch_create(const rlbm_params* params, int count, rlbm_batch** out);
 void rlbm_batch_destroy(rlbm_batch* b);

@@ -131,6 +131,7 @@ __device__ __forceinline__ void hrow_accum4(const S (&h0)[kMaxK], const S (&r)[4
 template <typename S, int QT>
 __device__ __forceinline__ void moments_sym_transpose(const Tables<S>& tb, const S (&gm)[9], S (&a)[QT]) {
   using O = Orbits<QT>;
+  static_assert(O::nd == 0 && O::n1 == 0, "adjoint symmetric path: massless stencils only");
 #pragma unroll
   for (int o = 0; o < O::n8; ++o) {
     const int i = 8 * o;
@@ -190,7 +191,7 @@ __device__ __forceinline__ void collide_vjp(const Tables<S>& tb, const Scalars& 
       return;
     }
   } else {
-    M = landau<S, SYM ? 1 : -1>(sc, mm);
+    M = landau<S, SYM ? (Orbits<QT>::massless ? 1 : 0) : -1>(sc, mm);
     if (!M.ok) atomicAdd(status, 1ULL);
   }
   S dM[9];

@@ -124,17 +124,21 @@ void compute_layout(const Quadrature& q, const rlbm_params& p, size_t elem, Scal
 // Rounding each weight on its own leaves the sum off by up to a few units in
 // the last place, which multiplies the streamed populations by that factor
 // every step and drifts the global sums of N^0 and T^{0a}.
-// True when the kernels' orbit-symmetric evaluation applies: the built-in
-// massless stencil (Q = 28 or 44) in orbit order (setup.cpp), every member's
-// momentum the signed / swapped image of its orbit's first member, and every
-// row of H exactly the first row with the matching column signs and (for a
-// swapped member) swapped columns; the (p, 0) rows without py-odd entries.
+// True when the kernels' orbit-symmetric evaluation applies: the stencil has
+// one of the compiled orbit compositions (massless Q = 28, 44; the built-in
+// massive Q = 33, 29, 25) in orbit order (setup.cpp), every member's momentum
+// and weight are the signed / swapped image of its orbit's first member, and
+// every row of H is exactly the first row with the matching column signs and
+// (for a swapped member) swapped columns; axis, diagonal and rest rows have
+// the zero or symmetric entries the kernels skip.
 bool orbit_symmetric(const rlbm_handle* h) {
   const Quadrature& q = h->q;
-  if (h->p.quadrature != RLBM_QUAD_MASSLESS || q.m != 0.0) return false;
-  int n8, n4;
-  if (q.Q == 28 && h->K == 9) { n8 = 3; n4 = 1; }
-  else if (q.Q == 44 && h->K == 16) { n8 = 4; n4 = 3; }
+  int n8, n4, nd, n1;
+  if (q.Q == 28 && h->K == 9 && q.m == 0.0) { n8 = 3; n4 = 1; nd = 0; n1 = 0; }
+  else if (q.Q == 44 && h->K == 16 && q.m == 0.0) { n8 = 4; n4 = 3; nd = 0; n1 = 0; }
+  else if (q.Q == 33 && h->K == 9) { n8 = 3; n4 = 1; nd = 1; n1 = 1; }
+  else if (q.Q == 29 && h->K == 9) { n8 = 2; n4 = 1; nd = 2; n1 = 1; }
+  else if (q.Q == 25 && h->K == 9) { n8 = 1; n4 = 2; nd = 2; n1 = 1; }
   else return false;
   const int K = h->K;
   auto row = [&](int i, int k) { return h->H[(size_t)i * K + k]; };
@@ -148,19 +152,31 @@ bool orbit_symmetric(const rlbm_handle* h) {
     return true;
   };
   const int sg[4][2] = {{1, 1}, {-1, 1}, {1, -1}, {-1, -1}};
-  for (int o = 0; o < n8; ++o)
+  int i0 = 0;
+  for (int o = 0; o < n8; ++o, i0 += 8) {
+    if (q.px[i0] == 0.0 || q.py[i0] == 0.0 || std::fabs(q.px[i0]) == std::fabs(q.py[i0])) return false;
     for (int m = 0; m < 8; ++m)
-      if (!check(8 * o, 8 * o + m, sg[m & 3][0], sg[m & 3][1], m >= 4)) return false;
-  for (int o = 0; o < n4; ++o) {
-    const int i0 = 8 * n8 + 4 * o;
-    if (q.py[i0] != 0.0) return false;
+      if (!check(i0, i0 + m, sg[m & 3][0], sg[m & 3][1], m >= 4)) return false;
+  }
+  for (int o = 0; o < n4; ++o, i0 += 4) {
+    if (q.py[i0] != 0.0 || q.px[i0] == 0.0) return false;
     for (int k = 0; k < K; ++k)
       if (mono_ay(k) && row(i0, k) != 0.0) return false;
     const int sgn4[4][3] = {{1, 1, 0}, {-1, 1, 0}, {1, 1, 1}, {1, -1, 1}};   // (sx, sy, swap)
     for (int m = 0; m < 4; ++m)
       if (!check(i0, i0 + m, sgn4[m][0], sgn4[m][1], sgn4[m][2] != 0)) return false;
   }
-  return true;
+  for (int o = 0; o < nd; ++o, i0 += 4) {
+    if (q.px[i0] != q.py[i0] || q.px[i0] == 0.0) return false;
+    for (int m = 0; m < 4; ++m)
+      if (!check(i0, i0 + m, sg[m][0], sg[m][1], false)) return false;
+  }
+  for (int o = 0; o < n1; ++o, ++i0) {
+    if (q.px[i0] != 0.0 || q.py[i0] != 0.0) return false;
+    for (int k = 0; k < K; ++k)
+      if ((mono_ax(k) || mono_ay(k)) && row(i0, k) != 0.0) return false;
+  }
+  return i0 == q.Q;
 }
 
 // Step kernel a handle uses: the caller's choice, else the direct-load

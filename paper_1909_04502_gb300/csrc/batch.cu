@@ -109,11 +109,11 @@ __device__ __forceinline__ void batch_tile(const BatchInst& I, int tile, int ste
   if constexpr (KIND == kKindMassless)
     cell_update<float, 28, true, 9, kOnLattice, true, false, true>(c_btab[KIND], I.s, fin, fout, I.tau_field, I.status, x, y);
   else if constexpr (KIND == kKindQ33)
-    cell_update<float, 33, true, 9, kOnLattice, true, false>(c_btab[KIND], I.s, fin, fout, I.tau_field, I.status, x, y);
+    cell_update<float, 33, true, 9, kOnLattice, true, false, true>(c_btab[KIND], I.s, fin, fout, I.tau_field, I.status, x, y);
   else if constexpr (KIND == kKindQ25)
-    cell_update<float, 25, true, 9, kOnLattice, true, false>(c_btab[KIND], I.s, fin, fout, I.tau_field, I.status, x, y);
+    cell_update<float, 25, true, 9, kOnLattice, true, false, true>(c_btab[KIND], I.s, fin, fout, I.tau_field, I.status, x, y);
   else if constexpr (KIND == kKindQ29)
-    cell_update<float, 29, true, 9, kOnLattice, true, false>(c_btab[KIND], I.s, fin, fout, I.tau_field, I.status, x, y);
+    cell_update<float, 29, true, 9, kOnLattice, true, false, true>(c_btab[KIND], I.s, fin, fout, I.tau_field, I.status, x, y);
   else
     cell_update<float, 28, true, 9, kBilinear, true, false, true>(c_btab[KIND], I.s, fin, fout, I.tau_field, I.status, x, y);
 }
@@ -193,9 +193,9 @@ int kind_of(const rlbm_handle* h, int* kind) {
     return -1;
   }
   if (h->q.Q == 28 && h->sc.sym) { *kind = kKindMassless; return 0; }
-  if (h->q.Q == 33) { *kind = kKindQ33; return 0; }
-  if (h->q.Q == 25) { *kind = kKindQ25; return 0; }
-  if (h->q.Q == 29) { *kind = kKindQ29; return 0; }
+  if (h->q.Q == 33 && h->sc.sym) { *kind = kKindQ33; return 0; }
+  if (h->q.Q == 25 && h->sc.sym) { *kind = kKindQ25; return 0; }
+  if (h->q.Q == 29 && h->sc.sym) { *kind = kKindQ29; return 0; }
   return -1;
 }
 

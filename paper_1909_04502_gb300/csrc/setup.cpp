@@ -406,14 +406,40 @@ bool massive_quadrature(const std::vector<int>& groups, double m, double v0, int
   q->order = order;
   q->v0 = v0;
   q->groups = groups;
-  for (int i = 0; i < Qf; ++i) {
-    if (wg[gid[i]] == 0.0) continue;
-    q->nx.push_back(vx[i]);
-    q->ny.push_back(vy[i]);
-    q->p0.push_back(p0[i]);
-    q->px.push_back(px[i]);
-    q->py.push_back(py[i]);
-    q->w.push_back(wg[gid[i]]);
+  // Populations in orbit order (the kernels' symmetric evaluation relies on
+  // it), each type in group order: eight-member orbits as the sign quartets
+  // (a, b), (-a, b), (a, -b), (-a, -b) of the generator and of its swap; axis
+  // quartets (p, 0), (-p, 0), (0, p), (0, -p); diagonal quartets (a, a),
+  // (-a, a), (a, -a), (-a, -a); the rest population.
+  auto emit = [&](int nx, int ny, double wgt) {
+    const double v2 = v0 * v0 * (nx * nx + ny * ny);
+    const double gam = 1.0 / std::sqrt(1.0 - v2);
+    q->nx.push_back(nx);
+    q->ny.push_back(ny);
+    q->p0.push_back(m * gam);
+    q->px.push_back(m * gam * v0 * nx);
+    q->py.push_back(m * gam * v0 * ny);
+    q->w.push_back(wgt);
+  };
+  for (int type = 0; type < 4; ++type) {
+    for (int g = 0; g < ng; ++g) {
+      if (wg[g] == 0.0) continue;
+      const int a = std::abs(groups[2 * g]), b = std::abs(groups[2 * g + 1]);
+      const int t = (a == 0 && b == 0) ? 3 : (a == 0 || b == 0) ? 1 : (a == b) ? 2 : 0;
+      if (t != type) continue;
+      if (t == 0) {
+        const int sg[4][2] = {{1, 1}, {-1, 1}, {1, -1}, {-1, -1}};
+        for (auto& z : sg) emit(z[0] * a, z[1] * b, wg[g]);
+        for (auto& z : sg) emit(z[0] * b, z[1] * a, wg[g]);
+      } else if (t == 1) {
+        const int p = std::max(a, b);
+        emit(p, 0, wg[g]); emit(-p, 0, wg[g]); emit(0, p, wg[g]); emit(0, -p, wg[g]);
+      } else if (t == 2) {
+        emit(a, a, wg[g]); emit(-a, a, wg[g]); emit(a, -a, wg[g]); emit(-a, -a, wg[g]);
+      } else {
+        emit(0, 0, wg[g]);
+      }
+    }
   }
   q->Q = (int)q->w.size();
   return true;

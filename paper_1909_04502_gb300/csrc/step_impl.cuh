@@ -196,7 +196,7 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 // and U = v / nu only needs FP32 accuracy.  About 24 FP64 operations per
 // cell.  The moments are reference + FP32 sums of g, and the eigenvalue is
 // written l = eps_ref + delta.
-// ML: 1 massless (known at compile time), -1 decided by sc.massless.
+// ML: 1 massless, 0 massive (known at compile time), -1 decided by sc.massless.
 template <int ML = -1>
 __device__ __forceinline__ Macro landau_fp32(const Scalars& sc, const float (&mm)[9]) {
   const float epsr = sc.f_T00_ref;
@@ -420,17 +420,46 @@ __device__ __forceinline__ void for_each_halo_image(const Scalars& s, int x, int
 //     four parity classes of H_k dM_k are summed once and combined.
 // The host enables this only after checking these identities on H exactly.
 // ---------------------------------------------------------------------------
+// Orbit composition of the stencils with a symmetric evaluation, in the
+// population order of setup.cpp: n8 eight-member orbits, then n4 axis
+// quartets, nd diagonal quartets and n1 rest populations.
+// (massless: the stencil belongs to m~ = 0, which fixes the EOS branch at
+// compile time)
 template <int QT>
 struct Orbits {
-  static constexpr int n8 = 0, n4 = 0;
+  static constexpr int n8 = 0, n4 = 0, nd = 0, n1 = 0;
+  static constexpr bool massless = false;
 };
 template <>
-struct Orbits<28> {   // order 2: 3 shells x 8 + 1 shell x 4
-  static constexpr int n8 = 3, n4 = 1;
+struct Orbits<28> {   // massless order 2: 3 shells x 8 + 1 shell x 4
+  static constexpr int n8 = 3, n4 = 1, nd = 0, n1 = 0;
+  static constexpr bool massless = true;
 };
 template <>
-struct Orbits<44> {   // order 3: 4 shells x 8 + 3 shells x 4
-  static constexpr int n8 = 4, n4 = 3;
+struct Orbits<44> {   // massless order 3: 4 shells x 8 + 3 shells x 4
+  static constexpr int n8 = 4, n4 = 3, nd = 0, n1 = 0;
+  static constexpr bool massless = true;
+};
+template <>
+struct Orbits<33> {   // built-in m~ = 1, order 2
+  static constexpr int n8 = 3, n4 = 1, nd = 1, n1 = 1;
+  static constexpr bool massless = false;
+};
+template <>
+struct Orbits<29> {   // built-in m~ = 5, order 2
+  static constexpr int n8 = 2, n4 = 1, nd = 2, n1 = 1;
+  static constexpr bool massless = false;
+};
+template <>
+struct Orbits<25> {   // built-in m~ = 10, order 2
+  static constexpr int n8 = 1, n4 = 2, nd = 2, n1 = 1;
+  static constexpr bool massless = false;
+};
+template <int QT>
+struct OrbitStart {
+  using O = Orbits<QT>;
+  static constexpr int axis = 8 * O::n8, diag = axis + 4 * O::n4, rest = diag + 4 * O::nd;
+  static_assert(rest + O::n1 == QT || QT == 0 || O::n8 + O::n4 == 0, "orbit composition must cover the stencil");
 };
 
 template <typename S, int QT>
@@ -459,7 +488,7 @@ __device__ __forceinline__ void moments_sym(const Tables<S>& tb, const S (&g)[QT
   }
 #pragma unroll
   for (int o = 0; o < O::n4; ++o) {
-    const int i = 8 * O::n8 + 4 * o;
+    const int i = OrbitStart<QT>::axis + 4 * o;
     const S S1 = g[i] + g[i + 1], D1 = g[i] - g[i + 1], S2 = g[i + 2] + g[i + 3], D2 = g[i + 2] - g[i + 3];
     const S Sab = S1 + S2;
     // c = p0, p, 0, p0^2, p0 p, 0, p^2, 0, 0 of the base (p, 0)
@@ -471,6 +500,28 @@ __device__ __forceinline__ void moments_sym(const Tables<S>& tb, const S (&g)[QT
     mm[5] = fma(tb.c[i][4], D2, mm[5]);
     mm[6] = fma(tb.c[i][6], S1, mm[6]);
     mm[8] = fma(tb.c[i][6], S2, mm[8]);
+  }
+#pragma unroll
+  for (int o = 0; o < O::nd; ++o) {
+    const int i = OrbitStart<QT>::diag + 4 * o;
+    // (a, a), (-a, a), (a, -a), (-a, -a): one sign quartet with a = b
+    const S u0 = g[i] + g[i + 1], u1 = g[i] - g[i + 1], u2 = g[i + 2] + g[i + 3], u3 = g[i + 2] - g[i + 3];
+    const S SA = u0 + u2, YA = u0 - u2, XA = u1 + u3, XYA = u1 - u3;
+    mm[0] = fma(tb.c[i][0], SA, mm[0]);
+    mm[1] = fma(tb.c[i][1], XA, mm[1]);
+    mm[2] = fma(tb.c[i][1], YA, mm[2]);
+    mm[3] = fma(tb.c[i][3], SA, mm[3]);
+    mm[4] = fma(tb.c[i][4], XA, mm[4]);
+    mm[5] = fma(tb.c[i][4], YA, mm[5]);
+    mm[6] = fma(tb.c[i][6], SA, mm[6]);
+    mm[7] = fma(tb.c[i][7], XYA, mm[7]);
+    mm[8] = fma(tb.c[i][6], SA, mm[8]);
+  }
+#pragma unroll
+  for (int o = 0; o < O::n1; ++o) {
+    const int i = OrbitStart<QT>::rest + o;   // p = (p0, 0, 0)
+    mm[0] = fma(tb.c[i][0], g[i], mm[0]);
+    mm[3] = fma(tb.c[i][3], g[i], mm[3]);
   }
 }
 
@@ -492,6 +543,33 @@ __device__ __forceinline__ void feq_orbit8(const S (&h)[kMaxK], const S (&dM)[KT
   f[0] = A + C; f[1] = B - D; f[2] = B + D; f[3] = A - C;
   const S Ab = Eb + OXYb, Bb = Eb - OXYb, Cb = OXb + OYb, Db = OXb - OYb;
   f[4] = Ab + Cb; f[5] = Bb - Db; f[6] = Bb + Db; f[7] = Ab - Cb;
+}
+
+// ... of the four members (a, a), (-a, a), (a, -a), (-a, -a) of a diagonal
+// quartet (their rows are the first row with the flips' column signs) ...
+template <typename S, int KT>
+__device__ __forceinline__ void feq_diag4(const S (&h)[kMaxK], const S (&dM)[KT], S (&f)[4]) {
+  S E = S(0), OX = S(0), OY = S(0), OXY = S(0);
+#pragma unroll
+  for (int k = 0; k < KT; ++k) {
+    const int ax = mono_ax(k), ay = mono_ay(k);
+    if (!ax && !ay) E = fma(h[k], dM[k], E);
+    else if (ax && !ay) OX = fma(h[k], dM[k], OX);
+    else if (!ax && ay) OY = fma(h[k], dM[k], OY);
+    else OXY = fma(h[k], dM[k], OXY);
+  }
+  const S A = E + OXY, B = E - OXY, C = OX + OY, D = OX - OY;
+  f[0] = A + C; f[1] = B - D; f[2] = B + D; f[3] = A - C;
+}
+
+// ... of a rest population (its row has only px- and py-even entries) ...
+template <typename S, int KT>
+__device__ __forceinline__ S feq_rest(const S (&h)[kMaxK], const S (&dM)[KT]) {
+  S E = S(0);
+#pragma unroll
+  for (int k = 0; k < KT; ++k)
+    if (!mono_ax(k) && !mono_ay(k)) E = fma(h[k], dM[k], E);
+  return E;
 }
 
 // ... and of the four members (p, 0), (-p, 0), (0, p), (0, -p) (the row of
@@ -526,7 +604,7 @@ __device__ __forceinline__ void collide_store(const Tables<S>& tb, const Scalars
   S mm[9];
   if constexpr (SYM) moments_sym<S, QT>(tb, g, mm);
   else moments9<S, QT, EX>(tb, s.Q, g, mm);
-  const Macro M = landau<S, SYM ? 1 : -1>(s, mm);
+  const Macro M = landau<S, SYM ? (Orbits<QT>::massless ? 1 : 0) : -1>(s, mm);
   if (!M.ok) atomicAdd(status, 1ULL);
   if constexpr (MOUT && sizeof(S) == 4) {
     const int cell = y * s.nx + x;
@@ -577,7 +655,7 @@ __device__ __forceinline__ void collide_store(const Tables<S>& tb, const Scalars
     }
 #pragma unroll
     for (int o = 0; o < O::n4; ++o) {
-      const int i0 = 8 * O::n8 + 4 * o;
+      const int i0 = OrbitStart<QT>::axis + 4 * o;
       S f[4];
       feq_orbit4<S, KT>(tb.H[i0], dM, f);
       const S X = Uxk * tb.vx[i0], Y = Uyk * tb.vx[i0];   // members (v,0), (-v,0), (0,v), (0,-v)
@@ -585,6 +663,20 @@ __device__ __forceinline__ void collide_store(const Tables<S>& tb, const Scalars
       relax(i0 + 1, f[1], U0k + X);
       relax(i0 + 2, f[2], U0k - Y);
       relax(i0 + 3, f[3], U0k + Y);
+    }
+#pragma unroll
+    for (int o = 0; o < O::nd; ++o) {
+      const int i0 = OrbitStart<QT>::diag + 4 * o;
+      S f[4], om[4];
+      feq_diag4<S, KT>(tb.H[i0], dM, f);
+      quartet_om(tb.vx[i0], tb.vy[i0], om);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) relax(i0 + m, f[m], om[m]);
+    }
+#pragma unroll
+    for (int o = 0; o < O::n1; ++o) {
+      const int i0 = OrbitStart<QT>::rest + o;
+      relax(i0, feq_rest<S, KT>(tb.H[i0], dM), U0k);
     }
   } else {
 #pragma unroll

@@ -7,20 +7,21 @@ namespace rlbm {
 
 template <typename S>
 cudaError_t launch_step_k9(const Tables<S>& tb, const StepArgs<S>& a, int mode, cudaStream_t st) {
-  // exact instantiations for the built-in stencils (massless Q = 28 with the
-  // orbit-symmetric evaluation; massive m~ = 10, 5, 1: Q = 25, 29, 33),
-  // bounded buckets otherwise
+  // exact orbit-symmetric instantiations for the built-in stencils (massless
+  // Q = 28; massive m~ = 10, 5, 1: Q = 25, 29, 33), bounded buckets otherwise
   if (a.s.Q == 28 && a.s.sym) {
     if constexpr (sizeof(S) == 4)
       if (a.macro) return launch_step_q<S, 28, true, 9, true, true>(tb, a, mode, st);
     return launch_step_q<S, 28, true, 9, true>(tb, a, mode, st);
   }
   if (a.macro) return cudaErrorInvalidValue;   // macroscopic output: built-in massless FP32 stencil only
-  switch (a.s.Q) {
-    case 25: return launch_step_q<S, 25, true, 9>(tb, a, mode, st);
-    case 29: return launch_step_q<S, 29, true, 9>(tb, a, mode, st);
-    case 33: return launch_step_q<S, 33, true, 9>(tb, a, mode, st);
-    default: break;
+  if (a.s.sym) {
+    switch (a.s.Q) {
+      case 25: return launch_step_q<S, 25, true, 9, true>(tb, a, mode, st);
+      case 29: return launch_step_q<S, 29, true, 9, true>(tb, a, mode, st);
+      case 33: return launch_step_q<S, 33, true, 9, true>(tb, a, mode, st);
+      default: break;
+    }
   }
   const int Q = a.s.Q;
   if (Q <= 32) return launch_step_q<S, 32, false, 9>(tb, a, mode, st);

@@ -163,3 +163,38 @@ def test_massless_tables_are_in_orbit_order_with_exactly_symmetric_H(rl, order):
             assert np.array_equal(H[i0 + m], row), (o, m)
         if o >= n8:
             assert p[i0, 2] == 0.0 and all(H[i0][k] == 0.0 for k, (_, a, b) in enumerate(basis) if b % 2)
+
+
+@pytest.mark.parametrize("m,Q,comp", [(1.0, 33, (3, 1, 1, 1)), (5.0, 29, (2, 1, 2, 1)), (10.0, 25, (1, 2, 2, 1))])
+def test_builtin_massive_tables_are_in_orbit_order_with_exactly_symmetric_H(rl, m, Q, comp):
+    """The built-in massive stencils come in orbit order too: eight-member
+    orbits (sign quartets of (a, b) and (b, a)), axis quartets (p, 0), (-p, 0),
+    (0, p), (0, -p), diagonal quartets (a, a), (-a, a), (a, -a), (-a, -a), the
+    rest population; weights and H rows are exact images of each orbit's first
+    member (what the kernels' symmetric evaluation uses)."""
+    d = rl.plan(nx=16, ny=16, m=m, order=2)
+    assert d["Q"] == Q
+    p, H, w = d["p"], d["H"], d["w"]
+    basis = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, 0, 1), (0, 2, 0), (0, 1, 1), (0, 0, 2)]
+    swap = [basis.index((e, b, a)) for (e, a, b) in basis]
+
+    def member(i0, sx, sy, sw):
+        bx, by = (p[i0, 2], p[i0, 1]) if sw else (p[i0, 1], p[i0, 2])
+        sgn = np.array([sx ** a * sy ** b for (_, a, b) in basis], dtype=float)
+        return np.array([p[i0, 0], sx * bx, sy * by]), sgn * (H[i0][swap] if sw else H[i0])
+
+    quart = [(1, 1, 0), (-1, 1, 0), (1, -1, 0), (-1, -1, 0)]
+    layouts = ([quart + [(sx, sy, 1) for sx, sy, _ in quart]] * comp[0]
+               + [[(1, 1, 0), (-1, 1, 0), (1, 1, 1), (1, -1, 1)]] * comp[1] + [quart] * comp[2])
+    i0 = 0
+    for lay in layouts:
+        for k, (sx, sy, sw) in enumerate(lay):
+            pm, row = member(i0, sx, sy, sw)
+            assert np.array_equal(p[i0 + k], pm) and w[i0 + k] == w[i0]
+            assert np.array_equal(H[i0 + k], row)
+        i0 += len(lay)
+    for _ in range(comp[3]):
+        assert p[i0, 1] == 0.0 and p[i0, 2] == 0.0
+        assert all(H[i0][k] == 0.0 for k, (_, a, b) in enumerate(basis) if a % 2 or b % 2)
+        i0 += 1
+    assert i0 == Q
