@@ -294,6 +294,20 @@ int rlbm_adjoint_backward(rlbm_adjoint* A, const double* ux_target, const double
                           double* loss, double* grad_tau, double* grad_ux0, double* grad_uy0, int out_on_device);
 const char* rlbm_adjoint_last_error(const rlbm_adjoint* A);
 
+/* One adjoint step, the building block of rlbm_adjoint_backward: the
+ * vector-Jacobian product of one collide-and-stream step (Eq. discrete-rbe,
+ * Sec. 6.2) with f(t) = S x(t-1) and f(t+1) = S C(f(t)):
+ *   a_out = dL/df(t) = C'(f(t))^T S^T a_next,   a_next = dL/df(t+1),
+ * and grad_tau[cell] += dL/dtau(cell) of this step.  x_prev = x(t-1), the
+ * post-collision populations the forward step started from; x_prev, a_next
+ * and a_out are device buffers in the handle's padded layout and storage
+ * type (rlbm_buffers), halo images included; a_out gets its halo images
+ * written.  grad_tau: device FP64 [ny][nx], accumulated.  All pointers are
+ * borrowed; asynchronous on the handle's stream.  Periodic boundaries,
+ * order 2, constant or per-cell tau (RLBM_ERR_UNSUPPORTED otherwise).
+ * No counterpart in the paper. */
+int rlbm_adjoint_step(rlbm_handle* h, const void* x_prev, const void* a_next, void* a_out, double* grad_tau);
+
 /* Message of the last error on this handle (or of the last failed
  * rlbm_create when h is NULL).  Never NULL. */
 const char* rlbm_last_error(const rlbm_handle* h);

@@ -722,6 +722,30 @@ int rlbm_adjoint_backward(rlbm_adjoint* A, const double* ux_target, const double
   return RLBM_OK;
 }
 
+int rlbm_adjoint_step(rlbm_handle* h, const void* x_prev, const void* a_next, void* a_out, double* grad_tau) {
+  if (!h || !x_prev || !a_next || !a_out || !grad_tau) return RLBM_ERR_INVALID_ARG;
+  if (h->p.boundary != RLBM_BC_PERIODIC || h->p.order != 2 || h->p.tau_mode == RLBM_TAU_ETA_OVER_S ||
+      h->q.Q > 40)
+    return RLBM_ERR_UNSUPPORTED;
+  const int mode = h->p.stream_mode == RLBM_BILINEAR ? kBilinear : kOnLattice;
+  const void* tf = h->p.tau_mode == RLBM_TAU_FIELD ? h->tau_field : nullptr;
+  cudaError_t e;
+  if (h->elem == 4) {
+    AdjArgs<float> aa{h->sc, (const float*)x_prev, (const float*)a_next, (float*)a_out, (const float*)tf, grad_tau,
+                      h->status};
+    e = adj_step<float>(*h->tf, aa, mode, h->stream);
+  } else {
+    AdjArgs<double> aa{h->sc, (const double*)x_prev, (const double*)a_next, (double*)a_out, (const double*)tf,
+                       grad_tau, h->status};
+    e = adj_step<double>(*h->td, aa, mode, h->stream);
+  }
+  if (e != cudaSuccess) {
+    h->err = std::string("adjoint step kernel: ") + cudaGetErrorString(e);
+    return RLBM_ERR_CUDA;
+  }
+  return RLBM_OK;
+}
+
 const char* rlbm_adjoint_last_error(const rlbm_adjoint* A) { return A ? A->err.c_str() : "null adjoint"; }
 
 }  // extern "C"

@@ -60,6 +60,7 @@ SIGNATURES = {
     "rlbm_set_tau_field": (ctypes.c_int, [_H, _VP, ctypes.c_int]),
     "rlbm_step": (ctypes.c_int, [_H, ctypes.c_int]),
     "rlbm_set_step_kernel": (ctypes.c_int, [_H, ctypes.c_int]),
+    "rlbm_adjoint_step": (ctypes.c_int, [_H, _VP, _VP, _VP, _VP]),
     "rlbm_step_kernel": (ctypes.c_int, [_H]),
     "rlbm_moments": (ctypes.c_int, [_H, _VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_int]),
     "rlbm_get_populations": (ctypes.c_int, [_H, _VP, ctypes.c_int]),

@@ -200,3 +200,49 @@ def test_calibration_full_size_gradient(rl):
     assert abs(ad - fd) < 1e-4 * abs(fd), info
     assert abs(ad32 - fd) < 1e-4 * abs(fd), info
     assert g_err < 1e-3, info
+
+
+def test_single_adjoint_step_entry_point(rl):
+    """rlbm_adjoint_step against central differences of one forward step
+    (FP64, on-lattice, periodic).  With f(t) = S x and x(t) = C(f(t)), and
+    L(x) = <a_next, S C(S x)>, the step returns a = C'^T S^T a_next, so
+    dL/dx . dx = <S^T a, dx> = <a, S dx>.  S is the periodic pull, applied on
+    the host with the oracle's streaming."""
+    import ctypes
+    import torch
+    nx, ny, tau = 24, 16, 0.9
+    fields = [np.ascontiguousarray(a) for a in inputs.random_smooth(nx, ny, seed=17, umax=0.2)]
+    mk = lambda: rl.Lattice(nx, ny, precision="fp64", tau=tau)
+    base = mk()
+    base.init(*fields)
+    base.step(2)
+    x = base.populations()
+    shifts = base.n
+    rng = np.random.default_rng(3)
+    a_next = rng.standard_normal(x.shape) * 1e-2
+    dx = rng.standard_normal(x.shape) * np.abs(x).max() * 1e-2
+    hx, ha, ho = mk(), mk(), mk()
+    hx.set_populations(x)
+    ha.set_populations(a_next)
+    ho.set_populations(np.zeros_like(x))
+    gt = torch.zeros((ny, nx), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    rc = rl.lib().rlbm_adjoint_step(hx.h, hx.buffers()[0], ha.buffers()[0], ho.buffers()[0], gt.data_ptr())
+    assert rc == 0
+    torch.cuda.synchronize()
+    a = ho.populations()
+
+    def L(xs):
+        hf = mk()
+        hf.set_populations(xs)
+        hf.step(1)
+        y = hf.populations()
+        hf.close()
+        return float(np.sum(a_next * OS.stream_onlattice(y, shifts, "periodic")))
+
+    h = 1e-4
+    fd = (L(x + h * dx) - L(x - h * dx)) / (2 * h)
+    ad = float(np.sum(a * OS.stream_onlattice(dx, shifts, "periodic")))
+    assert abs(ad - fd) < 1e-6 * abs(fd), (ad, fd)
+    for lat in (base, hx, ha, ho):
+        lat.close()
