@@ -303,7 +303,7 @@ struct AdjArgs {
 };
 
 template <typename S, int QT, bool EX, int MODE, bool SYM, bool MIN>
-__global__ void __launch_bounds__(kThreads, sizeof(S) == 4 ? 2 : 1) k_adj_step(const __grid_constant__ Tables<S> tb,
+__global__ void __launch_bounds__(kThreads, (sizeof(S) == 4 ? 512 : 256) / kThreads) k_adj_step(const __grid_constant__ Tables<S> tb,
                                                        const __grid_constant__ AdjArgs<S> a) {
   const int x = blockIdx.x * kBX + threadIdx.x;
   const int y = blockIdx.y * kBY + threadIdx.y;
