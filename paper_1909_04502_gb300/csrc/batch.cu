@@ -5,9 +5,9 @@
 //
 // Work decomposition: every instance's grid is cut into tiles of BX x BY
 // cells, numbered consecutively over all instances with the tiles of each
-// kind contiguous; block b of a kind's persistent grid takes that kind's
-// tiles b, b + G, b + 2G, ... of each time step, then waits at a grid-wide
-// barrier before the next step.  The barrier spins a
+// kind contiguous; block b of a kind's persistent grid of G blocks takes the
+// b-th of G equal contiguous chunks of that kind's tiles in each time step,
+// then waits at a grid-wide barrier before the next step.  The barrier spins a
 // bounded number of times; on timeout it records RLBM_ERR_TIMEOUT and every
 // block leaves.
 #include <cuda_runtime.h>
@@ -119,26 +119,34 @@ __device__ __forceinline__ void batch_tile(const BatchInst& I, int tile, int ste
 }
 
 // One persistent kernel per stencil kind: a kernel compiled for a single
-// population count keeps the per-kind register budget of the single-grid
-// kernel (a kernel holding every kind's cell update spills).  The tiles of
-// the kind's instances are the contiguous range [tile_lo, tile_hi).
+// population count keeps a per-kind register budget (a kernel holding every
+// kind's cell update spills).  768 resident threads per SM (80 registers):
+// the run-time offsets and the loop state need more registers than the
+// single-grid kernel's 64, and at 1024 threads the spills cost more than the
+// lost occupancy (measured 3-10 % slower).  The tiles of the kind's instances
+// are the contiguous range [tile_lo, tile_hi).
 template <int BX, int BY, int KIND>
-__global__ void __launch_bounds__(BX * BY, (BX * BY == 256) ? 4 : 8) k_batch(const __grid_constant__ BatchArgs a) {
+__global__ void __launch_bounds__(BX * BY, 768 / (BX * BY)) k_batch(const __grid_constant__ BatchArgs a) {
   __shared__ BatchInst s_inst;
-  __shared__ int s_idx;
-  if (threadIdx.x == 0 && threadIdx.y == 0) s_idx = -1;
+  constexpr int kWords = (int)(sizeof(BatchInst) / sizeof(int));
+  static_assert(sizeof(BatchInst) % sizeof(int) == 0, "descriptor copied as words");
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  // block b takes the contiguous chunk [lo, hi) of this kind's tiles, so the
+  // instance (and its descriptor) changes only at chunk or instance boundaries
+  const long long n = a.tile_hi - a.tile_lo;
+  const int lo = a.tile_lo + (int)(n * blockIdx.x / gridDim.x);
+  const int hi = a.tile_lo + (int)(n * (blockIdx.x + 1) / gridDim.x);
+  int have = -1;                      // instance held in s_inst (the same in every thread)
   for (int step = 0; step < a.nsteps; ++step) {
-    for (int t = a.tile_lo + blockIdx.x; t < a.tile_hi; t += gridDim.x) {
+    for (int t = lo; t < hi; ++t) {
       const int idx = __ldg(a.tile_inst + t);
-      __syncthreads();                // previous tile done; s_idx stable
-      const int have = s_idx;
-      __syncthreads();                // everyone has read s_idx before it changes
-      if (idx != have) {              // block-uniform: copy the descriptor once per instance change
-        if (threadIdx.x == 0 && threadIdx.y == 0) {
-          s_inst = a.inst[idx];
-          s_idx = idx;
-        }
+      if (idx != have) {              // block-uniform
+        __syncthreads();              // every thread is done with the previous descriptor
+        const int* src = reinterpret_cast<const int*>(a.inst + idx);
+        int* dst = reinterpret_cast<int*>(&s_inst);
+        for (int w = tid; w < kWords; w += BX * BY) dst[w] = src[w];
         __syncthreads();
+        have = idx;
       }
       batch_tile<BX, BY, KIND>(s_inst, t, step);
     }
