@@ -44,7 +44,7 @@ def stream_onlattice(fs, shifts, boundary="periodic"):
         yy = (ys - sy) % ny
         if boundary == "periodic":
             xx = (xs - sx) % nx
-        elif boundary == "freeflow_x":
+        elif boundary in ("freeflow_x", "eqwall_x"):
             xx = np.clip(xs - sx, 0, nx - 1)
         else:
             raise ValueError(boundary)
@@ -144,22 +144,52 @@ def tau_from_eta_over_s(T, eta_over_s, kappa, d=2):
     return eta_over_s * (d + 2) * kappa / T
 
 
-def collide(f, quad: Quadrature, exp: Expansion, tau):
-    """Steps 1-8 (no external force): returns f*(x) and the fields of f."""
+def forcing_term(feq, fl, quad: Quadrature, g):
+    """Step 6, scheme B of Sec. 4.4 (Delta t = 1): the external-force term of
+    Eq. rbe-rta-lattice-friendly, -(m K^a / p^0) df/dp^a, with df/dp^a taken
+    from the Maxwell-Juttner derivative -(U_a / T) f^eq, for a gravity-like
+    Minkowski force K = (g.p, p^0 g) (K^a p_a = 0):
+        F_i = (m / T) f^eq_i (K^a U_a) / p^0_i = (m / T) f^eq_i (U^0 g.v_i - g.U).
+    Reading: the sign follows the continuous equation, so that the fluid is
+    pushed along g (the printed discrete equation adds F^ext with the
+    opposite sign convention).  Massless particles (m = 0) feel no force."""
+    gx, gy = g
+    v = quad.velocity()
+    gv = gx * v[:, 0, None, None] + gy * v[:, 1, None, None]
+    gU = gx * fl.U[1] + gy * fl.U[2]
+    return (quad.m / fl.T) * feq * (fl.U[0] * gv - gU)
+
+
+def collide(f, quad: Quadrature, exp: Expansion, tau, g=None, eqwall=False):
+    """Steps 1-8: returns f*(x) and the fields of f.  g: optional gravity-like
+    force (gx, gy), added as forcing_term.  eqwall: equilibrium walls at the
+    first and last column (reading of the no-slip walls of Sec. 8.1: the
+    post-collision populations there are the equilibrium at zero flow speed,
+    f^eq(n, U = (1, 0, 0), T), with the cell's own n and T)."""
     fl = macroscopic(f, quad)
     feq = exp.feq(fl.n, fl.U, fl.T)                                    # step 5
     if isinstance(tau, tuple):                                          # step 7
         tau = tau_from_eta_over_s(fl.T, *tau)
     omega = relaxation_factor(fl.U, tau, quad.p)                        # step 8
-    return (1.0 - omega) * f + omega * feq, fl
+    fs = (1.0 - omega) * f + omega * feq
+    if g is not None:
+        fs = fs + forcing_term(feq, fl, quad, g)
+    if eqwall:
+        for col in (0, f.shape[2] - 1):
+            n, T = fl.n[:, col], fl.T[:, col]
+            rest = np.zeros((3,) + n.shape)
+            rest[0] = 1.0
+            fs[:, :, col] = exp.feq(n, rest, T)
+    return fs, fl
 
 
 class Simulation:
     """Time integration with the state convention of the module docstring."""
 
     def __init__(self, quad: Quadrature, exp: Expansion, nx, ny, tau=1.0,
-                 boundary="periodic", stream="onlattice", lam=None):
+                 boundary="periodic", stream="onlattice", lam=None, g=None):
         self.quad, self.exp = quad, exp
+        self.g = g                           # optional gravity-like force (gx, gy)
         self.nx, self.ny = nx, ny
         self.tau = tau                       # scalar, (ny, nx) array or (eta/s, kappa)
         self.boundary = boundary
@@ -189,6 +219,7 @@ class Simulation:
     def step(self, nsteps=1):
         for _ in range(nsteps):
             f = self.stream(self.fs)
-            self.fs, self.fields = collide(f, self.quad, self.exp, self.tau)
+            self.fs, self.fields = collide(f, self.quad, self.exp, self.tau, self.g,
+                                           self.boundary == "eqwall_x")
             self.t += 1
         return self.fs

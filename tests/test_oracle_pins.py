@@ -590,3 +590,61 @@ def test_oracle_sod_matches_app_d_solution():
     _, Pa, _ = P.riemann_ur_profile(s, w)
     i = np.where((w > s["w_H"]) & (Pa < Pmid))[0][0]
     assert abs(crossing(Pmid, -1.0, 0.0) - w[i]) < 0.02
+
+
+# ------------------------------------------------------------ forcing, walls
+
+
+@pytest.mark.parametrize("m", [1.0, 5.0])
+def test_forcing_term_moments_follow_from_the_equilibrium_stress(m):
+    """Scheme B with a gravity-like force (Sec. 4.4).  Its moments follow from
+    T_E^ab = (eps + P) U^a U^b - P eta^ab (exact for the quadrature at order
+    2): no particle source, momentum source n m U^0 g (along g), energy
+    source n m g.U, for any (n, U, T)."""
+    import paper_1909_04502_gb300.inputs as inputs
+    q = _massive_q(m)
+    e = L.Expansion(q)
+    n, ux, uy, T = inputs.random_smooth(8, 4, seed=3, umax=0.4, dn=0.3, dT=0.3)
+    U = P.four_velocity(ux, uy)
+    feq = e.feq(n, U, T)
+    fl = S.macroscopic(feq, q)
+    g = (3e-3, -2e-3)
+    F = S.forcing_term(feq, fl, q, g)
+    p0, px, py = (q.p[:, k, None, None] for k in range(3))
+    assert np.abs(np.sum(p0 * F, axis=0)).max() < 1e-13
+    assert np.allclose(np.sum(p0 * px * F, axis=0), n * m * U[0] * g[0], rtol=1e-10, atol=0)
+    assert np.allclose(np.sum(p0 * py * F, axis=0), n * m * U[0] * g[1], rtol=1e-10, atol=0)
+    assert np.allclose(np.sum(p0 * p0 * F, axis=0), n * m * (g[0] * U[1] + g[1] * U[2]), rtol=1e-9,
+                       atol=1e-15)
+
+
+def _massive_q(m):
+    """Order-2 quadrature at the middle of the v0 window where the oracle's
+    own solve gives non-negative weights: the Sec. 5.3 worked-example stencil
+    (m~ = 5) or App. H column C (m~ = 1)."""
+    groups = ([(0, 0), (1, 0), (1, 1), (2, 1), (2, 2), (3, 1)] if m >= 5 else
+              [(0, 0), (3, 3), (4, 2), (4, 3), (5, 0), (5, 1)])
+    ok = L.search_v0(groups, m, order=2, npts=400)
+    assert ok
+    q, res = L.massive_quadrature(groups, m, 0.5 * (ok[0] + ok[-1]), 2)
+    assert res < 1e-9
+    return q
+
+
+def test_equilibrium_walls_leave_the_wall_columns_at_rest():
+    """After a collision with equilibrium walls the first and last columns
+    carry no flow (N^x = N^y = 0, T^0x = T^0y = 0) and keep the n and T of
+    the streamed populations; interior columns are untouched."""
+    import paper_1909_04502_gb300.inputs as inputs
+    q = _massive_q(5.0)
+    e = L.Expansion(q)
+    n, ux, uy, T = inputs.random_smooth(8, 4, seed=9, umax=0.3)
+    f = e.feq(n, P.four_velocity(ux, uy), T)
+    fs0, _ = S.collide(f, q, e, 0.9)
+    fs, fl = S.collide(f, q, e, 0.9, eqwall=True)
+    for col in (0, 7):
+        after = S.macroscopic(fs[:, :, col:col + 1], q)
+        assert np.abs(after.N[1:]).max() < 1e-13 and np.abs(after.Tab[0, 1:]).max() < 1e-13
+        assert np.allclose(after.n[:, 0], fl.n[:, col], rtol=1e-12)
+        assert np.allclose(after.T[:, 0], fl.T[:, col], rtol=1e-12)
+    assert np.array_equal(fs[:, :, 1:7], fs0[:, :, 1:7])
