@@ -62,7 +62,12 @@ enum {
   RLBM_QUAD_CUSTOM = 2         /* caller table: custom_table / custom_Q           */
 };
 
-enum { RLBM_BC_PERIODIC = 0, RLBM_BC_FREEFLOW_X = 1 };
+/* Boundaries in x (y is always periodic): periodic; free-flow ends (pulls
+ * from beyond an end read the end cell); equilibrium walls at the first and
+ * last column (pulls as free-flow; after each collision the wall cells hold
+ * the equilibrium at zero flow speed with their own n and T -- the no-slip
+ * walls of the paper's Poiseuille validation, Sec. 8.1). */
+enum { RLBM_BC_PERIODIC = 0, RLBM_BC_FREEFLOW_X = 1, RLBM_BC_EQWALL_X = 2 };
 enum { RLBM_FP64 = 0, RLBM_FP32_STORE = 1 };   /* storage/collision precision    */
 enum { RLBM_ONLATTICE = 0, RLBM_BILINEAR = 1 };
 /* Step kernels (rlbm_set_step_kernel).  Both compute the same update (Sec.
@@ -99,6 +104,10 @@ typedef struct rlbm_params {
                          ||n_i|| for m~ = 0 and 1/v0 for m~ > 0)                     */
   double n_ref, T_ref;/* reference state of the shifted FP32 storage (default 1, 1) */
   void* stream;       /* cudaStream_t all work is issued on (NULL = legacy default) */
+  double gx, gy;      /* gravity-like acceleration g (lattice units): Minkowski force
+                         K = (g.p, p^0 g) added by forcing scheme B (Sec. 4.4),
+                         F_i = (m/T) f^eq_i (U^0 g.v_i - g.U) per step; acts on
+                         massive particles only (m~ > 0); default 0             */
 } rlbm_params;
 
 typedef struct rlbm_handle rlbm_handle;
@@ -274,7 +283,8 @@ const char* rlbm_batch_last_error(const rlbm_batch* b);
  * to the per-cell relaxation time tau(x) (constant in time) and the initial
  * velocity u0(x).  The backward pass recomputes the forward states segment
  * by segment from checkpoints taken every checkpoint_every steps.
- * Periodic boundaries, order 2, constant or per-cell tau; both precisions.
+ * Periodic boundaries, order 2, constant or per-cell tau, no external force;
+ * both precisions.
  * ------------------------------------------------------------------------ */
 typedef struct rlbm_adjoint rlbm_adjoint;
 
@@ -304,7 +314,8 @@ const char* rlbm_adjoint_last_error(const rlbm_adjoint* A);
  * type (rlbm_buffers), halo images included; a_out gets its halo images
  * written.  grad_tau: device FP64 [ny][nx], accumulated.  All pointers are
  * borrowed; asynchronous on the handle's stream.  Periodic boundaries,
- * order 2, constant or per-cell tau (RLBM_ERR_UNSUPPORTED otherwise).
+ * order 2, constant or per-cell tau, no external force (RLBM_ERR_UNSUPPORTED
+ * otherwise).
  * No counterpart in the paper. */
 int rlbm_adjoint_step(rlbm_handle* h, const void* x_prev, const void* a_next, void* a_out, double* grad_tau);
 

@@ -556,7 +556,7 @@ int rlbm_adjoint_create(rlbm_handle* h, int nsteps, int checkpoint_every, rlbm_a
   if (!h || !out || nsteps < 1 || checkpoint_every < 1) return RLBM_ERR_INVALID_ARG;
   *out = nullptr;
   if (h->p.boundary != RLBM_BC_PERIODIC || h->p.order != 2 || h->p.tau_mode == RLBM_TAU_ETA_OVER_S ||
-      h->q.Q > 40)
+      h->q.Q > 40 || h->sc.force)
     return RLBM_ERR_UNSUPPORTED;   // adjoint: periodic, order 2, constant or per-cell tau
   std::unique_ptr<rlbm_adjoint> A(new rlbm_adjoint());
   A->h = h;
@@ -725,7 +725,7 @@ int rlbm_adjoint_backward(rlbm_adjoint* A, const double* ux_target, const double
 int rlbm_adjoint_step(rlbm_handle* h, const void* x_prev, const void* a_next, void* a_out, double* grad_tau) {
   if (!h || !x_prev || !a_next || !a_out || !grad_tau) return RLBM_ERR_INVALID_ARG;
   if (h->p.boundary != RLBM_BC_PERIODIC || h->p.order != 2 || h->p.tau_mode == RLBM_TAU_ETA_OVER_S ||
-      h->q.Q > 40)
+      h->q.Q > 40 || h->sc.force)
     return RLBM_ERR_UNSUPPORTED;
   const int mode = h->p.stream_mode == RLBM_BILINEAR ? kBilinear : kOnLattice;
   const void* tf = h->p.tau_mode == RLBM_TAU_FIELD ? h->tau_field : nullptr;

@@ -85,6 +85,9 @@ __global__ void k_tau_import(const double* __restrict__ src, S* __restrict__ dst
 void finish_scalars(Scalars* s) {
   s->PE_ref = s->Tii_ref + s->T00_ref;
   s->n_ref2 = s->n_ref * s->n_ref;
+  s->force = (s->m > 0.0 && (s->gx != 0.0 || s->gy != 0.0)) ? 1 : 0;
+  s->f_gx = (float)s->gx;
+  s->f_gy = (float)s->gy;
   s->massless = (s->m == 0.0) ? 1 : 0;
   s->iplane = (int)s->plane;
   s->f_tau = (float)s->tau;
@@ -205,6 +208,17 @@ void quantize_unit_sum(const double (&w)[4], R (&out)[4]) {
   for (int j = 0; j < 4; ++j) out[j] = (R)std::ldexp((double)k[j], -bits);
 }
 
+// Reference populations of the shifted FP32 storage:
+// f_ref,i = sum_k H_ik M_k(n_ref, e0, T_ref) (zero when n_ref = 0).
+void reference_populations(rlbm_handle* h, int order, double m, double nr, double Tr) {
+  std::vector<double> Mref(h->K);
+  const double e0[3] = {1.0, 0.0, 0.0};
+  mj_moments(order, m, nr, e0, Tr, Mref.data());
+  h->fref.assign(h->q.Q, 0.0);
+  for (int i = 0; i < h->q.Q; ++i)
+    for (int k = 0; k < h->K; ++k) h->fref[i] += h->H[(size_t)i * h->K + k] * Mref[k];
+}
+
 template <typename R>
 void fill_tables(const rlbm_handle* h, const Scalars& s, Tables<R>* t) {
   std::memset(t, 0, sizeof(Tables<R>));
@@ -237,6 +251,7 @@ void fill_tables(const rlbm_handle* h, const Scalars& s, Tables<R>* t) {
     t->pl[i] = i * (int)s.plane;
     t->offp[i] = t->pl[i] + t->off[i];
     t->offr[i] = t->offp[i] + s.pitch;
+    t->fref[i] = (R)(i < (int)h->fref.size() ? h->fref[i] : 0.0);
   }
 }
 
@@ -354,7 +369,7 @@ int rlbm_create(const rlbm_params* p, rlbm_handle** out) {
     return fail(nullptr, RLBM_ERR_INVALID_ARG, "grid size out of range");
   if (p->precision != RLBM_FP64 && p->precision != RLBM_FP32_STORE)
     return fail(nullptr, RLBM_ERR_INVALID_ARG, "precision");
-  if (p->boundary != RLBM_BC_PERIODIC && p->boundary != RLBM_BC_FREEFLOW_X)
+  if (p->boundary != RLBM_BC_PERIODIC && p->boundary != RLBM_BC_FREEFLOW_X && p->boundary != RLBM_BC_EQWALL_X)
     return fail(nullptr, RLBM_ERR_INVALID_ARG, "boundary");
   if (p->stream_mode != RLBM_ONLATTICE && p->stream_mode != RLBM_BILINEAR)
     return fail(nullptr, RLBM_ERR_INVALID_ARG, "stream_mode");
@@ -402,17 +417,14 @@ int rlbm_create(const rlbm_params* p, rlbm_handle** out) {
   s.T00_ref = nr * (m * m + 2.0 * m * Tr + 2.0 * Tr * Tr) / (m + Tr);
   s.Tii_ref = nr * Tr;
   s.kappa_guess = (float)(Tr * (m + Tr) / (m * m + 2.0 * m * Tr + 2.0 * Tr * Tr));
+  s.gx = p->gx;
+  s.gy = p->gy;
   finish_scalars(&s);
-  s.sym = orbit_symmetric(h.get()) ? 1 : 0;
+  // the orbit-symmetric kernels carry neither the force term nor the walls
+  s.sym = (orbit_symmetric(h.get()) && !s.force && s.boundary != RLBM_BC_EQWALL_X) ? 1 : 0;
   if ((long long)h->q.Q * s.plane >= (1LL << 31))
     return fail(nullptr, RLBM_ERR_UNSUPPORTED, "grid too large: Q * plane must stay below 2^31 elements");
-  // reference populations f_ref,i = sum_k H_ik M_k(n_ref, e0, T_ref)
-  std::vector<double> Mref(h->K);
-  const double e0[3] = {1.0, 0.0, 0.0};
-  mj_moments(p->order, m, nr, e0, Tr, Mref.data());
-  h->fref.assign(h->q.Q, 0.0);
-  for (int i = 0; i < h->q.Q; ++i)
-    for (int k = 0; k < h->K; ++k) h->fref[i] += h->H[(size_t)i * h->K + k] * Mref[k];
+  reference_populations(h.get(), p->order, m, nr, Tr);
 
   h->stream = (cudaStream_t)p->stream;
   if (h->elem == 4) {
@@ -697,7 +709,7 @@ int rlbm_internal_prepare(const rlbm_params* p, Scalars* sc, Tables<float>* tf, 
     return RLBM_ERR_INVALID_ARG;
   }
   if (p->precision != RLBM_FP64 && p->precision != RLBM_FP32_STORE) { *err = "precision"; return RLBM_ERR_INVALID_ARG; }
-  if (p->boundary != RLBM_BC_PERIODIC && p->boundary != RLBM_BC_FREEFLOW_X) { *err = "boundary"; return RLBM_ERR_INVALID_ARG; }
+  if (p->boundary != RLBM_BC_PERIODIC && p->boundary != RLBM_BC_FREEFLOW_X && p->boundary != RLBM_BC_EQWALL_X) { *err = "boundary"; return RLBM_ERR_INVALID_ARG; }
   if (p->stream_mode != RLBM_ONLATTICE && p->stream_mode != RLBM_BILINEAR) { *err = "stream_mode"; return RLBM_ERR_INVALID_ARG; }
   if (p->stream_mode == RLBM_BILINEAR && !(p->lambda > 0.0)) { *err = "bilinear streaming needs lambda > 0"; return RLBM_ERR_INVALID_ARG; }
   if (p->tau_mode == RLBM_TAU_CONST && !(p->tau > 0.5)) { *err = "tau must exceed 1/2"; return RLBM_ERR_INVALID_ARG; }
@@ -739,12 +751,16 @@ int rlbm_internal_prepare(const rlbm_params* p, Scalars* sc, Tables<float>* tf, 
   s.T00_ref = nr * (m * m + 2.0 * m * Tr + 2.0 * Tr * Tr) / (m + Tr);
   s.Tii_ref = nr * Tr;
   s.kappa_guess = (float)(Tr * (m + Tr) / (m * m + 2.0 * m * Tr + 2.0 * Tr * Tr));
+  s.gx = p->gx;
+  s.gy = p->gy;
   finish_scalars(&s);
-  s.sym = orbit_symmetric(&h) ? 1 : 0;
+  // the orbit-symmetric kernels carry neither the force term nor the walls
+  s.sym = (orbit_symmetric(&h) && !s.force && s.boundary != RLBM_BC_EQWALL_X) ? 1 : 0;
   if ((long long)h.q.Q * s.plane >= (1LL << 31)) {
     *err = "grid too large: Q * plane must stay below 2^31 elements";
     return RLBM_ERR_UNSUPPORTED;
   }
+  reference_populations(&h, p->order, m, nr, Tr);
   if (p->precision == RLBM_FP32_STORE) fill_tables(&h, s, tf);
   else fill_tables(&h, s, td);
   return RLBM_OK;

@@ -39,6 +39,7 @@ struct Tables {
   int pl[kMaxQ];           // i * plane: start of population plane i
   int offp[kMaxQ];         // pl[i] + off[i]: pull source of population i relative to the cell
   int offr[kMaxQ];         // offp[i] + pitch: the bilinear taps' second row
+  R fref[kMaxQ];           // reference populations f_ref,i (0 without the storage shift)
 };
 
 struct Scalars {
@@ -59,7 +60,10 @@ struct Scalars {
   double n_ref2;           // n_ref^2
   float kappa_guess;       // P/eps of the reference EOS, for the FP32 first guess
   int massless;            // m == 0
-  int sym;                 // built-in massless stencil in orbit order with exactly symmetric H
+  int sym;                 // orbit-ordered stencil with exactly symmetric H (and no force, no walls)
+  int force;               // gravity-like force present (m > 0 and g != 0)
+  double gx, gy;           // its acceleration
+  float f_gx, f_gy;
   int iplane;              // plane as int (Q * plane < 2^31 is checked at creation)
   // FP32 copies of the scalars used by the FP32-storage kernels
   float f_tau, f_tau_coef, f_m, f_n_ref, f_T_ref, f_T00_ref, f_Tii_ref;

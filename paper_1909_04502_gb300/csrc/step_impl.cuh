@@ -679,13 +679,43 @@ __device__ __forceinline__ void collide_store(const Tables<S>& tb, const Scalars
       relax(i0, feq_rest<S, KT>(tb.H[i0], dM), U0k);
     }
   } else {
+    // Forcing scheme B (Sec. 4.4), gravity-like force K = (g.p, p^0 g):
+    // F_i = (m/T) f^eq_i (U^0 g.v_i - g.U), with the full f^eq (the stored
+    // shift f_ref added back).  Equilibrium walls (first and last column):
+    // the cell keeps f^eq(n, U = (1, 0, 0), T) instead.
+    S cf = S(0), gx = S(0), gy = S(0), gU = S(0);
+    if (s.force && M.ok) {
+      if constexpr (sizeof(S) == 4) { cf = __fdividef(s.f_m, M.fT); gx = s.f_gx; gy = s.f_gy; }
+      else { cf = s.m / M.T; gx = s.gx; gy = s.gy; }
+      gU = gx * Ux + gy * Uy;
+    }
+    const bool wall = s.boundary == 2 && (x == 0 || x == s.nx - 1) && M.ok;
+    S dMw[KT];
+    if (wall) {
+      if constexpr (sizeof(S) == 4)
+        eq_moments<S, KT>(M.fdn, M.fdT, M.fn, M.fT, S(1), S(0), S(0), s.f_m, s.f_n_ref, s.f_T_ref, dMw);
+      else
+        eq_moments<S, KT>(M.n - s.n_ref, M.T - s.T_ref, M.n, M.T, S(1), S(0), S(0), s.m, s.n_ref, s.T_ref, dMw);
+    }
 #pragma unroll
     for (int i = 0; i < QT; ++i) {
       if (i < Qn) {
+        if (wall) {
+          S fw = S(0);
+#pragma unroll
+          for (int k = 0; k < KT; ++k) fw = fma(tb.H[i][k], dMw[k], fw);
+          g[i] = fw;
+          obase[plane_of(i)] = fw;
+          continue;
+        }
         S feq = S(0);
 #pragma unroll
         for (int k = 0; k < KT; ++k) feq = fma(tb.H[i][k], dM[k], feq);
         relax(i, feq, kt * (U0 - Ux * tb.vx[i] - Uy * tb.vy[i]));
+        if (cf != S(0)) {
+          g[i] = fma(cf * (feq + tb.fref[i]), U0 * (gx * tb.vx[i] + gy * tb.vy[i]) - gU, g[i]);
+          obase[plane_of(i)] = g[i];
+        }
       }
     }
   }

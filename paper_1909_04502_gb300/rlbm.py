@@ -19,7 +19,7 @@ RLBM_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "CUDA", -4: "NONPHYSICAL", -5: "TIMEOUT",
           -6: "OOM", -7: "QUADRATURE"}
 QUAD = {"massless": 0, "massive": 1, "custom": 2}
-BC = {"periodic": 0, "freeflow_x": 1}
+BC = {"periodic": 0, "freeflow_x": 1, "eqwall_x": 2}
 PREC = {"fp64": 0, "fp32": 1}
 STREAM = {"onlattice": 0, "bilinear": 1}
 TAU = {"const": 0, "field": 1, "eta_over_s": 2}
@@ -41,7 +41,7 @@ class Params(ctypes.Structure):
         ("kappa", ctypes.c_double), ("boundary", ctypes.c_int), ("nx", ctypes.c_int),
         ("ny", ctypes.c_int), ("precision", ctypes.c_int), ("stream_mode", ctypes.c_int),
         ("lam", ctypes.c_double), ("n_ref", ctypes.c_double), ("T_ref", ctypes.c_double),
-        ("stream", ctypes.c_void_p),
+        ("stream", ctypes.c_void_p), ("gx", ctypes.c_double), ("gy", ctypes.c_double),
     ]
 
 
@@ -121,7 +121,7 @@ def _check(rc, handle=None):
 def make_params(nx, ny, m=0.0, order=2, quadrature=None, groups=None, v0=0.0, custom=None,
                 tau=1.0, tau_mode="const", eta_over_s=0.0, kappa=0.0, boundary="periodic",
                 precision="fp32", stream="onlattice", lam=0.0, n_ref=1.0, T_ref=1.0,
-                cuda_stream=None):
+                cuda_stream=None, g=(0.0, 0.0)):
     """Fill an rlbm_params struct; returns (params, keepalive) -- the second
     item holds arrays the struct points to."""
     p = Params()
@@ -155,6 +155,7 @@ def make_params(nx, ny, m=0.0, order=2, quadrature=None, groups=None, v0=0.0, cu
     p.lam = float(lam)
     p.n_ref, p.T_ref = float(n_ref), float(T_ref)
     p.stream = cuda_stream
+    p.gx, p.gy = float(g[0]), float(g[1])
     return p, keep
 
 

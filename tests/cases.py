@@ -38,9 +38,9 @@ def permutation(prod_n, prod_p, quad):
     return np.array([pos[key(quad.n[j], quad.p[j, 0])] for j in range(quad.Q)])
 
 
-def oracle_sim(quad, nx, ny, tau=1.0, boundary="periodic", stream="onlattice", lam=None):
+def oracle_sim(quad, nx, ny, tau=1.0, boundary="periodic", stream="onlattice", lam=None, g=None):
     return OS.Simulation(quad, OL.Expansion(quad), nx, ny, tau=tau, boundary=boundary,
-                         stream=stream, lam=lam)
+                         stream=stream, lam=lam, g=g)
 
 
 def rel_linf(a, b):
