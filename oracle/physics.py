@@ -87,18 +87,58 @@ def four_velocity(ux, uy):
     return np.stack([g, g * ux, g * uy], axis=0)
 
 
+def _exp_e1(z):
+    """e^z Gamma(0, z) = e^z E_1(z) for z > 0: scipy's exp1 times exp(z) up to
+    z = 500 (relative error ~1e-15), Tricomi's U(1, 1, z) beyond (the
+    exponential would overflow)."""
+    z = np.asarray(z, dtype=np.float64)
+    small = np.minimum(z, 500.0)
+    return np.where(z <= 500.0, special.exp1(small) * np.exp(small), special.hyperu(1.0, 1.0, z))
+
+
 def ce_shear_viscosity_coeff(zeta, d=2):
     """f(zeta) in eta = f(zeta) P tau, Chapman-Enskog (App. C, "To give a few
     examples"): d = 2: (2 G_2 - zeta^2 + e^zeta zeta^4 Gamma(0, zeta)/(zeta + 1))/8.
-    Gamma(0, z) = E_1(z); e^z E_1(z) is evaluated as Tricomi's U(1, 1, z).
-    UR limit (d+1)/(d+2) (Eq. ce-ur-limit)."""
+    Gamma(0, z) = E_1(z) (e^z E_1(z) by _exp_e1).  UR limit (d+1)/(d+2)
+    (Eq. ce-ur-limit)."""
     if d != 2:
         raise NotImplementedError
     z = np.asarray(zeta, dtype=np.float64)
     g = G_d(z, 2)
     zz = np.where(z > 0, z, 1.0)
-    tail = np.where(z > 0, z ** 4 * special.hyperu(1.0, 1.0, zz) / (z + 1.0), 0.0)
+    tail = np.where(z > 0, z ** 4 * _exp_e1(zz) / (z + 1.0), 0.0)
     return (2.0 * g - z * z + tail) / 8.0
+
+
+def ce_thermal_conductivity_coeff(zeta, d=2):
+    """g(zeta) in lambda = g(zeta) n tau (k_B = c = 1), Chapman-Enskog with
+    the Anderson-Witting collision, d = 2 (App. C, thermal conductivity):
+    G (G/2 - 1 - G zeta^2 e^zeta Gamma(0, zeta) / (2 (zeta + 1))), G = G_2.
+    UR limit (d+1)/d = 3/2.  The heat flux is q^a = lambda nabla^a T."""
+    if d != 2:
+        raise NotImplementedError
+    z = np.asarray(zeta, dtype=np.float64)
+    g = G_d(z, 2)
+    zz = np.where(z > 0, z, 1.0)
+    tail = np.where(z > 0, z * z * _exp_e1(zz) / (2.0 * (z + 1.0)), 0.0)
+    return g * (g / 2.0 - 1.0 - g * tail)
+
+
+def ce_bulk_viscosity_coeff(zeta, d=2):
+    """h(zeta) in mu = h(zeta) P tau, Chapman-Enskog with the Anderson-Witting
+    collision, d = 2 (App. C, bulk viscosity):
+    (zeta^4 + 3 zeta^2 + 2 G^3 - 12 G^2 + 18 G - zeta^2 G^2 + 2 zeta^2 G)
+      / (4 (G^2 - 4 G + 1 - zeta^2))  +  e^zeta zeta^4 Gamma(0, zeta) / (4 (zeta + 1)).
+    Zero in the UR limit.  The dynamic pressure is varpi = -mu nabla_a U^a."""
+    if d != 2:
+        raise NotImplementedError
+    z = np.asarray(zeta, dtype=np.float64)
+    g = G_d(z, 2)
+    zz = np.where(z > 0, z, 1.0)
+    num = z ** 4 + 3 * z * z + 2 * g ** 3 - 12 * g * g + 18 * g - z * z * g * g + 2 * z * z * g
+    den = 4.0 * (g * g - 4.0 * g + 1.0 - z * z)
+    tail = np.where(z > 0, z ** 4 * _exp_e1(zz) / (4.0 * (z + 1.0)), 0.0)
+    return np.where(z > 0, num / np.where(z > 0, den, 1.0) + tail, 0.0)
 
 
 def riemann_ur(nL, PL, nR, PR, d=2, c=1.0):

@@ -472,6 +472,55 @@ def test_ce_shear_viscosity_matches_the_chapman_enskog_integral(zeta):
     assert abs(float(P.ce_shear_viscosity_coeff(np.array(zeta))) - num / den) < 1e-8
 
 
+def _mj_radial(f, m, T=1.0):
+    """int_0^inf f(p, p0) e^{-(p0 - m)/T} dp by quadrature (p0 = sqrt(m^2 + p^2))."""
+    from scipy import integrate
+    return integrate.quad(lambda p: f(p, np.sqrt(m * m + p * p)) * np.exp(-(np.sqrt(m * m + p * p) - m) / T),
+                          0, np.inf, epsabs=0, epsrel=1e-12, limit=400)[0]
+
+
+@pytest.mark.parametrize("zeta", [0.0, 0.5, 1.0, 2.0, 5.0, 10.0])
+def test_ce_thermal_conductivity_matches_the_chapman_enskog_integral(zeta):
+    """App. C closed form against the first-order Anderson-Witting correction
+    integrated by quadrature.  A fluid at rest with a temperature gradient at
+    uniform pressure (d_x n / n = -d_x T / T) has df = -(tau / p0) p^x d_x f_eq,
+    d_x ln f_eq = d_x T ((p0 - <p0>) / T^2 - 1 / T); the diffusion current
+    V^x = int d^2p / p0 p^x df and the heat flux q^x = -h_e V^x = -lambda d_x T
+    (h_e = (eps + P) / n) give lambda = h_e V^x / d_x T."""
+    T, m, n, tau = 1.0, zeta, 1.0, 1.0
+    Z = 2 * np.pi * _mj_radial(lambda p, p0: p, m, T)
+    p0m = 2 * np.pi * _mj_radial(lambda p, p0: p * p0, m, T) / Z
+    # int d^2p (p_x^2 / p0^2) f_eq (...): angular average of p_x^2 is p^2 / 2
+    I = np.pi * _mj_radial(lambda p, p0: p ** 3 / p0 ** 2 * ((p0 - p0m) / T ** 2 - 1 / T), m, T) * n / Z
+    he = (n * p0m + n * T) / n
+    lam = -he * tau * I
+    assert abs(float(P.ce_thermal_conductivity_coeff(np.array(zeta))) - lam / (n * tau)) < 1e-10
+
+
+@pytest.mark.parametrize("zeta", [0.0, 0.5, 1.0, 2.0, 5.0, 10.0])
+def test_ce_bulk_viscosity_matches_the_chapman_enskog_integral(zeta):
+    """App. C closed form against the first-order Anderson-Witting correction
+    for a uniform expansion theta = d_x U^x of a fluid at rest with uniform
+    n, T: the Euler equations give d_t n = -n theta and
+    d_t T = -(T / e'(T)) theta (e = eps / n), so
+    p^mu d_mu ln f_eq = p0 (-theta + (p0 - <p0>) d_t T / T^2) + (p^x)^2 theta / T,
+    df = -(tau / p0) f_eq p^mu d_mu ln f_eq,
+    varpi = -(1/d) (dT^00 - dT^xx - dT^yy), mu = -varpi / theta;
+    the Landau matching dT^00 = 0 holds as well."""
+    T, m, n, tau, th = 1.0, zeta, 1.0, 1.0, 1.0
+    Z = 2 * np.pi * _mj_radial(lambda p, p0: p, m, T)
+    p0m = 2 * np.pi * _mj_radial(lambda p, p0: p * p0, m, T) / Z
+    p02 = 2 * np.pi * _mj_radial(lambda p, p0: p * p0 * p0, m, T) / Z
+    dTdt = -(T / ((p02 - p0m ** 2) / T ** 2)) * th
+    A = lambda p, p0: p0 * (-th + (p0 - p0m) / T ** 2 * dTdt) + p * p / 2 * th / T
+    dT00 = -tau * 2 * np.pi * _mj_radial(lambda p, p0: p * A(p, p0), m, T) * n / Z
+    dTii = -tau * 2 * np.pi * _mj_radial(lambda p, p0: p ** 3 / p0 ** 2 * A(p, p0), m, T) * n / Z
+    varpi = -(dT00 - dTii) / 2
+    assert abs(dT00) < 1e-12
+    mu = -varpi / th / (n * T * tau)
+    assert abs(float(P.ce_bulk_viscosity_coeff(np.array(zeta))) - mu) < 1e-10
+
+
 def _shear_wave_eta(order, Lx, tau, amp=0.01):
     q = L.massless_quadrature(order)
     e = L.Expansion(q)
