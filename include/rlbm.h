@@ -108,6 +108,9 @@ typedef struct rlbm_params {
                          K = (g.p, p^0 g) added by forcing scheme B (Sec. 4.4),
                          F_i = (m/T) f^eq_i (U^0 g.v_i - g.U) per step; acts on
                          massive particles only (m~ > 0); default 0             */
+  double wall_T[2];   /* RLBM_BC_EQWALL_X: temperature of the first / last column's
+                         equilibrium (the heated plates of the paper's thermal-
+                         conductivity runs, Sec. 7.2); 0 = the cell's own T       */
 } rlbm_params;
 
 typedef struct rlbm_handle rlbm_handle;

@@ -160,12 +160,15 @@ def forcing_term(feq, fl, quad: Quadrature, g):
     return (quad.m / fl.T) * feq * (fl.U[0] * gv - gU)
 
 
-def collide(f, quad: Quadrature, exp: Expansion, tau, g=None, eqwall=False):
+def collide(f, quad: Quadrature, exp: Expansion, tau, g=None, eqwall=False, wall_T=(0.0, 0.0)):
     """Steps 1-8: returns f*(x) and the fields of f.  g: optional gravity-like
     force (gx, gy), added as forcing_term.  eqwall: equilibrium walls at the
     first and last column (reading of the no-slip walls of Sec. 8.1: the
     post-collision populations there are the equilibrium at zero flow speed,
-    f^eq(n, U = (1, 0, 0), T), with the cell's own n and T)."""
+    f^eq(n, U = (1, 0, 0), T), with the cell's own n and T, or with the
+    prescribed wall temperature wall_T[side] > 0 -- the heated plates of the
+    thermal-conductivity runs of Sec. 7.2, whose density the paper takes from
+    the neighbouring points; reading: the cell's own n)."""
     fl = macroscopic(f, quad)
     feq = exp.feq(fl.n, fl.U, fl.T)                                    # step 5
     if isinstance(tau, tuple):                                          # step 7
@@ -175,8 +178,10 @@ def collide(f, quad: Quadrature, exp: Expansion, tau, g=None, eqwall=False):
     if g is not None:
         fs = fs + forcing_term(feq, fl, quad, g)
     if eqwall:
-        for col in (0, f.shape[2] - 1):
+        for side, col in enumerate((0, f.shape[2] - 1)):
             n, T = fl.n[:, col], fl.T[:, col]
+            if wall_T[side] > 0:
+                T = np.full_like(T, wall_T[side])
             rest = np.zeros((3,) + n.shape)
             rest[0] = 1.0
             fs[:, :, col] = exp.feq(n, rest, T)
@@ -187,9 +192,10 @@ class Simulation:
     """Time integration with the state convention of the module docstring."""
 
     def __init__(self, quad: Quadrature, exp: Expansion, nx, ny, tau=1.0,
-                 boundary="periodic", stream="onlattice", lam=None, g=None):
+                 boundary="periodic", stream="onlattice", lam=None, g=None, wall_T=(0.0, 0.0)):
         self.quad, self.exp = quad, exp
         self.g = g                           # optional gravity-like force (gx, gy)
+        self.wall_T = wall_T                 # equilibrium-wall temperatures (0: own T)
         self.nx, self.ny = nx, ny
         self.tau = tau                       # scalar, (ny, nx) array or (eta/s, kappa)
         self.boundary = boundary
@@ -220,6 +226,6 @@ class Simulation:
         for _ in range(nsteps):
             f = self.stream(self.fs)
             self.fs, self.fields = collide(f, self.quad, self.exp, self.tau, self.g,
-                                           self.boundary == "eqwall_x")
+                                           self.boundary == "eqwall_x", self.wall_T)
             self.t += 1
         return self.fs

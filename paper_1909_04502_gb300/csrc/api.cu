@@ -88,6 +88,8 @@ void finish_scalars(Scalars* s) {
   s->force = (s->m > 0.0 && (s->gx != 0.0 || s->gy != 0.0)) ? 1 : 0;
   s->f_gx = (float)s->gx;
   s->f_gy = (float)s->gy;
+  s->f_wall_T[0] = (float)s->wall_T[0];
+  s->f_wall_T[1] = (float)s->wall_T[1];
   s->massless = (s->m == 0.0) ? 1 : 0;
   s->iplane = (int)s->plane;
   s->f_tau = (float)s->tau;
@@ -419,6 +421,8 @@ int rlbm_create(const rlbm_params* p, rlbm_handle** out) {
   s.kappa_guess = (float)(Tr * (m + Tr) / (m * m + 2.0 * m * Tr + 2.0 * Tr * Tr));
   s.gx = p->gx;
   s.gy = p->gy;
+  s.wall_T[0] = p->wall_T[0];
+  s.wall_T[1] = p->wall_T[1];
   finish_scalars(&s);
   // the orbit-symmetric kernels carry neither the force term nor the walls
   s.sym = (orbit_symmetric(h.get()) && !s.force && s.boundary != RLBM_BC_EQWALL_X) ? 1 : 0;
@@ -753,6 +757,8 @@ int rlbm_internal_prepare(const rlbm_params* p, Scalars* sc, Tables<float>* tf, 
   s.kappa_guess = (float)(Tr * (m + Tr) / (m * m + 2.0 * m * Tr + 2.0 * Tr * Tr));
   s.gx = p->gx;
   s.gy = p->gy;
+  s.wall_T[0] = p->wall_T[0];
+  s.wall_T[1] = p->wall_T[1];
   finish_scalars(&s);
   // the orbit-symmetric kernels carry neither the force term nor the walls
   s.sym = (orbit_symmetric(&h) && !s.force && s.boundary != RLBM_BC_EQWALL_X) ? 1 : 0;

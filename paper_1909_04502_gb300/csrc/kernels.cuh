@@ -64,6 +64,8 @@ struct Scalars {
   int force;               // gravity-like force present (m > 0 and g != 0)
   double gx, gy;           // its acceleration
   float f_gx, f_gy;
+  double wall_T[2];        // equilibrium walls: prescribed temperature of the first / last column (0: own T)
+  float f_wall_T[2];
   int iplane;              // plane as int (Q * plane < 2^31 is checked at creation)
   // FP32 copies of the scalars used by the FP32-storage kernels
   float f_tau, f_tau_coef, f_m, f_n_ref, f_T_ref, f_T00_ref, f_Tii_ref;

@@ -682,7 +682,8 @@ __device__ __forceinline__ void collide_store(const Tables<S>& tb, const Scalars
     // Forcing scheme B (Sec. 4.4), gravity-like force K = (g.p, p^0 g):
     // F_i = (m/T) f^eq_i (U^0 g.v_i - g.U), with the full f^eq (the stored
     // shift f_ref added back).  Equilibrium walls (first and last column):
-    // the cell keeps f^eq(n, U = (1, 0, 0), T) instead.
+    // the cell keeps f^eq(n, U = (1, 0, 0), T_w) instead, T_w the prescribed
+    // wall temperature or the cell's own T.
     S cf = S(0), gx = S(0), gy = S(0), gU = S(0);
     if (s.force && M.ok) {
       if constexpr (sizeof(S) == 4) { cf = __fdividef(s.f_m, M.fT); gx = s.f_gx; gy = s.f_gy; }
@@ -692,10 +693,16 @@ __device__ __forceinline__ void collide_store(const Tables<S>& tb, const Scalars
     const bool wall = s.boundary == 2 && (x == 0 || x == s.nx - 1) && M.ok;
     S dMw[KT];
     if (wall) {
-      if constexpr (sizeof(S) == 4)
-        eq_moments<S, KT>(M.fdn, M.fdT, M.fn, M.fT, S(1), S(0), S(0), s.f_m, s.f_n_ref, s.f_T_ref, dMw);
-      else
-        eq_moments<S, KT>(M.n - s.n_ref, M.T - s.T_ref, M.n, M.T, S(1), S(0), S(0), s.m, s.n_ref, s.T_ref, dMw);
+      const int side = x == 0 ? 0 : 1;
+      if constexpr (sizeof(S) == 4) {
+        const bool fix = s.f_wall_T[side] > 0.f;
+        const float Tw = fix ? s.f_wall_T[side] : M.fT;
+        const float dTw = fix ? (float)(s.wall_T[side] - s.T_ref) : M.fdT;
+        eq_moments<S, KT>(M.fdn, dTw, M.fn, Tw, S(1), S(0), S(0), s.f_m, s.f_n_ref, s.f_T_ref, dMw);
+      } else {
+        const double Tw = s.wall_T[side] > 0.0 ? s.wall_T[side] : M.T;
+        eq_moments<S, KT>(M.n - s.n_ref, Tw - s.T_ref, M.n, Tw, S(1), S(0), S(0), s.m, s.n_ref, s.T_ref, dMw);
+      }
     }
 #pragma unroll
     for (int i = 0; i < QT; ++i) {

@@ -42,6 +42,7 @@ class Params(ctypes.Structure):
         ("ny", ctypes.c_int), ("precision", ctypes.c_int), ("stream_mode", ctypes.c_int),
         ("lam", ctypes.c_double), ("n_ref", ctypes.c_double), ("T_ref", ctypes.c_double),
         ("stream", ctypes.c_void_p), ("gx", ctypes.c_double), ("gy", ctypes.c_double),
+        ("wall_T", ctypes.c_double * 2),
     ]
 
 
@@ -121,7 +122,7 @@ def _check(rc, handle=None):
 def make_params(nx, ny, m=0.0, order=2, quadrature=None, groups=None, v0=0.0, custom=None,
                 tau=1.0, tau_mode="const", eta_over_s=0.0, kappa=0.0, boundary="periodic",
                 precision="fp32", stream="onlattice", lam=0.0, n_ref=1.0, T_ref=1.0,
-                cuda_stream=None, g=(0.0, 0.0)):
+                cuda_stream=None, g=(0.0, 0.0), wall_T=(0.0, 0.0)):
     """Fill an rlbm_params struct; returns (params, keepalive) -- the second
     item holds arrays the struct points to."""
     p = Params()
@@ -156,6 +157,7 @@ def make_params(nx, ny, m=0.0, order=2, quadrature=None, groups=None, v0=0.0, cu
     p.n_ref, p.T_ref = float(n_ref), float(T_ref)
     p.stream = cuda_stream
     p.gx, p.gy = float(g[0]), float(g[1])
+    p.wall_T[0], p.wall_T[1] = float(wall_T[0]), float(wall_T[1])
     return p, keep
 
 

@@ -38,9 +38,10 @@ def permutation(prod_n, prod_p, quad):
     return np.array([pos[key(quad.n[j], quad.p[j, 0])] for j in range(quad.Q)])
 
 
-def oracle_sim(quad, nx, ny, tau=1.0, boundary="periodic", stream="onlattice", lam=None, g=None):
+def oracle_sim(quad, nx, ny, tau=1.0, boundary="periodic", stream="onlattice", lam=None, g=None,
+               wall_T=(0.0, 0.0)):
     return OS.Simulation(quad, OL.Expansion(quad), nx, ny, tau=tau, boundary=boundary,
-                         stream=stream, lam=lam, g=g)
+                         stream=stream, lam=lam, g=g, wall_T=wall_T)
 
 
 def rel_linf(a, b):
