@@ -12,6 +12,8 @@ from __future__ import annotations
 import itertools
 import math
 from dataclasses import dataclass
+from decimal import Decimal, localcontext
+from fractions import Fraction
 
 import numpy as np
 from scipy import special
@@ -374,8 +376,20 @@ class Expansion:
                 raise ValueError("App. F/G closed forms are printed up to order 2")
             self.J = appF_polys_d2(quad.p, self.m)          # (9, Q)
         else:
-            self.C, self.mons = gram_schmidt_basis(self.order, self.m)
-            self.J = self.C @ eval_monomials(self.mons, quad.p)   # (K, Q)
+            # the basis and its values at the quadrature points in 50-digit
+            # decimal arithmetic, rounded once: in double the cancellation
+            # between monomials of p0 ~ m~ costs up to 1e-10 at m~ = 20
+            with localcontext() as ctx:
+                ctx.prec = 50
+                rows, self.mons = _gram_schmidt_decimal(self.order, self.m)
+                self.C = np.array([[float(x) for x in r] for r in rows])
+                pw = lambda x, k: math.prod([x] * k, start=Decimal(1))
+                J = []
+                for p0, px, py in quad.p:
+                    phi = [pw(Decimal(p0), c) * pw(Decimal(px), a) * pw(Decimal(py), b)
+                           for (c, a, b) in self.mons]
+                    J.append([float(sum(r[q] * phi[q] for q in range(len(phi)))) for r in rows])
+            self.J = np.array(J).T                                  # (K, Q)
 
     def projections(self, n, U, T):
         """a^(k) = n b^(k), shape (K, ...)."""
@@ -423,11 +437,127 @@ def solve_group_weights(groups, m, v0, order=2, basis="appF"):
     return w, float(np.max(np.abs(A @ w - b)))
 
 
-def massive_quadrature(groups, m, v0, order=2, basis=None, drop_zero=1e-300):
-    """Quadrature on an FS stencil with the weights of ``solve_group_weights``."""
+def _omega_moment_fraction(c, a, b, m):
+    """E_omega[p0^c px^a py^b] (d = 2) as an exact rational for a rational m:
+    the angular factor (a-1)!!(b-1)!!/(a+b)!! and the radial integral
+    int_0^inf e^{-s} (m+s)^c (s (2m+s))^{(a+b)/2} ds expanded into s^q e^{-s}
+    terms (each q!), the same formulas as ``omega_moment``."""
+    if a % 2 or b % 2:
+        return Fraction(0)
+    ang = Fraction(1)
+    for k in range(a - 1, 0, -2):
+        ang *= k
+    for k in range(b - 1, 0, -2):
+        ang *= k
+    for k in range(a + b, 0, -2):
+        ang /= k
+    poly = [Fraction(1)]
+    for _ in range(c):
+        poly = [(poly[q] * m if q < len(poly) else 0) + (poly[q - 1] if q else 0) for q in range(len(poly) + 1)]
+    for _ in range((a + b) // 2):
+        nxt = [Fraction(0)] * (len(poly) + 2)
+        for q, x in enumerate(poly):
+            nxt[q + 1] += 2 * m * x
+            nxt[q + 2] += x
+        poly = nxt
+    return ang * sum(x * math.factorial(q) for q, x in enumerate(poly))
+
+
+def _gram_schmidt_decimal(order, m):
+    """``gram_schmidt_basis`` in decimal arithmetic at the current context's
+    precision, on exact omega-moments: rows of C as lists of Decimal."""
+    mons = monomials(order)
+    nm = len(mons)
+    mf = Fraction(m)
+    D = lambda fr: Decimal(fr.numerator) / Decimal(fr.denominator)
+    G = [[D(_omega_moment_fraction(c1 + c2, a1 + a2, b1 + b2, mf)) for (c2, a2, b2) in mons]
+         for (c1, a1, b1) in mons]
+    Gdot = lambda u, v: sum(u[i] * sum(G[i][j] * v[j] for j in range(nm)) for i in range(nm))
+    rows = []
+    for i in range(nm):
+        v = [Decimal(0)] * nm
+        v[i] = Decimal(1)
+        for r in rows:
+            pr = Gdot(r, v)
+            v = [v[k] - pr * r[k] for k in range(nm)]
+        n2 = Gdot(v, v)
+        if n2 <= Decimal("1e-9") * G[i][i]:
+            continue
+        nrm = n2.sqrt()
+        rows.append([x / nrm for x in v])
+    return rows, mons
+
+
+def _basis_at_momenta_decimal(rows, mons, m, v0, vecs):
+    """J = C phi at the momenta of Eq. discrete-momentum-vectors / discrete-p0
+    for the stencil vectors ``vecs``, in decimal arithmetic (Q lists of K)."""
+    pw = lambda x, k: math.prod([x] * k, start=Decimal(1))   # Decimal 0 ** 0 is an error
+    dv0, dm = Decimal(v0), Decimal(Fraction(m).numerator) / Decimal(Fraction(m).denominator)
+    out = []
+    for nx, ny in vecs:
+        vx, vy = dv0 * int(nx), dv0 * int(ny)
+        gam = 1 / (1 - vx * vx - vy * vy).sqrt()
+        p0, px, py = dm * gam, dm * gam * vx, dm * gam * vy
+        phi = [pw(p0, c) * pw(px, a) * pw(py, b) for (c, a, b) in mons]
+        out.append([sum(r[q] * phi[q] for q in range(len(mons))) for r in rows])
+    return out
+
+
+def solve_group_weights_exact(groups, m, v0, order=2, digits=50):
+    """The group weights of Eq. mj-orthogonal-conditions in ``digits``-digit
+    decimal arithmetic: Gram-Schmidt (Sec. 5.2) on the generating set V with
+    exact omega-moments, J at the stencil momenta of Eq.
+    discrete-momentum-vectors / discrete-p0, the conditions summed per FS
+    group, and the least-squares solution through the normal equations
+    (Gaussian elimination with partial pivoting).  The same steps as
+    ``solve_group_weights`` with the GS basis; in double they lose up to 1e-8
+    of a weight at order 3 (m~ = 20) to the conditioning of the monomial
+    basis, here the result is limited by the final rounding.  Returns
+    (w, residual) as floats."""
+    with localcontext() as ctx:
+        ctx.prec = digits
+        rows, mons = _gram_schmidt_decimal(order, m)
+        K = len(rows)
+        vecs, gidx = stencil_from_groups(groups)
+        ng = len(groups)
+        A = [[Decimal(0)] * ng for _ in range(K * (K + 1) // 2)]
+        bvec = []
+        for l in range(K):
+            for k in range(l, K):
+                bvec.append(Decimal(1) if l == k else Decimal(0))
+        for J, g in zip(_basis_at_momenta_decimal(rows, mons, m, v0, vecs), gidx):
+            rr = 0
+            for l in range(K):
+                for k in range(l, K):
+                    A[rr][g] += J[l] * J[k]
+                    rr += 1
+        # normal equations A^T A w = A^T b
+        N = [[sum(A[r][i] * A[r][j] for r in range(len(A))) for j in range(ng)] for i in range(ng)]
+        y = [sum(A[r][i] * bvec[r] for r in range(len(A))) for i in range(ng)]
+        for c in range(ng):
+            piv = max(range(c, ng), key=lambda r: abs(N[r][c]))
+            N[c], N[piv], y[c], y[piv] = N[piv], N[c], y[piv], y[c]
+            for r in range(c + 1, ng):
+                f = N[r][c] / N[c][c]
+                N[r] = [N[r][j] - f * N[c][j] for j in range(ng)]
+                y[r] -= f * y[c]
+        w = [Decimal(0)] * ng
+        for c in range(ng - 1, -1, -1):
+            w[c] = (y[c] - sum(N[c][j] * w[j] for j in range(c + 1, ng))) / N[c][c]
+        res = max(abs(sum(A[r][g] * w[g] for g in range(ng)) - bvec[r]) for r in range(len(A)))
+        return np.array([float(x) for x in w]), float(res)
+
+
+def massive_quadrature(groups, m, v0, order=2, basis=None, drop_zero=1e-300, exact=True):
+    """Quadrature on an FS stencil with the weights of
+    ``solve_group_weights_exact`` (``exact``) or of ``solve_group_weights``
+    in double with the given basis."""
     if basis is None:
         basis = "appF" if order == 2 else "gs"
-    wg, res = solve_group_weights(groups, m, v0, order, basis)
+    if exact:
+        wg, res = solve_group_weights_exact(groups, m, v0, order)
+    else:
+        wg, res = solve_group_weights(groups, m, v0, order, basis)
     vecs, gidx = stencil_from_groups(groups)
     w = wg[gidx]
     keep = np.abs(w) > drop_zero

@@ -7,6 +7,7 @@ integration, a textbook routine (Gauss-Laguerre nodes), or an invariant.
 import json
 import math
 import os
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -138,6 +139,38 @@ def test_mass5_worked_example_weights():
     # weights sum to one (Eq. numerical-normalization-cond)
     sizes = [len(L.fs_orbit(x)) for x in groups]
     assert abs(np.dot(sizes, w) - 1.0) < 1e-13
+
+
+def test_exact_weights_match_printed_worked_example():
+    """The decimal-arithmetic solve gives the printed Sec. 5.3 weights and
+    leaves no residual above its working precision."""
+    g = gold("mass5_worked_example.json")
+    w, res = L.solve_group_weights_exact([tuple(x) for x in g["groups"]], g["m"], g["v0"])
+    assert res < 1e-40
+    assert np.allclose(w, g["weights"], rtol=0, atol=5e-14)
+
+
+@pytest.mark.parametrize("m,v0", [(20.0, 0.175), (5.0, 0.2199)])
+def test_exact_order3_weights_reproduce_omega_moments(m, v0):
+    """App. H stencil G_D^(o3) (order 3) with the exact weights: the rule
+    integrates every product of two members of V (degree <= 6) like the
+    weight omega itself, i.e. Eq. mj-orthogonal-conditions written in the
+    monomial basis (J = C phi with C invertible), checked against the exact
+    rational omega-moments without any Gram-Schmidt step (the double-
+    precision LAPACK solve misses them by 1e-11 to 1e-10)."""
+    groups = [(0, 0), (1, 0), (1, 1), (2, 0), (2, 1), (3, 1), (3, 2), (3, 3), (4, 0), (4, 2)]
+    q, res = L.massive_quadrature(groups, m, v0, order=3)
+    assert res < 1e-35
+    mons = L.monomials(3)
+    phi = L.eval_monomials(mons, q.p)
+    worst = 0.0
+    for i, (c1, a1, b1) in enumerate(mons):
+        for j, (c2, a2, b2) in enumerate(mons):
+            exact = float(L._omega_moment_fraction(c1 + c2, a1 + a2, b1 + b2, Fraction(m)))
+            got = math.fsum(q.w * phi[i] * phi[j])
+            scale = math.fsum(np.abs(q.w * phi[i] * phi[j]))
+            worst = max(worst, abs(got - exact) / scale)
+    assert worst < 1e-14
 
 
 def test_mass5_search_finds_printed_window_and_failing_stencil():
@@ -519,6 +552,55 @@ def test_ce_bulk_viscosity_matches_the_chapman_enskog_integral(zeta):
     assert abs(dT00) < 1e-12
     mu = -varpi / th / (n * T * tau)
     assert abs(float(P.ce_bulk_viscosity_coeff(np.array(zeta))) - mu) < 1e-10
+
+
+def _mj_on_fine_rule(m, ns=120, nth=64):
+    """The exact Maxwell-Juttner populations on a product rule for
+    int d^2p / p0 = int dp0 dtheta: Gauss-Laguerre in s = p0 - m (textbook
+    nodes) times the trapezoid rule in theta; f = n e^{-(p.U - m)/T} /
+    (2 pi T (m + T)) normalises N^0 = n at rest (d = 2)."""
+    s, ws = special.roots_laguerre(ns)
+    th = 2 * np.pi * np.arange(nth) / nth
+    S, TH = np.meshgrid(s, th, indexing="ij")
+    pm = np.sqrt(S * (2 * m + S))
+    p = np.stack([(m + S).ravel(), (pm * np.cos(TH)).ravel(), (pm * np.sin(TH)).ravel()], axis=1)
+    W = (ws[:, None] * np.exp(s)[:, None] * np.full((1, nth), 2 * np.pi / nth)).ravel()
+
+    def feq(n, ux, uy, T):
+        g = 1 / np.sqrt(1 - ux * ux - uy * uy)
+        pu = g * (p[:, 0] - p[:, 1] * ux - p[:, 2] * uy)
+        return W * n / (2 * np.pi * T * (m + T)) * np.exp(-(pu - m) / T)
+    return p, feq
+
+
+@pytest.mark.parametrize("zeta", [0.0, 0.5, 1.0, 2.0, 5.0, 10.0, 20.0])
+def test_first_order_coefficients_of_the_exact_distribution_are_app_c(zeta):
+    """``transport.first_order`` fed the exact MJ distribution on a fine rule
+    (instead of a lattice) gives the App. C closed forms of eta, lambda and mu,
+    and mu = 0 for massless particles."""
+    from oracle import transport as TR
+    p, feq = _mj_on_fine_rule(zeta)
+    assert abs(np.sum(feq(1.0, 0.0, 0.0, 1.0) * p[:, 0]) - 1.0) < 1e-13
+    r = TR.first_order(p, feq, zeta)
+    assert abs(r["eta"] - float(P.ce_shear_viscosity_coeff(np.array(zeta)))) < 1e-10
+    assert abs(r["lam"] - float(P.ce_thermal_conductivity_coeff(np.array(zeta)))) < 1e-10
+    assert abs(r["mu"] - float(P.ce_bulk_viscosity_coeff(np.array(zeta)))) < 2e-11
+    if zeta == 0.0:
+        assert abs(r["mu"]) < 1e-15
+
+
+def test_first_order_shear_coefficient_explains_the_lattice_viscosities():
+    """On the massless App. H tables the same routine gives eta / (P tau) =
+    1.307 (order 2) and 1.0021 (order 3) of the UR value 3/4 (Eq.
+    ce-ur-limit), the offsets the whole-scheme shear-wave pins measure as
+    0.98 (tau - 1/2) and 0.7516 (tau - 1/2)."""
+    from oracle import transport as TR
+    got = {}
+    for order in (2, 3):
+        q = L.massless_quadrature(order)
+        got[order] = TR.first_order(q.p, TR.lattice_feq(L.Expansion(q)), 0.0)["eta"]
+    assert abs(got[2] - 0.980) < 2e-3
+    assert abs(got[3] - 0.7516) < 2e-4
 
 
 def _shear_wave_eta(order, Lx, tau, amp=0.01):
