@@ -275,7 +275,7 @@ int build_quadrature(const rlbm_params* p, Quadrature* q, std::string* err) {
       return RLBM_ERR_QUADRATURE;
     }
     double res;
-    if (!massive_quadrature(g, p->m, v0, p->order, q, &res, nullptr) || res > 1e-9) {
+    if (!massive_quadrature(g, p->m, v0, p->order, q, &res, nullptr, true) || res > 1e-9) {
       *err = "orthonormality conditions not satisfied on this stencil";
       return RLBM_ERR_QUADRATURE;
     }

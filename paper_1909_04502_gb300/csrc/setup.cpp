@@ -349,8 +349,110 @@ bool massless_quadrature(int order, Quadrature* q, std::string* err) {
   return true;
 }
 
+namespace {
+
+// Group weights of Eq. mj-orthogonal-conditions in double-double.  The
+// orthonormal basis is J = L^{-1} phi' with L the Cholesky factor of the
+// shifted Gram matrix; s = p0 - m is formed as m v^2 / (r (1 + r)),
+// r = sqrt(1 - v^2), so no digits cancel; the conditions are summed per FS
+// group and solved in the least-squares sense through the column-equilibrated
+// normal equations.  At order 3 the same construction in double loses up to
+// 1e-9 of a weight (m~ = 20) to the conditioning of the basis; this one is
+// limited by the final rounding to double.
+bool group_weights_dd(const std::vector<int>& groups, double m, double v0, int order,
+                      std::vector<double>* wg_out, double* residual) {
+  const int ng = (int)groups.size() / 2;
+  auto B = moment_basis(order);
+  const int K = (int)B.size();
+  std::vector<dd> L = gram_shifted_dd(order, m);
+  for (int j = 0; j < K; ++j) {
+    dd d = L[j * K + j];
+    for (int k = 0; k < j; ++k) d = d - L[j * K + k] * L[j * K + k];
+    if (!(d.hi > 0.0)) return false;
+    d = dd_sqrt(d);
+    L[j * K + j] = d;
+    for (int i = j + 1; i < K; ++i) {
+      dd t = L[i * K + j];
+      for (int k = 0; k < j; ++k) t = t - L[i * K + k] * L[j * K + k];
+      L[i * K + j] = t / d;
+    }
+  }
+  const dd mm(m), sg = dd_sqrt(mm + dd(1.0));
+  const int rows = K * (K + 1) / 2;
+  std::vector<dd> A((size_t)rows * ng, dd(0.0)), J(K), phi(K);
+  for (int g = 0; g < ng; ++g)
+    for (auto v : fs_group(groups[2 * g], groups[2 * g + 1])) {
+      const dd vx = dd(v0) * dd((double)v.first), vy = dd(v0) * dd((double)v.second);
+      const dd v2 = vx * vx + vy * vy;
+      if (!(v2.hi < 1.0)) return false;
+      const dd r = dd_sqrt(dd(1.0) - v2);
+      const dd s = mm * v2 / (r * (dd(1.0) + r));
+      const dd qx = mm * vx / (r * sg), qy = mm * vy / (r * sg);
+      for (int k = 0; k < K; ++k) {
+        dd t = B[k].e ? s : dd(1.0);
+        for (int i = 0; i < B[k].a; ++i) t = t * qx;
+        for (int i = 0; i < B[k].b; ++i) t = t * qy;
+        phi[k] = t;
+      }
+      for (int k = 0; k < K; ++k) {
+        dd t = phi[k];
+        for (int j = 0; j < k; ++j) t = t - L[k * K + j] * J[j];
+        J[k] = t / L[k * K + k];
+      }
+      int rr = 0;
+      for (int l = 0; l < K; ++l)
+        for (int k = l; k < K; ++k, ++rr) A[(size_t)rr * ng + g] = A[(size_t)rr * ng + g] + J[l] * J[k];
+    }
+  // column scales D (powers of two, so scaling is exact), then (AD)^T (AD) y = (AD)^T b
+  std::vector<dd> D(ng);
+  for (int g = 0; g < ng; ++g) {
+    double n2 = 0.0;
+    for (int rr = 0; rr < rows; ++rr) n2 += A[(size_t)rr * ng + g].hi * A[(size_t)rr * ng + g].hi;
+    if (!(n2 > 0.0)) return false;
+    int e;
+    std::frexp(std::sqrt(n2), &e);
+    D[g] = dd(std::ldexp(1.0, -e));
+  }
+  std::vector<dd> N((size_t)ng * ng, dd(0.0)), y(ng, dd(0.0));
+  {
+    int rr = 0;
+    for (int l = 0; l < K; ++l)
+      for (int k = l; k < K; ++k, ++rr) {
+        const dd* a = &A[(size_t)rr * ng];
+        for (int i = 0; i < ng; ++i) {
+          const dd ai = a[i] * D[i];
+          if (l == k) y[i] = y[i] + ai;
+          for (int j = 0; j < ng; ++j) N[(size_t)i * ng + j] = N[(size_t)i * ng + j] + ai * (a[j] * D[j]);
+        }
+      }
+  }
+  std::vector<dd> Ni;
+  if (!spd_inverse_dd(N, ng, &Ni)) return false;
+  wg_out->assign(ng, 0.0);
+  std::vector<dd> w(ng);
+  for (int i = 0; i < ng; ++i) {
+    dd t(0.0);
+    for (int j = 0; j < ng; ++j) t = t + Ni[(size_t)i * ng + j] * y[j];
+    w[i] = t * D[i];
+    (*wg_out)[i] = w[i].to_double();
+  }
+  double res = 0.0;
+  int rr = 0;
+  for (int l = 0; l < K; ++l)
+    for (int k = l; k < K; ++k, ++rr) {
+      dd t(l == k ? -1.0 : 0.0);
+      for (int g = 0; g < ng; ++g) t = t + A[(size_t)rr * ng + g] * w[g];
+      res = std::max(res, std::fabs(t.to_double()));
+    }
+  *residual = res;
+  return true;
+}
+
+}  // namespace
+
 bool massive_quadrature(const std::vector<int>& groups, double m, double v0, int order,
-                        Quadrature* q, double* residual, std::vector<double>* group_w) {
+                        Quadrature* q, double* residual, std::vector<double>* group_w,
+                        bool precise) {
   const int ng = (int)groups.size() / 2;
   auto B = moment_basis(order);
   const int K = (int)B.size();
@@ -392,12 +494,16 @@ bool massive_quadrature(const std::vector<int>& groups, double m, double v0, int
       b[r] = (l == k) ? 1.0 : 0.0;
     }
   std::vector<double> wg;
-  if (!least_squares(A, b, rows, ng, &wg)) return false;
   double res = 0.0;
-  for (int rr = 0; rr < rows; ++rr) {
-    double s = -b[rr];
-    for (int g = 0; g < ng; ++g) s += A[(size_t)rr * ng + g] * wg[g];
-    res = std::max(res, std::fabs(s));
+  if (precise) {
+    if (!group_weights_dd(groups, m, v0, order, &wg, &res)) return false;
+  } else {
+    if (!least_squares(A, b, rows, ng, &wg)) return false;
+    for (int rr = 0; rr < rows; ++rr) {
+      double s = -b[rr];
+      for (int g = 0; g < ng; ++g) s += A[(size_t)rr * ng + g] * wg[g];
+      res = std::max(res, std::fabs(s));
+    }
   }
   *residual = res;
   if (group_w) *group_w = wg;
@@ -519,7 +625,7 @@ bool builtin_massive_search(double m, int order, Quadrature* q, std::string* err
     double v0;
     if (!search_v0(g, m, order, &v0, nullptr, nullptr)) continue;
     double res;
-    if (massive_quadrature(g, m, v0, order, q, &res, nullptr) && res < 1e-9) return true;
+    if (massive_quadrature(g, m, v0, order, q, &res, nullptr, true) && res < 1e-9) return true;
   }
   *err = "no built-in stencil yields a non-negative quadrature for this mass and order";
   return false;

@@ -46,9 +46,12 @@ bool massless_quadrature(int order, Quadrature* q, std::string* err);
 
 // Massive quadrature on the FS stencil generated by groups (Sec. 5.3):
 // weights per group from Eq. mj-orthogonal-conditions by least squares.
-// Returns the largest residual of the conditions in *residual.
+// Returns the largest residual of the conditions in *residual.  precise
+// solves in double-double (the tables a lattice runs on); the fast double
+// solve serves the v0 scan, which needs only the residual and the signs.
 bool massive_quadrature(const std::vector<int>& groups, double m, double v0, int order,
-                        Quadrature* q, double* residual, std::vector<double>* group_w);
+                        Quadrature* q, double* residual, std::vector<double>* group_w,
+                        bool precise = false);
 
 // Line search of Sec. 5.3: scan v0 over (0, 1/max||n||) and return the middle
 // of the widest interval where the conditions hold and every weight is >= 0.
