@@ -210,7 +210,7 @@ def main():
     ap.add_argument("--workload", default="tg512", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint measurements")
-    ap.add_argument("--only", default=None, choices=["batched", "adjoint"],
+    ap.add_argument("--only", default=None, choices=["batched", "adjoint", "paper"],
                     help="run only this extra measurement and print its JSON object")
     ap.add_argument("--_oracle_worker", default=None)
     args = ap.parse_args()
@@ -254,6 +254,8 @@ def main():
         if args.only == "batched":
             res = {"batched": bench_batched(torch, rlbm, inputs, stream),
                    "batched_small": bench_batched(torch, rlbm, inputs, stream, steps=50, side_hi=256)}
+        elif args.only == "paper":
+            res = {"massive_order3_tg512": bench_massive_order3(torch, rlbm, inputs, stream)}
         else:
             res = {"adjoint": bench_adjoint(torch, rlbm, inputs, stream)}
         if rank == 0:
@@ -355,6 +357,7 @@ def main():
         extras["batched"] = bench_batched(torch, rlbm, inputs, stream)
         extras["batched_small"] = bench_batched(torch, rlbm, inputs, stream, steps=50, side_hi=256)
         extras["adjoint"] = bench_adjoint(torch, rlbm, inputs, stream)
+        extras["massive_order3_tg512"] = bench_massive_order3(torch, rlbm, inputs, stream)
         if wl["workload"] == "tg512_bilinear_fp32":
             extras["viscosity"] = bench_tg_viscosity(rlbm, inputs)
 
@@ -510,6 +513,42 @@ def bench_adjoint(torch, rlbm, inputs, stream, L=512, nsteps=2000, K=100):
     adj.close()
     lat.close()
     return res
+
+
+def bench_massive_order3(torch, rlbm, inputs, stream, L=512, m=5.0, steps=50, warmup=5):
+    """The fused step on the setup of the paper's only performance table
+    (Taylor-Green, 512^2 periodic, zeta = 5, third-order on-lattice stencil),
+    in FP64 (the paper's precision) and with FP32 storage.  The built-in
+    zeta = 5 stencil has 49 vectors (App. H column C) where the paper's has
+    45, and the paper times its collide kernel alone on a P100 (55 MLUPS):
+    context, not a target.  L2 is flushed before every timed step."""
+    out = {"workload": f"tg{L}_zeta{m:g}_order3_onlattice", "paper_collide_only_p100_mlups": 55.0}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    fields = [__import__("numpy").ascontiguousarray(a) for a in inputs.taylor_green(L, u0=0.1)]
+    peak, _ = _peaks()
+    for prec, elem in (("fp64", 8), ("fp32", 4)):
+        lat = rlbm.Lattice(L, L, m=m, order=3, tau=1.0, stream="onlattice", precision=prec,
+                           cuda_stream=stream.cuda_stream)
+        lat.init(*fields)
+        for _ in range(warmup):
+            flush.zero_()
+            lat.step(1)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            lat.step(1)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        st = lat.sync_status(raise_on_error=False)
+        gbs = 2 * lat.Q * elem * L * L / (ms * 1e-3) / 1e9
+        out[prec] = {"Q": lat.Q, "ms_per_step": round(ms, 5), "mlups": round(L * L / (ms * 1e-3) / 1e6, 1),
+                     "algorithmic_gbs": round(gbs, 1), "frac_of_hbm": round(gbs / peak, 4),
+                     "nonphysical": st[1]}
+        lat.close()
+    return out
 
 
 def bench_tg_viscosity(rlbm, inputs, L=512, tau=1.0, u0=0.1, steps=5000, every=100):

@@ -748,10 +748,18 @@ __device__ __forceinline__ void cell_update(const Tables<S>& tb, const Scalars& 
 // FP32 storage: 1024 resident threads per SM (eight 32 x 4 blocks, at most
 // 64 registers per thread) -- the FP64 polish and the gather latency need
 // the resident warps; 32 x 4 blocks measured 3-7 % faster than 32 x 8.
+// FP64 storage with more than 56 populations: 256 threads per SM, so that a
+// cell's 64-72 doubles stay in registers (12 % faster at Q = 65); up to 56
+// populations the spills of 512 threads cost less than the lost warps (3 %).
 // SYM: orbit-symmetric moments and equilibrium (built-in massless stencils).
 // MOUT: also write the macroscopic state (a.macro).
+template <typename S, int QT>
+constexpr int step_threads_per_sm() {
+  return sizeof(S) == 4 ? (QT <= 40 ? 1024 : 512) : (QT <= 56 ? 512 : 256);
+}
+
 template <typename S, int QT, bool EX, int KT, int MODE, bool SYM, bool MOUT = false>
-__global__ void __launch_bounds__(kThreads, ((sizeof(S) == 4 && QT <= 40) ? 1024 : 512) / kThreads) k_step(const __grid_constant__ Tables<S> tb,
+__global__ void __launch_bounds__(kThreads, step_threads_per_sm<S, QT>() / kThreads) k_step(const __grid_constant__ Tables<S> tb,
                                                    const __grid_constant__ StepArgs<S> a) {
   const int x = blockIdx.x * kBX + threadIdx.x;
   const int y = blockIdx.y * kBY + threadIdx.y;
