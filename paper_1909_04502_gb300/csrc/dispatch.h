@@ -1,5 +1,5 @@
 // Host-callable launchers of the fused RLBM kernels (defined in step_o2.cu,
-// step_o3.cu).
+// step_o3.cu, step_o3m.cu).
 #pragma once
 #include "kernels.cuh"
 
@@ -9,6 +9,8 @@ template <typename S>
 cudaError_t launch_step_k9(const Tables<S>& tb, const StepArgs<S>& a, int mode, cudaStream_t st);
 template <typename S>
 cudaError_t launch_step_k16(const Tables<S>& tb, const StepArgs<S>& a, int mode, cudaStream_t st);
+template <typename S>
+cudaError_t launch_step_k16_massive_sym(const Tables<S>& tb, const StepArgs<S>& a, int mode, cudaStream_t st);
 template <typename S>
 cudaError_t launch_fields(const Tables<S>& tb, const MomentArgs<S>& a, int mode, cudaStream_t st);
 template <typename S>

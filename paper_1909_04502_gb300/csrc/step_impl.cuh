@@ -455,6 +455,26 @@ struct Orbits<25> {   // built-in m~ = 10, order 2
   static constexpr int n8 = 1, n4 = 2, nd = 2, n1 = 1;
   static constexpr bool massless = false;
 };
+template <>
+struct Orbits<65> {   // built-in order 3, App. H column A (m~ = 1.5 ... 4)
+  static constexpr int n8 = 7, n4 = 0, nd = 2, n1 = 1;
+  static constexpr bool massless = false;
+};
+template <>
+struct Orbits<57> {   // built-in order 3, App. H column B (m~ = 3)
+  static constexpr int n8 = 5, n4 = 1, nd = 3, n1 = 1;
+  static constexpr bool massless = false;
+};
+template <>
+struct Orbits<49> {   // built-in order 3, App. H column C (m~ = 5)
+  static constexpr int n8 = 3, n4 = 4, nd = 2, n1 = 1;
+  static constexpr bool massless = false;
+};
+template <>
+struct Orbits<53> {   // built-in order 3, App. H column D (m~ = 7 ... 20)
+  static constexpr int n8 = 4, n4 = 3, nd = 2, n1 = 1;
+  static constexpr bool massless = false;
+};
 template <int QT>
 struct OrbitStart {
   using O = Orbits<QT>;

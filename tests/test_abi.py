@@ -165,17 +165,23 @@ def test_massless_tables_are_in_orbit_order_with_exactly_symmetric_H(rl, order):
             assert p[i0, 2] == 0.0 and all(H[i0][k] == 0.0 for k, (_, a, b) in enumerate(basis) if b % 2)
 
 
-@pytest.mark.parametrize("m,Q,comp", [(1.0, 33, (3, 1, 1, 1)), (5.0, 29, (2, 1, 2, 1)), (10.0, 25, (1, 2, 2, 1))])
-def test_builtin_massive_tables_are_in_orbit_order_with_exactly_symmetric_H(rl, m, Q, comp):
+@pytest.mark.parametrize("m,order,Q,comp", [
+    (1.0, 2, 33, (3, 1, 1, 1)), (5.0, 2, 29, (2, 1, 2, 1)), (10.0, 2, 25, (1, 2, 2, 1)),
+    (2.0, 3, 65, (7, 0, 2, 1)), (3.0, 3, 57, (5, 1, 3, 1)), (5.0, 3, 49, (3, 4, 2, 1)),
+    (10.0, 3, 53, (4, 3, 2, 1))])
+def test_builtin_massive_tables_are_in_orbit_order_with_exactly_symmetric_H(rl, m, order, Q, comp):
     """The built-in massive stencils come in orbit order too: eight-member
     orbits (sign quartets of (a, b) and (b, a)), axis quartets (p, 0), (-p, 0),
     (0, p), (0, -p), diagonal quartets (a, a), (-a, a), (a, -a), (-a, -a), the
     rest population; weights and H rows are exact images of each orbit's first
     member (what the kernels' symmetric evaluation uses)."""
-    d = rl.plan(nx=16, ny=16, m=m, order=2)
+    d = rl.plan(nx=16, ny=16, m=m, order=order)
     assert d["Q"] == Q
     p, H, w = d["p"], d["H"], d["w"]
+    # exponents (e, a, b) of p0^e px^a py^b in the library's moment order
     basis = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, 0, 1), (0, 2, 0), (0, 1, 1), (0, 0, 2)]
+    if order == 3:
+        basis += [(1, 2, 0), (1, 1, 1), (1, 0, 2), (0, 3, 0), (0, 2, 1), (0, 1, 2), (0, 0, 3)]
     swap = [basis.index((e, b, a)) for (e, a, b) in basis]
 
     def member(i0, sx, sy, sw):
