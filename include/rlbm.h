@@ -130,7 +130,8 @@ int rlbm_create(const rlbm_params* p, rlbm_handle** out);
  * f^eq_i = sum_k H_ik M_k with M the Maxwell-Juttner moments of the basis
  * p0^e px^a py^b, e in {0,1}, e + a + b <= N, in the order 1 | p0 px py |
  * p0px p0py pxpx pxpy pypy | p0pxpx p0pxpy p0pypy pxpxpx pxpxpy pxpypy
- * pypypy), v0 the massive parameter.  Arrays must hold 72 rows (72*16 for H). */
+ * pypypy; at N = 3 the members with p0 are shifted, (p0 - m) px^a py^b), v0
+ * the massive parameter.  Arrays must hold 72 rows (72*16 for H). */
 int rlbm_plan(const rlbm_params* p, int* Q, int* K, int* nvec, double* pmom, double* w,
               double* H, double* v0);
 

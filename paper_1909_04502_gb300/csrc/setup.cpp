@@ -664,19 +664,59 @@ bool equilibrium_matrix(const Quadrature& q, std::vector<double>* H, std::string
       r[k] = t;
     }
     for (int k = 0; k < K; ++k) row[k] = dd(0.0);
-    // multiply by A^{-1}: phi'_k = sg^{-(a+b)} (phi_k - m phi_partner(k)) for e = 1
+    // multiply by A^{-1}: phi'_k = sg^{-(a+b)} (phi_k - m phi_partner(k)) for e = 1.
+    // Order 3 keeps the shifted p0 monomials (p0 - m) p^a p^b as the basis
+    // (only the px, py scale is undone): the moments of that basis are
+    // evaluated without cancellation, while those of p0^e p^a p^b at large m
+    // cancel to a part in 1e3-1e4 in f^eq.
+    const bool keep_shift = q.order == 3;
     for (int k = 0; k < K; ++k) {
       dd sc = dd(q.w[i]) * r[k];
       for (int t = 0; t < B[k].a + B[k].b; ++t) sc = sc / sg;
       row[k] = row[k] + sc;
-      if (B[k].e == 1) row[partner[k]] = row[partner[k]] - dd(q.m) * sc;
+      if (B[k].e == 1 && !keep_shift) row[partner[k]] = row[partner[k]] - dd(q.m) * sc;
     }
     for (int k = 0; k < K; ++k) (*H)[(size_t)i * K + k] = row[k].to_double();
   }
   return true;
 }
 
+void mj_moments_shifted3(double m, double n, const double U[3], double T, double* M) {
+  // App. B moments (see mj_moments) of the order-3 basis with shifted p0
+  // monomials: for X = 1, px, py, pxpx, pxpy, pypy,
+  //   <(p0 - m) X> = <p0 X> - m <X>,
+  // rewritten with U0 - 1 = |u|^2 / (U0 + 1), r2 - m = T (2m + 3T)/(m + T) and
+  // r3 - m r2 = 3T (m^2 + 4mT + 5T^2)/(m + T) so that every term is positive.
+  const double U0 = U[0], Ux = U[1], Uy = U[2];
+  const double u0m1 = (Ux * Ux + Uy * Uy) / (U0 + 1.0);
+  const double mT = m + T;
+  const double r2 = (m * m + 3.0 * m * T + 3.0 * T * T) / mT;
+  const double r3 = (m * m * m + 6.0 * m * m * T + 15.0 * m * T * T + 15.0 * T * T * T) / mT;
+  const double A2 = r2 * u0m1 + T * (2.0 * m + 3.0 * T) / mT;                       // r2 U0 - m
+  const double A3 = r3 * u0m1 + 3.0 * T * (m * m + 4.0 * m * T + 5.0 * T * T) / mT;  // r3 U0 - m r2
+  M[0] = n / mT;
+  M[1] = n * (u0m1 + T / mT);
+  M[2] = n * Ux;
+  M[3] = n * Uy;
+  M[4] = n * Ux * A2;
+  M[5] = n * Uy * A2;
+  M[6] = n * (r2 * Ux * Ux + T);
+  M[7] = n * r2 * Ux * Uy;
+  M[8] = n * (r2 * Uy * Uy + T);
+  M[9] = n * (Ux * Ux * A3 + T * A2);
+  M[10] = n * Ux * Uy * A3;
+  M[11] = n * (Uy * Uy * A3 + T * A2);
+  M[12] = n * (r3 * Ux * Ux * Ux + 3.0 * T * r2 * Ux);
+  M[13] = n * (r3 * Ux * Ux * Uy + T * r2 * Uy);
+  M[14] = n * (r3 * Ux * Uy * Uy + T * r2 * Ux);
+  M[15] = n * (r3 * Uy * Uy * Uy + 3.0 * T * r2 * Uy);
+}
+
 void mj_moments(int order, double m, double n, const double U[3], double T, double* M) {
+  if (order == 3) {
+    mj_moments_shifted3(m, n, U, T, M);
+    return;
+  }
   // App. B: B Z^{a1..ar} = n T^{r-1} sum_k (-1)^k (A_{r-k}/A_1) <U_{r-2k} eta_k>,
   // with, for d = 2 (half-integer Bessel functions are elementary):
   //   A_0/(A_1 T) = 1/(m + T), T A_2/A_1 = (m^2 + 3mT + 3T^2)/(m + T),

@@ -64,11 +64,14 @@ bool builtin_massive(double m, int order, Quadrature* q, std::string* err);
 bool builtin_massive_search(double m, int order, Quadrature* q, std::string* err);   // uncached
 
 // Equilibrium matrix H (Q x K, row-major) with f^eq_i = sum_k H_ik M_k(n, U, T),
-// M the Maxwell-Juttner moments of moment_basis(order):
+// M the Maxwell-Juttner moments of moment_basis(order), where at order 3 the
+// monomials with p0 are taken shifted, (p0 - m) p^a p^b:
 // H = W Phi G^{-1}  (Eq. mj-discrete-feq with J = C phi and C^T C = G^{-1}).
 bool equilibrium_matrix(const Quadrature& q, std::vector<double>* H, std::string* err);
 
-// Maxwell-Juttner moments of moment_basis(order) for (n, U, T) (App. B).
+// Maxwell-Juttner moments of that basis for (n, U, T) (App. B); order 3
+// through mj_moments_shifted3.
 void mj_moments(int order, double m, double n, const double U[3], double T, double* M);
+void mj_moments_shifted3(double m, double n, const double U[3], double T, double* M);
 
 }  // namespace rlbm

@@ -330,16 +330,37 @@ __device__ __forceinline__ void eq_moments(S dn, S dT, S n, S T, S U0, S Ux, S U
   dM[7] = nr2 * Ux * Uy;
   dM[8] = nr2 * Uy * Uy + D3;
   if constexpr (KT == 16) {
+    // Order 3: the members with p0 are the shifted (p0 - m) X, X = 1, px, py,
+    // pxpx, pxpy, pypy (the basis the host builds H for), with
+    //   <(p0 - m) X> = <p0 X> - m <X>,  r2 U0 - m = r2 (U0 - 1) + T c2,
+    //   r3 U0 - m r2 = r3 (U0 - 1) + T c3,
+    //   c2 = (2m + 3T)/(m + T),  c3 = 3 (m^2 + 4mT + 5T^2)/(m + T):
+    // positive terms only, where <p0 X> and m <X> cancel to 1e-3 at m~ = 20.
+    // Differences from the reference (n_ref, rest, T_ref):
+    //   <p0 - m>:  n (U0 - 1) + (dn T (m + T_ref) + n_ref m dT) / ((m + T)(m + T_ref)),
+    //   T (r2 U0 - m) part of <(p0 - m) pxpx>:  n T r2 (U0 - 1) + dn T^2 c2
+    //     + n_ref (h(T) - h(T_ref)),  h(T) = T^2 (2m + 3T)/(m + T),
+    //   h(T) - h(T_ref) = dT (2m^2 (T + T_ref) + 2m T T_ref
+    //     + 3m (T^2 + T T_ref + T_ref^2) + 3 T T_ref (T + T_ref)) / ((m + T)(m + T_ref)).
+    // one quotient for the five divisions by (m + T) and (m + T)(m + T_ref)
+    const S iden = qdiv(S(1), mT * mTr), imT = iden * mTr;
     const S q2 = T * r2;
-    const S r3 = qdiv(m * m * m + S(6) * m * m * T + S(15) * m * T * T + S(15) * T * T * T, mT);
-    const S Nh = dT * (m * (m * m + S(3) * m * (T + Tr) + S(3) * (T * T + T * Tr + Tr * Tr)) +
-                       S(3) * T * Tr * (m + T + Tr));
-    const S dh = qdiv(Nh, mT * mTr);
-    const S D4 = dn * q2 * U0 + nr * (q2 * U0m1 + dh);
+    const S r3 = (m * m * m + S(6) * m * m * T + S(15) * m * T * T + S(15) * T * T * T) * imT;
+    const S c2 = (S(2) * m + S(3) * T) * imT;
+    const S c3 = S(3) * (m * m + S(4) * m * T + S(5) * T * T) * imT;
+    const S A2 = r2 * U0m1 + T * c2;
+    const S A3 = r3 * U0m1 + T * c3;
+    dM[1] = n * U0m1 + (dn * T * mTr + nr * m * dT) * iden;
+    dM[4] = n * Ux * A2;
+    dM[5] = n * Uy * A2;
+    const S Nh = dT * (S(2) * m * m * (T + Tr) + S(2) * m * T * Tr + S(3) * m * (T * T + T * Tr + Tr * Tr) +
+                       S(3) * T * Tr * (T + Tr));
+    const S D5 = n * T * r2 * U0m1 + dn * T * T * c2 + nr * Nh * iden;
+    const S nA3 = n * A3;
     const S nr3 = n * r3, nq2 = n * q2;
-    dM[9] = nr3 * U0 * Ux * Ux + D4;
-    dM[10] = nr3 * U0 * Ux * Uy;
-    dM[11] = nr3 * U0 * Uy * Uy + D4;
+    dM[9] = nA3 * Ux * Ux + D5;
+    dM[10] = nA3 * Ux * Uy;
+    dM[11] = nA3 * Uy * Uy + D5;
     dM[12] = nr3 * Ux * Ux * Ux + S(3) * nq2 * Ux;
     dM[13] = nr3 * Ux * Ux * Uy + nq2 * Uy;
     dM[14] = nr3 * Ux * Uy * Uy + nq2 * Ux;
