@@ -87,17 +87,22 @@ def test_mass5_example_weights_from_product_solver(rl):
 
 
 def _mj_vector(order, m, n, U, T):
-    """MJ moments of the product basis p0^e px^a py^b via the oracle's App. B."""
+    """MJ moments of the product basis p0^e px^a py^b via the oracle's App. B;
+    at order 3 the members with p0 are shifted, <(p0 - m) X> = <p0 X> - m <X>."""
     mons = []
     for deg in range(order + 1):
         if deg >= 1:
             mons += [(1, a, deg - 1 - a) for a in range(deg - 1, -1, -1)]
         mons += [(0, a, deg - a) for a in range(deg, -1, -1)]
-    return np.array([OL.mj_monomial_moment(mo, n, U, T, m) for mo in mons])
+    M = {mo: OL.mj_monomial_moment(mo, n, U, T, m) for mo in mons}
+    if order == 3:
+        return np.array([M[mo] - m * M[(0, mo[1], mo[2])] if mo[0] == 1 else M[mo] for mo in mons])
+    return np.array([M[mo] for mo in mons])
 
 
 @pytest.mark.parametrize("case", [("massless", 2, 0.0), ("massless", 3, 0.0), ("massive", 2, 1.0),
-                                  ("massive", 2, 5.0), ("massive", 2, 10.0)])
+                                  ("massive", 2, 5.0), ("massive", 2, 10.0), ("massive", 3, 2.0),
+                                  ("massive", 3, 5.0)])
 def test_equilibrium_matrix_reproduces_oracle_feq(rl, case):
     kind, order, m = case
     d = rl.plan(nx=8, ny=8, m=m, order=order)
@@ -120,7 +125,8 @@ def test_equilibrium_matrix_reproduces_oracle_feq(rl, case):
         U = OP.four_velocity(np.array(u[0]), np.array(u[1]))
         feq_o = e.feq(np.array(n), U, np.array(T))
         feq_p = d["H"] @ _mj_vector(order, m, n, U, T)
-        # massive weights come from two independent least-squares solves (~2e-13 apart)
+        # both sides round the same exact weights; the rest is the rounding of
+        # the two equilibrium evaluations (raw monomials on the oracle side)
         tol = 1e-13 if kind == "massless" else 5e-13
         assert np.abs(feq_p[idx] - feq_o).max() < tol * np.abs(feq_o).max()
 
