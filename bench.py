@@ -210,7 +210,7 @@ def main():
     ap.add_argument("--workload", default="tg512", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint measurements")
-    ap.add_argument("--only", default=None, choices=["batched", "adjoint", "paper"],
+    ap.add_argument("--only", default=None, choices=["batched", "adjoint", "paper", "kh"],
                     help="run only this extra measurement and print its JSON object")
     ap.add_argument("--_oracle_worker", default=None)
     args = ap.parse_args()
@@ -256,6 +256,8 @@ def main():
                    "batched_small": bench_batched(torch, rlbm, inputs, stream, steps=50, side_hi=256)}
         elif args.only == "paper":
             res = {"massive_order3_tg512": bench_massive_order3(torch, rlbm, inputs, stream)}
+        elif args.only == "kh":
+            res = {"kelvin_helmholtz_2048": bench_kh(torch, rlbm, inputs, stream)}
         else:
             res = {"adjoint": bench_adjoint(torch, rlbm, inputs, stream)}
         if rank == 0:
@@ -358,6 +360,7 @@ def main():
         extras["batched_small"] = bench_batched(torch, rlbm, inputs, stream, steps=50, side_hi=256)
         extras["adjoint"] = bench_adjoint(torch, rlbm, inputs, stream)
         extras["massive_order3_tg512"] = bench_massive_order3(torch, rlbm, inputs, stream)
+        extras["kelvin_helmholtz_2048"] = bench_kh(torch, rlbm, inputs, stream)
         if wl["workload"] == "tg512_bilinear_fp32":
             extras["viscosity"] = bench_tg_viscosity(rlbm, inputs)
 
@@ -548,6 +551,38 @@ def bench_massive_order3(torch, rlbm, inputs, stream, L=512, m=5.0, steps=50, wa
                      "algorithmic_gbs": round(gbs, 1), "frac_of_hbm": round(gbs / peak, 4),
                      "nonphysical": st[1]}
         lat.close()
+    return out
+
+
+def bench_kh(torch, rlbm, inputs, stream, L=2048, steps=20, warmup=5):
+    """The zeta = 1, order-3 Kelvin-Helmholtz shear layer (2048^2, +-0.3c,
+    tanh width 20 cells, 1e-3 seeded perturbation, FP32 storage): zeta = m~/T~
+    with m~ = T~ = 1.5, the smallest mass with a built-in order-3 stencil
+    (Q = 65), tau = 0.85.  Each buffer holds 1.09 GB, more than L2, so no
+    flush is needed; every step is timed with its own events."""
+    m = T0 = 1.5
+    fields = [__import__("numpy").ascontiguousarray(a) for a in inputs.kelvin_helmholtz(L, T0=T0)]
+    lat = rlbm.Lattice(L, L, m=m, order=3, tau=0.85, precision="fp32", n_ref=1.0, T_ref=T0,
+                       cuda_stream=stream.cuda_stream)
+    lat.init(*fields)
+    for _ in range(warmup):
+        lat.step(1)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for a, b in ev:
+        a.record(stream)
+        lat.step(1)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    st = lat.sync_status(raise_on_error=False)
+    peak, _ = _peaks()
+    gbs = 2 * lat.Q * 4 * L * L / (ms * 1e-3) / 1e9
+    out = {"workload": f"kh{L}_zeta1_order3_fp32", "m": m, "T": T0, "Q": lat.Q, "ms_per_step": round(ms, 4),
+           "mlups": round(L * L / (ms * 1e-3) / 1e6, 1), "algorithmic_gbs": round(gbs, 1),
+           "frac_of_hbm": round(gbs / peak, 4), "full_run_s_estimate": round(10000 * ms / 1e3, 2),
+           "nonphysical": st[1]}
+    lat.close()
     return out
 
 

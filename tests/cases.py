@@ -57,12 +57,12 @@ class _DeviceView:
                                          "version": 3, "strides": None}
 
 
-def device_patch(lat, cx, cy, R, quad, idx):
+def device_patch(lat, cx, cy, R, quad, idx, ref=(1.0, 1.0)):
     """Post-collision populations f*(t) of the (2R+1)^2 cells around (cx, cy)
     (periodic), read from the handle's current device buffer, as FP64 in the
     oracle's population order [Q][2R+1][2R+1].  FP32 storage holds
-    f - f_ref; f_ref is the oracle's rest-frame equilibrium at (n_ref, T_ref)
-    = (1, 1), which equals the library's to rounding."""
+    f - f_ref; f_ref is the oracle's rest-frame equilibrium at the handle's
+    (n_ref, T_ref) = ref, which equals the library's to rounding."""
     import torch
     cur, _, elem, plane, (pitch, hx, hy, px) = lat.buffers()
     Q = lat.Q
@@ -76,7 +76,8 @@ def device_patch(lat, cx, cy, R, quad, idx):
     f = f[idx]                                  # oracle order
     if elem == 4:
         one = np.ones((1, 1))
-        f = f + OL.Expansion(quad).feq(one, np.array([1.0, 0.0, 0.0]).reshape(3, 1, 1), one)[:, :1, :1]
+        f = f + OL.Expansion(quad).feq(ref[0] * one, np.array([1.0, 0.0, 0.0]).reshape(3, 1, 1),
+                                       ref[1] * one)[:, :1, :1]
     return f
 
 
