@@ -60,10 +60,14 @@ def landau(Nvec, Tmat):
     with LAPACK ``eig``; eps is the largest real eigenvalue and U its
     eigenvector normalised to U^a U_a = 1, U^0 > 0.  n = U_a N^a.
     Nvec: (3, ...), Tmat: (3, 3, ...).  Returns eps, U (3, ...), n, ok mask
-    (ok = eigenvector timelike and eigenvalue real and positive).
+    (ok = finite moments, eigenvector timelike, eigenvalue real and positive).
     """
     shp = Nvec.shape[1:]
     A = np.moveaxis(Tmat.reshape(3, 3, -1), -1, 0) @ ETA       # (C, 3, 3)
+    # a cell with non-finite moments is non-physical (no eigenpair); it is
+    # solved as the identity so that LAPACK sees finite input, and flagged
+    finite = np.all(np.isfinite(A), axis=(1, 2)) & np.all(np.isfinite(Nvec.reshape(3, -1)), axis=0)
+    A = np.where(finite[:, None, None], A, np.eye(3))
     lam, vec = np.linalg.eig(A)
     lam_r = lam.real
     idx = np.argmax(lam_r, axis=1)
@@ -71,7 +75,7 @@ def landau(Nvec, Tmat):
     eps = lam_r[np.arange(C), idx]
     v = vec[np.arange(C), :, idx].real                         # (C, 3)
     norm2 = v[:, 0] ** 2 - v[:, 1] ** 2 - v[:, 2] ** 2
-    ok = (norm2 > 0) & (eps > 0) & (np.abs(lam[np.arange(C), idx].imag) == 0)
+    ok = (norm2 > 0) & (eps > 0) & (np.abs(lam[np.arange(C), idx].imag) == 0) & finite
     U = v / np.sqrt(np.abs(norm2))[:, None]
     U = U * np.sign(U[:, :1])
     U = U.T.reshape((3,) + shp)

@@ -359,6 +359,20 @@ def _boost(beta_x, beta_y):
     return L_
 
 
+def test_landau_flags_non_finite_cells_instead_of_raising():
+    """A cell whose moments are not finite has no Landau frame: it is flagged
+    (reading of Sec. 4 for non-physical states), and the other cells of the
+    same call are solved as usual."""
+    N = np.zeros((3, 2))
+    Tm = np.zeros((3, 3, 2))
+    N[0] = 1.0
+    Tm[0, 0], Tm[1, 1], Tm[2, 2] = 2.0, 1.0, 1.0            # rest frame, eps = 2, P = 1
+    Tm[0, 0, 1] = np.nan
+    eps, U, n, ok = P.landau(N, Tm)
+    assert ok.tolist() == [True, False]
+    assert abs(eps[0] - 2.0) < 1e-14 and abs(n[0] - 1.0) < 1e-14 and abs(U[0, 0] - 1.0) < 1e-14
+
+
 @pytest.mark.parametrize("beta", [(0.0, 0.0), (0.3, 0.1), (-0.6, 0.5), (0.9, 0.0), (0.0, -0.9)])
 def test_landau_solve_is_lorentz_consistent(beta):
     """Boost a rest-frame tensor (ideal part + a traceless shear part) and
