@@ -1,0 +1,130 @@
+"""Pins of the (3+1)-d massless oracle (oracle/d3.py) against what the paper
+and mathematics fix: the App. H digits read as stated there, textbook
+Gauss-Laguerre nodes, closed-form moments, Lorentz boosts and conservation."""
+import math
+
+import numpy as np
+import pytest
+from scipy import special
+
+from oracle import d3
+
+
+@pytest.fixture(scope="module")
+def quad():
+    return d3.massless_quadrature_3d(2)
+
+
+def test_shells_are_the_generalized_laguerre_nodes(quad):
+    """d^3p/p0 = p0 dp0 dOmega on the light cone: the radial weight is
+    p0 e^{-p0}, whose 3-point Gauss rule has the nodes of L_3^(1)."""
+    x, _ = special.roots_genlaguerre(3, 1)
+    assert np.allclose(np.unique(quad.p[:, 0]), np.sort(x), rtol=0, atol=1e-13)
+
+
+def test_stencil_and_weights(quad):
+    assert quad.Q == 78
+    assert np.all(np.sum(quad.n ** 2, axis=1) == 9)          # one speed: |n_i| = 3
+    assert abs(quad.w.sum() - 1.0) < 1e-14
+
+
+def test_reading_integrates_every_omega_moment_up_to_degree_four(quad):
+    """The rule integrates p0^c0 px^a py^b pz^c like omega for c0+a+b+c <= 4
+    (2N at N = 2), which fixes the reading of the weight column; the printed
+    group (2, 1, 1) in place of (2, 2, 1) misses them."""
+    p, w = quad.p, quad.w
+    worst = 0.0
+    for c0, a, b, c in [(c0, a, b, c) for c0 in range(5) for a in range(5) for b in range(5)
+                        for c in range(5) if c0 + a + b + c <= 4]:
+        got = np.sum(w * p[:, 0] ** c0 * p[:, 1] ** a * p[:, 2] ** b * p[:, 3] ** c)
+        want = d3.omega_moment_3d(c0, a, b, c)
+        worst = max(worst, abs(got - want) / max(1.0, abs(want)))
+    assert worst < 1e-13
+    # the group as printed, (2, 1, 1), with the same weights does not
+    alt = []
+    for j, p0 in enumerate(d3.MASSLESS_D3[2]["shells"]):
+        for g, gen in enumerate([(2, 1, 1), (3, 0, 0)]):
+            wj = d3.MASSLESS_D3[2]["weights_printed"][2 * j + g]
+            alt += [(p0, np.array(v) / np.linalg.norm(v), wj) for v in d3.fs_orbit3(gen)] if wj else []
+    pa = np.array([[p0, *(p0 * v)] for p0, v, _ in alt])
+    wa = np.array([wj for _, _, wj in alt])
+    assert abs(np.sum(wa * pa[:, 1] ** 2 * pa[:, 2] ** 2) - d3.omega_moment_3d(0, 2, 2, 0)) > 0.1
+    # the angular factor against a direct quadrature over the sphere
+    th, wt = np.polynomial.legendre.leggauss(20)
+    ph = 2 * np.pi * np.arange(40) / 40
+    nx = np.sqrt(1 - th[:, None] ** 2) * np.cos(ph)[None, :]
+    ny = np.sqrt(1 - th[:, None] ** 2) * np.sin(ph)[None, :]
+    nz = th[:, None] * np.ones_like(ph)[None, :]
+    for a, b, c in [(2, 0, 0), (2, 2, 0), (4, 0, 0), (2, 2, 2)]:
+        direct = np.sum(wt[:, None] * nx ** a * ny ** b * nz ** c) * (2 * np.pi / 40) / (4 * np.pi)
+        assert abs(direct * math.factorial(a + b + c + 1) - d3.omega_moment_3d(0, a, b, c)) < 1e-12
+
+
+def test_equilibrium_recovers_N_and_T_and_the_rest_state(quad):
+    E = d3.Expansion3(quad)
+    assert E.J.shape[0] == 14                                   # p0^2 = |p|^2 drops one member
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        n, T = rng.uniform(0.5, 1.5), rng.uniform(0.7, 1.4)
+        u = rng.uniform(-0.3, 0.3, 3)
+        g = 1 / math.sqrt(1 - u @ u)
+        U = np.concatenate([[g], g * u])
+        f = E.feq(np.array(n), U, np.array(T))
+        N = quad.p.T @ f
+        Tab = np.einsum("qa,qb,q->ab", quad.p, quad.p, f)
+        assert np.abs(N - n * U).max() < 1e-13
+        assert np.abs(Tab - (4 * n * T * np.outer(U, U) - n * T * d3.ETA4)).max() < 1e-12
+    # at rest and T = 1 the MJ distribution is (n/2) omega (<1> = n/(2T) while
+    # omega integrates to 1), so f^eq_i = (n/2) w_i
+    f0 = E.feq(np.array(1.3), np.array([1.0, 0, 0, 0]), np.array(1.0))
+    assert np.abs(f0 - 0.65 * quad.w).max() < 1e-14
+
+
+@pytest.mark.parametrize("beta", [(0.0, 0.0, 0.0), (0.3, -0.2, 0.1), (0.0, 0.0, -0.7), (0.5, 0.5, 0.5)])
+def test_landau4_recovers_a_boosted_ideal_fluid(beta):
+    """Rest-frame T = diag(eps, P, P, P) boosted by beta: the solve returns
+    eps and U = gamma (1, beta)."""
+    b = np.array(beta)
+    g = 1 / math.sqrt(1 - b @ b)
+    U = np.concatenate([[g], g * b])
+    eps, P, n = 2.7, 0.9, 1.1
+    Tm = (eps + P) * np.outer(U, U) - P * d3.ETA4
+    e, Uo, no, ok = d3.landau4((n * U)[:, None], Tm[:, :, None])
+    assert ok[0] and abs(e[0] - eps) < 1e-12 and np.abs(Uo[:, 0] - U).max() < 1e-12 and abs(no[0] - n) < 1e-12
+
+
+def test_collision_conserves_and_equilibrium_is_fixed(quad):
+    E = d3.Expansion3(quad)
+    rng = np.random.default_rng(5)
+    f = E.feq(np.array(1.0), np.array([1.0, 0, 0, 0]), np.array(1.0))[:, None] * \
+        (1 + 0.05 * rng.standard_normal((quad.Q, 7)))
+    fs, _ = d3.collide3(f, quad, E, 0.9)
+    for a in range(4):
+        assert np.abs(quad.p[:, 0] @ (fs - f)).max() < 1e-14
+        assert np.abs((quad.p[:, 0] * quad.p[:, a]) @ (fs - f)).max() < 1e-13
+    u = np.array([0.2, -0.1, 0.05])
+    g = 1 / math.sqrt(1 - u @ u)
+    feq = E.feq(np.array(1.2), np.concatenate([[g], g * u]), np.array(0.9))[:, None]
+    fs, _ = d3.collide3(feq, quad, E, 0.9)
+    assert np.abs(fs - feq).max() < 1e-14
+
+
+def test_streaming_permutes_and_a_periodic_run_conserves(quad):
+    E = d3.Expansion3(quad)
+    nx, ny, nz = 9, 7, 6
+    sim = d3.Simulation3(quad, E, nx, ny, nz, tau=0.8)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    ux = 0.1 * np.sin(2 * np.pi * y / ny)
+    uy = 0.05 * np.cos(2 * np.pi * z / nz)
+    uz = 0.05 * np.sin(2 * np.pi * x / nx)
+    T = 1 + 0.05 * np.cos(2 * np.pi * x / nx)
+    sim.init(np.ones_like(T), ux, uy, uz, T)
+    s = d3.stream3(sim.fs, quad.n)
+    assert np.allclose(np.sort(s.ravel()), np.sort(sim.fs.ravel()), rtol=0, atol=0)
+    c0 = quad.p[:, 0] @ sim.fs.reshape(quad.Q, -1)
+    N0, T0 = c0.sum(), [(quad.p[:, 0] * quad.p[:, a]) @ sim.fs.reshape(quad.Q, -1) for a in range(4)]
+    sim.step(6)
+    assert np.all(sim.fields.ok)
+    assert abs((quad.p[:, 0] @ sim.fs.reshape(quad.Q, -1)).sum() - N0) < 1e-12 * N0
+    for a in range(4):
+        assert abs(((quad.p[:, 0] * quad.p[:, a]) @ sim.fs.reshape(quad.Q, -1)).sum() - T0[a].sum()) < 1e-12 * T0[0].sum()
