@@ -44,7 +44,7 @@ extern "C" {
 enum {
   RLBM_OK = 0,
   RLBM_ERR_INVALID_ARG = -1,   /* bad parameter or size                        */
-  RLBM_ERR_UNSUPPORTED = -2,   /* valid but not implemented (e.g. d = 3)       */
+  RLBM_ERR_UNSUPPORTED = -2,   /* valid but not implemented                    */
   RLBM_ERR_CUDA = -3,          /* a CUDA runtime call failed                   */
   RLBM_ERR_NONPHYSICAL = -4,   /* a cell had no physical Landau frame          */
   RLBM_ERR_TIMEOUT = -5,       /* a bounded device-side wait gave up           */
@@ -329,6 +329,59 @@ const char* rlbm_last_error(const rlbm_handle* h);
 
 /* Static description of an error code. */
 const char* rlbm_strerror(int code);
+
+/* ------------------------------------------------------------------------
+ * (3+1) dimensions: massless particles, expansion order 2 (Sec. 5-6 with
+ * d = 3).  Stencil and weights: App. H, "(3+1) dimensions", order 2, read
+ * with the group (+-2, +-2, +-1) (the printed (+-2, +-1, +-1) does not have
+ * the common length 3 of a massless stencil) and the weights shell by shell
+ * (per shell the (2, 2, 1) group, then (3, 0, 0)): Q = 78.  FP64 storage and
+ * arithmetic, on-lattice streaming, periodic in x, y and z, constant tau.
+ * EOS eps = 3 n T.  Fields are row-major [z][y][x] arrays of nx*ny*nz doubles.
+ * ------------------------------------------------------------------------ */
+typedef struct rlbm3_handle rlbm3_handle;
+
+/* Host-only: Q and the tables rlbm3_create builds -- stencil vectors nvec
+ * (3*Q ints), momenta p (4*Q), weights w (Q), equilibrium matrix H (Q*14,
+ * f^eq_i = sum_k H_ik M_k with M the MJ moments of 1 | p0 px py pz | p0px
+ * p0py p0pz pxpx pxpy pxpz pypy pypz pzpz); arrays nullable, 80 rows. */
+int rlbm3_plan(int* Q, int* nvec, double* p, double* w, double* H);
+
+/* Tables on the host (double-double), two population buffers on the current
+ * device; stream: cudaStream_t all work is issued on.  Each side at least 3
+ * cells (the stencil length) and nx*ny*nz <= 2^28.  Synchronous. */
+int rlbm3_create(int nx, int ny, int nz, double tau, void* stream, rlbm3_handle** out);
+void rlbm3_destroy(rlbm3_handle* h);
+
+/* Q, stencil vectors nvec (3*Q ints, nullable), momenta p (4*Q: p0, px, py,
+ * pz; nullable), weights w (Q, nullable) in the library's population order. */
+int rlbm3_stencil(const rlbm3_handle* h, int* Q, int* nvec, double* p, double* w);
+
+/* f*(0) = f^eq(n, U(u), T) from host (on_device = 0: copied, then synchronous)
+ * or device arrays (on_device = 1: borrowed, asynchronous). */
+int rlbm3_init(rlbm3_handle* h, const double* n, const double* ux, const double* uy, const double* uz,
+               const double* T, int on_device);
+
+/* nsteps fused steps (pull, moments, Landau frame, equilibrium, relaxation),
+ * asynchronous on the handle's stream. */
+int rlbm3_step(rlbm3_handle* h, int nsteps);
+
+/* Fields of the populations f(t) before the collision of step t (f*(t-1)
+ * pulled; at t = 0 the initial equilibrium): out = [6][nz][ny][nx] doubles
+ * (n, ux, uy, uz, T, eps; n is NaN where the cell has no Landau frame), host
+ * (synchronous) or device (asynchronous). */
+int rlbm3_moments(rlbm3_handle* h, double* out, int on_device);
+
+/* Post-collision populations f*(t), host array [Q][nz][ny][nx].  Synchronous. */
+int rlbm3_get_populations(rlbm3_handle* h, double* f);
+
+/* Synchronise; RLBM_ERR_NONPHYSICAL if cell updates were left unrelaxed since
+ * the last call (their number in *count, nullable), else RLBM_OK. */
+int rlbm3_sync_status(rlbm3_handle* h, long long* count);
+
+/* Message of the last error on this handle (or of the last failed
+ * rlbm3_create when h is NULL).  Never NULL. */
+const char* rlbm3_last_error(const rlbm3_handle* h);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,47 @@
+// Kernel-side tables and arguments of the (3+1)-d massless step (step3.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "setup.h"
+
+namespace rlbm {
+
+struct Tables3 {
+  double c[kMaxQ3][4];    // p0, px, py, pz of population i
+  double v[kMaxQ3][3];    // microscopic velocity p / p0
+  double H[kMaxQ3][14];   // equilibrium matrix: f^eq_i = sum_k H_ik M_k
+  int off[kMaxQ3];        // pull source of population i relative to the cell: i * plane - n_i . strides
+};
+
+struct Scalars3 {
+  int Q, nx, ny, nz;
+  int h, px, pitch;       // halo width, x offset of the interior, row pitch (elements)
+  long long slab, plane;  // elements per z-slab and per population plane
+  double tau;
+};
+
+struct Step3Args {
+  const double* fin;
+  double* fout;
+  unsigned long long* status;
+  Scalars3 s;
+};
+
+struct Init3Args {
+  double* f;
+  const double *n, *ux, *uy, *uz, *T;   // device fields, row-major [z][y][x]
+  Scalars3 s;
+};
+
+struct Fields3Args {
+  const double* fin;      // f*(t-1), pulled (pull = 1), or f*(0) read in place (pull = 0)
+  int pull;
+  double* out;            // [6][nz][ny][nx]: n, ux, uy, uz, T, eps
+  Scalars3 s;
+};
+
+cudaError_t launch_step3(const Tables3& tb, const Step3Args& a, cudaStream_t st);
+cudaError_t launch_init3(const Tables3& tb, const Init3Args& a, cudaStream_t st);
+cudaError_t launch_fields3(const Tables3& tb, const Fields3Args& a, cudaStream_t st);
+
+}  // namespace rlbm

@@ -6,6 +6,9 @@
 // integrals), App. H (stencils and massless tables) of arXiv:1909.04502.
 #include "setup.h"
 
+#include <array>
+#include <set>
+
 #include "dd.h"
 
 #include <algorithm>
@@ -744,6 +747,101 @@ void mj_moments(int order, double m, double n, const double U[3], double T, doub
     }
     M[k] = v;
   }
+}
+
+// ---------------------------------------------------------------------------
+// (3+1)-d massless tables, order 2 (App. H "(3+1) dimensions").
+// ---------------------------------------------------------------------------
+
+namespace {
+
+dd dd_factorial(int k) {
+  dd r(1.0);
+  for (int t = 2; t <= k; ++t) r = r * dd((double)t);
+  return r;
+}
+
+dd dd_dfact(int k) {
+  dd r(1.0);
+  for (int t = k; t > 1; t -= 2) r = r * dd((double)t);
+  return r;
+}
+
+// E_omega[p0^c0 px^a py^b pz^c] for omega = e^{-p0} on the light cone
+// (d^3p/p0 = p0 dp0 dOmega), normalised to 1: the angular mean of
+// nx^a ny^b nz^c, (a-1)!!(b-1)!!(c-1)!!/(a+b+c+1)!! for even a, b, c, times
+// (c0+a+b+c+1)!.
+dd omega_moment3_dd(int c0, int a, int b, int c) {
+  if ((a & 1) || (b & 1) || (c & 1)) return dd(0.0);
+  return dd_dfact(a - 1) * dd_dfact(b - 1) * dd_dfact(c - 1) / dd_dfact(a + b + c + 1) *
+         dd_factorial(c0 + a + b + c + 1);
+}
+
+}  // namespace
+
+const int kBasis3[14][4] = {{0, 0, 0, 0}, {1, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, 1, 0}, {0, 0, 0, 1},
+                             {1, 1, 0, 0}, {1, 0, 1, 0}, {1, 0, 0, 1}, {0, 2, 0, 0}, {0, 1, 1, 0},
+                             {0, 1, 0, 1}, {0, 0, 2, 0}, {0, 0, 1, 1}, {0, 0, 0, 2}};
+
+bool massless3_tables(Quadrature3* q, std::string* err) {
+  // Stencil {(+-2, +-2, +-1)FS, (+-3, 0, 0)FS} (all of length 3: the printed
+  // first group, (+-2, +-1, +-1), is not of the common length a massless
+  // stencil needs), shell energies p0_j as printed, weights read shell by
+  // shell, per shell the (2, 2, 1) group then the (3, 0, 0) group (this
+  // reading integrates the weight's moments up to degree 4; the others do
+  // not).  p_ij = p0_j (1, n_i / 3).
+  static const double shells[3] = {0.9358222275240878, 3.3054072893322786, 7.7587704831436335};
+  static const double col[6] = {0.0245283950433191, 0.0, 0.0163006691342629, 0.0,
+                                0.0003891858228425, 0.0017936666649682};
+  static const int gens[2][3] = {{2, 2, 1}, {3, 0, 0}};
+  *q = Quadrature3();
+  for (int j = 0; j < 3; ++j)
+    for (int g = 0; g < 2; ++g) {
+      const double wgt = col[2 * j + g];
+      if (wgt == 0.0) continue;
+      std::set<std::array<int, 3>> orbit;
+      int perm[3] = {0, 1, 2};
+      do {
+        for (int sgn = 0; sgn < 8; ++sgn) {
+          std::array<int, 3> v;
+          for (int k = 0; k < 3; ++k) v[k] = ((sgn >> k) & 1 ? -1 : 1) * gens[g][perm[k]];
+          orbit.insert(v);
+        }
+      } while (std::next_permutation(perm, perm + 3));
+      for (const auto& v : orbit) {
+        for (int k = 0; k < 3; ++k) q->n.push_back(v[k]);
+        q->p.push_back(shells[j]);
+        for (int k = 0; k < 3; ++k) q->p.push_back(shells[j] * v[k] / 3.0);
+        q->w.push_back(wgt);
+      }
+    }
+  q->Q = (int)q->w.size();
+  if (q->Q > kMaxQ3) { *err = "3-d stencil larger than the kernels accept"; return false; }
+  // H = W Phi G^{-1} in double-double, Phi and G in the basis kBasis3
+  const int K = 14;
+  std::vector<dd> G(K * K), Gi;
+  for (int k = 0; k < K; ++k)
+    for (int l = 0; l < K; ++l)
+      G[k * K + l] = omega_moment3_dd(kBasis3[k][0] + kBasis3[l][0], kBasis3[k][1] + kBasis3[l][1],
+                                      kBasis3[k][2] + kBasis3[l][2], kBasis3[k][3] + kBasis3[l][3]);
+  if (!spd_inverse_dd(G, K, &Gi)) { *err = "3-d Gram matrix not positive definite"; return false; }
+  q->H.assign((size_t)q->Q * K, 0.0);
+  for (int i = 0; i < q->Q; ++i) {
+    const double* pi = &q->p[4 * i];
+    dd phi[14];
+    for (int k = 0; k < K; ++k) {
+      dd v(1.0);
+      for (int c = 0; c < 4; ++c)
+        for (int t = 0; t < kBasis3[k][c]; ++t) v = v * dd(pi[c]);
+      phi[k] = v;
+    }
+    for (int k = 0; k < K; ++k) {
+      dd t(0.0);
+      for (int l = 0; l < K; ++l) t = t + phi[l] * Gi[l * K + k];
+      q->H[(size_t)i * K + k] = (dd(q->w[i]) * t).to_double();
+    }
+  }
+  return true;
 }
 
 }  // namespace rlbm

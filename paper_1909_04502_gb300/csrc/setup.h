@@ -74,4 +74,19 @@ bool equilibrium_matrix(const Quadrature& q, std::vector<double>* H, std::string
 void mj_moments(int order, double m, double n, const double U[3], double T, double* M);
 void mj_moments_shifted3(double m, double n, const double U[3], double T, double* M);
 
+
+// (3+1)-d massless order-2 stencil (App. H, read as in setup.cpp) with its
+// equilibrium matrix: f^eq_i = sum_k H_ik M_k, M the MJ moments of the
+// basis kBasis3 (1 | p0 px py pz | p0px p0py p0pz pxpx pxpy pxpz pypy pypz pzpz).
+constexpr int kMaxQ3 = 80;
+struct Quadrature3 {
+  int Q = 0;
+  std::vector<int> n;       // 3 Q stencil vectors
+  std::vector<double> p;    // 4 Q momenta (p0, px, py, pz)
+  std::vector<double> w;    // Q weights
+  std::vector<double> H;    // Q x 14
+};
+extern const int kBasis3[14][4];
+bool massless3_tables(Quadrature3* q, std::string* err);
+
 }  // namespace rlbm

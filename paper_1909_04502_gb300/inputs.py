@@ -72,6 +72,34 @@ def random_smooth(nx, ny, seed=0, umax=0.3, dn=0.2, dT=0.2, modes=3):
     return n, ux, uy, T
 
 
+def random_smooth3(nx, ny, nz, seed=0, umax=0.2, dn=0.2, dT=0.2, modes=3):
+    """Smooth periodic random fields on an (nz, ny, nx) grid (a few low
+    Fourier modes each): n, ux, uy, uz, T for three-dimensional parity tests."""
+    rng = np.random.default_rng(seed)
+    Z, Y, X = np.meshgrid(2 * np.pi * np.arange(nz) / nz, 2 * np.pi * np.arange(ny) / ny,
+                          2 * np.pi * np.arange(nx) / nx, indexing="ij")
+
+    def field():
+        f = np.zeros((nz, ny, nx))
+        for _ in range(modes):
+            kx, ky, kz = rng.integers(0, 3, 3)
+            f += rng.uniform(-1, 1) * np.cos(kx * X + ky * Y + kz * Z + rng.uniform(0, 2 * np.pi))
+        return f / modes
+
+    n = 1.0 + dn * field()
+    T = 1.0 + dT * field()
+    return n, umax * field(), umax * field(), umax * field(), T
+
+
+def taylor_green3(L, nz, u0=0.2, n0=1.0, T0=1.0):
+    """The Taylor-Green flow of ``taylor_green`` (u_x = u0 cos x sin y,
+    u_y = -u0 cos y sin x on x_i = 2 pi i / L), uniform along z (nz cells),
+    u_z = 0: the setup the paper runs with its (3+1)-dimensional solver."""
+    n, ux, uy, T = taylor_green(L, u0=u0, n0=n0, T0=T0)
+    rep = lambda a: np.ascontiguousarray(np.broadcast_to(a, (nz,) + a.shape))
+    return rep(n), rep(ux), rep(uy), np.zeros((nz, L, L)), rep(T)
+
+
 def smooth_tau(nx, ny, seed=5, lo=0.6, hi=2.0):
     """Hidden relaxation-time field: 1 + 0.3 * (four random low-k cosines),
     clipped to [lo, hi]."""

@@ -56,6 +56,17 @@ SIGNATURES = {
     "rlbm_default_params": (None, [ctypes.POINTER(Params)]),
     "rlbm_create": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(_H)]),
     "rlbm_plan": (ctypes.c_int, [ctypes.POINTER(Params), _IP, _IP, _IP, _DP, _DP, _DP, _DP]),
+    "rlbm3_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _VP,
+                                    ctypes.POINTER(_H)]),
+    "rlbm3_destroy": (None, [_H]),
+    "rlbm3_plan": (ctypes.c_int, [_IP, _IP, _DP, _DP, _DP]),
+    "rlbm3_stencil": (ctypes.c_int, [_H, _IP, _IP, _DP, _DP]),
+    "rlbm3_init": (ctypes.c_int, [_H, _VP, _VP, _VP, _VP, _VP, ctypes.c_int]),
+    "rlbm3_step": (ctypes.c_int, [_H, ctypes.c_int]),
+    "rlbm3_moments": (ctypes.c_int, [_H, _VP, ctypes.c_int]),
+    "rlbm3_get_populations": (ctypes.c_int, [_H, _DP]),
+    "rlbm3_sync_status": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_longlong)]),
+    "rlbm3_last_error": (ctypes.c_char_p, [_H]),
     "rlbm_destroy": (None, [_H]),
     "rlbm_init": (ctypes.c_int, [_H, _VP, _VP, _VP, _VP, ctypes.c_int]),
     "rlbm_set_tau_field": (ctypes.c_int, [_H, _VP, ctypes.c_int]),
@@ -472,6 +483,88 @@ class Adjoint:
         if getattr(self, "a", None):
             lib().rlbm_adjoint_destroy(self.a)
             self.a = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plan3():
+    """Host-only (3+1)-d tables: dict with Q, n (Q,3), p (Q,4), w, H (Q,14)."""
+    Q = ctypes.c_int()
+    nvec = np.zeros(3 * 80, dtype=np.int32)
+    pm, w, H = np.zeros(4 * 80), np.zeros(80), np.zeros(14 * 80)
+    rc = lib().rlbm3_plan(ctypes.byref(Q), nvec.ctypes.data_as(_IP), pm.ctypes.data_as(_DP),
+                          w.ctypes.data_as(_DP), H.ctypes.data_as(_DP))
+    if rc != RLBM_OK:
+        raise RLBMError(rc, lib().rlbm3_last_error(None).decode())
+    q = Q.value
+    return dict(Q=q, n=nvec[:3 * q].reshape(q, 3).copy(), p=pm[:4 * q].reshape(q, 4).copy(), w=w[:q].copy(),
+                H=H[:14 * q].reshape(q, 14).copy())
+
+
+class Lattice3:
+    """A (3+1)-d massless periodic lattice (order 2, FP64) behind the rlbm3_*
+    calls; fields are numpy (nz, ny, nx) arrays or CUDA float64 tensors."""
+
+    def __init__(self, nx, ny, nz, tau=1.0, cuda_stream=None):
+        if cuda_stream is None:
+            cuda_stream = _current_stream()
+        self.nx, self.ny, self.nz = nx, ny, nz
+        h = _H()
+        rc = lib().rlbm3_create(nx, ny, nz, tau, cuda_stream, ctypes.byref(h))
+        if rc != RLBM_OK:
+            raise RLBMError(rc, lib().rlbm3_last_error(None).decode())
+        self.h = h
+        Q = ctypes.c_int()
+        nvec = np.zeros(3 * 80, dtype=np.int32)
+        pm = np.zeros(4 * 80)
+        w = np.zeros(80)
+        self._chk(lib().rlbm3_stencil(self.h, ctypes.byref(Q), nvec.ctypes.data_as(_IP), pm.ctypes.data_as(_DP),
+                                      w.ctypes.data_as(_DP)))
+        self.Q = Q.value
+        self.n = nvec[:3 * self.Q].reshape(self.Q, 3).copy()
+        self.p = pm[:4 * self.Q].reshape(self.Q, 4).copy()
+        self.w = w[:self.Q].copy()
+
+    def _chk(self, rc):
+        if rc != RLBM_OK:
+            raise RLBMError(rc, lib().rlbm3_last_error(self.h).decode())
+
+    def init(self, n, ux, uy, uz, T):
+        ptrs = [_ptr(a) for a in (n, ux, uy, uz, T)]
+        dev = {d for _, d in ptrs}
+        if len(dev) != 1:
+            raise ValueError("fields must all live on the host or all on the device")
+        self._chk(lib().rlbm3_init(self.h, *[p for p, _ in ptrs], dev.pop()))
+
+    def step(self, k=1):
+        self._chk(lib().rlbm3_step(self.h, int(k)))
+
+    def moments(self):
+        """dict n, ux, uy, uz, T, eps of f(t) as (nz, ny, nx) host arrays."""
+        out = np.empty((6, self.nz, self.ny, self.nx))
+        self._chk(lib().rlbm3_moments(self.h, out.ctypes.data, 0))
+        return dict(zip(("n", "ux", "uy", "uz", "T", "eps"), out))
+
+    def populations(self):
+        f = np.empty((self.Q, self.nz, self.ny, self.nx))
+        self._chk(lib().rlbm3_get_populations(self.h, f.ctypes.data_as(_DP)))
+        return f
+
+    def sync_status(self):
+        c = ctypes.c_longlong()
+        rc = lib().rlbm3_sync_status(self.h, ctypes.byref(c))
+        if rc not in (RLBM_OK, -4):             # -4: NONPHYSICAL, reported with the count
+            self._chk(rc)
+        return rc, c.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().rlbm3_destroy(self.h)
+            self.h = None
 
     def __del__(self):
         try:

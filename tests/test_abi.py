@@ -210,3 +210,31 @@ def test_builtin_massive_tables_are_in_orbit_order_with_exactly_symmetric_H(rl, 
         assert all(H[i0][k] == 0.0 for k, (_, a, b) in enumerate(basis) if a % 2 or b % 2)
         i0 += 1
     assert i0 == Q
+
+
+def test_d3_tables_agree_with_oracle(rl):
+    """The (3+1)-d massless tables: the same stencil, momenta and weights as
+    the oracle's reading of App. H, and an equilibrium matrix that reproduces
+    the oracle's f^eq at random states."""
+    from oracle import d3
+    d = rl.plan3()
+    q = d3.massless_quadrature_3d(2)
+    assert d["Q"] == q.Q == 78
+    key = lambda n, p0: (tuple(int(v) for v in n), round(float(p0), 12))
+    ko = {key(n, p[0]): i for i, (n, p) in enumerate(zip(q.n, q.p))}
+    idx = np.array([ko[key(n, p[0])] for n, p in zip(d["n"], d["p"])])
+    assert sorted(idx.tolist()) == list(range(78))
+    assert np.abs(d["p"] - q.p[idx]).max() < 1e-15 and np.array_equal(d["w"], q.w[idx])
+    E = d3.Expansion3(q)
+    rng = np.random.default_rng(2)
+    for _ in range(5):
+        n, T = rng.uniform(0.5, 1.5), rng.uniform(0.7, 1.4)
+        u = rng.uniform(-0.3, 0.3, 3)
+        g = 1 / np.sqrt(1 - u @ u)
+        U = np.concatenate([[g], g * u])
+        M = np.array([n / (2 * T), n * U[0], n * U[1], n * U[2], n * U[3],
+                      4 * n * T * U[0] * U[1], 4 * n * T * U[0] * U[2], 4 * n * T * U[0] * U[3],
+                      4 * n * T * U[1] ** 2 + n * T, 4 * n * T * U[1] * U[2], 4 * n * T * U[1] * U[3],
+                      4 * n * T * U[2] ** 2 + n * T, 4 * n * T * U[2] * U[3], 4 * n * T * U[3] ** 2 + n * T])
+        fo = E.feq(np.array(n), U, np.array(T))
+        assert np.abs(d["H"] @ M - fo[idx]).max() < 1e-13 * np.abs(fo).max()
