@@ -210,7 +210,7 @@ def main():
     ap.add_argument("--workload", default="tg512", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint measurements")
-    ap.add_argument("--only", default=None, choices=["batched", "adjoint", "paper", "kh"],
+    ap.add_argument("--only", default=None, choices=["batched", "adjoint", "paper", "kh", "d3"],
                     help="run only this extra measurement and print its JSON object")
     ap.add_argument("--_oracle_worker", default=None)
     args = ap.parse_args()
@@ -258,6 +258,8 @@ def main():
             res = {"massive_order3_tg512": bench_massive_order3(torch, rlbm, inputs, stream)}
         elif args.only == "kh":
             res = {"kelvin_helmholtz_2048": bench_kh(torch, rlbm, inputs, stream)}
+        elif args.only == "d3":
+            res = {"d3_taylor_green_192": bench_d3(torch, rlbm, inputs, stream)}
         else:
             res = {"adjoint": bench_adjoint(torch, rlbm, inputs, stream)}
         if rank == 0:
@@ -361,6 +363,7 @@ def main():
         extras["adjoint"] = bench_adjoint(torch, rlbm, inputs, stream)
         extras["massive_order3_tg512"] = bench_massive_order3(torch, rlbm, inputs, stream)
         extras["kelvin_helmholtz_2048"] = bench_kh(torch, rlbm, inputs, stream)
+        extras["d3_taylor_green_192"] = bench_d3(torch, rlbm, inputs, stream)
         if wl["workload"] == "tg512_bilinear_fp32":
             extras["viscosity"] = bench_tg_viscosity(rlbm, inputs)
 
@@ -582,6 +585,34 @@ def bench_kh(torch, rlbm, inputs, stream, L=2048, steps=20, warmup=5):
            "mlups": round(L * L / (ms * 1e-3) / 1e6, 1), "algorithmic_gbs": round(gbs, 1),
            "frac_of_hbm": round(gbs / peak, 4), "full_run_s_estimate": round(10000 * ms / 1e3, 2),
            "nonphysical": st[1]}
+    lat.close()
+    return out
+
+
+def bench_d3(torch, rlbm, inputs, stream, L=192, steps=10, warmup=3):
+    """The (3+1)-d massless step (order 2, Q = 78, FP64) on the Taylor-Green
+    flow uniform along z, 192^3 cells (the paper's 3-d performance figure is
+    for 192^3, zeta = 5, 143 vectors, its collide kernel alone on a P100:
+    14 MLUPS; context only).  Each buffer holds 8.3 GB, far more than L2."""
+    fields = [__import__("numpy").ascontiguousarray(a) for a in inputs.taylor_green3(L, L, u0=0.2)]
+    lat = rlbm.Lattice3(L, L, L, tau=0.8, cuda_stream=stream.cuda_stream)
+    lat.init(*fields)
+    lat.step(warmup)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for a, b in ev:
+        a.record(stream)
+        lat.step(1)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    rc, bad = lat.sync_status()
+    peak, _ = _peaks()
+    gbs = 2 * lat.Q * 8 * L ** 3 / (ms * 1e-3) / 1e9
+    out = {"workload": f"tg{L}^3_massless_order2_fp64", "Q": lat.Q, "ms_per_step": round(ms, 3),
+           "mlups": round(L ** 3 / (ms * 1e-3) / 1e6, 1), "algorithmic_gbs": round(gbs, 1),
+           "frac_of_hbm": round(gbs / peak, 4), "bound": "fp64 pipe", "paper_3d_collide_only_p100_mlups": 14.0,
+           "nonphysical": bad}
     lat.close()
     return out
 
