@@ -75,3 +75,33 @@ def lattice_feq(expansion):
         U = np.array([g, g * ux, g * uy])
         return expansion.feq(np.array(float(n)), U, np.array(float(T)))
     return feq
+
+
+def first_order_3d(p, feq):
+    """``first_order`` for massless particles in d = 3: eta / (P tau) and
+    mu / (P tau) (the latter zero: T^mu_mu = 0 on the light cone).
+
+    p:   (Q, 4) momenta (p0, px, py, pz);
+    feq: callable (n, ux, uy, uz, T) -> (Q,) equilibrium populations.
+    Shear flow d_y U^x = 1 at rest, n = T = 1 (d_t = 0):
+    f^(1) = -tau (p^y / p0) d f_eq / d U^x, eta = -sum_i p^x p^y f^(1)_i;
+    uniform expansion theta = d_x U^x = 1: d_t n = -n, d_t T = -T / c_v with
+    c_v = 3 (eps = 3 n T), mu = (1/3) sum_i (p.p) f^(1)_i."""
+    p = np.asarray(p, dtype=np.float64)
+    p0, px, py, pz = p[:, 0], p[:, 1], p[:, 2], p[:, 3]
+    f_n = _ddx(lambda h: feq(1.0 + h, 0.0, 0.0, 0.0, 1.0))
+    f_T = _ddx(lambda h: feq(1.0, 0.0, 0.0, 0.0, 1.0 + h))
+    f_ux = _ddx(lambda h: feq(1.0, h, 0.0, 0.0, 1.0))
+    shear = -(py / p0) * f_ux
+    bulk = -(1.0 / p0) * (p0 * (-f_n - f_T / 3.0) + px * f_ux)
+    msq = p0 * p0 - px * px - py * py - pz * pz
+    return dict(eta=-float(np.sum(px * py * shear)), mu=float(np.sum(msq * bulk)) / 3.0)
+
+
+def lattice_feq_3d(expansion):
+    """The equilibrium of an oracle ``d3.Expansion3`` as ``first_order_3d`` takes it."""
+    def feq(n, ux, uy, uz, T):
+        g = 1.0 / np.sqrt(1.0 - ux * ux - uy * uy - uz * uz)
+        U = np.array([g, g * ux, g * uy, g * uz])
+        return expansion.feq(np.array(float(n)), U, np.array(float(T)))
+    return feq

@@ -92,3 +92,35 @@ def test_taylor_green_run_conserves_N0_and_T0a(rl):
         assert abs(t1[a] - t0[a]) <= tol * t0[1]
     assert np.abs(lat.moments()["ux"]).max() < 0.9 * u0
     lat.close()
+
+
+@pytest.mark.parametrize("tau", [0.8, 1.2])
+def test_shear_wave_decays_at_the_lattice_viscosity(rl, tau):
+    """u_y = A sin(2 pi x / L) on 192 x 3 x 3 cells (dx = 1/3: a population
+    moves 3 cells per step at c) decays at eta k^2 / (eps + P), eps + P = 4 n T,
+    with eta = (the order-2 table's first-order coefficient, 0.937, against
+    the UR 4/5 of Eq. ce-ur-limit) P (tau - 1/2)."""
+    from oracle import transport as TR
+    q = d3.massless_quadrature_3d(2)
+    coef = TR.first_order_3d(q.p, TR.lattice_feq_3d(d3.Expansion3(q)))["eta"]
+    L = 192
+    x = np.arange(L)
+    s = np.sin(2 * np.pi * x / L)
+    one = np.ones((3, 3, L))
+    z = np.zeros((3, 3, L))
+    lat = rl.Lattice3(L, 3, 3, tau=tau)
+    lat.init(one, z, np.ascontiguousarray(1e-4 * s * one), z.copy(), one.copy())
+    k = 2 * np.pi / (L / 3.0)
+    pred = coef * (tau - 0.5) * k * k / 4.0
+    ts, a = [], []
+    every = max(1, int(0.02 / pred))
+    for t in range(every, int(1.0 / pred), every):
+        lat.step(every)
+        uy = lat.moments()["uy"].mean(axis=(0, 1))
+        ts.append(t)
+        a.append(np.sum(uy * s) / np.sum(s * s))
+    assert lat.sync_status()[0] == 0
+    lat.close()
+    sl = slice(len(ts) // 5, None)
+    rate = -np.polyfit(np.array(ts)[sl], np.log(np.array(a)[sl]), 1)[0]
+    assert abs(rate / pred - 1) < 0.02, (rate, pred)

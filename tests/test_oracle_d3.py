@@ -128,3 +128,41 @@ def test_streaming_permutes_and_a_periodic_run_conserves(quad):
     assert abs((quad.p[:, 0] @ sim.fs.reshape(quad.Q, -1)).sum() - N0) < 1e-12 * N0
     for a in range(4):
         assert abs(((quad.p[:, 0] * quad.p[:, a]) @ sim.fs.reshape(quad.Q, -1)).sum() - T0[a].sum()) < 1e-12 * T0[0].sum()
+
+
+def test_first_order_3d_of_the_exact_distribution_is_the_ur_limit():
+    """``transport.first_order_3d`` fed the exact massless MJ distribution on
+    a fine rule (Gauss-Laguerre in p0 for the weight p0 e^{-p0}, Gauss-Legendre
+    in cos(theta), trapezoid in phi) gives eta / (P tau) = (d+1)/(d+2) = 4/5
+    (Eq. ce-ur-limit, d = 3) and mu = 0."""
+    from oracle import transport as TR
+    r, wr = special.roots_genlaguerre(40, 1)
+    ct, wt = np.polynomial.legendre.leggauss(24)
+    nph = 48
+    ph = 2 * np.pi * np.arange(nph) / nph
+    R, C, PH = np.meshgrid(r, ct, ph, indexing="ij")
+    S = np.sqrt(1 - C ** 2)
+    p = np.stack([R, R * S * np.cos(PH), R * S * np.sin(PH), R * C], axis=-1).reshape(-1, 4)
+    # int d^3p/p0 g = int p0 dp0 dOmega g; Gauss-Laguerre(alpha = 1) carries p0 e^{-p0}
+    W = (wr[:, None, None] * np.exp(r)[:, None, None] * wt[None, :, None] * np.full((1, 1, nph), 2 * np.pi / nph)).reshape(-1)
+
+    def feq(n, ux, uy, uz, T):
+        g = 1 / np.sqrt(1 - ux * ux - uy * uy - uz * uz)
+        pu = g * (p[:, 0] - p[:, 1] * ux - p[:, 2] * uy - p[:, 3] * uz)
+        return W * n / (8 * np.pi * T ** 3) * np.exp(-pu / T)
+
+    assert abs(np.sum(feq(1.0, 0, 0, 0, 1.0) * p[:, 0]) - 1.0) < 1e-12
+    c = TR.first_order_3d(p, feq)
+    assert abs(c["eta"] - 0.8) < 1e-9
+    assert abs(c["mu"]) < 1e-10
+
+
+def test_first_order_3d_on_the_lattice():
+    """On the order-2 (3+1)-d table the shear coefficient departs from 4/5
+    (the quadrature does not integrate the 1/p0-weighted correction exactly)
+    and mu stays zero (massless)."""
+    from oracle import transport as TR
+    q = d3.massless_quadrature_3d(2)
+    c = TR.first_order_3d(q.p, TR.lattice_feq_3d(d3.Expansion3(q)))
+    assert abs(c["mu"]) < 1e-10
+    assert 0.5 < c["eta"] < 1.5
