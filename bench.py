@@ -212,6 +212,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint measurements")
     ap.add_argument("--only", default=None, choices=["batched", "adjoint", "paper", "kh", "d3"],
                     help="run only this extra measurement and print its JSON object")
+    ap.add_argument("--side", type=int, default=None,
+                    help="grid side for --only kh / d3 (default 2048 / 192); smaller sides serve profiling")
     ap.add_argument("--_oracle_worker", default=None)
     args = ap.parse_args()
     if args._oracle_worker is not None:
@@ -257,9 +259,9 @@ def main():
         elif args.only == "paper":
             res = {"massive_order3_tg512": bench_massive_order3(torch, rlbm, inputs, stream)}
         elif args.only == "kh":
-            res = {"kelvin_helmholtz_2048": bench_kh(torch, rlbm, inputs, stream)}
+            res = {"kelvin_helmholtz": bench_kh(torch, rlbm, inputs, stream, L=args.side or 2048)}
         elif args.only == "d3":
-            res = {"d3_taylor_green_192": bench_d3(torch, rlbm, inputs, stream)}
+            res = {"d3_taylor_green": bench_d3(torch, rlbm, inputs, stream, L=args.side or 192)}
         else:
             res = {"adjoint": bench_adjoint(torch, rlbm, inputs, stream)}
         if rank == 0:
