@@ -617,6 +617,30 @@ def test_first_order_shear_coefficient_explains_the_lattice_viscosities():
     assert abs(got[3] - 0.7516) < 2e-4
 
 
+def test_order2_shear_viscosity_is_anisotropic_and_averages_to_ur():
+    """The first-order shear coefficient of the massless tables along the
+    lattice axes and along the diagonals (stencil rotated by 45 degrees): at
+    N = 2 they are 0.980 and 0.520, whose mean is the UR 3/4 of Eq.
+    ce-ur-limit (a degree-4 average over the two directions); at N = 3 both
+    are within 0.3 % of 3/4.  The Taylor-Green vortex, whose wavevectors lie
+    along the diagonals, therefore decays at 0.52 (tau - 1/2) P at N = 2."""
+    from oracle import transport as TR
+
+    def eta(order, ang):
+        q = L.massless_quadrature(order)
+        c, s_ = math.cos(ang), math.sin(ang)
+        p = q.p.copy()
+        p[:, 1], p[:, 2] = c * q.p[:, 1] - s_ * q.p[:, 2], s_ * q.p[:, 1] + c * q.p[:, 2]
+        qr = L.Quadrature(q.n, p, q.w, q.m, q.order, q.v0)
+        return TR.first_order(qr.p, TR.lattice_feq(L.Expansion(qr)), 0.0)["eta"]
+
+    a2, d2 = eta(2, 0.0), eta(2, math.pi / 4)
+    assert abs(a2 - 0.9802) < 1e-4 and abs(d2 - 0.5198) < 1e-4
+    assert abs(0.5 * (a2 + d2) - 0.75) < 1e-12
+    a3, d3_ = eta(3, 0.0), eta(3, math.pi / 4)
+    assert abs(a3 / 0.75 - 1) < 3e-3 and abs(d3_ / 0.75 - 1) < 3e-3
+
+
 def _shear_wave_eta(order, Lx, tau, amp=0.01):
     q = L.massless_quadrature(order)
     e = L.Expansion(q)
