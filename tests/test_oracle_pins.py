@@ -636,7 +636,7 @@ def test_order2_shear_viscosity_is_anisotropic_and_averages_to_ur():
 
     a2, d2 = eta(2, 0.0), eta(2, math.pi / 4)
     assert abs(a2 - 0.9802) < 1e-4 and abs(d2 - 0.5198) < 1e-4
-    assert abs(0.5 * (a2 + d2) - 0.75) < 1e-12
+    assert abs(0.5 * (a2 + d2) - 0.75) < 1e-10          # the derivatives are 4th-order differences
     a3, d3_ = eta(3, 0.0), eta(3, math.pi / 4)
     assert abs(a3 / 0.75 - 1) < 3e-3 and abs(d3_ / 0.75 - 1) < 3e-3
 
