@@ -335,8 +335,8 @@ const char* rlbm_strerror(int code);
  * d = 3).  Stencil and weights: App. H, "(3+1) dimensions", order 2, read
  * with the group (+-2, +-2, +-1) (the printed (+-2, +-1, +-1) does not have
  * the common length 3 of a massless stencil) and the weights shell by shell
- * (per shell the (2, 2, 1) group, then (3, 0, 0)): Q = 78.  FP64 storage and
- * arithmetic, on-lattice streaming, periodic in x, y and z, constant tau.
+ * (per shell the (2, 2, 1) group, then (3, 0, 0)): Q = 78.  On-lattice
+ * streaming, periodic in x, y and z, constant tau.
  * EOS eps = 3 n T.  Fields are row-major [z][y][x] arrays of nx*ny*nz doubles.
  * ------------------------------------------------------------------------ */
 typedef struct rlbm3_handle rlbm3_handle;
@@ -348,9 +348,13 @@ typedef struct rlbm3_handle rlbm3_handle;
 int rlbm3_plan(int* Q, int* nvec, double* p, double* w, double* H);
 
 /* Tables on the host (double-double), two population buffers on the current
- * device; stream: cudaStream_t all work is issued on.  Each side at least 3
- * cells (the stencil length) and nx*ny*nz <= 2^28.  Synchronous. */
-int rlbm3_create(int nx, int ny, int nz, double tau, void* stream, rlbm3_handle** out);
+ * device; stream: cudaStream_t all work is issued on.  precision: RLBM_FP64
+ * (f stored and collided in FP64) or RLBM_FP32_STORE (g = f - f_ref stored
+ * and collided in FP32, f_ref the equilibrium at n = T = 1 at rest; the
+ * Landau root is corrected, and n, its difference from 1, eps and T are
+ * evaluated, in FP64).  Each side at least 3 cells (the stencil length) and
+ * nx*ny*nz <= 2^28.  Synchronous. */
+int rlbm3_create(int nx, int ny, int nz, double tau, int precision, void* stream, rlbm3_handle** out);
 void rlbm3_destroy(rlbm3_handle* h);
 
 /* Q, stencil vectors nvec (3*Q ints, nullable), momenta p (4*Q: p0, px, py,
@@ -372,7 +376,8 @@ int rlbm3_step(rlbm3_handle* h, int nsteps);
  * (synchronous) or device (asynchronous). */
 int rlbm3_moments(rlbm3_handle* h, double* out, int on_device);
 
-/* Post-collision populations f*(t), host array [Q][nz][ny][nx].  Synchronous. */
+/* Post-collision populations f*(t) (g + f_ref for FP32 storage), host array
+ * [Q][nz][ny][nx] of doubles.  Synchronous. */
 int rlbm3_get_populations(rlbm3_handle* h, double* f);
 
 /* Synchronise; RLBM_ERR_NONPHYSICAL if cell updates were left unrelaxed since

@@ -15,7 +15,8 @@ struct rlbm3_handle {
   Quadrature3 q;
   Scalars3 sc{};
   std::unique_ptr<Tables3> tb;
-  double* buf[2] = {nullptr, nullptr};
+  size_t elem = 8;                // bytes per stored population (8: f, 4: g = f - f_ref)
+  void* buf[2] = {nullptr, nullptr};
   int cur = 0;                    // buf[cur] holds f*(t)
   bool have_prev = false;         // buf[cur ^ 1] holds f*(t-1)
   double* fields = nullptr;       // [6][ncell]
@@ -24,7 +25,7 @@ struct rlbm3_handle {
   cudaStream_t stream = nullptr;
   std::string err = "no error";
   ~rlbm3_handle() {
-    for (double* b : buf) cudaFree(b);
+    for (void* b : buf) cudaFree(b);
     cudaFree(fields);
     cudaFree(staging);
     cudaFree(status);
@@ -66,9 +67,10 @@ int rlbm3_plan(int* Q, int* nvec, double* p, double* w, double* H) {
   return RLBM_OK;
 }
 
-int rlbm3_create(int nx, int ny, int nz, double tau, void* stream, rlbm3_handle** out) {
+int rlbm3_create(int nx, int ny, int nz, double tau, int precision, void* stream, rlbm3_handle** out) {
   if (!out) return fail3(nullptr, RLBM_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
+  if (precision != RLBM_FP64 && precision != RLBM_FP32_STORE) return fail3(nullptr, RLBM_ERR_INVALID_ARG, "precision");
   // every side at least the stencil length 3, so that each halo cell is the
   // image of exactly one interior cell
   if (nx < 3 || ny < 3 || nz < 3 || (long long)nx * ny * nz > (1LL << 28))
@@ -86,6 +88,9 @@ int rlbm3_create(int nx, int ny, int nz, double tau, void* stream, rlbm3_handle*
   s.slab = (long long)(ny + 2 * s.h) * s.pitch;
   s.plane = ((long long)(nz + 2 * s.h) * s.slab + 31) / 32 * 32;
   s.tau = tau;
+  h->elem = precision == RLBM_FP32_STORE ? 4 : 8;
+  s.n_ref = h->elem == 4 ? 1.0 : 0.0;
+  s.T_ref = h->elem == 4 ? 1.0 : 0.0;
   if ((long long)s.Q * s.plane >= (1LL << 31)) return fail3(nullptr, RLBM_ERR_UNSUPPORTED, "grid too large");
   h->tb.reset(new Tables3());
   std::memset(h->tb.get(), 0, sizeof(Tables3));
@@ -93,11 +98,23 @@ int rlbm3_create(int nx, int ny, int nz, double tau, void* stream, rlbm3_handle*
     for (int u = 0; u < 4; ++u) h->tb->c[i][u] = h->q.p[4 * i + u];
     for (int u = 0; u < 3; ++u) h->tb->v[i][u] = h->q.p[4 * i + 1 + u] / h->q.p[4 * i];
     for (int k = 0; k < 14; ++k) h->tb->H[i][k] = h->q.H[(size_t)i * 14 + k];
+    for (int u = 0; u < 4; ++u) h->tb->cf[i][u] = (float)h->tb->c[i][u];
+    for (int u = 0; u < 3; ++u) h->tb->vf[i][u] = (float)h->tb->v[i][u];
+    for (int k = 0; k < 14; ++k) h->tb->Hf[i][k] = (float)h->tb->H[i][k];
+    // reference populations f_ref,i = f^eq_i(n_ref, rest, T_ref): the MJ
+    // moments of the basis at rest are n/(2T), n, 0, 0, 0, 0, 0, 0, nT, 0, 0, nT, 0, nT
+    if (h->elem == 4) {
+      const double nr = s.n_ref, Tr = s.T_ref;
+      const double Mr[14] = {nr / (2.0 * Tr), nr, 0, 0, 0, 0, 0, 0, nr * Tr, 0, 0, nr * Tr, 0, nr * Tr};
+      double f = 0.0;
+      for (int k = 0; k < 14; ++k) f += h->q.H[(size_t)i * 14 + k] * Mr[k];
+      h->tb->fref[i] = f;
+    }
     const int* n = &h->q.n[3 * i];
     h->tb->off[i] = (int)((long long)i * s.plane - ((long long)n[2] * s.slab + (long long)n[1] * s.pitch + n[0]));
   }
   h->stream = (cudaStream_t)stream;
-  const size_t bytes = (size_t)s.Q * s.plane * sizeof(double);
+  const size_t bytes = (size_t)s.Q * s.plane * h->elem;
   const size_t nc = (size_t)nx * ny * nz;
   for (int b = 0; b < 2; ++b) {
     cudaError_t e = cudaMalloc(&h->buf[b], bytes);
@@ -135,12 +152,8 @@ int rlbm3_init(rlbm3_handle* h, const double* n, const double* ux, const double*
                const double* T, int on_device) {
   if (!h || !n || !ux || !uy || !uz || !T) return fail3(h, RLBM_ERR_INVALID_ARG, "null argument");
   const size_t nc = (size_t)h->sc.nx * h->sc.ny * h->sc.nz;
-  Init3Args a{};
-  a.f = h->buf[h->cur];
-  a.s = h->sc;
-  if (on_device) {
-    a.n = n; a.ux = ux; a.uy = uy; a.uz = uz; a.T = T;
-  } else {
+  const double* fp[5] = {n, ux, uy, uz, T};
+  if (!on_device) {
     if (!h->staging) {
       cudaError_t e = cudaMalloc(&h->staging, 5 * nc * sizeof(double));
       if (e != cudaSuccess) { cudaGetLastError(); return fail3(h, RLBM_ERR_OOM, "staging"); }
@@ -151,10 +164,16 @@ int rlbm3_init(rlbm3_handle* h, const double* n, const double* ux, const double*
                                       h->stream);
       if (e != cudaSuccess) return cuda_fail3(h, e, "copy of the initial fields");
     }
-    a.n = h->staging; a.ux = h->staging + nc; a.uy = h->staging + 2 * nc; a.uz = h->staging + 3 * nc;
-    a.T = h->staging + 4 * nc;
+    for (int k = 0; k < 5; ++k) fp[k] = h->staging + k * nc;
   }
-  cudaError_t e = launch_init3(*h->tb, a, h->stream);
+  cudaError_t e;
+  if (h->elem == 4) {
+    Init3Args<float> a{(float*)h->buf[h->cur], fp[0], fp[1], fp[2], fp[3], fp[4], h->sc};
+    e = launch_init3<float>(*h->tb, a, h->stream);
+  } else {
+    Init3Args<double> a{(double*)h->buf[h->cur], fp[0], fp[1], fp[2], fp[3], fp[4], h->sc};
+    e = launch_init3<double>(*h->tb, a, h->stream);
+  }
   if (e != cudaSuccess) return cuda_fail3(h, e, "init kernel");
   h->have_prev = false;
   if (!on_device) {
@@ -167,12 +186,14 @@ int rlbm3_init(rlbm3_handle* h, const double* n, const double* ux, const double*
 int rlbm3_step(rlbm3_handle* h, int nsteps) {
   if (!h || nsteps < 0) return fail3(h, RLBM_ERR_INVALID_ARG, "bad argument");
   for (int t = 0; t < nsteps; ++t) {
-    Step3Args a{};
-    a.fin = h->buf[h->cur];
-    a.fout = h->buf[h->cur ^ 1];
-    a.status = h->status;
-    a.s = h->sc;
-    cudaError_t e = launch_step3(*h->tb, a, h->stream);
+    cudaError_t e;
+    if (h->elem == 4) {
+      Step3Args<float> a{(const float*)h->buf[h->cur], (float*)h->buf[h->cur ^ 1], h->status, h->sc};
+      e = launch_step3<float>(*h->tb, a, h->stream);
+    } else {
+      Step3Args<double> a{(const double*)h->buf[h->cur], (double*)h->buf[h->cur ^ 1], h->status, h->sc};
+      e = launch_step3<double>(*h->tb, a, h->stream);
+    }
     if (e != cudaSuccess) return cuda_fail3(h, e, "step kernel");
     h->cur ^= 1;
     h->have_prev = true;
@@ -183,12 +204,17 @@ int rlbm3_step(rlbm3_handle* h, int nsteps) {
 int rlbm3_moments(rlbm3_handle* h, double* out, int on_device) {
   if (!h || !out) return fail3(h, RLBM_ERR_INVALID_ARG, "null argument");
   const size_t nc = (size_t)h->sc.nx * h->sc.ny * h->sc.nz;
-  Fields3Args a{};
-  a.fin = h->have_prev ? h->buf[h->cur ^ 1] : h->buf[h->cur];
-  a.pull = h->have_prev ? 1 : 0;
-  a.out = on_device ? out : h->fields;
-  a.s = h->sc;
-  cudaError_t e = launch_fields3(*h->tb, a, h->stream);
+  const void* fin = h->have_prev ? h->buf[h->cur ^ 1] : h->buf[h->cur];
+  double* dst = on_device ? out : h->fields;
+  const int pull = h->have_prev ? 1 : 0;
+  cudaError_t e;
+  if (h->elem == 4) {
+    Fields3Args<float> a{(const float*)fin, pull, dst, h->sc};
+    e = launch_fields3<float>(*h->tb, a, h->stream);
+  } else {
+    Fields3Args<double> a{(const double*)fin, pull, dst, h->sc};
+    e = launch_fields3<double>(*h->tb, a, h->stream);
+  }
   if (e != cudaSuccess) return cuda_fail3(h, e, "fields kernel");
   if (!on_device) {
     e = cudaMemcpyAsync(out, h->fields, 6 * nc * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
@@ -201,17 +227,20 @@ int rlbm3_moments(rlbm3_handle* h, double* out, int on_device) {
 int rlbm3_get_populations(rlbm3_handle* h, double* f) {
   if (!h || !f) return fail3(h, RLBM_ERR_INVALID_ARG, "null argument");
   const Scalars3& s = h->sc;
-  std::vector<double> host((size_t)s.Q * s.plane);
-  cudaError_t e = cudaMemcpyAsync(host.data(), h->buf[h->cur], host.size() * sizeof(double),
-                                  cudaMemcpyDeviceToHost, h->stream);
+  std::vector<unsigned char> host((size_t)s.Q * s.plane * h->elem);
+  cudaError_t e = cudaMemcpyAsync(host.data(), h->buf[h->cur], host.size(), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail3(h, e, "population copy");
+  const float* hf = (const float*)host.data();
+  const double* hd = (const double*)host.data();
   size_t o = 0;
   for (int i = 0; i < s.Q; ++i)
     for (int z = 0; z < s.nz; ++z)
       for (int y = 0; y < s.ny; ++y)
-        for (int x = 0; x < s.nx; ++x)
-          f[o++] = host[(size_t)i * s.plane + (size_t)(z + s.h) * s.slab + (size_t)(y + s.h) * s.pitch + x + s.px];
+        for (int x = 0; x < s.nx; ++x) {
+          const size_t j = (size_t)i * s.plane + (size_t)(z + s.h) * s.slab + (size_t)(y + s.h) * s.pitch + x + s.px;
+          f[o++] = h->elem == 4 ? (double)hf[j] + h->tb->fref[i] : hd[j];
+        }
   return RLBM_OK;
 }
 

@@ -10,6 +10,10 @@ struct Tables3 {
   double c[kMaxQ3][4];    // p0, px, py, pz of population i
   double v[kMaxQ3][3];    // microscopic velocity p / p0
   double H[kMaxQ3][14];   // equilibrium matrix: f^eq_i = sum_k H_ik M_k
+  double fref[kMaxQ3];    // FP32 storage: f_ref,i = f^eq_i(n_ref, rest, T_ref) (stored g = f - f_ref)
+  float cf[kMaxQ3][4];    // FP32 copies of c, v, H
+  float vf[kMaxQ3][3];
+  float Hf[kMaxQ3][14];
   int off[kMaxQ3];        // pull source of population i relative to the cell: i * plane - n_i . strides
 };
 
@@ -18,30 +22,38 @@ struct Scalars3 {
   int h, px, pitch;       // halo width, x offset of the interior, row pitch (elements)
   long long slab, plane;  // elements per z-slab and per population plane
   double tau;
+  double n_ref, T_ref;    // FP32 storage reference state (0, 0 for FP64 storage)
 };
 
+// S: storage type (double: f; float: g = f - f_ref)
+template <typename S>
 struct Step3Args {
-  const double* fin;
-  double* fout;
+  const S* fin;
+  S* fout;
   unsigned long long* status;
   Scalars3 s;
 };
 
+template <typename S>
 struct Init3Args {
-  double* f;
+  S* f;
   const double *n, *ux, *uy, *uz, *T;   // device fields, row-major [z][y][x]
   Scalars3 s;
 };
 
+template <typename S>
 struct Fields3Args {
-  const double* fin;      // f*(t-1), pulled (pull = 1), or f*(0) read in place (pull = 0)
+  const S* fin;           // f*(t-1), pulled (pull = 1), or f*(0) read in place (pull = 0)
   int pull;
   double* out;            // [6][nz][ny][nx]: n, ux, uy, uz, T, eps
   Scalars3 s;
 };
 
-cudaError_t launch_step3(const Tables3& tb, const Step3Args& a, cudaStream_t st);
-cudaError_t launch_init3(const Tables3& tb, const Init3Args& a, cudaStream_t st);
-cudaError_t launch_fields3(const Tables3& tb, const Fields3Args& a, cudaStream_t st);
+template <typename S>
+cudaError_t launch_step3(const Tables3& tb, const Step3Args<S>& a, cudaStream_t st);
+template <typename S>
+cudaError_t launch_init3(const Tables3& tb, const Init3Args<S>& a, cudaStream_t st);
+template <typename S>
+cudaError_t launch_fields3(const Tables3& tb, const Fields3Args<S>& a, cudaStream_t st);
 
 }  // namespace rlbm

@@ -56,8 +56,8 @@ SIGNATURES = {
     "rlbm_default_params": (None, [ctypes.POINTER(Params)]),
     "rlbm_create": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(_H)]),
     "rlbm_plan": (ctypes.c_int, [ctypes.POINTER(Params), _IP, _IP, _IP, _DP, _DP, _DP, _DP]),
-    "rlbm3_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _VP,
-                                    ctypes.POINTER(_H)]),
+    "rlbm3_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                    _VP, ctypes.POINTER(_H)]),
     "rlbm3_destroy": (None, [_H]),
     "rlbm3_plan": (ctypes.c_int, [_IP, _IP, _DP, _DP, _DP]),
     "rlbm3_stencil": (ctypes.c_int, [_H, _IP, _IP, _DP, _DP]),
@@ -506,15 +506,16 @@ def plan3():
 
 
 class Lattice3:
-    """A (3+1)-d massless periodic lattice (order 2, FP64) behind the rlbm3_*
-    calls; fields are numpy (nz, ny, nx) arrays or CUDA float64 tensors."""
+    """A (3+1)-d massless periodic lattice (order 2; FP64 or FP32 storage)
+    behind the rlbm3_* calls; fields are numpy (nz, ny, nx) arrays or CUDA
+    float64 tensors."""
 
-    def __init__(self, nx, ny, nz, tau=1.0, cuda_stream=None):
+    def __init__(self, nx, ny, nz, tau=1.0, precision="fp64", cuda_stream=None):
         if cuda_stream is None:
             cuda_stream = _current_stream()
         self.nx, self.ny, self.nz = nx, ny, nz
         h = _H()
-        rc = lib().rlbm3_create(nx, ny, nz, tau, cuda_stream, ctypes.byref(h))
+        rc = lib().rlbm3_create(nx, ny, nz, tau, PREC[precision], cuda_stream, ctypes.byref(h))
         if rc != RLBM_OK:
             raise RLBMError(rc, lib().rlbm3_last_error(None).decode())
         self.h = h

@@ -21,8 +21,8 @@ def rl():
     return rlbm
 
 
-def _pair(rl, nx, ny, nz, tau, fields):
-    lat = rl.Lattice3(nx, ny, nz, tau=tau)
+def _pair(rl, nx, ny, nz, tau, fields, precision="fp64"):
+    lat = rl.Lattice3(nx, ny, nz, tau=tau, precision=precision)
     q = d3.massless_quadrature_3d(2)
     key = lambda n, p0: (tuple(int(v) for v in n), round(float(p0), 12))
     ko = {key(n, p[0]): i for i, (n, p) in enumerate(zip(q.n, q.p))}
@@ -34,22 +34,24 @@ def _pair(rl, nx, ny, nz, tau, fields):
     return lat, sim, idx
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
 @pytest.mark.parametrize("nx,ny,nz,tau", [(13, 11, 9, 0.9), (37, 5, 3, 1.3), (3, 4, 33, 0.7)])
-def test_step_matches_oracle(rl, nx, ny, nz, tau):
+def test_step_matches_oracle(rl, nx, ny, nz, tau, precision, tol):
     """Ragged grids, one with a side of one tile and a tail, the others down
-    to the minimum side of 3 (every halo cell an image), 8 steps: FP64 bar."""
-    lat, sim, idx = _pair(rl, nx, ny, nz, tau, inputs.random_smooth3(nx, ny, nz, seed=nx, umax=0.2))
+    to the minimum side of 3 (every halo cell an image), 8 steps: the FP64
+    bar for FP64 storage, 1e-5 for FP32 storage (populations and fields)."""
+    lat, sim, idx = _pair(rl, nx, ny, nz, tau, inputs.random_smooth3(nx, ny, nz, seed=nx, umax=0.2), precision)
     for _ in range(2):
         lat.step(4)
         sim.step(4)
         f = lat.populations()
-        assert rel_linf(f, sim.fs[idx]) <= 1e-12
+        assert rel_linf(f, sim.fs[idx]) <= tol
     mo = lat.moments()
     fl = sim.fields
-    assert rel_linf(mo["n"], fl.n) <= 1e-12 and rel_linf(mo["T"], fl.T) <= 1e-12
+    assert rel_linf(mo["n"], fl.n) <= tol and rel_linf(mo["T"], fl.T) <= tol
     umax = max(np.abs(fl.u(k)).max() for k in (1, 2, 3))
     for k, name in ((1, "ux"), (2, "uy"), (3, "uz")):
-        assert np.abs(mo[name] - fl.u(k)).max() <= 1e-12 * umax
+        assert np.abs(mo[name] - fl.u(k)).max() <= tol * umax
     assert lat.sync_status()[0] == 0
     lat.close()
 
@@ -124,3 +126,29 @@ def test_shear_wave_decays_at_the_lattice_viscosity(rl, tau):
     sl = slice(len(ts) // 5, None)
     rate = -np.polyfit(np.array(ts)[sl], np.log(np.array(a)[sl]), 1)[0]
     assert abs(rate / pred - 1) < 0.02, (rate, pred)
+
+
+def test_fp32_taylor_green_run_conserves_within_the_rounding_bound(rl):
+    """FP32 storage (g = f - f_ref, f_ref = w_i / 2 at n = T = 1 at rest), the
+    Taylor-Green flow of the FP64 test for 500 steps: each step rounds the
+    stored g to FP32 and forms f^eq from FP32 tables, so a sum of c_i g_i
+    moves by at most about 2 * 2^-24 * sum |c_i g_i| per step (the flow only
+    decays, so the start bounds every step)."""
+    L, nz, steps = 64, 4, 500
+    lat = rl.Lattice3(L, L, nz, tau=0.8, precision="fp32")
+    lat.init(*[np.ascontiguousarray(a) for a in inputs.taylor_green3(L, nz, u0=0.2)])
+    p, w = lat.p, lat.w
+
+    def sums():
+        f = lat.populations().reshape(lat.Q, -1)
+        g = f - 0.5 * w[:, None]
+        c = [p[:, 0]] + [p[:, 0] * p[:, a] for a in range(4)]
+        return [float(np.sum(ci @ f)) for ci in c], [float(np.sum(np.abs(ci) @ np.abs(g))) for ci in c]
+
+    t0, g0 = sums()
+    lat.step(steps)
+    t1, _ = sums()
+    assert lat.sync_status()[0] == 0
+    for a in range(5):
+        assert abs(t1[a] - t0[a]) <= 2 * steps * 2.0 ** -24 * g0[a], (a, t1[a] - t0[a], g0[a])
+    lat.close()
