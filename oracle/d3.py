@@ -1,8 +1,8 @@
 """(3+1)-dimensional massless RLBM step, FP64 (oracle; test infrastructure only).
 
 Covers the d = 3 case of Sec. 5 and Sec. 6.2 for massless particles at
-expansion order N = 2 (lattice units c = k_B = T0 = 1):
-- the App. H "(3+1) dimensions" order-2 quadrature, p_ij = p0_j (1, n_i/|n_i|);
+expansion orders N = 2 and 3 (lattice units c = k_B = T0 = 1):
+- the App. H "(3+1) dimensions" quadratures, p_ij = p0_j (1, n_i/|n_i|);
 - the Gram-Schmidt basis of Sec. 5.2 under the massless weight
   omega = e^{-p0} (d^3p / p0 = p0 dp0 dOmega on the light cone);
 - the equilibrium of Eq. mj-discrete-feq with projections from the
@@ -39,6 +39,15 @@ MASSLESS_D3 = {
         weights_printed=[0.0245283950433191, 0.0, 0.0163006691342629, 0.0,
                          0.0003891858228425, 0.0017936666649682],
     ),
+    # order 3 (v0 = 1/sqrt(41)): the groups as printed, four shells (the nodes
+    # of L_4^(1)), the twelve printed weights read shell-major like order 2
+    3: dict(
+        groups=[(4, 4, 3), (5, 4, 0), (6, 2, 1)],
+        shells=[0.7432919279814314, 2.5716350076462784, 5.7311787516890996, 10.953894312683190],
+        weights_printed=[0.0, 0.0, 0.0093098040253911, 0.0085195569675087, 0.0,
+                         0.0056909667738262, 0.0013041770173120, 0.0, 0.0008932820065742,
+                         0.0000029126213348, 0.0000338363537565, 0.0000090390475856],
+    ),
 }
 
 
@@ -65,7 +74,8 @@ class Quadrature3:
 
 def massless_quadrature_3d(order=2):
     """Eq. ur-discrete-momentum-vectors in d = 3 with the App. H weights
-    (reading above); zero-weight (group, shell) pairs are dropped."""
+    (readings above; per shell the groups in table order); zero-weight
+    (group, shell) pairs are dropped."""
     tab = MASSLESS_D3[order]
     G, S, W = tab["groups"], tab["shells"], tab["weights_printed"]
     ns, ps, ws = [], [], []
@@ -137,8 +147,10 @@ def eval_monomials_3d(mons, p):
 
 
 def mj_moment_3d(mon, n, U, T):
-    """App. B moments of the massless MJ distribution in d = 3 up to rank 2:
-    <1> = n / (2T), <p^a> = n U^a, <p^a p^b> = n (4 T U^a U^b - T eta^ab)."""
+    """App. B moments of the massless MJ distribution in d = 3 up to rank 3:
+    <1> = n / (2T), <p^a> = n U^a, <p^a p^b> = n (4 T U^a U^b - T eta^ab),
+    <p^a p^b p^c> = n (24 T^2 U^a U^b U^c - 4 T^2 (eta^ab U^c + eta^ac U^b + eta^bc U^a))
+    (traceless, as massless moments must be)."""
     idx = [k for k in range(4) for _ in range(mon[k])]
     if len(idx) == 0:
         return n / (2.0 * T)
@@ -147,7 +159,11 @@ def mj_moment_3d(mon, n, U, T):
     if len(idx) == 2:
         a, b = idx
         return n * (4.0 * T * U[a] * U[b] - T * ETA4[a, b])
-    raise ValueError("moments above rank 2 are not needed at order 2")
+    if len(idx) == 3:
+        a, b, c = idx
+        return n * (24.0 * T * T * U[a] * U[b] * U[c]
+                    - 4.0 * T * T * (ETA4[a, b] * U[c] + ETA4[a, c] * U[b] + ETA4[b, c] * U[a]))
+    raise ValueError("moments above rank 3 are not needed up to order 3")
 
 
 class Expansion3:
@@ -155,6 +171,7 @@ class Expansion3:
 
     def __init__(self, quad: Quadrature3, order=2):
         self.quad = quad
+        self.order = order
         self.C, self.mons = gram_schmidt_basis_3d(order)
         self.J = self.C @ eval_monomials_3d(self.mons, quad.p)      # (K, Q)
 
