@@ -592,16 +592,17 @@ def bench_kh(torch, rlbm, inputs, stream, L=2048, steps=20, warmup=5):
 
 
 def bench_d3(torch, rlbm, inputs, stream, L=192, steps=10, warmup=3):
-    """The (3+1)-d massless step (order 2, Q = 78) in FP64 and with FP32
-    storage on the Taylor-Green flow uniform along z, 192^3 cells (the
-    paper's 3-d performance figure is for 192^3, zeta = 5, 143 vectors, its
-    collide kernel alone on a P100: 14 MLUPS; context only).  Each buffer
-    holds 4.1-8.3 GB, far more than L2."""
+    """The (3+1)-d massless step, order 2 (Q = 78) and order 3 (Q = 288), in
+    FP64 and with FP32 storage on the Taylor-Green flow uniform along z,
+    192^3 cells (the paper's 3-d performance figure is for 192^3, zeta = 5,
+    143 vectors, its collide kernel alone on a P100: 14 MLUPS; context only).
+    Each buffer holds 4.1-16.3 GB, far more than L2."""
     fields = [__import__("numpy").ascontiguousarray(a) for a in inputs.taylor_green3(L, L, u0=0.2)]
     peak, _ = _peaks()
-    out = {"workload": f"tg{L}^3_massless_order2", "paper_3d_collide_only_p100_mlups": 14.0}
-    for prec, elem in (("fp64", 8), ("fp32", 4)):
-        lat = rlbm.Lattice3(L, L, L, tau=0.8, precision=prec, cuda_stream=stream.cuda_stream)
+    out = {"workload": f"tg{L}^3_massless", "paper_3d_collide_only_p100_mlups": 14.0}
+    for order, prec, elem in ((2, "fp64", 8), (2, "fp32", 4), (3, "fp64", 8), (3, "fp32", 4)):
+        key = prec if order == 2 else f"order3_{prec}"
+        lat = rlbm.Lattice3(L, L, L, tau=0.8, precision=prec, cuda_stream=stream.cuda_stream, order=order)
         lat.init(*fields)
         lat.step(warmup)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -614,7 +615,7 @@ def bench_d3(torch, rlbm, inputs, stream, L=192, steps=10, warmup=3):
         ms = sum(a.elapsed_time(b) for a, b in ev) / steps
         rc, bad = lat.sync_status()
         gbs = 2 * lat.Q * elem * L ** 3 / (ms * 1e-3) / 1e9
-        out[prec] = {"Q": lat.Q, "ms_per_step": round(ms, 3), "mlups": round(L ** 3 / (ms * 1e-3) / 1e6, 1),
+        out[key] = {"Q": lat.Q, "ms_per_step": round(ms, 3), "mlups": round(L ** 3 / (ms * 1e-3) / 1e6, 1),
                      "algorithmic_gbs": round(gbs, 1), "frac_of_hbm": round(gbs / peak, 4), "nonphysical": bad}
         lat.close()
     return out

@@ -341,20 +341,27 @@ const char* rlbm_strerror(int code);
  * ------------------------------------------------------------------------ */
 typedef struct rlbm3_handle rlbm3_handle;
 
-/* Host-only: Q and the tables rlbm3_create builds -- stencil vectors nvec
- * (3*Q ints), momenta p (4*Q), weights w (Q), equilibrium matrix H (Q*14,
- * f^eq_i = sum_k H_ik M_k with M the MJ moments of 1 | p0 px py pz | p0px
- * p0py p0pz pxpx pxpy pxpz pypy pypz pzpz); arrays nullable, 80 rows. */
-int rlbm3_plan(int* Q, int* nvec, double* p, double* w, double* H);
+/* Host-only: Q, K and the tables rlbm3_create builds for expansion order
+ * `order` (2 or 3) -- stencil vectors nvec (3*Q ints), momenta p (4*Q),
+ * weights w (Q), equilibrium matrix H (Q*K, row-major, f^eq_i = sum_k H_ik
+ * M_k with M the MJ moments of the basis 1 | p0 px py pz | p0px p0py p0pz
+ * pxpx pxpy pxpz pypy pypz pzpz, K = 14, and at order 3 further p0 (xx xy xz
+ * yy yz zz) | xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz, K = 30); arrays
+ * nullable, room for 80 rows (order 2) or 288 rows (order 3).
+ * RLBM_ERR_INVALID_ARG for another order. */
+int rlbm3_plan(int order, int* Q, int* K, int* nvec, double* p, double* w, double* H);
 
 /* Tables on the host (double-double), two population buffers on the current
- * device; stream: cudaStream_t all work is issued on.  precision: RLBM_FP64
- * (f stored and collided in FP64) or RLBM_FP32_STORE (g = f - f_ref stored
- * and collided in FP32, f_ref the equilibrium at n = T = 1 at rest; the
- * Landau root is corrected, and n, its difference from 1, eps and T are
- * evaluated, in FP64).  Each side at least 3 cells (the stencil length) and
- * nx*ny*nz <= 2^28.  Synchronous. */
-int rlbm3_create(int nx, int ny, int nz, double tau, int precision, void* stream, rlbm3_handle** out);
+ * device; stream: cudaStream_t all work is issued on.  order: 2 (App. H
+ * order-2 stencil, Q = 78, halo 3) or 3 (App. H order-3 stencil, v0 =
+ * 1/sqrt(41), Q = 288, halo 6).  precision: RLBM_FP64 (f stored and collided
+ * in FP64) or RLBM_FP32_STORE (g = f - f_ref stored and collided in FP32,
+ * f_ref the equilibrium at n = T = 1 at rest; the Landau root is corrected,
+ * and n, its difference from 1, eps and T are evaluated, in FP64).  Each side
+ * at least the halo width (3, or 6 at order 3) and nx*ny*nz <= 2^28.
+ * Synchronous. */
+int rlbm3_create(int nx, int ny, int nz, double tau, int order, int precision, void* stream,
+                 rlbm3_handle** out);
 void rlbm3_destroy(rlbm3_handle* h);
 
 /* Q, stencil vectors nvec (3*Q ints, nullable), momenta p (4*Q: p0, px, py,

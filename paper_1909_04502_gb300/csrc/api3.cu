@@ -23,12 +23,26 @@ struct rlbm3_handle {
   double* staging = nullptr;      // 5 input fields on the device (init from host)
   unsigned long long* status = nullptr;
   cudaStream_t stream = nullptr;
+  std::vector<double> fref;       // reference populations (FP32 storage)
+  // order 3: tables in device memory
+  void* dH = nullptr;             // Q x 30, storage precision
+  void* dc = nullptr;             // Q x 4
+  void* dv = nullptr;             // Q x 3
+  double* dHd = nullptr;          // Q x 30 FP64 (init)
+  double* dcd = nullptr;          // Q x 4 FP64 (fields)
+  double* dfref = nullptr;        // Q
+  int* doff = nullptr;            // Q
   std::string err = "no error";
   ~rlbm3_handle() {
     for (void* b : buf) cudaFree(b);
     cudaFree(fields);
     cudaFree(staging);
     cudaFree(status);
+    for (void* d : {dH, dc, dv}) cudaFree(d);
+    cudaFree(dHd);
+    cudaFree(dcd);
+    cudaFree(dfref);
+    cudaFree(doff);
   }
 };
 
@@ -46,44 +60,67 @@ int cuda_fail3(rlbm3_handle* h, cudaError_t e, const char* what) {
   return fail3(h, RLBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// MJ moments of the basis at rest (n, T): <1> = n/(2T), <p0> = n,
+// <p^i p^i> = nT, <p0 p^i p^i> = 4 n T^2 (order 3), the others zero.
+std::vector<double> rest_moments(int K, double n, double T) {
+  std::vector<double> M(K, 0.0);
+  M[0] = n / (2.0 * T);
+  M[1] = n;
+  M[8] = M[11] = M[13] = n * T;
+  if (K == 30) M[14] = M[17] = M[19] = 4.0 * n * T * T;
+  return M;
+}
+
+template <typename T>
+int upload(void** dst, const std::vector<T>& v) {
+  if (cudaMalloc(dst, v.size() * sizeof(T)) != cudaSuccess) { cudaGetLastError(); return RLBM_ERR_OOM; }
+  if (cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) return RLBM_ERR_CUDA;
+  return RLBM_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
 const char* rlbm3_last_error(const rlbm3_handle* h) { return h ? h->err.c_str() : g_err3.c_str(); }
 
-int rlbm3_plan(int* Q, int* nvec, double* p, double* w, double* H) {
-  if (!Q) return fail3(nullptr, RLBM_ERR_INVALID_ARG, "null argument");
+int rlbm3_plan(int order, int* Q, int* K, int* nvec, double* p, double* w, double* H) {
+  if (!Q || !K) return fail3(nullptr, RLBM_ERR_INVALID_ARG, "null argument");
   Quadrature3 q;
   std::string err;
-  if (!massless3_tables(&q, &err)) return fail3(nullptr, RLBM_ERR_QUADRATURE, err);
+  if (!massless3_tables(order, &q, &err)) return fail3(nullptr, RLBM_ERR_INVALID_ARG, err);
   *Q = q.Q;
+  *K = q.K;
   for (int i = 0; i < q.Q; ++i) {
     if (nvec) for (int k = 0; k < 3; ++k) nvec[3 * i + k] = q.n[3 * i + k];
     if (p) for (int k = 0; k < 4; ++k) p[4 * i + k] = q.p[4 * i + k];
     if (w) w[i] = q.w[i];
-    if (H) for (int k = 0; k < 14; ++k) H[14 * i + k] = q.H[(size_t)i * 14 + k];
+    if (H) for (int k = 0; k < q.K; ++k) H[(size_t)q.K * i + k] = q.H[(size_t)i * q.K + k];
   }
   return RLBM_OK;
 }
 
-int rlbm3_create(int nx, int ny, int nz, double tau, int precision, void* stream, rlbm3_handle** out) {
+int rlbm3_create(int nx, int ny, int nz, double tau, int order, int precision, void* stream,
+                 rlbm3_handle** out) {
   if (!out) return fail3(nullptr, RLBM_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
   if (precision != RLBM_FP64 && precision != RLBM_FP32_STORE) return fail3(nullptr, RLBM_ERR_INVALID_ARG, "precision");
-  // every side at least the stencil length 3, so that each halo cell is the
-  // image of exactly one interior cell
-  if (nx < 3 || ny < 3 || nz < 3 || (long long)nx * ny * nz > (1LL << 28))
-    return fail3(nullptr, RLBM_ERR_INVALID_ARG, "grid size out of range (each side 3 ... )");
+  if (order != 2 && order != 3) return fail3(nullptr, RLBM_ERR_INVALID_ARG, "order must be 2 or 3");
+  // halo: the largest stencil component (3 at order 2, 6 at order 3); every
+  // side at least that long, so that each halo cell is the image of exactly
+  // one interior cell
+  const int halo = order == 2 ? 3 : 6;
+  if (nx < halo || ny < halo || nz < halo || (long long)nx * ny * nz > (1LL << 28))
+    return fail3(nullptr, RLBM_ERR_INVALID_ARG, "grid size out of range (each side at least the halo width)");
   if (!(tau > 0.5)) return fail3(nullptr, RLBM_ERR_INVALID_ARG, "tau must exceed 1/2");
   std::unique_ptr<rlbm3_handle> h(new rlbm3_handle());
   std::string err;
-  if (!massless3_tables(&h->q, &err)) return fail3(nullptr, RLBM_ERR_QUADRATURE, err);
+  if (!massless3_tables(order, &h->q, &err)) return fail3(nullptr, RLBM_ERR_QUADRATURE, err);
   Scalars3& s = h->sc;
   s.Q = h->q.Q;
   s.nx = nx; s.ny = ny; s.nz = nz;
-  s.h = 3;
-  s.px = 4;                                          // 32-byte aligned interior rows
+  s.h = halo;
+  s.px = order == 2 ? 4 : 8;                         // 32-byte aligned interior rows, >= h
   s.pitch = ((s.px + nx + s.h) + 3) / 4 * 4;
   s.slab = (long long)(ny + 2 * s.h) * s.pitch;
   s.plane = ((long long)(nz + 2 * s.h) * s.slab + 31) / 32 * 32;
@@ -91,27 +128,57 @@ int rlbm3_create(int nx, int ny, int nz, double tau, int precision, void* stream
   h->elem = precision == RLBM_FP32_STORE ? 4 : 8;
   s.n_ref = h->elem == 4 ? 1.0 : 0.0;
   s.T_ref = h->elem == 4 ? 1.0 : 0.0;
-  if ((long long)s.Q * s.plane >= (1LL << 31)) return fail3(nullptr, RLBM_ERR_UNSUPPORTED, "grid too large");
+  // order 2 keeps 32-bit pull offsets i * plane - shift; order 3 adds the
+  // plane offset in 64 bits and keeps only the shift
+  if (order == 2 && (long long)s.Q * s.plane >= (1LL << 31))
+    return fail3(nullptr, RLBM_ERR_UNSUPPORTED, "grid too large for the order-2 table");
+  const int K = h->q.K;
+  h->fref.assign(s.Q, 0.0);
+  if (h->elem == 4) {
+    const std::vector<double> Mr = rest_moments(K, s.n_ref, s.T_ref);
+    for (int i = 0; i < s.Q; ++i)
+      for (int k = 0; k < K; ++k) h->fref[i] += h->q.H[(size_t)i * K + k] * Mr[k];
+  }
+  std::vector<int> offs(s.Q);
+  for (int i = 0; i < s.Q; ++i) {
+    const int* n = &h->q.n[3 * i];
+    const long long shift = (long long)n[2] * s.slab + (long long)n[1] * s.pitch + n[0];
+    offs[i] = (int)(order == 2 ? (long long)i * s.plane - shift : -shift);
+  }
   h->tb.reset(new Tables3());
   std::memset(h->tb.get(), 0, sizeof(Tables3));
-  for (int i = 0; i < s.Q; ++i) {
+  if (order == 3) {
+    std::vector<double> c(4 * s.Q), v(3 * s.Q);
+    for (int i = 0; i < s.Q; ++i) {
+      for (int u = 0; u < 4; ++u) c[4 * i + u] = h->q.p[4 * i + u];
+      for (int u = 0; u < 3; ++u) v[3 * i + u] = h->q.p[4 * i + 1 + u] / h->q.p[4 * i];
+    }
+    int rc = RLBM_OK;
+    if (h->elem == 4) {
+      std::vector<float> Hf(h->q.H.begin(), h->q.H.end()), cf(c.begin(), c.end()), vf(v.begin(), v.end());
+      if (!rc) rc = upload(&h->dH, Hf);
+      if (!rc) rc = upload(&h->dc, cf);
+      if (!rc) rc = upload(&h->dv, vf);
+    } else {
+      if (!rc) rc = upload(&h->dH, h->q.H);
+      if (!rc) rc = upload(&h->dc, c);
+      if (!rc) rc = upload(&h->dv, v);
+    }
+    if (!rc) rc = upload((void**)&h->dHd, h->q.H);
+    if (!rc) rc = upload((void**)&h->dcd, c);
+    if (!rc) rc = upload((void**)&h->dfref, h->fref);
+    if (!rc) rc = upload((void**)&h->doff, offs);
+    if (rc) return fail3(nullptr, rc, "order-3 tables");
+  }
+  for (int i = 0; i < s.Q && order == 2; ++i) {
     for (int u = 0; u < 4; ++u) h->tb->c[i][u] = h->q.p[4 * i + u];
     for (int u = 0; u < 3; ++u) h->tb->v[i][u] = h->q.p[4 * i + 1 + u] / h->q.p[4 * i];
     for (int k = 0; k < 14; ++k) h->tb->H[i][k] = h->q.H[(size_t)i * 14 + k];
     for (int u = 0; u < 4; ++u) h->tb->cf[i][u] = (float)h->tb->c[i][u];
     for (int u = 0; u < 3; ++u) h->tb->vf[i][u] = (float)h->tb->v[i][u];
     for (int k = 0; k < 14; ++k) h->tb->Hf[i][k] = (float)h->tb->H[i][k];
-    // reference populations f_ref,i = f^eq_i(n_ref, rest, T_ref): the MJ
-    // moments of the basis at rest are n/(2T), n, 0, 0, 0, 0, 0, 0, nT, 0, 0, nT, 0, nT
-    if (h->elem == 4) {
-      const double nr = s.n_ref, Tr = s.T_ref;
-      const double Mr[14] = {nr / (2.0 * Tr), nr, 0, 0, 0, 0, 0, 0, nr * Tr, 0, 0, nr * Tr, 0, nr * Tr};
-      double f = 0.0;
-      for (int k = 0; k < 14; ++k) f += h->q.H[(size_t)i * 14 + k] * Mr[k];
-      h->tb->fref[i] = f;
-    }
-    const int* n = &h->q.n[3 * i];
-    h->tb->off[i] = (int)((long long)i * s.plane - ((long long)n[2] * s.slab + (long long)n[1] * s.pitch + n[0]));
+    h->tb->fref[i] = h->fref[i];
+    h->tb->off[i] = offs[i];
   }
   h->stream = (cudaStream_t)stream;
   const size_t bytes = (size_t)s.Q * s.plane * h->elem;
@@ -167,7 +234,15 @@ int rlbm3_init(rlbm3_handle* h, const double* n, const double* ux, const double*
     for (int k = 0; k < 5; ++k) fp[k] = h->staging + k * nc;
   }
   cudaError_t e;
-  if (h->elem == 4) {
+  if (h->q.order == 3) {
+    if (h->elem == 4) {
+      Init3qArgs<float> a{(float*)h->buf[h->cur], fp[0], fp[1], fp[2], fp[3], fp[4], h->sc, h->dHd, h->dfref};
+      e = launch_init3q<float>(a, h->stream);
+    } else {
+      Init3qArgs<double> a{(double*)h->buf[h->cur], fp[0], fp[1], fp[2], fp[3], fp[4], h->sc, h->dHd, h->dfref};
+      e = launch_init3q<double>(a, h->stream);
+    }
+  } else if (h->elem == 4) {
     Init3Args<float> a{(float*)h->buf[h->cur], fp[0], fp[1], fp[2], fp[3], fp[4], h->sc};
     e = launch_init3<float>(*h->tb, a, h->stream);
   } else {
@@ -187,7 +262,17 @@ int rlbm3_step(rlbm3_handle* h, int nsteps) {
   if (!h || nsteps < 0) return fail3(h, RLBM_ERR_INVALID_ARG, "bad argument");
   for (int t = 0; t < nsteps; ++t) {
     cudaError_t e;
-    if (h->elem == 4) {
+    if (h->q.order == 3) {
+      if (h->elem == 4) {
+        Step3qArgs<float> a{(const float*)h->buf[h->cur], (float*)h->buf[h->cur ^ 1], h->status, h->sc,
+                            (const float*)h->dH, (const float*)h->dc, (const float*)h->dv, h->doff};
+        e = launch_step3q<float>(a, h->stream);
+      } else {
+        Step3qArgs<double> a{(const double*)h->buf[h->cur], (double*)h->buf[h->cur ^ 1], h->status, h->sc,
+                             (const double*)h->dH, (const double*)h->dc, (const double*)h->dv, h->doff};
+        e = launch_step3q<double>(a, h->stream);
+      }
+    } else if (h->elem == 4) {
       Step3Args<float> a{(const float*)h->buf[h->cur], (float*)h->buf[h->cur ^ 1], h->status, h->sc};
       e = launch_step3<float>(*h->tb, a, h->stream);
     } else {
@@ -208,7 +293,15 @@ int rlbm3_moments(rlbm3_handle* h, double* out, int on_device) {
   double* dst = on_device ? out : h->fields;
   const int pull = h->have_prev ? 1 : 0;
   cudaError_t e;
-  if (h->elem == 4) {
+  if (h->q.order == 3) {
+    if (h->elem == 4) {
+      Fields3qArgs<float> a{(const float*)fin, pull, dst, h->sc, h->dcd, h->doff, h->dfref};
+      e = launch_fields3q<float>(a, h->stream);
+    } else {
+      Fields3qArgs<double> a{(const double*)fin, pull, dst, h->sc, h->dcd, h->doff, h->dfref};
+      e = launch_fields3q<double>(a, h->stream);
+    }
+  } else if (h->elem == 4) {
     Fields3Args<float> a{(const float*)fin, pull, dst, h->sc};
     e = launch_fields3<float>(*h->tb, a, h->stream);
   } else {
@@ -239,7 +332,7 @@ int rlbm3_get_populations(rlbm3_handle* h, double* f) {
       for (int y = 0; y < s.ny; ++y)
         for (int x = 0; x < s.nx; ++x) {
           const size_t j = (size_t)i * s.plane + (size_t)(z + s.h) * s.slab + (size_t)(y + s.h) * s.pitch + x + s.px;
-          f[o++] = h->elem == 4 ? (double)hf[j] + h->tb->fref[i] : hd[j];
+          f[o++] = h->elem == 4 ? (double)hf[j] + h->fref[i] : hd[j];
         }
   return RLBM_OK;
 }

@@ -49,6 +49,46 @@ struct Fields3Args {
   Scalars3 s;
 };
 
+// Order 3 (Q = 288, K = 30): tables in global memory (device arrays).
+template <typename S>
+struct Step3qArgs {
+  const S* fin;
+  S* fout;
+  unsigned long long* status;
+  Scalars3 s;
+  const S* H;      // Q x 30 in the storage precision
+  const S* c;      // Q x 4
+  const S* v;      // Q x 3
+  const int* off;  // Q pull shifts -n_i . strides (the plane offset i * plane is added in 64 bits)
+};
+
+template <typename S>
+struct Init3qArgs {
+  S* f;
+  const double *n, *ux, *uy, *uz, *T;
+  Scalars3 s;
+  const double* H;      // Q x 30
+  const double* fref;   // Q
+};
+
+template <typename S>
+struct Fields3qArgs {
+  const S* fin;
+  int pull;
+  double* out;
+  Scalars3 s;
+  const double* c;      // Q x 4
+  const int* off;       // Q pull shifts, as in Step3qArgs
+  const double* fref;   // Q
+};
+
+template <typename S>
+cudaError_t launch_step3q(const Step3qArgs<S>& a, cudaStream_t st);
+template <typename S>
+cudaError_t launch_init3q(const Init3qArgs<S>& a, cudaStream_t st);
+template <typename S>
+cudaError_t launch_fields3q(const Fields3qArgs<S>& a, cudaStream_t st);
+
 template <typename S>
 cudaError_t launch_step3(const Tables3& tb, const Step3Args<S>& a, cudaStream_t st);
 template <typename S>

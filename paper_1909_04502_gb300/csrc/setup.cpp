@@ -782,57 +782,80 @@ dd omega_moment3_dd(int c0, int a, int b, int c) {
 const int kBasis3[14][4] = {{0, 0, 0, 0}, {1, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, 1, 0}, {0, 0, 0, 1},
                              {1, 1, 0, 0}, {1, 0, 1, 0}, {1, 0, 0, 1}, {0, 2, 0, 0}, {0, 1, 1, 0},
                              {0, 1, 0, 1}, {0, 0, 2, 0}, {0, 0, 1, 1}, {0, 0, 0, 2}};
+const int kBasis3o3[30][4] = {
+    {0, 0, 0, 0}, {1, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, 1, 0}, {0, 0, 0, 1},
+    {1, 1, 0, 0}, {1, 0, 1, 0}, {1, 0, 0, 1}, {0, 2, 0, 0}, {0, 1, 1, 0},
+    {0, 1, 0, 1}, {0, 0, 2, 0}, {0, 0, 1, 1}, {0, 0, 0, 2},
+    {1, 2, 0, 0}, {1, 1, 1, 0}, {1, 1, 0, 1}, {1, 0, 2, 0}, {1, 0, 1, 1}, {1, 0, 0, 2},
+    {0, 3, 0, 0}, {0, 2, 1, 0}, {0, 2, 0, 1}, {0, 1, 2, 0}, {0, 1, 1, 1}, {0, 1, 0, 2},
+    {0, 0, 3, 0}, {0, 0, 2, 1}, {0, 0, 1, 2}, {0, 0, 0, 3}};
 
-bool massless3_tables(Quadrature3* q, std::string* err) {
-  // Stencil {(+-2, +-2, +-1)FS, (+-3, 0, 0)FS} (all of length 3: the printed
-  // first group, (+-2, +-1, +-1), is not of the common length a massless
-  // stencil needs), shell energies p0_j as printed, weights read shell by
-  // shell, per shell the (2, 2, 1) group then the (3, 0, 0) group (this
-  // reading integrates the weight's moments up to degree 4; the others do
-  // not).  p_ij = p0_j (1, n_i / 3).
-  static const double shells[3] = {0.9358222275240878, 3.3054072893322786, 7.7587704831436335};
-  static const double col[6] = {0.0245283950433191, 0.0, 0.0163006691342629, 0.0,
-                                0.0003891858228425, 0.0017936666649682};
-  static const int gens[2][3] = {{2, 2, 1}, {3, 0, 0}};
+bool massless3_tables(int order, Quadrature3* q, std::string* err) {
+  // Order 2: stencil {(+-2, +-2, +-1)FS, (+-3, 0, 0)FS} (all of length 3: the
+  // printed first group, (+-2, +-1, +-1), is not of the common length a
+  // massless stencil needs), weights read shell by shell, per shell the
+  // (2, 2, 1) group then the (3, 0, 0) group.  Order 3: stencil {(+-4, +-4,
+  // +-3)FS, (+-5, +-4, 0)FS, (+-6, +-2, +-1)FS} (length sqrt(41)), weights shell
+  // by shell, per shell the groups in that order.  These readings integrate
+  // the weight's moments up to degree 2N; the others do not.  Shell energies
+  // p0_j as printed; p_ij = p0_j (1, n_i / |n_i|).
+  static const double sh2[3] = {0.9358222275240878, 3.3054072893322786, 7.7587704831436335};
+  static const double col2[6] = {0.0245283950433191, 0.0, 0.0163006691342629, 0.0,
+                                 0.0003891858228425, 0.0017936666649682};
+  static const int gen2[2][3] = {{2, 2, 1}, {3, 0, 0}};
+  static const double sh3[4] = {0.7432919279814314, 2.5716350076462784, 5.7311787516890996,
+                                10.953894312683190};
+  static const double col3[12] = {0.0, 0.0, 0.0093098040253911, 0.0085195569675087, 0.0,
+                                  0.0056909667738262, 0.0013041770173120, 0.0, 0.0008932820065742,
+                                  0.0000029126213348, 0.0000338363537565, 0.0000090390475856};
+  static const int gen3[3][3] = {{4, 4, 3}, {5, 4, 0}, {6, 2, 1}};
+  if (order != 2 && order != 3) { *err = "3-d order must be 2 or 3"; return false; }
+  const int ns = order == 2 ? 3 : 4, ng = order == 2 ? 2 : 3;
+  const double* shells = order == 2 ? sh2 : sh3;
+  const double* col = order == 2 ? col2 : col3;
   *q = Quadrature3();
-  for (int j = 0; j < 3; ++j)
-    for (int g = 0; g < 2; ++g) {
-      const double wgt = col[2 * j + g];
+  q->order = order;
+  q->K = order == 2 ? 14 : 30;
+  for (int j = 0; j < ns; ++j)
+    for (int g = 0; g < ng; ++g) {
+      const double wgt = col[ng * j + g];
       if (wgt == 0.0) continue;
+      const int* gen = order == 2 ? gen2[g] : gen3[g];
       std::set<std::array<int, 3>> orbit;
       int perm[3] = {0, 1, 2};
       do {
         for (int sgn = 0; sgn < 8; ++sgn) {
           std::array<int, 3> v;
-          for (int k = 0; k < 3; ++k) v[k] = ((sgn >> k) & 1 ? -1 : 1) * gens[g][perm[k]];
+          for (int k = 0; k < 3; ++k) v[k] = ((sgn >> k) & 1 ? -1 : 1) * gen[perm[k]];
           orbit.insert(v);
         }
       } while (std::next_permutation(perm, perm + 3));
       for (const auto& v : orbit) {
+        const double len = std::sqrt((double)(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
         for (int k = 0; k < 3; ++k) q->n.push_back(v[k]);
         q->p.push_back(shells[j]);
-        for (int k = 0; k < 3; ++k) q->p.push_back(shells[j] * v[k] / 3.0);
+        for (int k = 0; k < 3; ++k) q->p.push_back(shells[j] * v[k] / len);
         q->w.push_back(wgt);
       }
     }
   q->Q = (int)q->w.size();
-  if (q->Q > kMaxQ3) { *err = "3-d stencil larger than the kernels accept"; return false; }
-  // H = W Phi G^{-1} in double-double, Phi and G in the basis kBasis3
-  const int K = 14;
+  if (q->Q > (order == 2 ? kMaxQ3 : kMaxQ3o3)) { *err = "3-d stencil larger than the kernels accept"; return false; }
+  // H = W Phi G^{-1} in double-double, Phi and G in the basis kBasis3 / kBasis3o3
+  const int K = q->K;
+  const int (*B)[4] = order == 2 ? kBasis3 : kBasis3o3;
   std::vector<dd> G(K * K), Gi;
   for (int k = 0; k < K; ++k)
     for (int l = 0; l < K; ++l)
-      G[k * K + l] = omega_moment3_dd(kBasis3[k][0] + kBasis3[l][0], kBasis3[k][1] + kBasis3[l][1],
-                                      kBasis3[k][2] + kBasis3[l][2], kBasis3[k][3] + kBasis3[l][3]);
+      G[k * K + l] = omega_moment3_dd(B[k][0] + B[l][0], B[k][1] + B[l][1], B[k][2] + B[l][2], B[k][3] + B[l][3]);
   if (!spd_inverse_dd(G, K, &Gi)) { *err = "3-d Gram matrix not positive definite"; return false; }
   q->H.assign((size_t)q->Q * K, 0.0);
+  std::vector<dd> phi(K);
   for (int i = 0; i < q->Q; ++i) {
     const double* pi = &q->p[4 * i];
-    dd phi[14];
     for (int k = 0; k < K; ++k) {
       dd v(1.0);
       for (int c = 0; c < 4; ++c)
-        for (int t = 0; t < kBasis3[k][c]; ++t) v = v * dd(pi[c]);
+        for (int t = 0; t < B[k][c]; ++t) v = v * dd(pi[c]);
       phi[k] = v;
     }
     for (int k = 0; k < K; ++k) {

@@ -75,18 +75,21 @@ void mj_moments(int order, double m, double n, const double U[3], double T, doub
 void mj_moments_shifted3(double m, double n, const double U[3], double T, double* M);
 
 
-// (3+1)-d massless order-2 stencil (App. H, read as in setup.cpp) with its
-// equilibrium matrix: f^eq_i = sum_k H_ik M_k, M the MJ moments of the
-// basis kBasis3 (1 | p0 px py pz | p0px p0py p0pz pxpx pxpy pxpz pypy pypz pzpz).
-constexpr int kMaxQ3 = 80;
+// (3+1)-d massless stencils of orders 2 and 3 (App. H, read as in setup.cpp)
+// with their equilibrium matrices: f^eq_i = sum_k H_ik M_k, M the MJ moments
+// of the basis kBasis3 (order 2) or kBasis3o3 (order 3).
+constexpr int kMaxQ3 = 80;       // order 2 (Q = 78)
+constexpr int kMaxQ3o3 = 288;    // order 3
 struct Quadrature3 {
-  int Q = 0;
+  int Q = 0, order = 2, K = 14;
   std::vector<int> n;       // 3 Q stencil vectors
   std::vector<double> p;    // 4 Q momenta (p0, px, py, pz)
   std::vector<double> w;    // Q weights
-  std::vector<double> H;    // Q x 14
+  std::vector<double> H;    // Q x K
 };
-extern const int kBasis3[14][4];
-bool massless3_tables(Quadrature3* q, std::string* err);
+extern const int kBasis3[14][4];     // order 2: 1 | p0 px py pz | p0px p0py p0pz pxpx pxpy pxpz pypy pypz pzpz
+extern const int kBasis3o3[30][4];   // order 3: the 14 above, then p0 x (pxpx pxpy pxpz pypy pypz pzpz) and
+                                     // pxpxpx pxpxpy pxpxpz pxpypy pxpypz pxpzpz pypypy pypypz pypzpz pzpzpz
+bool massless3_tables(int order, Quadrature3* q, std::string* err);
 
 }  // namespace rlbm

@@ -11,130 +11,11 @@
 // periodic images, so that every pull is the cell index plus a constant.
 #include <cuda_runtime.h>
 
-#include "d3.h"
+#include "d3_impl.cuh"
 
 namespace rlbm {
 
 namespace {
-
-__device__ __forceinline__ long long sidx3(const Scalars3& s, int x, int y, int z) {
-  return (long long)(z + s.h) * s.slab + (long long)(y + s.h) * s.pitch + (x + s.px);
-}
-
-// periodic images of coordinate c in [-h, n + h), other than c itself
-__device__ __forceinline__ int images1(int c, int n, int h, int (&out)[2]) {
-  int k = 0;
-  if (c + n < n + h) out[k++] = c + n;
-  if (c - n >= -h) out[k++] = c - n;
-  return k;
-}
-
-template <typename R>
-__device__ __forceinline__ R det3(R a, R b, R c, R d, R e, R f, R g, R hh, R i) {
-  return a * (e * i - f * hh) - b * (d * i - f * g) + c * (d * hh - e * g);
-}
-
-// det(B) by complementary 2 x 2 minors of rows (0, 1) and (2, 3), and
-// d det(B - l I)/dl = -(sum of the principal 3 x 3 minors)
-template <typename R>
-__device__ __forceinline__ R det4(const R (&B)[4][4]) {
-  const R s0 = B[0][0] * B[1][1] - B[1][0] * B[0][1], s1 = B[0][0] * B[1][2] - B[1][0] * B[0][2];
-  const R s2 = B[0][0] * B[1][3] - B[1][0] * B[0][3], s3 = B[0][1] * B[1][2] - B[1][1] * B[0][2];
-  const R s4 = B[0][1] * B[1][3] - B[1][1] * B[0][3], s5 = B[0][2] * B[1][3] - B[1][2] * B[0][3];
-  const R c5 = B[2][2] * B[3][3] - B[3][2] * B[2][3], c4 = B[2][1] * B[3][3] - B[3][1] * B[2][3];
-  const R c3 = B[2][1] * B[3][2] - B[3][1] * B[2][2], c2 = B[2][0] * B[3][3] - B[3][0] * B[2][3];
-  const R c1 = B[2][0] * B[3][2] - B[3][0] * B[2][2], c0 = B[2][0] * B[3][1] - B[3][0] * B[2][1];
-  return s0 * c5 - s1 * c4 + s2 * c3 + s3 * c2 - s4 * c1 + s5 * c0;
-}
-
-template <typename R>
-__device__ __forceinline__ R ddet4(const R (&B)[4][4]) {
-  const R m0 = det3(B[1][1], B[1][2], B[1][3], B[2][1], B[2][2], B[2][3], B[3][1], B[3][2], B[3][3]);
-  const R m1 = det3(B[0][0], B[0][2], B[0][3], B[2][0], B[2][2], B[2][3], B[3][0], B[3][2], B[3][3]);
-  const R m2 = det3(B[0][0], B[0][1], B[0][3], B[1][0], B[1][1], B[1][3], B[3][0], B[3][1], B[3][3]);
-  const R m3 = det3(B[0][0], B[0][1], B[0][2], B[1][0], B[1][1], B[1][2], B[2][0], B[2][1], B[2][2]);
-  return -(m0 + m1 + m2 + m3);
-}
-
-// right null vector of B from the first column of adj(B):
-// v_i = (-1)^i det(B without row 0 and column i)
-template <typename R>
-__device__ __forceinline__ void adj_col0(const R (&B)[4][4], R (&v)[4]) {
-  v[0] = det3(B[1][1], B[1][2], B[1][3], B[2][1], B[2][2], B[2][3], B[3][1], B[3][2], B[3][3]);
-  v[1] = -det3(B[1][0], B[1][2], B[1][3], B[2][0], B[2][2], B[2][3], B[3][0], B[3][2], B[3][3]);
-  v[2] = det3(B[1][0], B[1][1], B[1][3], B[2][0], B[2][1], B[2][3], B[3][0], B[3][1], B[3][3]);
-  v[3] = -det3(B[1][0], B[1][1], B[1][2], B[2][0], B[2][1], B[2][2], B[3][0], B[3][1], B[3][2]);
-}
-
-struct Macro3 {
-  double n, T, eps, U[4];
-  bool ok;
-};
-
-// Largest eigenvalue eps of A^a_b = T^ac eta_cb and its timelike eigenvector:
-// Newton on p(l) = det(A - l I) from the ideal-fluid root for P = eps / 3,
-// p'(l) = -(sum of the principal 3 x 3 minors of A - l I); U from the first
-// column of adj(A - l I) (a right null vector), normalised to U.U = 1, U^0 > 0.
-__device__ Macro3 landau3(const double (&N)[4], const double (&Tm)[4][4]) {
-  double A[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) A[a][b] = b == 0 ? Tm[a][b] : -Tm[a][b];
-  const double E = Tm[0][0], M2 = Tm[0][1] * Tm[0][1] + Tm[0][2] * Tm[0][2] + Tm[0][3] * Tm[0][3];
-  const double k = 1.0 / 3.0;
-  double lam = (-(1.0 - k) * E + sqrt(fmax((1.0 - k) * (1.0 - k) * E * E + 4.0 * k * (E * E - M2), 0.0))) /
-               (2.0 * k);
-  double B[4][4];
-  for (int it = 0; it < 8; ++it) {
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) B[a][b] = A[a][b] - (a == b ? lam : 0.0);
-    const double dp = ddet4(B);
-    if (!(dp != 0.0)) break;
-    const double step = det4(B) / dp;
-    lam -= step;
-    if (fabs(step) <= 1e-15 * fabs(lam)) break;
-  }
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) B[a][b] = A[a][b] - (a == b ? lam : 0.0);
-  double v[4];
-  adj_col0(B, v);
-  const double nu2 = v[0] * v[0] - v[1] * v[1] - v[2] * v[2] - v[3] * v[3];
-  Macro3 M;
-  const double inu = (v[0] > 0.0 ? 1.0 : -1.0) / sqrt(fabs(nu2));
-#pragma unroll
-  for (int a = 0; a < 4; ++a) M.U[a] = v[a] * inu;
-  M.n = M.U[0] * N[0] - M.U[1] * N[1] - M.U[2] * N[2] - M.U[3] * N[3];
-  M.eps = lam;
-  M.T = lam / (3.0 * M.n);
-  M.ok = nu2 > 0.0 && M.n > 0.0 && M.T > 0.0 && isfinite(M.T) && isfinite(M.U[0]);
-  return M;
-}
-
-// MJ moments of the basis 1 | p0 px py pz | p0px p0py p0pz pxpx pxpy pxpz pypy
-// pypz pzpz for massless particles in d = 3 (App. B): <1> = n/(2T),
-// <p^a> = n U^a, <p^a p^b> = n (4T U^a U^b - T eta^ab).
-__device__ __forceinline__ void mj_moments3(double n, double T, const double (&U)[4], double (&M)[14]) {
-  const double q = 4.0 * n * T;
-  M[0] = n / (2.0 * T);
-  M[1] = n * U[0];
-  M[2] = n * U[1];
-  M[3] = n * U[2];
-  M[4] = n * U[3];
-  M[5] = q * U[0] * U[1];
-  M[6] = q * U[0] * U[2];
-  M[7] = q * U[0] * U[3];
-  M[8] = q * U[1] * U[1] + n * T;
-  M[9] = q * U[1] * U[2];
-  M[10] = q * U[1] * U[3];
-  M[11] = q * U[2] * U[2] + n * T;
-  M[12] = q * U[2] * U[3];
-  M[13] = q * U[3] * U[3] + n * T;
-}
 
 template <int QT>
 __global__ void __launch_bounds__(128) k_step3(const __grid_constant__ Tables3 tb,
@@ -230,79 +111,12 @@ __global__ void __launch_bounds__(128) k_step3f(const __grid_constant__ Tables3 
       for (int v = u; v < 4; ++v) Tm[u][v] = fmaf(gu, tb.cf[i][v], Tm[u][v]);
     }
   }
-  const double nr = s.n_ref, Tr = s.T_ref, er = 3.0 * nr * Tr, Pr = nr * Tr;
-  // full moments (reference in FP64) and the mixed tensor A = T eta
-  double Nd[4] = {nr + (double)N[0], (double)N[1], (double)N[2], (double)N[3]};
-  double A[4][4];
-  float Af[4][4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      double t = (double)(u <= v ? Tm[u][v] : Tm[v][u]);
-      if (u == v) t += (u == 0 ? er : Pr);
-      A[u][v] = v == 0 ? t : -t;
-      Af[u][v] = (float)A[u][v];
-    }
-  // FP32 root from the ideal-fluid guess (P = eps / 3)
-  const float E = Af[0][0], M2 = Af[1][0] * Af[1][0] + Af[2][0] * Af[2][0] + Af[3][0] * Af[3][0];
-  const float k = 1.f / 3.f;
-  float lam = (-(1.f - k) * E + sqrtf(fmaxf((1.f - k) * (1.f - k) * E * E + 4.f * k * (E * E - M2), 0.f))) /
-              (2.f * k);
-  float Bf[4][4];
-  float dpf = -1.f;
-#pragma unroll
-  for (int it = 0; it < 3; ++it) {
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) Bf[u][v] = Af[u][v] - (u == v ? lam : 0.f);
-    dpf = ddet4(Bf);
-    lam -= det4(Bf) / dpf;
-  }
-  // FP64 residual at the FP32 root, one Newton correction
-  double B[4][4];
-  double ld = (double)lam;
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) B[u][v] = A[u][v] - (u == v ? ld : 0.0);
-  ld -= det4(B) / (double)dpf;
-#pragma unroll
-  for (int u = 0; u < 4; ++u) B[u][u] = A[u][u] - ld;
-  double vv[4];
-  adj_col0(B, vv);
-  const double nu2 = vv[0] * vv[0] - vv[1] * vv[1] - vv[2] * vv[2] - vv[3] * vv[3];
-  const double w = vv[0] * Nd[0] - vv[1] * Nd[1] - vv[2] * Nd[2] - vv[3] * Nd[3];
-  const double nu = sqrt(fabs(nu2));
-  const double sgn = vv[0] > 0.0 ? 1.0 : -1.0;
-  const double n = sgn * w / nu;
-  const double dn = (w * w - nr * nr * nu2) / (nu * (sgn * w + nr * nu));
-  const double deps = ld - er;
-  const double dT = (deps - 3.0 * Tr * dn) / (3.0 * n);
-  const double T = Tr + dT;
-  const bool ok = nu2 > 0.0 && n > 0.0 && T > 0.0 && isfinite(T) && isfinite(dn);
+  const Macro3f M = landau3f(N, Tm, s);
+  const bool ok = M.ok;
   if (!ok) atomicAdd(a.status, 1ULL);
-  const float inu = (float)(sgn / nu);
-  const float U0 = (float)vv[0] * inu, Ux = (float)vv[1] * inu, Uy = (float)vv[2] * inu, Uz = (float)vv[3] * inu;
-  const float fn = (float)n, fT = (float)T, fdn = (float)dn, fdT = (float)dT, fnr = (float)nr, fTr = (float)Tr;
+  const float U0 = M.U0, Ux = M.Ux, Uy = M.Uy, Uz = M.Uz;
   float dM[14];
-  const float U0m1 = (Ux * Ux + Uy * Uy + Uz * Uz) / (U0 + 1.f);
-  const float q = 4.f * fn * fT, iso = fdn * fT + fnr * fdT;
-  dM[0] = (fdn * fTr - fnr * fdT) / (2.f * fT * fTr);
-  dM[1] = fdn * U0 + fnr * U0m1;
-  dM[2] = fn * Ux;
-  dM[3] = fn * Uy;
-  dM[4] = fn * Uz;
-  dM[5] = q * U0 * Ux;
-  dM[6] = q * U0 * Uy;
-  dM[7] = q * U0 * Uz;
-  dM[8] = q * Ux * Ux + iso;
-  dM[9] = q * Ux * Uy;
-  dM[10] = q * Ux * Uz;
-  dM[11] = q * Uy * Uy + iso;
-  dM[12] = q * Uy * Uz;
-  dM[13] = q * Uz * Uz + iso;
+  mj_delta3<14>(M, (float)s.n_ref, (float)s.T_ref, dM);
   const float kt = ok ? (float)(1.0 / s.tau) : 0.f;
   int ix[2], iy[2], iz[2];
   const int nx2 = images1(x, s.nx, s.h, ix), ny2 = images1(y, s.ny, s.h, iy), nz2 = images1(z, s.nz, s.h, iz);

@@ -1,0 +1,219 @@
+// (3+1)-dimensional massless RLBM step at order 3 (App. H, v0 = 1/sqrt(41),
+// Q = 288, K = 30): the step of step3.cu with four threads per cell.  Each
+// thread pulls and relaxes 72 populations (i = lane + 4 j); the moment sums
+// are combined across the four threads with warp shuffles, and each of them
+// solves the Landau frame.  The stencil tables (p, v, the 288 x 30
+// equilibrium matrix and the pull shifts) live in global memory and are
+// staged once per block in shared memory; blocks are persistent and walk
+// rows of 32 cells.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "d3_impl.cuh"
+
+namespace rlbm {
+
+namespace {
+
+constexpr int kQo3 = 288, kKo3 = 30, kPer = kQo3 / 4;
+
+template <typename S>
+struct SharedTables3 {
+  S H[kQo3][kKo3];
+  S c[kQo3][4];
+  S v[kQo3][3];
+  int off[kQo3];
+};
+
+template <typename S>
+__global__ void __launch_bounds__(128) k_step3q(const __grid_constant__ Step3qArgs<S> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SharedTables3<S>& t = *reinterpret_cast<SharedTables3<S>*>(smem_raw);
+  const Scalars3& s = a.s;
+  for (int e = threadIdx.x; e < kQo3 * kKo3; e += blockDim.x) (&t.H[0][0])[e] = a.H[e];
+  for (int e = threadIdx.x; e < kQo3 * 4; e += blockDim.x) (&t.c[0][0])[e] = a.c[e];
+  for (int e = threadIdx.x; e < kQo3 * 3; e += blockDim.x) (&t.v[0][0])[e] = a.v[e];
+  for (int e = threadIdx.x; e < kQo3; e += blockDim.x) t.off[e] = a.off[e];
+  __syncthreads();
+  const int lane = threadIdx.x & 3, cell = threadIdx.x >> 2;
+  const int nxs = (s.nx + 31) / 32;
+  const long long nseg = (long long)nxs * s.ny * s.nz;
+  for (long long seg = blockIdx.x; seg < nseg; seg += gridDim.x) {
+    const int xs = (int)(seg % nxs);
+    const int y = (int)((seg / nxs) % s.ny), z = (int)(seg / ((long long)nxs * s.ny));
+    const int x = xs * 32 + cell;
+    const bool active = x < s.nx;
+    const long long si = sidx3(s, active ? x : s.nx - 1, y, z);   // inactive lanes read a valid cell
+    const S* __restrict__ base = a.fin + si;
+    // moments: partial sums over this thread's populations, then across the quad
+    S N[4] = {S(0), S(0), S(0), S(0)}, Tm[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int w = 0; w < 4; ++w) Tm[u][w] = S(0);
+#pragma unroll 4
+    for (int j = 0; j < kPer; ++j) {
+      const int i = lane + 4 * j;
+      const S g = __ldg(base + (long long)i * s.plane + t.off[i]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const S gu = g * t.c[i][u];
+        N[u] += gu;
+#pragma unroll
+        for (int w = u; w < 4; ++w) Tm[u][w] = fma(gu, t.c[i][w], Tm[u][w]);
+      }
+    }
+#pragma unroll
+    for (int m = 1; m <= 2; m <<= 1) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        N[u] += __shfl_xor_sync(0xffffffffu, N[u], m);
+#pragma unroll
+        for (int w = u; w < 4; ++w) Tm[u][w] += __shfl_xor_sync(0xffffffffu, Tm[u][w], m);
+      }
+    }
+    // Landau frame, equilibrium moments
+    S Mk[kKo3];
+    bool ok;
+    S U0, Ux, Uy, Uz, kt;
+    if constexpr (sizeof(S) == 8) {
+      double Nd[4], Td[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        Nd[u] = N[u];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) Td[u][w] = u <= w ? Tm[u][w] : Tm[w][u];
+      }
+      const Macro3 M = landau3(Nd, Td);
+      ok = M.ok;
+      double Md[kKo3];
+      mj_full3<kKo3>(M.n, M.T, M.U, Md);
+#pragma unroll
+      for (int k = 0; k < kKo3; ++k) Mk[k] = Md[k];
+      U0 = M.U[0]; Ux = M.U[1]; Uy = M.U[2]; Uz = M.U[3];
+    } else {
+      const Macro3f M = landau3f(N, Tm, s);
+      ok = M.ok;
+      mj_delta3<kKo3>(M, (float)s.n_ref, (float)s.T_ref, Mk);
+      U0 = M.U0; Ux = M.Ux; Uy = M.Uy; Uz = M.Uz;
+    }
+    if (active && lane == 0 && !ok) atomicAdd(a.status, 1ULL);
+    kt = ok ? (S)(1.0 / s.tau) : S(0);
+    long long img[26];
+    const int nimg = active ? cell_images(s, x, y, z, img) : 0;
+    // equilibrium, relaxation and store of this thread's populations
+#pragma unroll 2
+    for (int j = 0; j < kPer; ++j) {
+      const int i = lane + 4 * j;
+      const long long pl = (long long)i * s.plane;
+      const S g = __ldg(base + pl + t.off[i]);
+      S geq = S(0);
+#pragma unroll
+      for (int k = 0; k < kKo3; ++k) geq = fma(t.H[i][k], Mk[k], geq);
+      const S om = kt * (U0 - t.v[i][0] * Ux - t.v[i][1] * Uy - t.v[i][2] * Uz);
+      const S gn = fma(om, geq - g, g);
+      if (active) {
+        a.fout[pl + si] = gn;
+        for (int m = 0; m < nimg; ++m) a.fout[pl + img[m]] = gn;
+      }
+    }
+  }
+}
+
+// f*(0) = f^eq(n, U, T) (stored f, or f - f_ref for FP32), one thread per cell.
+template <typename S>
+__global__ void __launch_bounds__(128) k_init3q(const __grid_constant__ Init3qArgs<S> a) {
+  const Scalars3& s = a.s;
+  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y, z = blockIdx.z;
+  if (x >= s.nx || y >= s.ny || z >= s.nz) return;
+  const long long c = ((long long)z * s.ny + y) * s.nx + x;
+  const double ux = a.ux[c], uy = a.uy[c], uz = a.uz[c];
+  const double g = 1.0 / sqrt(1.0 - ux * ux - uy * uy - uz * uz);
+  const double U[4] = {g, g * ux, g * uy, g * uz};
+  double Mm[kKo3];
+  mj_full3<kKo3>(a.n[c], a.T[c], U, Mm);
+  long long img[26];
+  const int nimg = cell_images(s, x, y, z, img);
+  const long long si = sidx3(s, x, y, z);
+  for (int i = 0; i < s.Q; ++i) {
+    double feq = 0.0;
+    for (int k = 0; k < kKo3; ++k) feq = fma(a.H[(size_t)i * kKo3 + k], Mm[k], feq);
+    const S val = (S)(sizeof(S) == 4 ? feq - a.fref[i] : feq);
+    const long long pl = (long long)i * s.plane;
+    a.f[pl + si] = val;
+    for (int m = 0; m < nimg; ++m) a.f[pl + img[m]] = val;
+  }
+}
+
+// Fields of f(t) (pulled from f*(t-1), or f*(0) in place), FP64.
+template <typename S>
+__global__ void __launch_bounds__(128) k_fields3q(const __grid_constant__ Fields3qArgs<S> a) {
+  const Scalars3& s = a.s;
+  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y, z = blockIdx.z;
+  if (x >= s.nx || y >= s.ny || z >= s.nz) return;
+  const S* __restrict__ base = a.fin + sidx3(s, x, y, z);
+  double N[4] = {0.0, 0.0, 0.0, 0.0}, Tm[4][4];
+  for (int u = 0; u < 4; ++u)
+    for (int w = 0; w < 4; ++w) Tm[u][w] = 0.0;
+  for (int i = 0; i < s.Q; ++i) {
+    double f = (double)base[(long long)i * s.plane + (a.pull ? a.off[i] : 0)];
+    if (sizeof(S) == 4) f += a.fref[i];
+    for (int u = 0; u < 4; ++u) {
+      N[u] += f * a.c[4 * i + u];
+      for (int w = u; w < 4; ++w) Tm[u][w] = fma(f * a.c[4 * i + u], a.c[4 * i + w], Tm[u][w]);
+    }
+  }
+  for (int u = 0; u < 4; ++u)
+    for (int w = 0; w < u; ++w) Tm[u][w] = Tm[w][u];
+  const Macro3 M = landau3(N, Tm);
+  const long long c = ((long long)z * s.ny + y) * s.nx + x;
+  const long long nc = (long long)s.nx * s.ny * s.nz;
+  a.out[c] = M.ok ? M.n : __longlong_as_double(0x7ff8000000000000LL);
+  a.out[nc + c] = M.U[1] / M.U[0];
+  a.out[2 * nc + c] = M.U[2] / M.U[0];
+  a.out[3 * nc + c] = M.U[3] / M.U[0];
+  a.out[4 * nc + c] = M.T;
+  a.out[5 * nc + c] = M.eps;
+}
+
+dim3 grid3q(const Scalars3& s) { return dim3((s.nx + 31) / 32, (s.ny + 3) / 4, s.nz); }
+
+}  // namespace
+
+template <typename S>
+cudaError_t launch_step3q(const Step3qArgs<S>& a, cudaStream_t st) {
+  if (a.s.Q != kQo3) return cudaErrorInvalidValue;
+  const int smem = (int)sizeof(SharedTables3<S>);
+  cudaError_t e = cudaFuncSetAttribute(k_step3q<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step3q<S>, 128, smem)) != cudaSuccess) return e;
+  const long long nseg = (long long)((a.s.nx + 31) / 32) * a.s.ny * a.s.nz;
+  const long long grid = std::min<long long>(nseg, (long long)sms * (per > 0 ? per : 1));
+  k_step3q<S><<<(unsigned)grid, 128, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_init3q(const Init3qArgs<S>& a, cudaStream_t st) {
+  k_init3q<S><<<grid3q(a.s), dim3(32, 4), 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_fields3q(const Fields3qArgs<S>& a, cudaStream_t st) {
+  k_fields3q<S><<<grid3q(a.s), dim3(32, 4), 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_step3q<float>(const Step3qArgs<float>&, cudaStream_t);
+template cudaError_t launch_step3q<double>(const Step3qArgs<double>&, cudaStream_t);
+template cudaError_t launch_init3q<float>(const Init3qArgs<float>&, cudaStream_t);
+template cudaError_t launch_init3q<double>(const Init3qArgs<double>&, cudaStream_t);
+template cudaError_t launch_fields3q<float>(const Fields3qArgs<float>&, cudaStream_t);
+template cudaError_t launch_fields3q<double>(const Fields3qArgs<double>&, cudaStream_t);
+
+}  // namespace rlbm

@@ -57,9 +57,9 @@ SIGNATURES = {
     "rlbm_create": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(_H)]),
     "rlbm_plan": (ctypes.c_int, [ctypes.POINTER(Params), _IP, _IP, _IP, _DP, _DP, _DP, _DP]),
     "rlbm3_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
-                                    _VP, ctypes.POINTER(_H)]),
+                                    ctypes.c_int, _VP, ctypes.POINTER(_H)]),
     "rlbm3_destroy": (None, [_H]),
-    "rlbm3_plan": (ctypes.c_int, [_IP, _IP, _DP, _DP, _DP]),
+    "rlbm3_plan": (ctypes.c_int, [ctypes.c_int, _IP, _IP, _IP, _DP, _DP, _DP]),
     "rlbm3_stencil": (ctypes.c_int, [_H, _IP, _IP, _DP, _DP]),
     "rlbm3_init": (ctypes.c_int, [_H, _VP, _VP, _VP, _VP, _VP, ctypes.c_int]),
     "rlbm3_step": (ctypes.c_int, [_H, ctypes.c_int]),
@@ -491,38 +491,40 @@ class Adjoint:
             pass
 
 
-def plan3():
-    """Host-only (3+1)-d tables: dict with Q, n (Q,3), p (Q,4), w, H (Q,14)."""
-    Q = ctypes.c_int()
-    nvec = np.zeros(3 * 80, dtype=np.int32)
-    pm, w, H = np.zeros(4 * 80), np.zeros(80), np.zeros(14 * 80)
-    rc = lib().rlbm3_plan(ctypes.byref(Q), nvec.ctypes.data_as(_IP), pm.ctypes.data_as(_DP),
-                          w.ctypes.data_as(_DP), H.ctypes.data_as(_DP))
+def plan3(order=2):
+    """Host-only (3+1)-d tables of expansion order 2 or 3: dict with Q, K,
+    n (Q,3), p (Q,4), w, H (Q,K)."""
+    Q, K = ctypes.c_int(), ctypes.c_int()
+    cap = 288
+    nvec = np.zeros(3 * cap, dtype=np.int32)
+    pm, w, H = np.zeros(4 * cap), np.zeros(cap), np.zeros(30 * cap)
+    rc = lib().rlbm3_plan(int(order), ctypes.byref(Q), ctypes.byref(K), nvec.ctypes.data_as(_IP),
+                          pm.ctypes.data_as(_DP), w.ctypes.data_as(_DP), H.ctypes.data_as(_DP))
     if rc != RLBM_OK:
         raise RLBMError(rc, lib().rlbm3_last_error(None).decode())
-    q = Q.value
-    return dict(Q=q, n=nvec[:3 * q].reshape(q, 3).copy(), p=pm[:4 * q].reshape(q, 4).copy(), w=w[:q].copy(),
-                H=H[:14 * q].reshape(q, 14).copy())
+    q, k = Q.value, K.value
+    return dict(Q=q, K=k, n=nvec[:3 * q].reshape(q, 3).copy(), p=pm[:4 * q].reshape(q, 4).copy(),
+                w=w[:q].copy(), H=H[:k * q].reshape(q, k).copy())
 
 
 class Lattice3:
-    """A (3+1)-d massless periodic lattice (order 2; FP64 or FP32 storage)
-    behind the rlbm3_* calls; fields are numpy (nz, ny, nx) arrays or CUDA
-    float64 tensors."""
+    """A (3+1)-d massless periodic lattice (expansion order 2 or 3; FP64 or
+    FP32 storage) behind the rlbm3_* calls; fields are numpy (nz, ny, nx)
+    arrays or CUDA float64 tensors."""
 
-    def __init__(self, nx, ny, nz, tau=1.0, precision="fp64", cuda_stream=None):
+    def __init__(self, nx, ny, nz, tau=1.0, precision="fp64", cuda_stream=None, order=2):
         if cuda_stream is None:
             cuda_stream = _current_stream()
         self.nx, self.ny, self.nz = nx, ny, nz
         h = _H()
-        rc = lib().rlbm3_create(nx, ny, nz, tau, PREC[precision], cuda_stream, ctypes.byref(h))
+        rc = lib().rlbm3_create(nx, ny, nz, tau, int(order), PREC[precision], cuda_stream, ctypes.byref(h))
         if rc != RLBM_OK:
             raise RLBMError(rc, lib().rlbm3_last_error(None).decode())
         self.h = h
         Q = ctypes.c_int()
-        nvec = np.zeros(3 * 80, dtype=np.int32)
-        pm = np.zeros(4 * 80)
-        w = np.zeros(80)
+        nvec = np.zeros(3 * 288, dtype=np.int32)
+        pm = np.zeros(4 * 288)
+        w = np.zeros(288)
         self._chk(lib().rlbm3_stencil(self.h, ctypes.byref(Q), nvec.ctypes.data_as(_IP), pm.ctypes.data_as(_DP),
                                       w.ctypes.data_as(_DP)))
         self.Q = Q.value

@@ -212,29 +212,43 @@ def test_builtin_massive_tables_are_in_orbit_order_with_exactly_symmetric_H(rl, 
     assert i0 == Q
 
 
-def test_d3_tables_agree_with_oracle(rl):
+# the library's moment order: 1 | p0 px py pz | p0px p0py p0pz pxpx pxpy pxpz
+# pypy pypz pzpz, then (order 3) p0 (xx xy xz yy yz zz) | xxx ... zzz
+_D3_BASIS = [(0, 0, 0, 0), (1, 0, 0, 0), (0, 1, 0, 0), (0, 0, 1, 0), (0, 0, 0, 1),
+             (1, 1, 0, 0), (1, 0, 1, 0), (1, 0, 0, 1), (0, 2, 0, 0), (0, 1, 1, 0),
+             (0, 1, 0, 1), (0, 0, 2, 0), (0, 0, 1, 1), (0, 0, 0, 2),
+             (1, 2, 0, 0), (1, 1, 1, 0), (1, 1, 0, 1), (1, 0, 2, 0), (1, 0, 1, 1), (1, 0, 0, 2),
+             (0, 3, 0, 0), (0, 2, 1, 0), (0, 2, 0, 1), (0, 1, 2, 0), (0, 1, 1, 1), (0, 1, 0, 2),
+             (0, 0, 3, 0), (0, 0, 2, 1), (0, 0, 1, 2), (0, 0, 0, 3)]
+
+
+@pytest.mark.parametrize("order,Q,K", [(2, 78, 14), (3, 288, 30)])
+def test_d3_tables_agree_with_oracle(rl, order, Q, K):
     """The (3+1)-d massless tables: the same stencil, momenta and weights as
     the oracle's reading of App. H, and an equilibrium matrix that reproduces
-    the oracle's f^eq at random states."""
+    the oracle's f^eq at random states (moments from the oracle's App. B
+    closed forms, in the library's order)."""
     from oracle import d3
-    d = rl.plan3()
-    q = d3.massless_quadrature_3d(2)
-    assert d["Q"] == q.Q == 78
+    d = rl.plan3(order)
+    q = d3.massless_quadrature_3d(order)
+    assert d["Q"] == q.Q == Q and d["K"] == K
     key = lambda n, p0: (tuple(int(v) for v in n), round(float(p0), 12))
     ko = {key(n, p[0]): i for i, (n, p) in enumerate(zip(q.n, q.p))}
     idx = np.array([ko[key(n, p[0])] for n, p in zip(d["n"], d["p"])])
-    assert sorted(idx.tolist()) == list(range(78))
-    assert np.abs(d["p"] - q.p[idx]).max() < 1e-15 and np.array_equal(d["w"], q.w[idx])
-    E = d3.Expansion3(q)
+    assert sorted(idx.tolist()) == list(range(Q))
+    assert np.abs(d["p"] - q.p[idx]).max() < 1e-14 * q.p[:, 0].max() and np.array_equal(d["w"], q.w[idx])
+    E = d3.Expansion3(q, order=order)
     rng = np.random.default_rng(2)
     for _ in range(5):
         n, T = rng.uniform(0.5, 1.5), rng.uniform(0.7, 1.4)
         u = rng.uniform(-0.3, 0.3, 3)
         g = 1 / np.sqrt(1 - u @ u)
         U = np.concatenate([[g], g * u])
-        M = np.array([n / (2 * T), n * U[0], n * U[1], n * U[2], n * U[3],
-                      4 * n * T * U[0] * U[1], 4 * n * T * U[0] * U[2], 4 * n * T * U[0] * U[3],
-                      4 * n * T * U[1] ** 2 + n * T, 4 * n * T * U[1] * U[2], 4 * n * T * U[1] * U[3],
-                      4 * n * T * U[2] ** 2 + n * T, 4 * n * T * U[2] * U[3], 4 * n * T * U[3] ** 2 + n * T])
+        M = np.array([d3.mj_moment_3d(mon, n, U, T) for mon in _D3_BASIS[:K]])
         fo = E.feq(np.array(n), U, np.array(T))
         assert np.abs(d["H"] @ M - fo[idx]).max() < 1e-13 * np.abs(fo).max()
+
+
+def test_d3_plan_rejects_other_orders(rl):
+    with pytest.raises(rl.RLBMError):
+        rl.plan3(4)
