@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "d3.h"
+#include "fpconv.cuh"
 
 namespace rlbm {
 namespace {
@@ -50,13 +51,29 @@ __device__ __forceinline__ R ddet4(const R (&B)[4][4]) {
 }
 
 // right null vector of B from the first column of adj(B):
-// v_i = (-1)^i det(B without row 0 and column i)
+// v_i = (-1)^i det(B without row 0 and column i), each 3 x 3 minor expanded
+// along row 1 over the six 2 x 2 minors c_ab of rows 2 and 3; B v = det(B) e_0,
+// so det(B) = sum_i B[0][i] v_i.
 template <typename R>
 __device__ __forceinline__ void adj_col0(const R (&B)[4][4], R (&v)[4]) {
-  v[0] = det3(B[1][1], B[1][2], B[1][3], B[2][1], B[2][2], B[2][3], B[3][1], B[3][2], B[3][3]);
-  v[1] = -det3(B[1][0], B[1][2], B[1][3], B[2][0], B[2][2], B[2][3], B[3][0], B[3][2], B[3][3]);
-  v[2] = det3(B[1][0], B[1][1], B[1][3], B[2][0], B[2][1], B[2][3], B[3][0], B[3][1], B[3][3]);
-  v[3] = -det3(B[1][0], B[1][1], B[1][2], B[2][0], B[2][1], B[2][2], B[3][0], B[3][1], B[3][2]);
+  const R c01 = B[2][0] * B[3][1] - B[2][1] * B[3][0], c02 = B[2][0] * B[3][2] - B[2][2] * B[3][0];
+  const R c03 = B[2][0] * B[3][3] - B[2][3] * B[3][0], c12 = B[2][1] * B[3][2] - B[2][2] * B[3][1];
+  const R c13 = B[2][1] * B[3][3] - B[2][3] * B[3][1], c23 = B[2][2] * B[3][3] - B[2][3] * B[3][2];
+  v[0] = B[1][1] * c23 - B[1][2] * c13 + B[1][3] * c12;
+  v[1] = -(B[1][0] * c23 - B[1][2] * c03 + B[1][3] * c02);
+  v[2] = B[1][0] * c13 - B[1][1] * c03 + B[1][3] * c01;
+  v[3] = -(B[1][0] * c12 - B[1][1] * c02 + B[1][2] * c01);
+}
+
+// d v / d l for B = A - l I: each minor differentiated through the diagonal
+// entries it keeps (d det / d B_rr = cofactor of B_rr).
+template <typename R>
+__device__ __forceinline__ void dadj_col0(const R (&B)[4][4], R (&d)[4]) {
+  d[0] = -((B[2][2] * B[3][3] - B[2][3] * B[3][2]) + (B[1][1] * B[3][3] - B[1][3] * B[3][1]) +
+           (B[1][1] * B[2][2] - B[1][2] * B[2][1]));
+  d[1] = (B[1][0] * B[3][3] - B[1][3] * B[3][0]) + (B[1][0] * B[2][2] - B[1][2] * B[2][0]);
+  d[2] = (B[2][0] * B[3][3] - B[2][3] * B[3][0]) - (B[1][0] * B[2][1] - B[1][1] * B[2][0]);
+  d[3] = -((B[2][0] * B[3][2] - B[2][2] * B[3][0]) + (B[1][0] * B[3][1] - B[1][1] * B[3][0]));
 }
 
 struct Macro3 {
@@ -131,10 +148,15 @@ __device__ __forceinline__ void mj_moments3(double n, double T, const double (&U
 
 
 // FP32 storage (g = f - f_ref, f_ref at (n_ref, rest, T_ref)): the Landau root
-// in FP32 (Newton on det(A - l I) from the ideal-fluid root), one Newton
-// correction with the residual in FP64, and in FP64 the eigenvector
-// (cofactors), nu^2 = v.v, w = v.N and from them n, dn = n - n_ref,
-// eps and dT = T - T_ref; U in FP32.
+// in FP32 (Newton on det(A - l I) from the ideal-fluid root), then one Newton
+// correction whose residual is evaluated in FP64: the cofactor vector v of
+// B = A - l I at the FP32 root and p(l) = B[0] . v.  The eigenvector at the
+// corrected root is v + dl dv/dl (dv/dl in FP32; the remainder is O(dl^2)),
+// and from it, in FP64, nu^2 = v.v, w = v.N (n = w / nu) and the numerator
+// of dn = n - n_ref = (w^2 - n_ref^2 nu^2) / (nu (w + n_ref nu)); the
+// quotients, U = v / nu and dT = (d_eps - 3 T_ref dn) / (3 n) (from
+// eps = 3 n T) in FP32.  About 50 FP64 operations per cell; conversions on
+// the integer pipe (fpconv.cuh).
 struct Macro3f {
   float U0, Ux, Uy, Uz, n, T, dn, dT;
   bool ok;
@@ -142,18 +164,16 @@ struct Macro3f {
 
 __device__ __forceinline__ Macro3f landau3f(const float (&N)[4], const float (&Tm)[4][4], const Scalars3& s) {
   const double nr = s.n_ref, Tr = s.T_ref, er = 3.0 * nr * Tr, Pr = nr * Tr;
-  // full moments (reference in FP64) and the mixed tensor A = T eta
-  double Nd[4] = {nr + (double)N[0], (double)N[1], (double)N[2], (double)N[3]};
-  double A[4][4];
+  const float fnr = d2f(nr), fTr = d2f(Tr), fer = d2f(er), fPr = d2f(Pr);
+  // the mixed tensor A = T eta in FP32 (reference diagonal added)
   float Af[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      double t = (double)(u <= v ? Tm[u][v] : Tm[v][u]);
-      if (u == v) t += (u == 0 ? er : Pr);
-      A[u][v] = v == 0 ? t : -t;
-      Af[u][v] = (float)A[u][v];
+      float t = u <= v ? Tm[u][v] : Tm[v][u];
+      if (u == v) t += (u == 0 ? fer : fPr);
+      Af[u][v] = v == 0 ? t : -t;
     }
   // FP32 root from the ideal-fluid guess (P = eps / 3)
   const float E = Af[0][0], M2 = Af[1][0] * Af[1][0] + Af[2][0] * Af[2][0] + Af[3][0] * Af[3][0];
@@ -171,39 +191,55 @@ __device__ __forceinline__ Macro3f landau3f(const float (&N)[4], const float (&T
     dpf = ddet4(Bf);
     lam -= det4(Bf) / dpf;
   }
-  // FP64 residual at the FP32 root, one Newton correction
+  // FP64 residual at the FP32 root: B = A - l I with A's entries exact from
+  // the FP32 sums and the FP64 reference
+  const double ld = f2d(lam);
+  const double d0 = ld - er, d1 = Pr + ld;
   double B[4][4];
-  double ld = (double)lam;
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) B[u][v] = A[u][v] - (u == v ? ld : 0.0);
-  ld -= det4(B) / (double)dpf;
+    for (int v = 0; v < 4; ++v) {
+      const double t = f2d(u <= v ? Tm[u][v] : Tm[v][u]);
+      B[u][v] = v == 0 ? t : -t;
+    }
+  B[0][0] = f2d(Tm[0][0]) - d0;
 #pragma unroll
-  for (int u = 0; u < 4; ++u) B[u][u] = A[u][u] - ld;
+  for (int u = 1; u < 4; ++u) B[u][u] = -(f2d(Tm[u][u]) + d1);
   double vv[4];
   adj_col0(B, vv);
-  const double nu2 = vv[0] * vv[0] - vv[1] * vv[1] - vv[2] * vv[2] - vv[3] * vv[3];
-  const double w = vv[0] * Nd[0] - vv[1] * Nd[1] - vv[2] * Nd[2] - vv[3] * Nd[3];
-  const double nu = sqrt(fabs(nu2));
-  const double sgn = vv[0] > 0.0 ? 1.0 : -1.0;
-  const double n = sgn * w / nu;
-  const double dn = (w * w - nr * nr * nu2) / (nu * (sgn * w + nr * nu));
-  const double deps = ld - er;
-  const double dT = (deps - 3.0 * Tr * dn) / (3.0 * n);
-  const double T = Tr + dT;
-  const bool ok = nu2 > 0.0 && n > 0.0 && T > 0.0 && isfinite(T) && isfinite(dn);
-  const float inu = (float)(sgn / nu);
+  const double p = B[0][0] * vv[0] + B[0][1] * vv[1] + B[0][2] * vv[2] + B[0][3] * vv[3];
+  const float dl = -__fdividef(d2f(p), dpf);
+  // the eigenvector at l + dl to first order
+#pragma unroll
+  for (int u = 0; u < 4; ++u) Bf[u][u] = Af[u][u] - lam;
+  float dv[4];
+  dadj_col0(Bf, dv);
+  double vc[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) vc[u] = vv[u] + f2d(dl * dv[u]);
+  const double nu2 = vc[0] * vc[0] - vc[1] * vc[1] - vc[2] * vc[2] - vc[3] * vc[3];
+  const double w = vc[0] * (nr + f2d(N[0])) - vc[1] * f2d(N[1]) - vc[2] * f2d(N[2]) - vc[3] * f2d(N[3]);
+  const double num = fma(w, w, -(nr * nr) * nu2);
+  const double deps = d0 + f2d(dl);
+  // FP32 quotients
+  const float fnu2 = d2f(nu2);
+  const float inu = rsqrtf(fnu2);
+  const float fnu = fnu2 * inu;
+  const float sgn = __double2hiint(vc[0]) < 0 ? -1.f : 1.f;
+  const float fw = sgn * d2f(w);
   Macro3f M;
-  M.U0 = (float)vv[0] * inu;
-  M.Ux = (float)vv[1] * inu;
-  M.Uy = (float)vv[2] * inu;
-  M.Uz = (float)vv[3] * inu;
-  M.n = (float)n;
-  M.T = (float)T;
-  M.dn = (float)dn;
-  M.dT = (float)dT;
-  M.ok = ok;
+  M.n = fw * inu;
+  M.dn = __fdividef(d2f(num), fnu * (fw + fnr * fnu));
+  M.dT = __fdividef(d2f(deps) - 3.f * fTr * M.dn, 3.f * M.n);
+  M.T = fTr + M.dT;
+  const float su = sgn * inu;
+  M.U0 = d2f(vc[0]) * su;
+  M.Ux = d2f(vc[1]) * su;
+  M.Uy = d2f(vc[2]) * su;
+  M.Uz = d2f(vc[3]) * su;
+  M.ok = (__double2hiint(nu2) > 0) && (M.n > 0.f) && (M.T > 0.f) && isfinite(M.T) && isfinite(M.dn) &&
+         isfinite(M.n);
   return M;
 }
 

@@ -121,6 +121,107 @@ __global__ void __launch_bounds__(128) k_step3q(const __grid_constant__ Step3qAr
   }
 }
 
+// FP32 storage: one thread per cell, a warp per row segment of 32 cells.
+// The four threads per cell of k_step3q would each repeat the FP64 polish of
+// the Landau root and read one table entry per FMA; here every thread of a
+// warp reads the same table row, so a 16-byte shared load broadcasts four
+// entries of H (rows padded to 32 with zero columns, Mk[30..31] = 0) and the
+// Landau solve runs once per cell.  The populations are read twice (moments,
+// then relaxation); the second read mostly finds them in L2.
+struct SharedTables3f {
+  float4 H[kQo3][8];
+  float4 c[kQo3];
+  float4 v[kQo3];
+  int off[kQo3];
+};
+
+template <int WARPS, int BATCH, int MINB>
+__global__ void __launch_bounds__(32 * WARPS, MINB) k_step3q_cell(const __grid_constant__ Step3qArgs<float> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SharedTables3f& t = *reinterpret_cast<SharedTables3f*>(smem_raw);
+  const Scalars3& s = a.s;
+  for (int e = threadIdx.x; e < kQo3 * 32; e += blockDim.x) {
+    const int i = e >> 5, k = e & 31;
+    reinterpret_cast<float*>(&t.H[i][0])[k] = k < kKo3 ? a.H[i * kKo3 + k] : 0.f;
+  }
+  for (int i = threadIdx.x; i < kQo3; i += blockDim.x) {
+    t.c[i] = make_float4(a.c[4 * i], a.c[4 * i + 1], a.c[4 * i + 2], a.c[4 * i + 3]);
+    t.v[i] = make_float4(a.v[3 * i], a.v[3 * i + 1], a.v[3 * i + 2], 0.f);
+    t.off[i] = a.off[i];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nxs = (s.nx + 31) / 32;
+  const long long nseg = (long long)nxs * s.ny * s.nz;
+  for (long long seg = (long long)blockIdx.x * WARPS + warp; seg < nseg; seg += (long long)gridDim.x * WARPS) {
+    const int xs = (int)(seg % nxs);
+    const int y = (int)((seg / nxs) % s.ny), z = (int)(seg / ((long long)nxs * s.ny));
+    const int x = xs * 32 + lane;
+    if (x >= s.nx) continue;
+    const long long si = sidx3(s, x, y, z);
+    const float* __restrict__ base = a.fin + si;
+    float N[4] = {0.f, 0.f, 0.f, 0.f}, Tm[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int w = 0; w < 4; ++w) Tm[u][w] = 0.f;
+    for (int i0 = 0; i0 < kQo3; i0 += BATCH) {
+      float g[BATCH];
+#pragma unroll
+      for (int j = 0; j < BATCH; ++j) g[j] = __ldg(base + (long long)(i0 + j) * s.plane + t.off[i0 + j]);
+#pragma unroll
+      for (int j = 0; j < BATCH; ++j) {
+        const float4 c = t.c[i0 + j];
+        const float cu[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float gu = g[j] * cu[u];
+          N[u] += gu;
+#pragma unroll
+          for (int w = u; w < 4; ++w) Tm[u][w] = fmaf(gu, cu[w], Tm[u][w]);
+        }
+      }
+    }
+    const Macro3f M = landau3f(N, Tm, s);
+    float Mk[32];
+    {
+      float Md[kKo3];
+      mj_delta3<kKo3>(M, (float)s.n_ref, (float)s.T_ref, Md);
+#pragma unroll
+      for (int k = 0; k < kKo3; ++k) Mk[k] = Md[k];
+      Mk[30] = Mk[31] = 0.f;
+    }
+    if (!M.ok) atomicAdd(a.status, 1ULL);
+    const float kt = M.ok ? (float)(1.0 / s.tau) : 0.f;
+    long long img[26];
+    const int nimg = cell_images(s, x, y, z, img);
+    for (int i0 = 0; i0 < kQo3; i0 += BATCH) {
+      float g[BATCH];
+#pragma unroll
+      for (int j = 0; j < BATCH; ++j) g[j] = __ldg(base + (long long)(i0 + j) * s.plane + t.off[i0 + j]);
+#pragma unroll
+      for (int j = 0; j < BATCH; ++j) {
+        const int i = i0 + j;
+        float geq = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float4 h = t.H[i][q];
+          geq = fmaf(h.x, Mk[4 * q], geq);
+          geq = fmaf(h.y, Mk[4 * q + 1], geq);
+          geq = fmaf(h.z, Mk[4 * q + 2], geq);
+          geq = fmaf(h.w, Mk[4 * q + 3], geq);
+        }
+        const float4 v = t.v[i];
+        const float om = kt * (M.U0 - v.x * M.Ux - v.y * M.Uy - v.z * M.Uz);
+        const float gn = fmaf(om, geq - g[j], g[j]);
+        const long long pl = (long long)i * s.plane;
+        a.fout[pl + si] = gn;
+        for (int m = 0; m < nimg; ++m) a.fout[pl + img[m]] = gn;
+      }
+    }
+  }
+}
+
 // f*(0) = f^eq(n, U, T) (stored f, or f - f_ref for FP32), one thread per cell.
 template <typename S>
 __global__ void __launch_bounds__(128) k_init3q(const __grid_constant__ Init3qArgs<S> a) {
@@ -181,9 +282,33 @@ dim3 grid3q(const Scalars3& s) { return dim3((s.nx + 31) / 32, (s.ny + 3) / 4, s
 
 }  // namespace
 
+template <int WARPS, int BATCH, int MINB>
+cudaError_t launch_cell(const Step3qArgs<float>& a, cudaStream_t st) {
+  auto kern = k_step3q_cell<WARPS, BATCH, MINB>;
+  const int smem = (int)sizeof(SharedTables3f);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 32 * WARPS, smem)) != cudaSuccess) return e;
+  const long long nseg = (long long)((a.s.nx + 31) / 32) * a.s.ny * a.s.nz;
+  const long long blocks = (nseg + WARPS - 1) / WARPS;
+  const long long grid = std::min<long long>(blocks, (long long)sms * (per > 0 ? per : 1));
+  kern<<<(unsigned)grid, 32 * WARPS, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+// 5 warps per block, 4 blocks per SM (80 registers, 189 KB of tables): at
+// 192^3 the fastest of 8-40 warps per SM and load batches of 4-16 (fewer
+// warps hide less latency, more of them push the second read of the
+// populations out of L2).
+cudaError_t launch_step3q_cell(const Step3qArgs<float>& a, cudaStream_t st) { return launch_cell<5, 8, 4>(a, st); }
+
 template <typename S>
 cudaError_t launch_step3q(const Step3qArgs<S>& a, cudaStream_t st) {
   if (a.s.Q != kQo3) return cudaErrorInvalidValue;
+  if constexpr (sizeof(S) == 4) return launch_step3q_cell(a, st);
   const int smem = (int)sizeof(SharedTables3<S>);
   cudaError_t e = cudaFuncSetAttribute(k_step3q<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;

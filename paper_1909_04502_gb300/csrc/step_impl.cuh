@@ -3,6 +3,7 @@
 // field extraction.  Instantiated per precision / order in step_o2.cu and
 // step_o3.cu.
 #pragma once
+#include "fpconv.cuh"
 #include "kernels.cuh"
 
 namespace rlbm {
@@ -14,45 +15,6 @@ constexpr int kThreads = kBX * kBY;
 
 // kernel parameters are limited to 32764 bytes
 static_assert(sizeof(Tables<double>) + sizeof(MomentArgs<double>) <= 32764, "kernel parameter space");
-
-// ---------------------------------------------------------------------------
-// Exact FP32 -> FP64 and rounding FP64 -> FP32 conversions on the integer
-// pipe (IEEE-754 bit layouts), keeping the FP64 pipe for arithmetic (a
-// hardware conversion costs about as much as an FP64 multiply on this part).
-// Zero and FP32 denormals map to signed zero; infinities and NaNs keep their
-// class.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ double f2d(float f) {
-  const unsigned b = __float_as_uint(f);
-  const unsigned sgn = b & 0x80000000u;
-  const unsigned e = (b >> 23) & 0xFFu;
-  const unsigned man = b & 0x7FFFFFu;
-  unsigned hi = sgn | ((e + 896u) << 20) | (man >> 3);
-  unsigned lo = man << 29;
-  hi = (e == 0u) ? sgn : ((e == 0xFFu) ? (sgn | 0x7FF00000u | (man >> 3)) : hi);
-  lo = (e == 0u) ? 0u : lo;
-  return __hiloint2double((int)hi, (int)lo);
-}
-
-__device__ __forceinline__ float d2f(double d) {
-  // round to nearest (ties away from zero) on the magnitude bits: adding half
-  // of the discarded 29-bit tail carries into mantissa and exponent as needed
-  // (32-bit halves with an explicit carry keep this on the integer pipe)
-  const unsigned lo = (unsigned)__double2loint(d);
-  const unsigned hw = (unsigned)__double2hiint(d);
-  const unsigned sgn = hw & 0x80000000u;
-  unsigned hi = hw & 0x7FFFFFFFu;
-  const unsigned ed = hi >> 20;
-  const unsigned lo2 = lo + (1u << 28);
-  hi += (lo2 < lo) ? 1u : 0u;
-  const int e = (int)(hi >> 20) - 896;
-  const unsigned man = ((hi & 0xFFFFFu) << 3) | (lo2 >> 29);
-  unsigned b = sgn | ((unsigned)e << 23) | man;
-  const bool is_nan = (ed == 0x7FFu) && (((hw & 0xFFFFFu) | lo) != 0u);
-  const unsigned special = is_nan ? 0x7FC00000u : (sgn | 0x7F800000u);
-  b = (e <= 0) ? sgn : ((e >= 255 || ed == 0x7FFu) ? special : b);
-  return __uint_as_float(b);
-}
 
 // ---------------------------------------------------------------------------
 // Step 1 of the update: streaming by pull (Eq. discrete-rbe, left side) from
