@@ -58,7 +58,7 @@ def _peaks():
 
 def _kernel_source_sha():
     h = hashlib.sha256()
-    for name in ("step_impl.cuh", "kernels.cuh"):
+    for name in ("step_impl.cuh", "kernels.cuh", "fpconv.cuh"):
         with open(os.path.join(ROOT, "paper_1909_04502_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
