@@ -80,13 +80,13 @@ __global__ void __launch_bounds__(128) k_step3(const __grid_constant__ Tables3 t
 }
 
 // FP32 storage: g = f - f_ref is stored and collided in FP32; the moments are
-// FP32 sums of g plus the reference moments in FP64; the Landau root is
+// FP32 sums of g (the reference moments enter in FP64); the Landau root is
 // found in FP32 (Newton on det(A - l I)) and corrected by one Newton step
-// with the residual in FP64; the eigenvector (cofactors), nu^2 = v.v and
-// w = v.N, and from them n, dn = n - n_ref, eps and dT = T - T_ref, are
-// evaluated in FP64; the equilibrium differences dM = M(n, U, T) - M_ref are
-// written so that each is accurate relative to itself, and the equilibrium,
-// the relaxation and the store are FP32.
+// whose residual, the eigenvector's nu^2 = v.v, w = v.N and the numerator of
+// dn = n - n_ref are evaluated in FP64 (landau3f); the equilibrium
+// differences dM = M(n, U, T) - M_ref are written so that each is accurate
+// relative to itself, and the equilibrium, the relaxation and the store are
+// FP32.
 template <int QT>
 __global__ void __launch_bounds__(128) k_step3f(const __grid_constant__ Tables3 tb,
                                                 const __grid_constant__ Step3Args<float> a) {
