@@ -1,6 +1,7 @@
 // C ABI of the (3+1)-d massless step (include/rlbm.h, rlbm3_*).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -24,6 +25,7 @@ struct rlbm3_handle {
   unsigned long long* status = nullptr;
   cudaStream_t stream = nullptr;
   std::vector<double> fref;       // reference populations (FP32 storage)
+  bool sym = false;               // order 2 in sign-orbit form (FP64 step)
   // order 3: tables in device memory
   void* dH = nullptr;             // Q x 30, storage precision
   void* dc = nullptr;             // Q x 4
@@ -170,6 +172,19 @@ int rlbm3_create(int nx, int ny, int nz, double tau, int order, int precision, v
     if (!rc) rc = upload((void**)&h->doff, offs);
     if (rc) return fail3(nullptr, rc, "order-3 tables");
   }
+  if (order == 2) {
+    // sign-orbit form: 9 runs of 8, then the axis pairs along x, y and z
+    static const int kMasks[kRuns3] = {7, 7, 7, 7, 7, 7, 7, 7, 7, 1, 2, 4};
+    h->sym = h->q.sym && (int)h->q.orbit_mask.size() == kRuns3 &&
+             std::equal(h->q.orbit_mask.begin(), h->q.orbit_mask.end(), kMasks);
+    for (int r = 0; r < kRuns3 && h->sym; ++r) {
+      const double* p = &h->q.p[4 * (r < 9 ? 8 * r : 72 + 2 * (r - 9))];
+      const double mono[14] = {p[0], p[1], p[2], p[3], p[0] * p[0], p[0] * p[1], p[0] * p[2],
+                               p[0] * p[3], p[1] * p[1], p[1] * p[2], p[1] * p[3], p[2] * p[2],
+                               p[2] * p[3], p[3] * p[3]};
+      for (int k = 0; k < 14; ++k) h->tb->mono[r][k] = mono[k];
+    }
+  }
   for (int i = 0; i < s.Q && order == 2; ++i) {
     for (int u = 0; u < 4; ++u) h->tb->c[i][u] = h->q.p[4 * i + u];
     for (int u = 0; u < 3; ++u) h->tb->v[i][u] = h->q.p[4 * i + 1 + u] / h->q.p[4 * i];
@@ -277,7 +292,7 @@ int rlbm3_step(rlbm3_handle* h, int nsteps) {
       e = launch_step3<float>(*h->tb, a, h->stream);
     } else {
       Step3Args<double> a{(const double*)h->buf[h->cur], (double*)h->buf[h->cur ^ 1], h->status, h->sc};
-      e = launch_step3<double>(*h->tb, a, h->stream);
+      e = h->sym ? launch_step3_sym(*h->tb, a, h->stream) : launch_step3<double>(*h->tb, a, h->stream);
     }
     if (e != cudaSuccess) return cuda_fail3(h, e, "step kernel");
     h->cur ^= 1;

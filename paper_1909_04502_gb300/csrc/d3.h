@@ -6,6 +6,8 @@
 
 namespace rlbm {
 
+constexpr int kRuns3 = 12;   // sign-orbit runs of the order-2 table
+
 struct Tables3 {
   double c[kMaxQ3][4];    // p0, px, py, pz of population i
   double v[kMaxQ3][3];    // microscopic velocity p / p0
@@ -15,6 +17,10 @@ struct Tables3 {
   float vf[kMaxQ3][3];
   float Hf[kMaxQ3][14];
   int off[kMaxQ3];        // pull source of population i relative to the cell: i * plane - n_i . strides
+  // sign-orbit form (order 2: 9 runs of 8, then the axis pairs along x, y, z):
+  // the moment monomials p0, px, py, pz, p0p0, p0px, p0py, p0pz, pxpx, pxpy,
+  // pxpz, pypy, pypz, pzpz of each run's first member (all components >= 0)
+  double mono[kRuns3][14];
 };
 
 struct Scalars3 {
@@ -91,6 +97,8 @@ cudaError_t launch_fields3q(const Fields3qArgs<S>& a, cudaStream_t st);
 
 template <typename S>
 cudaError_t launch_step3(const Tables3& tb, const Step3Args<S>& a, cudaStream_t st);
+// FP64 step of the order-2 table in sign-orbit form (Tables3::mono filled)
+cudaError_t launch_step3_sym(const Tables3& tb, const Step3Args<double>& a, cudaStream_t st);
 template <typename S>
 cudaError_t launch_init3(const Tables3& tb, const Init3Args<S>& a, cudaStream_t st);
 template <typename S>

@@ -7,6 +7,7 @@
 #include "setup.h"
 
 #include <array>
+#include <functional>
 #include <set>
 
 #include "dd.h"
@@ -821,21 +822,26 @@ bool massless3_tables(int order, Quadrature3* q, std::string* err) {
       const double wgt = col[ng * j + g];
       if (wgt == 0.0) continue;
       const int* gen = order == 2 ? gen2[g] : gen3[g];
-      std::set<std::array<int, 3>> orbit;
+      // the distinct permutations of |gen| (descending), each followed by its
+      // sign variants: member s negates component k where bit k of s is set,
+      // s running over the subsets of the non-zero components
+      std::set<std::array<int, 3>, std::greater<std::array<int, 3>>> pats;
       int perm[3] = {0, 1, 2};
       do {
-        for (int sgn = 0; sgn < 8; ++sgn) {
-          std::array<int, 3> v;
-          for (int k = 0; k < 3; ++k) v[k] = ((sgn >> k) & 1 ? -1 : 1) * gen[perm[k]];
-          orbit.insert(v);
-        }
+        pats.insert({gen[perm[0]], gen[perm[1]], gen[perm[2]]});
       } while (std::next_permutation(perm, perm + 3));
-      for (const auto& v : orbit) {
-        const double len = std::sqrt((double)(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
-        for (int k = 0; k < 3; ++k) q->n.push_back(v[k]);
-        q->p.push_back(shells[j]);
-        for (int k = 0; k < 3; ++k) q->p.push_back(shells[j] * v[k] / len);
-        q->w.push_back(wgt);
+      for (const auto& a : pats) {
+        int mask = 0;
+        for (int k = 0; k < 3; ++k) mask |= (a[k] != 0) << k;
+        q->orbit_mask.push_back(mask);
+        const double len = std::sqrt((double)(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]));
+        for (int sgn = 0; sgn < 8; ++sgn) {
+          if (sgn & ~mask) continue;
+          for (int k = 0; k < 3; ++k) q->n.push_back(((sgn >> k) & 1 ? -1 : 1) * a[k]);
+          q->p.push_back(shells[j]);
+          for (int k = 0; k < 3; ++k) q->p.push_back(shells[j] * (((sgn >> k) & 1 ? -1 : 1) * a[k]) / len);
+          q->w.push_back(wgt);
+        }
       }
     }
   q->Q = (int)q->w.size();
@@ -863,6 +869,23 @@ bool massless3_tables(int order, Quadrature3* q, std::string* err) {
       for (int l = 0; l < K; ++l) t = t + phi[l] * Gi[l * K + k];
       q->H[(size_t)i * K + k] = (dd(q->w[i]) * t).to_double();
     }
+  }
+  // the sign-orbit identities of H, checked exactly
+  q->sym = true;
+  for (size_t r = 0, i0 = 0; r < q->orbit_mask.size(); ++r) {
+    const int mask = q->orbit_mask[r];
+    int s = 0;
+    for (int sgn = 0; sgn < 8; ++sgn) {
+      if (sgn & ~mask) continue;
+      const size_t i = i0 + s++;
+      for (int k = 0; k < K; ++k) {
+        int par = 0;
+        for (int c = 0; c < 3; ++c) par ^= ((sgn >> c) & 1) & (B[k][1 + c] & 1);
+        const double want = par ? -q->H[i0 * K + k] : q->H[i0 * K + k];
+        if (q->H[i * K + k] != want) q->sym = false;
+      }
+    }
+    i0 += s;
   }
   return true;
 }

@@ -86,6 +86,14 @@ struct Quadrature3 {
   std::vector<double> p;    // 4 Q momenta (p0, px, py, pz)
   std::vector<double> w;    // Q weights
   std::vector<double> H;    // Q x K
+  // Sign orbits: populations come in runs that share |n_i|, p0 and w; member
+  // s of a run negates component k where bit k of s is set (s over the
+  // components that are not zero, in increasing order).  orbit_mask[r] holds
+  // the run's non-zero components (bit k: component k); sym is true when
+  // every run also satisfies H_{s,k} = sigma_k(s) H_{0,k} exactly, sigma_k(s)
+  // the sign the basis member k takes under the flips of s.
+  std::vector<int> orbit_mask;
+  bool sym = false;
 };
 extern const int kBasis3[14][4];     // order 2: 1 | p0 px py pz | p0px p0py p0pz pxpx pxpy pxpz pypy pypz pzpz
 extern const int kBasis3o3[30][4];   // order 3: the 14 above, then p0 x (pxpx pxpy pxpz pypy pypz pzpz) and

@@ -17,6 +17,12 @@ namespace rlbm {
 
 namespace {
 
+// spatial exponents (x, y, z) of the order-2 basis members 1 | p0 px py pz |
+// p0px p0py p0pz pxpx pxpy pxpz pypy pypz pzpz
+__device__ constexpr int kBasis3Exp[14][3] = {{0, 0, 0}, {0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1},
+                                              {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0}, {1, 1, 0},
+                                              {1, 0, 1}, {0, 2, 0}, {0, 1, 1}, {0, 0, 2}};
+
 template <int QT>
 __global__ void __launch_bounds__(128) k_step3(const __grid_constant__ Tables3 tb,
                                                const __grid_constant__ Step3Args<double> a) {
@@ -76,6 +82,146 @@ __global__ void __launch_bounds__(128) k_step3(const __grid_constant__ Tables3 t
     const long long pl = (long long)i * s.plane;
     out[pl + si] = g;
     for (int m = 0; m < nimg; ++m) out[pl + img[m]] = g;
+  }
+}
+
+// The FP64 step in sign-orbit form.  Populations come in runs whose members
+// share p0 and |p| componentwise: 9 runs of 8 (member s negates the
+// components whose bit is set in s) and the pairs (+-3, 0, 0), (0, +-3, 0),
+// (0, 0, +-3).  Per run of 8, a Walsh-Hadamard transform of the pulled values
+// gives the sums F_c = sum_s chi_c(s) f_s over the sign characters c; each
+// moment of rank <= 2 needs one of them times the first member's monomial
+// (e.g. T^xy += a b F_xy).  The equilibrium rows of a run are the first row
+// with the sign chi_k(s) of each basis member k (checked exactly on the host),
+// so f^eq_s = sum over the seven characters of chi(s) C_chi, with C_chi the
+// first row's partial sums over the members of that character; the relaxation
+// rates follow from v_s . U = sx vx Ux + sy vy Uy + sz vz Uz.  About 110 FP64
+// operations per run of 8 against about 270 for eight rows.
+__global__ void __launch_bounds__(128) k_step3s(const __grid_constant__ Tables3 tb,
+                                                const __grid_constant__ Step3Args<double> a) {
+  const Scalars3& s = a.s;
+  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y, z = blockIdx.z;
+  if (x >= s.nx || y >= s.ny || z >= s.nz) return;
+  const long long si = sidx3(s, x, y, z);
+  const double* __restrict__ base = a.fin + si;
+  // pass 1: moments m = N0 Nx Ny Nz T00 T0x T0y T0z Txx Txy Txz Tyy Tyz Tzz
+  double m[14];
+#pragma unroll
+  for (int k = 0; k < 14; ++k) m[k] = 0.0;
+#pragma unroll 1
+  for (int r = 0; r < 9; ++r) {
+    double f[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) f[q] = __ldg(base + tb.off[8 * r + q]);
+    // F[c]: sum_s (-1)^{popcount(s & c)} f_s
+#pragma unroll
+    for (int h = 1; h < 8; h <<= 1)
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (!(q & h)) {
+          const double u = f[q], v = f[q | h];
+          f[q] = u + v;
+          f[q | h] = u - v;
+        }
+    const double* c = tb.mono[r];
+    m[0] = fma(c[0], f[0], m[0]);
+    m[1] = fma(c[1], f[1], m[1]);
+    m[2] = fma(c[2], f[2], m[2]);
+    m[3] = fma(c[3], f[4], m[3]);
+    m[4] = fma(c[4], f[0], m[4]);
+    m[5] = fma(c[5], f[1], m[5]);
+    m[6] = fma(c[6], f[2], m[6]);
+    m[7] = fma(c[7], f[4], m[7]);
+    m[8] = fma(c[8], f[0], m[8]);
+    m[9] = fma(c[9], f[3], m[9]);
+    m[10] = fma(c[10], f[5], m[10]);
+    m[11] = fma(c[11], f[0], m[11]);
+    m[12] = fma(c[12], f[6], m[12]);
+    m[13] = fma(c[13], f[0], m[13]);
+  }
+  // the axis pairs: N^a, T^0a odd, T^00, T^aa, N^0 even
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const double fp = __ldg(base + tb.off[72 + 2 * ax]), fm = __ldg(base + tb.off[73 + 2 * ax]);
+    const double S = fp + fm, D = fp - fm;
+    const double* c = tb.mono[9 + ax];
+    const int taa = ax == 0 ? 8 : (ax == 1 ? 11 : 13);
+    m[0] = fma(c[0], S, m[0]);
+    m[4] = fma(c[4], S, m[4]);
+    m[1 + ax] = fma(c[1 + ax], D, m[1 + ax]);
+    m[5 + ax] = fma(c[5 + ax], D, m[5 + ax]);
+    m[taa] = fma(c[taa], S, m[taa]);
+  }
+  const double N[4] = {m[0], m[1], m[2], m[3]};
+  const double Tm[4][4] = {{m[4], m[5], m[6], m[7]},
+                           {m[5], m[8], m[9], m[10]},
+                           {m[6], m[9], m[11], m[12]},
+                           {m[7], m[10], m[12], m[13]}};
+  const Macro3 M = landau3(N, Tm);
+  if (!M.ok) atomicAdd(a.status, 1ULL);
+  double Mm[14];
+  mj_moments3(M.n, M.T, M.U, Mm);
+  const double kt = M.ok ? 1.0 / s.tau : 0.0;
+  const double kU0 = kt * M.U[0], kUx = kt * M.U[1], kUy = kt * M.U[2], kUz = kt * M.U[3];
+  long long img[26];
+  const int nimg = cell_images(s, x, y, z, img);
+  double* __restrict__ out = a.fout;
+  // pass 2: equilibrium, relaxation, store (the pulled values are read again)
+#pragma unroll 1
+  for (int r = 0; r < 9; ++r) {
+    const double* H0 = tb.H[8 * r];
+    // partial sums over the basis members of each sign character
+    const double C0 = fma(H0[0], Mm[0], fma(H0[1], Mm[1], fma(H0[8], Mm[8], fma(H0[11], Mm[11], H0[13] * Mm[13]))));
+    const double Cx = fma(H0[2], Mm[2], H0[5] * Mm[5]);
+    const double Cy = fma(H0[3], Mm[3], H0[6] * Mm[6]);
+    const double Cz = fma(H0[4], Mm[4], H0[7] * Mm[7]);
+    const double Cxy = H0[9] * Mm[9], Cxz = H0[10] * Mm[10], Cyz = H0[12] * Mm[12];
+    // f^eq_s = C0 + sx Cx + sy Cy + sz Cz + sx sy Cxy + sx sz Cxz + sy sz Cyz
+    const double t0 = C0 + Cy, t1 = C0 - Cy, u0 = Cx + Cxy, u1 = Cx - Cxy;
+    const double P[4] = {t0 + u0, t0 - u0, t1 + u1, t1 - u1};
+    const double v0 = Cz + Cyz, v1 = Cz - Cyz;
+    const double Qz[4] = {v0 + Cxz, v0 - Cxz, v1 + Cxz, v1 - Cxz};
+    // tau^-1 (U0 - v_s . U)
+    const double* vb = tb.v[8 * r];
+    const double X = vb[0] * kUx, Y = vb[1] * kUy, Z = vb[2] * kUz;
+    const double r0 = kU0 - X, r1 = kU0 + X;
+    const double R[4] = {r0 - Y, r1 - Y, r0 + Y, r1 + Y};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int i = 8 * r + q;
+      const double feq = (q & 4) ? P[q & 3] - Qz[q & 3] : P[q & 3] + Qz[q & 3];
+      const double om = (q & 4) ? R[q & 3] + Z : R[q & 3] - Z;
+      const double f = __ldg(base + tb.off[i]);
+      const double g = fma(om, feq - f, f);
+      const long long pl = (long long)i * s.plane;
+      out[pl + si] = g;
+      for (int mm = 0; mm < nimg; ++mm) out[pl + img[mm]] = g;
+    }
+  }
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const int i0 = 72 + 2 * ax;
+    const double* H0 = tb.H[i0];
+    double Ce = 0.0, Co = 0.0;
+#pragma unroll
+    for (int k = 0; k < 14; ++k) {
+      // basis members odd in component ax: p_a, p0 p_a and the mixed p_a p_b
+      const int ex = kBasis3Exp[k][ax];
+      if (ex & 1) Co = fma(H0[k], Mm[k], Co);
+      else Ce = fma(H0[k], Mm[k], Ce);
+    }
+    const double va = tb.v[i0][ax] * (ax == 0 ? kUx : (ax == 1 ? kUy : kUz));
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int i = i0 + q;
+      const double feq = q ? Ce - Co : Ce + Co;
+      const double om = q ? kU0 + va : kU0 - va;
+      const double f = __ldg(base + tb.off[i]);
+      const double g = fma(om, feq - f, f);
+      const long long pl = (long long)i * s.plane;
+      out[pl + si] = g;
+      for (int mm = 0; mm < nimg; ++mm) out[pl + img[mm]] = g;
+    }
   }
 }
 
@@ -213,6 +359,12 @@ template <>
 cudaError_t launch_step3<double>(const Tables3& tb, const Step3Args<double>& a, cudaStream_t st) {
   if (a.s.Q != 78) return cudaErrorInvalidValue;
   k_step3<78><<<grid3(a.s), dim3(32, 4), 0, st>>>(tb, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step3_sym(const Tables3& tb, const Step3Args<double>& a, cudaStream_t st) {
+  if (a.s.Q != 78) return cudaErrorInvalidValue;
+  k_step3s<<<grid3(a.s), dim3(32, 4), 0, st>>>(tb, a);
   return cudaGetLastError();
 }
 

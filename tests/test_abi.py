@@ -249,6 +249,37 @@ def test_d3_tables_agree_with_oracle(rl, order, Q, K):
         assert np.abs(d["H"] @ M - fo[idx]).max() < 1e-13 * np.abs(fo).max()
 
 
+@pytest.mark.parametrize("order", [2, 3])
+def test_d3_tables_come_in_sign_orbits(rl, order):
+    """The (3+1)-d tables in sign-orbit order: each run shares p0, the weight
+    and |n| componentwise, its member s negates the components whose bit is
+    set in s (over the non-zero components), and its equilibrium rows are the
+    first row times the sign each basis member takes, exactly; at order 2 the
+    runs are nine of eight, then the axis pairs along x, y and z (the layout
+    the sign-orbit FP64 kernel takes)."""
+    d = rl.plan3(order)
+    n, p, w, H = d["n"], d["p"], d["w"], d["H"]
+    basis = np.array(_D3_BASIS[:d["K"]])
+    i, masks = 0, []
+    while i < d["Q"]:
+        a = n[i]
+        assert np.all(a >= 0)
+        mask = sum(1 << k for k in range(3) if a[k])
+        members = [sg for sg in range(8) if not (sg & ~mask)]
+        for j, sg in enumerate(members):
+            sign = np.array([-1 if (sg >> k) & 1 else 1 for k in range(3)])
+            assert np.array_equal(n[i + j], sign * a)
+            assert p[i + j, 0] == p[i, 0] and np.array_equal(p[i + j, 1:], sign * p[i, 1:])
+            assert w[i + j] == w[i]
+            chi = np.prod(sign[None, :] ** basis[:, 1:], axis=1)
+            assert np.array_equal(H[i + j], chi * H[i])
+        masks.append(mask)
+        i += len(members)
+    assert i == d["Q"]
+    if order == 2:
+        assert masks == [7] * 9 + [1, 2, 4]
+
+
 def test_d3_plan_rejects_other_orders(rl):
     with pytest.raises(rl.RLBMError):
         rl.plan3(4)
