@@ -26,7 +26,8 @@ struct rlbm3_handle {
   cudaStream_t stream = nullptr;
   std::vector<double> fref;       // reference populations (FP32 storage)
   bool sym = false;               // order 2 in sign-orbit form (FP64 step)
-  std::unique_ptr<Tables3s3> ts3; // order 3 in sign-orbit form (FP64 step), or null
+  // order 3 in sign-orbit form (FP64 step), or null
+  std::unique_ptr<Tables3s3<double>> ts3d;
   // order 3: tables in device memory
   void* dH = nullptr;             // Q x 30, storage precision
   void* dc = nullptr;             // Q x 4
@@ -79,6 +80,44 @@ int upload(void** dst, const std::vector<T>& v) {
   if (cudaMalloc(dst, v.size() * sizeof(T)) != cudaSuccess) { cudaGetLastError(); return RLBM_ERR_OOM; }
   if (cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) return RLBM_ERR_CUDA;
   return RLBM_OK;
+}
+
+// The order-3 run tables (sign-orbit form): 33 runs of 8 and 6 runs of 4
+// with the non-zero components x y, x z, x y, x z, y z, y z; null when the
+// table has another layout.
+template <typename S>
+std::unique_ptr<Tables3s3<S>> order3_runs(const Quadrature3& q, const std::vector<int>& offs) {
+  static const int kMask4[kRuns4o3] = {3, 5, 3, 5, 6, 6};
+  std::unique_ptr<Tables3s3<S>> t(new Tables3s3<S>());
+  std::memset(t.get(), 0, sizeof(Tables3s3<S>));
+  int n8 = 0, n4 = 0, i0 = 0;
+  for (int mask : q.orbit_mask) {
+    const int size = mask == 7 ? 8 : 4;
+    if (i0 + size > q.Q || q.K != 30) return nullptr;
+    const double* p = &q.p[4 * i0];
+    const double mono[14] = {p[0], p[1], p[2], p[3], p[0] * p[0], p[0] * p[1], p[0] * p[2],
+                             p[0] * p[3], p[1] * p[1], p[1] * p[2], p[1] * p[3], p[2] * p[2],
+                             p[2] * p[3], p[3] * p[3]};
+    S *H, *mo, *v;
+    if (mask == 7 && n8 < kRuns8o3) {
+      t->start8[n8] = i0;
+      H = t->H8[n8], mo = t->mono8[n8], v = t->v8[n8];
+      ++n8;
+    } else if (mask != 7 && n4 < kRuns4o3 && mask == kMask4[n4]) {
+      t->start4[n4] = i0;
+      H = t->H4[n4], mo = t->mono4[n4], v = t->v4[n4];
+      ++n4;
+    } else {
+      return nullptr;
+    }
+    for (int k = 0; k < 30; ++k) H[k] = (S)q.H[(size_t)i0 * 30 + k];
+    for (int k = 0; k < 14; ++k) mo[k] = (S)mono[k];
+    for (int k = 0; k < 3; ++k) v[k] = (S)(p[1 + k] / p[0]);
+    i0 += size;
+  }
+  if (n8 != kRuns8o3 || n4 != kRuns4o3 || i0 != q.Q || (int)offs.size() != q.Q) return nullptr;
+  for (int i = 0; i < q.Q; ++i) t->off[i] = offs[i];
+  return t;
 }
 
 }  // namespace
@@ -173,42 +212,7 @@ int rlbm3_create(int nx, int ny, int nz, double tau, int order, int precision, v
     if (!rc) rc = upload((void**)&h->doff, offs);
     if (rc) return fail3(nullptr, rc, "order-3 tables");
   }
-  if (order == 3 && h->elem == 8 && h->q.sym) {
-    // sign-orbit form: 33 runs of 8 and 6 runs of 4 with the non-zero
-    // components x y, x z, x y, x z, y z, y z
-    static const int kMask4[kRuns4o3] = {3, 5, 3, 5, 6, 6};
-    std::unique_ptr<Tables3s3> t(new Tables3s3());
-    std::memset(t.get(), 0, sizeof(Tables3s3));
-    int n8 = 0, n4 = 0, i0 = 0;
-    bool ok = true;
-    for (int mask : h->q.orbit_mask) {
-      const int size = mask == 7 ? 8 : 4;
-      const double* p = &h->q.p[4 * i0];
-      const double mono[14] = {p[0], p[1], p[2], p[3], p[0] * p[0], p[0] * p[1], p[0] * p[2],
-                               p[0] * p[3], p[1] * p[1], p[1] * p[2], p[1] * p[3], p[2] * p[2],
-                               p[2] * p[3], p[3] * p[3]};
-      if (mask == 7 && n8 < kRuns8o3) {
-        t->start8[n8] = i0;
-        for (int k = 0; k < 30; ++k) t->H8[n8][k] = h->q.H[(size_t)i0 * 30 + k];
-        for (int k = 0; k < 14; ++k) t->mono8[n8][k] = mono[k];
-        for (int k = 0; k < 3; ++k) t->v8[n8][k] = p[1 + k] / p[0];
-        ++n8;
-      } else if (mask != 7 && n4 < kRuns4o3 && mask == kMask4[n4]) {
-        t->start4[n4] = i0;
-        for (int k = 0; k < 30; ++k) t->H4[n4][k] = h->q.H[(size_t)i0 * 30 + k];
-        for (int k = 0; k < 14; ++k) t->mono4[n4][k] = mono[k];
-        for (int k = 0; k < 3; ++k) t->v4[n4][k] = p[1 + k] / p[0];
-        ++n4;
-      } else {
-        ok = false;
-      }
-      i0 += size;
-    }
-    if (ok && n8 == kRuns8o3 && n4 == kRuns4o3 && i0 == s.Q) {
-      for (int i = 0; i < s.Q; ++i) t->off[i] = offs[i];
-      h->ts3 = std::move(t);
-    }
-  }
+  if (order == 3 && h->q.sym && h->elem == 8) h->ts3d = order3_runs<double>(h->q, offs);
   if (order == 2) {
     // sign-orbit form: 9 runs of 8, then the axis pairs along x, y and z
     static const int kMasks[kRuns3] = {7, 7, 7, 7, 7, 7, 7, 7, 7, 1, 2, 4};
@@ -322,7 +326,7 @@ int rlbm3_step(rlbm3_handle* h, int nsteps) {
       } else {
         Step3qArgs<double> a{(const double*)h->buf[h->cur], (double*)h->buf[h->cur ^ 1], h->status, h->sc,
                              (const double*)h->dH, (const double*)h->dc, (const double*)h->dv, h->doff};
-        e = h->ts3 ? launch_step3q_sym(*h->ts3, a, h->stream) : launch_step3q<double>(a, h->stream);
+        e = h->ts3d ? launch_step3q_sym(*h->ts3d, a, h->stream) : launch_step3q<double>(a, h->stream);
       }
     } else if (h->elem == 4) {
       Step3Args<float> a{(const float*)h->buf[h->cur], (float*)h->buf[h->cur ^ 1], h->status, h->sc};

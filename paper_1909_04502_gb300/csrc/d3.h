@@ -102,16 +102,19 @@ cudaError_t launch_step3(const Tables3& tb, const Step3Args<S>& a, cudaStream_t 
 // run's first member's equilibrium row, moment monomials (as Tables3::mono)
 // and velocity p / p0, the runs' first populations and the pull shifts.
 constexpr int kRuns8o3 = 33, kRuns4o3 = 6;
+template <typename S>
 struct Tables3s3 {
-  double H8[kRuns8o3][30], mono8[kRuns8o3][14], v8[kRuns8o3][3];
-  double H4[kRuns4o3][30], mono4[kRuns4o3][14], v4[kRuns4o3][3];
+  S H8[kRuns8o3][30], mono8[kRuns8o3][14], v8[kRuns8o3][3];
+  S H4[kRuns4o3][30], mono4[kRuns4o3][14], v4[kRuns4o3][3];
   int start8[kRuns8o3], start4[kRuns4o3];
   int off[288];           // pull shifts -n_i . strides (i * plane added in 64 bits)
 };
-cudaError_t launch_step3q_sym(const Tables3s3& tb, const Step3qArgs<double>& a, cudaStream_t st);
+template <typename S>
+cudaError_t launch_step3q_sym(const Tables3s3<S>& tb, const Step3qArgs<S>& a, cudaStream_t st);
 
 // FP64 step of the order-2 table in sign-orbit form (Tables3::mono filled)
-cudaError_t launch_step3_sym(const Tables3& tb, const Step3Args<double>& a, cudaStream_t st);
+template <typename S>
+cudaError_t launch_step3_sym(const Tables3& tb, const Step3Args<S>& a, cudaStream_t st);
 template <typename S>
 cudaError_t launch_init3(const Tables3& tb, const Init3Args<S>& a, cudaStream_t st);
 template <typename S>

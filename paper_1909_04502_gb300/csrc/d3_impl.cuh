@@ -318,6 +318,79 @@ __device__ __forceinline__ void mj_delta3(const Macro3f& M, float nr, float Tr, 
   }
 }
 
+// The collision frame from the 14 moment sums m = N0 Nx Ny Nz T00 T0x T0y
+// T0z Txx Txy Txz Tyy Tyz Tzz (of f in FP64 storage, of g = f - f_ref in FP32
+// storage): the moments Mk of the K-member basis that the equilibrium H Mk
+// needs (full moments in FP64, differences from the reference in FP32), and
+// tau^-1 U (zero where the cell has no Landau frame, which leaves it
+// unrelaxed).  Returns whether the frame exists.
+template <typename S, int K>
+__device__ __forceinline__ bool frame3(const S (&m)[14], const Scalars3& s, S (&Mk)[K], S& kU0, S (&kU)[3]) {
+  if constexpr (sizeof(S) == 8) {
+    const double N[4] = {m[0], m[1], m[2], m[3]};
+    const double Tm[4][4] = {{m[4], m[5], m[6], m[7]},
+                             {m[5], m[8], m[9], m[10]},
+                             {m[6], m[9], m[11], m[12]},
+                             {m[7], m[10], m[12], m[13]}};
+    const Macro3 M = landau3(N, Tm);
+    mj_full3<K>(M.n, M.T, M.U, Mk);
+    const double kt = M.ok ? 1.0 / s.tau : 0.0;
+    kU0 = kt * M.U[0];
+    kU[0] = kt * M.U[1];
+    kU[1] = kt * M.U[2];
+    kU[2] = kt * M.U[3];
+    return M.ok;
+  } else {
+    const float N[4] = {m[0], m[1], m[2], m[3]};
+    const float Tm[4][4] = {{m[4], m[5], m[6], m[7]},
+                            {m[5], m[8], m[9], m[10]},
+                            {m[6], m[9], m[11], m[12]},
+                            {m[7], m[10], m[12], m[13]}};
+    const Macro3f M = landau3f(N, Tm, s);
+    mj_delta3<K>(M, (float)s.n_ref, (float)s.T_ref, Mk);
+    const float kt = M.ok ? (float)(1.0 / s.tau) : 0.f;
+    kU0 = kt * M.U0;
+    kU[0] = kt * M.Ux;
+    kU[1] = kt * M.Uy;
+    kU[2] = kt * M.Uz;
+    return M.ok;
+  }
+}
+
+// Walsh-Hadamard transform in place: v[c] <- sum_s (-1)^{popcount(c & s)} v[s]
+template <typename S, int L>
+__device__ __forceinline__ void fwht(S (&v)[L]) {
+#pragma unroll
+  for (int hb = 1; hb < L; hb <<= 1)
+#pragma unroll
+    for (int q = 0; q < L; ++q)
+      if (!(q & hb)) {
+        const S u = v[q], w = v[q | hb];
+        v[q] = u + w;
+        v[q | hb] = u - w;
+      }
+}
+
+// the moment sums of a run of 8 from its transformed values F (F[c] = sum_s
+// chi_c(s) f_s) and its first member's monomials c (Tables3::mono order)
+template <typename S, typename C>
+__device__ __forceinline__ void moments_run8(const S (&F)[8], const C* c, S (&m)[14]) {
+  m[0] = fma((S)c[0], F[0], m[0]);
+  m[1] = fma((S)c[1], F[1], m[1]);
+  m[2] = fma((S)c[2], F[2], m[2]);
+  m[3] = fma((S)c[3], F[4], m[3]);
+  m[4] = fma((S)c[4], F[0], m[4]);
+  m[5] = fma((S)c[5], F[1], m[5]);
+  m[6] = fma((S)c[6], F[2], m[6]);
+  m[7] = fma((S)c[7], F[4], m[7]);
+  m[8] = fma((S)c[8], F[0], m[8]);
+  m[9] = fma((S)c[9], F[3], m[9]);
+  m[10] = fma((S)c[10], F[5], m[10]);
+  m[11] = fma((S)c[11], F[0], m[11]);
+  m[12] = fma((S)c[12], F[6], m[12]);
+  m[13] = fma((S)c[13], F[0], m[13]);
+}
+
 // periodic images of a cell (every side at least h: at most 26)
 __device__ __forceinline__ int cell_images(const Scalars3& s, int x, int y, int z, long long (&img)[26]) {
   int ix[2], iy[2], iz[2];

@@ -85,114 +85,102 @@ __global__ void __launch_bounds__(128) k_step3(const __grid_constant__ Tables3 t
   }
 }
 
-// The FP64 step in sign-orbit form.  Populations come in runs whose members
-// share p0 and |p| componentwise: 9 runs of 8 (member s negates the
-// components whose bit is set in s) and the pairs (+-3, 0, 0), (0, +-3, 0),
-// (0, 0, +-3).  Per run of 8, a Walsh-Hadamard transform of the pulled values
-// gives the sums F_c = sum_s chi_c(s) f_s over the sign characters c; each
-// moment of rank <= 2 needs one of them times the first member's monomial
-// (e.g. T^xy += a b F_xy).  The equilibrium rows of a run are the first row
-// with the sign chi_k(s) of each basis member k (checked exactly on the host),
-// so f^eq_s = sum over the seven characters of chi(s) C_chi, with C_chi the
-// first row's partial sums over the members of that character; the relaxation
-// rates follow from v_s . U = sx vx Ux + sy vy Uy + sz vz Uz.  About 110 FP64
-// operations per run of 8 against about 270 for eight rows.
+// The FP64 step in sign-orbit form (the kernel is written for either storage
+// type; with FP32 storage it measured 7 % slower than k_step3f, which is
+// bound by load latency rather than arithmetic, so only FP64 uses it).
+// Populations come in runs whose members share p0 and |p| componentwise:
+// 9 runs of 8 (member s negates the components whose bit is set in s) and
+// the pairs (+-3, 0, 0), (0, +-3, 0), (0, 0, +-3).  Per run of 8, a
+// Walsh-Hadamard transform of the pulled values gives the sums
+// F_c = sum_s chi_c(s) f_s over the sign characters c; each moment of rank
+// <= 2 needs one of them times the first member's monomial (e.g. T^xy += a b
+// F_xy).  The equilibrium rows of a run are the first row with the sign
+// chi_k(s) of each basis member k (checked exactly on the host), so f^eq_s =
+// sum over the seven characters of chi(s) C_chi, with C_chi the first row's
+// partial sums over the members of that character; the relaxation rates
+// follow from v_s . U = sx vx Ux + sy vy Uy + sz vz Uz.  About 110 operations
+// per run of 8 against about 270 for eight rows.
+template <typename S>
+__device__ __forceinline__ const S* row_H(const Tables3& tb, int i) {
+  if constexpr (sizeof(S) == 8) return tb.H[i];
+  else return tb.Hf[i];
+}
+template <typename S>
+__device__ __forceinline__ const S* row_v(const Tables3& tb, int i) {
+  if constexpr (sizeof(S) == 8) return tb.v[i];
+  else return tb.vf[i];
+}
+template <typename S>
+__device__ __forceinline__ const S* row_mono(const Tables3& tb, int r) {
+  static_assert(sizeof(S) == 8, "the monomial table is FP64");
+  return tb.mono[r];
+}
+
+template <typename S>
 __global__ void __launch_bounds__(128) k_step3s(const __grid_constant__ Tables3 tb,
-                                                const __grid_constant__ Step3Args<double> a) {
+                                                const __grid_constant__ Step3Args<S> a) {
   const Scalars3& s = a.s;
   const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y, z = blockIdx.z;
   if (x >= s.nx || y >= s.ny || z >= s.nz) return;
   const long long si = sidx3(s, x, y, z);
-  const double* __restrict__ base = a.fin + si;
+  const S* __restrict__ base = a.fin + si;
   // pass 1: moments m = N0 Nx Ny Nz T00 T0x T0y T0z Txx Txy Txz Tyy Tyz Tzz
-  double m[14];
+  S m[14];
 #pragma unroll
-  for (int k = 0; k < 14; ++k) m[k] = 0.0;
+  for (int k = 0; k < 14; ++k) m[k] = S(0);
 #pragma unroll 1
   for (int r = 0; r < 9; ++r) {
-    double f[8];
+    S f[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) f[q] = __ldg(base + tb.off[8 * r + q]);
-    // F[c]: sum_s (-1)^{popcount(s & c)} f_s
-#pragma unroll
-    for (int h = 1; h < 8; h <<= 1)
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (!(q & h)) {
-          const double u = f[q], v = f[q | h];
-          f[q] = u + v;
-          f[q | h] = u - v;
-        }
-    const double* c = tb.mono[r];
-    m[0] = fma(c[0], f[0], m[0]);
-    m[1] = fma(c[1], f[1], m[1]);
-    m[2] = fma(c[2], f[2], m[2]);
-    m[3] = fma(c[3], f[4], m[3]);
-    m[4] = fma(c[4], f[0], m[4]);
-    m[5] = fma(c[5], f[1], m[5]);
-    m[6] = fma(c[6], f[2], m[6]);
-    m[7] = fma(c[7], f[4], m[7]);
-    m[8] = fma(c[8], f[0], m[8]);
-    m[9] = fma(c[9], f[3], m[9]);
-    m[10] = fma(c[10], f[5], m[10]);
-    m[11] = fma(c[11], f[0], m[11]);
-    m[12] = fma(c[12], f[6], m[12]);
-    m[13] = fma(c[13], f[0], m[13]);
+    fwht(f);
+    moments_run8(f, row_mono<S>(tb, r), m);
   }
   // the axis pairs: N^a, T^0a odd, T^00, T^aa, N^0 even
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) {
-    const double fp = __ldg(base + tb.off[72 + 2 * ax]), fm = __ldg(base + tb.off[73 + 2 * ax]);
-    const double S = fp + fm, D = fp - fm;
-    const double* c = tb.mono[9 + ax];
+    const S fp = __ldg(base + tb.off[72 + 2 * ax]), fm = __ldg(base + tb.off[73 + 2 * ax]);
+    const S Sm = fp + fm, D = fp - fm;
+    const S* c = row_mono<S>(tb, 9 + ax);
     const int taa = ax == 0 ? 8 : (ax == 1 ? 11 : 13);
-    m[0] = fma(c[0], S, m[0]);
-    m[4] = fma(c[4], S, m[4]);
+    m[0] = fma(c[0], Sm, m[0]);
+    m[4] = fma(c[4], Sm, m[4]);
     m[1 + ax] = fma(c[1 + ax], D, m[1 + ax]);
     m[5 + ax] = fma(c[5 + ax], D, m[5 + ax]);
-    m[taa] = fma(c[taa], S, m[taa]);
+    m[taa] = fma(c[taa], Sm, m[taa]);
   }
-  const double N[4] = {m[0], m[1], m[2], m[3]};
-  const double Tm[4][4] = {{m[4], m[5], m[6], m[7]},
-                           {m[5], m[8], m[9], m[10]},
-                           {m[6], m[9], m[11], m[12]},
-                           {m[7], m[10], m[12], m[13]}};
-  const Macro3 M = landau3(N, Tm);
-  if (!M.ok) atomicAdd(a.status, 1ULL);
-  double Mm[14];
-  mj_moments3(M.n, M.T, M.U, Mm);
-  const double kt = M.ok ? 1.0 / s.tau : 0.0;
-  const double kU0 = kt * M.U[0], kUx = kt * M.U[1], kUy = kt * M.U[2], kUz = kt * M.U[3];
+  S Mm[14], kU0, kU[3];
+  if (!frame3(m, s, Mm, kU0, kU)) atomicAdd(a.status, 1ULL);
   long long img[26];
   const int nimg = cell_images(s, x, y, z, img);
-  double* __restrict__ out = a.fout;
+  S* __restrict__ out = a.fout;
   // pass 2: equilibrium, relaxation, store (the pulled values are read again)
 #pragma unroll 1
   for (int r = 0; r < 9; ++r) {
-    const double* H0 = tb.H[8 * r];
-    // partial sums over the basis members of each sign character
-    const double C0 = fma(H0[0], Mm[0], fma(H0[1], Mm[1], fma(H0[8], Mm[8], fma(H0[11], Mm[11], H0[13] * Mm[13]))));
-    const double Cx = fma(H0[2], Mm[2], H0[5] * Mm[5]);
-    const double Cy = fma(H0[3], Mm[3], H0[6] * Mm[6]);
-    const double Cz = fma(H0[4], Mm[4], H0[7] * Mm[7]);
-    const double Cxy = H0[9] * Mm[9], Cxz = H0[10] * Mm[10], Cyz = H0[12] * Mm[12];
-    // f^eq_s = C0 + sx Cx + sy Cy + sz Cz + sx sy Cxy + sx sz Cxz + sy sz Cyz
-    const double t0 = C0 + Cy, t1 = C0 - Cy, u0 = Cx + Cxy, u1 = Cx - Cxy;
-    const double P[4] = {t0 + u0, t0 - u0, t1 + u1, t1 - u1};
-    const double v0 = Cz + Cyz, v1 = Cz - Cyz;
-    const double Qz[4] = {v0 + Cxz, v0 - Cxz, v1 + Cxz, v1 - Cxz};
+    const S* H0 = row_H<S>(tb, 8 * r);
+    // partial sums over the basis members of each sign character, then
+    // f^eq_s = sum_c chi_c(s) C_c
+    S C[8];
+    C[0] = fma(H0[0], Mm[0], fma(H0[1], Mm[1], fma(H0[8], Mm[8], fma(H0[11], Mm[11], H0[13] * Mm[13]))));
+    C[1] = fma(H0[2], Mm[2], H0[5] * Mm[5]);
+    C[2] = fma(H0[3], Mm[3], H0[6] * Mm[6]);
+    C[4] = fma(H0[4], Mm[4], H0[7] * Mm[7]);
+    C[3] = H0[9] * Mm[9];
+    C[5] = H0[10] * Mm[10];
+    C[6] = H0[12] * Mm[12];
+    C[7] = S(0);
+    fwht(C);
     // tau^-1 (U0 - v_s . U)
-    const double* vb = tb.v[8 * r];
-    const double X = vb[0] * kUx, Y = vb[1] * kUy, Z = vb[2] * kUz;
-    const double r0 = kU0 - X, r1 = kU0 + X;
-    const double R[4] = {r0 - Y, r1 - Y, r0 + Y, r1 + Y};
+    const S* vb = row_v<S>(tb, 8 * r);
+    const S X = vb[0] * kU[0], Y = vb[1] * kU[1], Z = vb[2] * kU[2];
+    const S r0 = kU0 - X, r1 = kU0 + X;
+    const S R[4] = {r0 - Y, r1 - Y, r0 + Y, r1 + Y};
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int i = 8 * r + q;
-      const double feq = (q & 4) ? P[q & 3] - Qz[q & 3] : P[q & 3] + Qz[q & 3];
-      const double om = (q & 4) ? R[q & 3] + Z : R[q & 3] - Z;
-      const double f = __ldg(base + tb.off[i]);
-      const double g = fma(om, feq - f, f);
+      const S om = (q & 4) ? R[q & 3] + Z : R[q & 3] - Z;
+      const S f = __ldg(base + tb.off[i]);
+      const S g = fma(om, C[q] - f, f);
       const long long pl = (long long)i * s.plane;
       out[pl + si] = g;
       for (int mm = 0; mm < nimg; ++mm) out[pl + img[mm]] = g;
@@ -201,23 +189,22 @@ __global__ void __launch_bounds__(128) k_step3s(const __grid_constant__ Tables3 
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) {
     const int i0 = 72 + 2 * ax;
-    const double* H0 = tb.H[i0];
-    double Ce = 0.0, Co = 0.0;
+    const S* H0 = row_H<S>(tb, i0);
+    S Ce = S(0), Co = S(0);
 #pragma unroll
     for (int k = 0; k < 14; ++k) {
       // basis members odd in component ax: p_a, p0 p_a and the mixed p_a p_b
-      const int ex = kBasis3Exp[k][ax];
-      if (ex & 1) Co = fma(H0[k], Mm[k], Co);
+      if (kBasis3Exp[k][ax] & 1) Co = fma(H0[k], Mm[k], Co);
       else Ce = fma(H0[k], Mm[k], Ce);
     }
-    const double va = tb.v[i0][ax] * (ax == 0 ? kUx : (ax == 1 ? kUy : kUz));
+    const S va = row_v<S>(tb, i0)[ax] * kU[ax];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const int i = i0 + q;
-      const double feq = q ? Ce - Co : Ce + Co;
-      const double om = q ? kU0 + va : kU0 - va;
-      const double f = __ldg(base + tb.off[i]);
-      const double g = fma(om, feq - f, f);
+      const S feq = q ? Ce - Co : Ce + Co;
+      const S om = q ? kU0 + va : kU0 - va;
+      const S f = __ldg(base + tb.off[i]);
+      const S g = fma(om, feq - f, f);
       const long long pl = (long long)i * s.plane;
       out[pl + si] = g;
       for (int mm = 0; mm < nimg; ++mm) out[pl + img[mm]] = g;
@@ -362,11 +349,13 @@ cudaError_t launch_step3<double>(const Tables3& tb, const Step3Args<double>& a, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_step3_sym(const Tables3& tb, const Step3Args<double>& a, cudaStream_t st) {
+template <typename S>
+cudaError_t launch_step3_sym(const Tables3& tb, const Step3Args<S>& a, cudaStream_t st) {
   if (a.s.Q != 78) return cudaErrorInvalidValue;
-  k_step3s<<<grid3(a.s), dim3(32, 4), 0, st>>>(tb, a);
+  k_step3s<S><<<grid3(a.s), dim3(32, 4), 0, st>>>(tb, a);
   return cudaGetLastError();
 }
+template cudaError_t launch_step3_sym<double>(const Tables3&, const Step3Args<double>&, cudaStream_t);
 
 template <>
 cudaError_t launch_step3<float>(const Tables3& tb, const Step3Args<float>& a, cudaStream_t st) {

@@ -222,14 +222,17 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_step3q_cell(const __grid_c
   }
 }
 
-// FP64 storage in sign-orbit form, one thread per cell: the order-2 scheme
-// of k_step3s with the 30-member basis.  Runs of 8: a Walsh-Hadamard
-// transform of the pulled values gives the moment sums; the first H row's
-// partial sums over the eight parity classes of the basis (class of member k:
-// the parities of its x, y, z exponents), transformed back, give the eight
-// equilibrium values.  Runs of 4 do the same over their two non-zero
-// components (basis members odd in the zero component have H = 0 there).
-// About 5 k FP64 operations per cell against 16 k row by row.
+// Sign-orbit form, one thread per cell: the order-2 scheme of k_step3s with
+// the 30-member basis (written for either storage type; with FP32 storage it
+// measured 29 % slower than k_step3q_cell, whose bound is the latency of the
+// population loads, so only FP64 uses it).  Runs of
+// 8: a Walsh-Hadamard transform of the pulled values gives the moment sums;
+// the first H row's partial sums over the eight parity classes of the basis
+// (class of member k: the parities of its x, y, z exponents), transformed
+// back, give the eight equilibrium values.  Runs of 4 do the same over their
+// two non-zero components (basis members odd in the zero component have H = 0
+// there).  About 5 k operations per cell against 16 k row by row; the run
+// tables are kernel parameters.
 __device__ constexpr int kBasis3o3Par[30] = {
     // parity class (bit 0: x odd, bit 1: y odd, bit 2: z odd) of the members of
     // 1 | p0 px py pz | p0px p0py p0pz pxpx pxpy pxpz pypy pypz pzpz |
@@ -237,115 +240,75 @@ __device__ constexpr int kBasis3o3Par[30] = {
     0, 0, 1, 2, 4, 1, 2, 4, 0, 3, 5, 0, 6, 0, 0, 3, 5, 0, 6, 0, 1, 2, 4, 1, 7, 1, 2, 4, 2, 4};
 __device__ constexpr int kMask4o3[kRuns4o3] = {3, 5, 3, 5, 6, 6};
 
-__global__ void __launch_bounds__(128) k_step3qs(const __grid_constant__ Tables3s3 tb,
-                                                 const __grid_constant__ Step3qArgs<double> a) {
+template <typename S>
+__global__ void __launch_bounds__(128) k_step3qs(const __grid_constant__ Tables3s3<S> tb,
+                                                 const __grid_constant__ Step3qArgs<S> a) {
   const Scalars3& s = a.s;
   const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y, z = blockIdx.z;
   if (x >= s.nx || y >= s.ny || z >= s.nz) return;
   const long long si = sidx3(s, x, y, z);
-  const double* __restrict__ base = a.fin + si;
+  const S* __restrict__ base = a.fin + si;
   const long long P = s.plane;
   // pass 1: m = N0 Nx Ny Nz T00 T0x T0y T0z Txx Txy Txz Tyy Tyz Tzz
-  double m[14];
+  S m[14];
 #pragma unroll
-  for (int k = 0; k < 14; ++k) m[k] = 0.0;
+  for (int k = 0; k < 14; ++k) m[k] = S(0);
 #pragma unroll 1
   for (int r = 0; r < kRuns8o3; ++r) {
     const int i0 = tb.start8[r];
-    double f[8];
+    S f[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) f[q] = __ldg(base + (long long)(i0 + q) * P + tb.off[i0 + q]);
-#pragma unroll
-    for (int hb = 1; hb < 8; hb <<= 1)
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (!(q & hb)) {
-          const double u = f[q], v = f[q | hb];
-          f[q] = u + v;
-          f[q | hb] = u - v;
-        }
-    const double* c = tb.mono8[r];
-    m[0] = fma(c[0], f[0], m[0]);
-    m[1] = fma(c[1], f[1], m[1]);
-    m[2] = fma(c[2], f[2], m[2]);
-    m[3] = fma(c[3], f[4], m[3]);
-    m[4] = fma(c[4], f[0], m[4]);
-    m[5] = fma(c[5], f[1], m[5]);
-    m[6] = fma(c[6], f[2], m[6]);
-    m[7] = fma(c[7], f[4], m[7]);
-    m[8] = fma(c[8], f[0], m[8]);
-    m[9] = fma(c[9], f[3], m[9]);
-    m[10] = fma(c[10], f[5], m[10]);
-    m[11] = fma(c[11], f[0], m[11]);
-    m[12] = fma(c[12], f[6], m[12]);
-    m[13] = fma(c[13], f[0], m[13]);
+    fwht(f);
+    moments_run8(f, tb.mono8[r], m);
   }
 #pragma unroll
   for (int r = 0; r < kRuns4o3; ++r) {
     const int j = kMask4o3[r] & 1 ? 0 : 1, k = kMask4o3[r] & 4 ? 2 : 1;   // the non-zero components, j < k
     const int i0 = tb.start4[r];
-    double f[4];
+    S f[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) f[q] = __ldg(base + (long long)(i0 + q) * P + tb.off[i0 + q]);
-    const double a0 = f[0] + f[1], a1 = f[0] - f[1], a2 = f[2] + f[3], a3 = f[2] - f[3];
-    const double G0 = a0 + a2, Gj = a1 + a3, Gk = a0 - a2, Gjk = a1 - a3;
-    const double* c = tb.mono4[r];
+    fwht(f);                      // f = (sum, sum s_j, sum s_k, sum s_j s_k)
+    const S* c = tb.mono4[r];
     const int djj = j == 0 ? 8 : 11, dkk = k == 1 ? 11 : 13, djk = j == 0 ? (k == 1 ? 9 : 10) : 12;
-    m[0] = fma(c[0], G0, m[0]);
-    m[4] = fma(c[4], G0, m[4]);
-    m[1 + j] = fma(c[1 + j], Gj, m[1 + j]);
-    m[1 + k] = fma(c[1 + k], Gk, m[1 + k]);
-    m[5 + j] = fma(c[5 + j], Gj, m[5 + j]);
-    m[5 + k] = fma(c[5 + k], Gk, m[5 + k]);
-    m[djj] = fma(c[djj], G0, m[djj]);
-    m[dkk] = fma(c[dkk], G0, m[dkk]);
-    m[djk] = fma(c[djk], Gjk, m[djk]);
+    m[0] = fma(c[0], f[0], m[0]);
+    m[4] = fma(c[4], f[0], m[4]);
+    m[1 + j] = fma(c[1 + j], f[1], m[1 + j]);
+    m[1 + k] = fma(c[1 + k], f[2], m[1 + k]);
+    m[5 + j] = fma(c[5 + j], f[1], m[5 + j]);
+    m[5 + k] = fma(c[5 + k], f[2], m[5 + k]);
+    m[djj] = fma(c[djj], f[0], m[djj]);
+    m[dkk] = fma(c[dkk], f[0], m[dkk]);
+    m[djk] = fma(c[djk], f[3], m[djk]);
   }
-  const double N[4] = {m[0], m[1], m[2], m[3]};
-  const double Tm[4][4] = {{m[4], m[5], m[6], m[7]},
-                           {m[5], m[8], m[9], m[10]},
-                           {m[6], m[9], m[11], m[12]},
-                           {m[7], m[10], m[12], m[13]}};
-  const Macro3 M = landau3(N, Tm);
-  if (!M.ok) atomicAdd(a.status, 1ULL);
-  double Mm[kKo3];
-  mj_full3<kKo3>(M.n, M.T, M.U, Mm);
-  const double kt = M.ok ? 1.0 / s.tau : 0.0;
-  const double kU0 = kt * M.U[0], kU[3] = {kt * M.U[1], kt * M.U[2], kt * M.U[3]};
+  S Mm[kKo3], kU0, kU[3];
+  if (!frame3(m, s, Mm, kU0, kU)) atomicAdd(a.status, 1ULL);
   long long img[26];
   const int nimg = cell_images(s, x, y, z, img);
-  double* __restrict__ out = a.fout;
+  S* __restrict__ out = a.fout;
   // pass 2
 #pragma unroll 1
   for (int r = 0; r < kRuns8o3; ++r) {
     const int i0 = tb.start8[r];
-    const double* H0 = tb.H8[r];
-    double C[8];
+    const S* H0 = tb.H8[r];
+    S C[8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) C[c] = 0.0;
+    for (int c = 0; c < 8; ++c) C[c] = S(0);
 #pragma unroll
     for (int k = 0; k < kKo3; ++k) C[kBasis3o3Par[k]] = fma(H0[k], Mm[k], C[kBasis3o3Par[k]]);
-    // f^eq_s = sum_c (-1)^{popcount(s & c)} C_c
-#pragma unroll
-    for (int hb = 1; hb < 8; hb <<= 1)
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (!(q & hb)) {
-          const double u = C[q], v = C[q | hb];
-          C[q] = u + v;
-          C[q | hb] = u - v;
-        }
-    const double* vb = tb.v8[r];
-    const double X = vb[0] * kU[0], Y = vb[1] * kU[1], Z = vb[2] * kU[2];
-    const double r0 = kU0 - X, r1 = kU0 + X;
-    const double R[4] = {r0 - Y, r1 - Y, r0 + Y, r1 + Y};
+    fwht(C);                      // C[q] = f^eq of member q
+    const S* vb = tb.v8[r];
+    const S X = vb[0] * kU[0], Y = vb[1] * kU[1], Z = vb[2] * kU[2];
+    const S r0 = kU0 - X, r1 = kU0 + X;
+    const S R[4] = {r0 - Y, r1 - Y, r0 + Y, r1 + Y};
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int i = i0 + q;
-      const double om = (q & 4) ? R[q & 3] + Z : R[q & 3] - Z;
+      const S om = (q & 4) ? R[q & 3] + Z : R[q & 3] - Z;
       const long long pl = (long long)i * P;
-      const double f = __ldg(base + pl + tb.off[i]);
-      const double g = fma(om, C[q] - f, f);
+      const S f = __ldg(base + pl + tb.off[i]);
+      const S g = fma(om, C[q] - f, f);
       out[pl + si] = g;
       for (int mm = 0; mm < nimg; ++mm) out[pl + img[mm]] = g;
     }
@@ -354,25 +317,24 @@ __global__ void __launch_bounds__(128) k_step3qs(const __grid_constant__ Tables3
   for (int r = 0; r < kRuns4o3; ++r) {
     const int j = kMask4o3[r] & 1 ? 0 : 1, k = kMask4o3[r] & 4 ? 2 : 1;
     const int i0 = tb.start4[r];
-    const double* H0 = tb.H4[r];
-    double C[4] = {0.0, 0.0, 0.0, 0.0};
+    const S* H0 = tb.H4[r];
+    S C[4] = {S(0), S(0), S(0), S(0)};
 #pragma unroll
     for (int kk = 0; kk < kKo3; ++kk) {
       const int par = kBasis3o3Par[kk];
       const int c = ((par >> j) & 1) | (((par >> k) & 1) << 1);
       C[c] = fma(H0[kk], Mm[kk], C[c]);
     }
-    const double b0 = C[0] + C[1], b1 = C[0] - C[1], b2 = C[2] + C[3], b3 = C[2] - C[3];
-    const double feq[4] = {b0 + b2, b1 + b3, b0 - b2, b1 - b3};
-    const double* vb = tb.v4[r];
-    const double Xj = vb[j] * kU[j], Xk = vb[k] * kU[k];
-    const double om[4] = {kU0 - Xj - Xk, kU0 + Xj - Xk, kU0 - Xj + Xk, kU0 + Xj + Xk};
+    fwht(C);                      // C[q] = f^eq of member q (bit 0: j negated, bit 1: k negated)
+    const S* vb = tb.v4[r];
+    const S Xj = vb[j] * kU[j], Xk = vb[k] * kU[k];
+    const S om[4] = {kU0 - Xj - Xk, kU0 + Xj - Xk, kU0 - Xj + Xk, kU0 + Xj + Xk};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int i = i0 + q;
       const long long pl = (long long)i * P;
-      const double f = __ldg(base + pl + tb.off[i]);
-      const double g = fma(om[q], feq[q] - f, f);
+      const S f = __ldg(base + pl + tb.off[i]);
+      const S g = fma(om[q], C[q] - f, f);
       out[pl + si] = g;
       for (int mm = 0; mm < nimg; ++mm) out[pl + img[mm]] = g;
     }
@@ -479,11 +441,13 @@ cudaError_t launch_step3q(const Step3qArgs<S>& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_step3q_sym(const Tables3s3& tb, const Step3qArgs<double>& a, cudaStream_t st) {
+template <typename S>
+cudaError_t launch_step3q_sym(const Tables3s3<S>& tb, const Step3qArgs<S>& a, cudaStream_t st) {
   if (a.s.Q != kQo3) return cudaErrorInvalidValue;
-  k_step3qs<<<grid3q(a.s), dim3(32, 4), 0, st>>>(tb, a);
+  k_step3qs<S><<<grid3q(a.s), dim3(32, 4), 0, st>>>(tb, a);
   return cudaGetLastError();
 }
+template cudaError_t launch_step3q_sym<double>(const Tables3s3<double>&, const Step3qArgs<double>&, cudaStream_t);
 
 template <typename S>
 cudaError_t launch_init3q(const Init3qArgs<S>& a, cudaStream_t st) {
