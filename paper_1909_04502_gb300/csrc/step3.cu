@@ -1,9 +1,10 @@
-// (3+1)-dimensional massless RLBM step, order 2 (Sec. 5-6 with d = 3), FP64
-// storage and arithmetic (k_step3) or FP32 storage (k_step3f):
+// (3+1)-dimensional massless RLBM step, order 2 (Sec. 5-6 with d = 3):
 // on-lattice pull, the moments N^a and T^ab, the Landau frame of the 4 x 4
 // mixed tensor (Sec. 4), n = U.N, T = eps / (3n) (Eq. ultra-relativistic-eos,
 // d = 3), f^eq = H M(n, U, T) (Eq. mj-discrete-feq), Anderson-Witting
-// relaxation, store with the periodic halo images.
+// relaxation, store with the periodic halo images.  Kernels: k_step3s (FP64,
+// the table in sign-orbit form), k_step3f (FP32 storage of g = f - f_ref),
+// k_step3 (FP64, any population order).
 //
 // Layout: one plane per population, cell (x, y, z) at
 //   (z + h) * slab + (y + h) * pitch + (x + px),  slab = (ny + 2h) * pitch,

@@ -1,11 +1,18 @@
 // (3+1)-dimensional massless RLBM step at order 3 (App. H, v0 = 1/sqrt(41),
-// Q = 288, K = 30): the step of step3.cu with four threads per cell.  Each
-// thread pulls and relaxes 72 populations (i = lane + 4 j); the moment sums
-// are combined across the four threads with warp shuffles, and each of them
-// solves the Landau frame.  The stencil tables (p, v, the 288 x 30
-// equilibrium matrix and the pull shifts) live in global memory and are
-// staged once per block in shared memory; blocks are persistent and walk
-// rows of 32 cells.
+// Q = 288, K = 30), the order-2 step of step3.cu with the 30-member basis.
+// Three kernels:
+// - k_step3qs (FP64, the table in sign-orbit form): one thread per cell over
+//   33 runs of 8 and 6 runs of 4 sign variants, the run tables as kernel
+//   parameters;
+// - k_step3q_cell (FP32 storage of g = f - f_ref): one thread per cell, a warp
+//   per 32-cell row segment, the 288 x 30 table in shared memory read by
+//   broadcast 16-byte loads;
+// - k_step3q (either storage type, any population order): four threads per
+//   cell, 72 populations each (i = lane + 4 j), the moment sums combined with
+//   warp shuffles, the tables staged in shared memory, persistent blocks
+//   walking rows of 32 cells.
+// Pull offsets are the plane offset i * plane (64-bit) plus a per-population
+// shift, since 288 planes of a large grid exceed 2^31 elements.
 #include <cuda_runtime.h>
 
 #include <algorithm>
