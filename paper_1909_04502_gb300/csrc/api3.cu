@@ -25,8 +25,8 @@ struct rlbm3_handle {
   unsigned long long* status = nullptr;
   cudaStream_t stream = nullptr;
   std::vector<double> fref;       // reference populations (FP32 storage)
-  bool sym = false;               // order 2 in sign-orbit form (FP64 step)
-  // order 3 in sign-orbit form (FP64 step), or null
+  bool sym = false;               // order 2 in sign-orbit form (the FP64 step needs it)
+  // order 3 in sign-orbit form (the FP64 step needs it), or null
   std::unique_ptr<Tables3s3<double>> ts3d;
   // order 3: tables in device memory
   void* dH = nullptr;             // Q x 30, storage precision
@@ -196,15 +196,11 @@ int rlbm3_create(int nx, int ny, int nz, double tau, int order, int precision, v
       for (int u = 0; u < 3; ++u) v[3 * i + u] = h->q.p[4 * i + 1 + u] / h->q.p[4 * i];
     }
     int rc = RLBM_OK;
-    if (h->elem == 4) {
+    if (h->elem == 4) {         // the FP32 step's tables (the FP64 step takes its run tables as parameters)
       std::vector<float> Hf(h->q.H.begin(), h->q.H.end()), cf(c.begin(), c.end()), vf(v.begin(), v.end());
       if (!rc) rc = upload(&h->dH, Hf);
       if (!rc) rc = upload(&h->dc, cf);
       if (!rc) rc = upload(&h->dv, vf);
-    } else {
-      if (!rc) rc = upload(&h->dH, h->q.H);
-      if (!rc) rc = upload(&h->dc, c);
-      if (!rc) rc = upload(&h->dv, v);
     }
     if (!rc) rc = upload((void**)&h->dHd, h->q.H);
     if (!rc) rc = upload((void**)&h->dcd, c);
@@ -226,6 +222,9 @@ int rlbm3_create(int nx, int ny, int nz, double tau, int order, int precision, v
       for (int k = 0; k < 14; ++k) h->tb->mono[r][k] = mono[k];
     }
   }
+  // the FP64 kernels take the table in sign-orbit form (checked exactly above)
+  if (h->elem == 8 && (order == 2 ? !h->sym : !h->ts3d))
+    return fail3(nullptr, RLBM_ERR_QUADRATURE, "3-d table not in sign-orbit form");
   for (int i = 0; i < s.Q && order == 2; ++i) {
     for (int u = 0; u < 4; ++u) h->tb->c[i][u] = h->q.p[4 * i + u];
     for (int u = 0; u < 3; ++u) h->tb->v[i][u] = h->q.p[4 * i + 1 + u] / h->q.p[4 * i];
@@ -322,18 +321,18 @@ int rlbm3_step(rlbm3_handle* h, int nsteps) {
       if (h->elem == 4) {
         Step3qArgs<float> a{(const float*)h->buf[h->cur], (float*)h->buf[h->cur ^ 1], h->status, h->sc,
                             (const float*)h->dH, (const float*)h->dc, (const float*)h->dv, h->doff};
-        e = launch_step3q<float>(a, h->stream);
+        e = launch_step3q_cell(a, h->stream);
       } else {
         Step3qArgs<double> a{(const double*)h->buf[h->cur], (double*)h->buf[h->cur ^ 1], h->status, h->sc,
                              (const double*)h->dH, (const double*)h->dc, (const double*)h->dv, h->doff};
-        e = h->ts3d ? launch_step3q_sym(*h->ts3d, a, h->stream) : launch_step3q<double>(a, h->stream);
+        e = launch_step3q_sym(*h->ts3d, a, h->stream);
       }
     } else if (h->elem == 4) {
       Step3Args<float> a{(const float*)h->buf[h->cur], (float*)h->buf[h->cur ^ 1], h->status, h->sc};
-      e = launch_step3<float>(*h->tb, a, h->stream);
+      e = launch_step3f(*h->tb, a, h->stream);
     } else {
       Step3Args<double> a{(const double*)h->buf[h->cur], (double*)h->buf[h->cur ^ 1], h->status, h->sc};
-      e = h->sym ? launch_step3_sym(*h->tb, a, h->stream) : launch_step3<double>(*h->tb, a, h->stream);
+      e = launch_step3_sym(*h->tb, a, h->stream);
     }
     if (e != cudaSuccess) return cuda_fail3(h, e, "step kernel");
     h->cur ^= 1;

@@ -88,15 +88,15 @@ struct Fields3qArgs {
   const double* fref;   // Q
 };
 
-template <typename S>
-cudaError_t launch_step3q(const Step3qArgs<S>& a, cudaStream_t st);
+// order 3, FP32 storage (k_step3q_cell)
+cudaError_t launch_step3q_cell(const Step3qArgs<float>& a, cudaStream_t st);
 template <typename S>
 cudaError_t launch_init3q(const Init3qArgs<S>& a, cudaStream_t st);
 template <typename S>
 cudaError_t launch_fields3q(const Fields3qArgs<S>& a, cudaStream_t st);
 
-template <typename S>
-cudaError_t launch_step3(const Tables3& tb, const Step3Args<S>& a, cudaStream_t st);
+// order 2, FP32 storage (k_step3f)
+cudaError_t launch_step3f(const Tables3& tb, const Step3Args<float>& a, cudaStream_t st);
 // The order-3 table in sign-orbit form: 33 runs of 8 and 6 runs of 4 (the
 // (5, 4, 0) patterns, non-zero components x y, x z, x y, x z, y z, y z), each
 // run's first member's equilibrium row, moment monomials (as Tables3::mono)

@@ -3,8 +3,7 @@
 // mixed tensor (Sec. 4), n = U.N, T = eps / (3n) (Eq. ultra-relativistic-eos,
 // d = 3), f^eq = H M(n, U, T) (Eq. mj-discrete-feq), Anderson-Witting
 // relaxation, store with the periodic halo images.  Kernels: k_step3s (FP64,
-// the table in sign-orbit form), k_step3f (FP32 storage of g = f - f_ref),
-// k_step3 (FP64, any population order).
+// the table in sign-orbit form) and k_step3f (FP32 storage of g = f - f_ref).
 //
 // Layout: one plane per population, cell (x, y, z) at
 //   (z + h) * slab + (y + h) * pitch + (x + px),  slab = (ny + 2h) * pitch,
@@ -23,68 +22,6 @@ namespace {
 __device__ constexpr int kBasis3Exp[14][3] = {{0, 0, 0}, {0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1},
                                               {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0}, {1, 1, 0},
                                               {1, 0, 1}, {0, 2, 0}, {0, 1, 1}, {0, 0, 2}};
-
-template <int QT>
-__global__ void __launch_bounds__(128) k_step3(const __grid_constant__ Tables3 tb,
-                                               const __grid_constant__ Step3Args<double> a) {
-  const Scalars3& s = a.s;
-  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y, z = blockIdx.z;
-  if (x >= s.nx || y >= s.ny || z >= s.nz) return;
-  const long long si = sidx3(s, x, y, z);
-  const double* __restrict__ base = a.fin + si;
-  // pass 1: pull and moments
-  double N[4] = {0.0, 0.0, 0.0, 0.0}, Tm[4][4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) Tm[u][v] = 0.0;
-#pragma unroll 6
-  for (int i = 0; i < QT; ++i) {
-    const double f = __ldg(base + tb.off[i]);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const double fu = f * tb.c[i][u];
-      N[u] += fu;
-#pragma unroll
-      for (int v = u; v < 4; ++v) Tm[u][v] = fma(fu, tb.c[i][v], Tm[u][v]);
-    }
-  }
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int v = 0; v < u; ++v) Tm[u][v] = Tm[v][u];
-  const Macro3 M = landau3(N, Tm);
-  if (!M.ok) atomicAdd(a.status, 1ULL);
-  double Mm[14];
-  mj_moments3(M.n, M.T, M.U, Mm);
-  const double kt = M.ok ? 1.0 / s.tau : 0.0;
-  // halo images of this cell: every side is at least h long, so each axis
-  // gives at most two images (c + n, c - n) and a cell at most 3^3 - 1 = 26
-  int ix[2], iy[2], iz[2];
-  const int nx2 = images1(x, s.nx, s.h, ix), ny2 = images1(y, s.ny, s.h, iy), nz2 = images1(z, s.nz, s.h, iz);
-  long long img[26];
-  int nimg = 0;
-  for (int cz = -1; cz < nz2; ++cz)
-    for (int cy = -1; cy < ny2; ++cy)
-      for (int cx = -1; cx < nx2; ++cx) {
-        if (cx < 0 && cy < 0 && cz < 0) continue;
-        img[nimg++] = sidx3(s, cx < 0 ? x : ix[cx], cy < 0 ? y : iy[cy], cz < 0 ? z : iz[cz]);
-      }
-  // pass 2: equilibrium, relaxation, store (the pulled value is read again)
-  double* __restrict__ out = a.fout;
-#pragma unroll 2
-  for (int i = 0; i < QT; ++i) {
-    const double f = __ldg(base + tb.off[i]);
-    double feq = 0.0;
-#pragma unroll
-    for (int k = 0; k < 14; ++k) feq = fma(tb.H[i][k], Mm[k], feq);
-    const double om = kt * (M.U[0] - tb.v[i][0] * M.U[1] - tb.v[i][1] * M.U[2] - tb.v[i][2] * M.U[3]);
-    const double g = fma(om, feq - f, f);
-    const long long pl = (long long)i * s.plane;
-    out[pl + si] = g;
-    for (int m = 0; m < nimg; ++m) out[pl + img[m]] = g;
-  }
-}
 
 // The FP64 step in sign-orbit form (the kernel is written for either storage
 // type; with FP32 storage it measured 7 % slower than k_step3f, which is
@@ -346,13 +283,6 @@ dim3 grid3(const Scalars3& s) { return dim3((s.nx + 31) / 32, (s.ny + 3) / 4, s.
 
 }  // namespace
 
-template <>
-cudaError_t launch_step3<double>(const Tables3& tb, const Step3Args<double>& a, cudaStream_t st) {
-  if (a.s.Q != 78) return cudaErrorInvalidValue;
-  k_step3<78><<<grid3(a.s), dim3(32, 4), 0, st>>>(tb, a);
-  return cudaGetLastError();
-}
-
 template <typename S>
 cudaError_t launch_step3_sym(const Tables3& tb, const Step3Args<S>& a, cudaStream_t st) {
   if (a.s.Q != 78) return cudaErrorInvalidValue;
@@ -361,8 +291,7 @@ cudaError_t launch_step3_sym(const Tables3& tb, const Step3Args<S>& a, cudaStrea
 }
 template cudaError_t launch_step3_sym<double>(const Tables3&, const Step3Args<double>&, cudaStream_t);
 
-template <>
-cudaError_t launch_step3<float>(const Tables3& tb, const Step3Args<float>& a, cudaStream_t st) {
+cudaError_t launch_step3f(const Tables3& tb, const Step3Args<float>& a, cudaStream_t st) {
   if (a.s.Q != 78) return cudaErrorInvalidValue;
   k_step3f<78><<<grid3(a.s), dim3(32, 4), 0, st>>>(tb, a);
   return cudaGetLastError();

@@ -1,16 +1,14 @@
 // (3+1)-dimensional massless RLBM step at order 3 (App. H, v0 = 1/sqrt(41),
 // Q = 288, K = 30), the order-2 step of step3.cu with the 30-member basis.
-// Three kernels:
+// Two kernels:
 // - k_step3qs (FP64, the table in sign-orbit form): one thread per cell over
 //   33 runs of 8 and 6 runs of 4 sign variants, the run tables as kernel
 //   parameters;
 // - k_step3q_cell (FP32 storage of g = f - f_ref): one thread per cell, a warp
 //   per 32-cell row segment, the 288 x 30 table in shared memory read by
-//   broadcast 16-byte loads;
-// - k_step3q (either storage type, any population order): four threads per
-//   cell, 72 populations each (i = lane + 4 j), the moment sums combined with
-//   warp shuffles, the tables staged in shared memory, persistent blocks
-//   walking rows of 32 cells.
+//   broadcast 16-byte loads.
+// (An earlier form with four threads per cell, 72 populations each and the
+// moment sums combined by warp shuffles, ran 3-6x slower than these.)
 // Pull offsets are the plane offset i * plane (64-bit) plus a per-population
 // shift, since 288 planes of a large grid exceed 2^31 elements.
 #include <cuda_runtime.h>
@@ -23,115 +21,12 @@ namespace rlbm {
 
 namespace {
 
-constexpr int kQo3 = 288, kKo3 = 30, kPer = kQo3 / 4;
-
-template <typename S>
-struct SharedTables3 {
-  S H[kQo3][kKo3];
-  S c[kQo3][4];
-  S v[kQo3][3];
-  int off[kQo3];
-};
-
-template <typename S>
-__global__ void __launch_bounds__(128) k_step3q(const __grid_constant__ Step3qArgs<S> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  SharedTables3<S>& t = *reinterpret_cast<SharedTables3<S>*>(smem_raw);
-  const Scalars3& s = a.s;
-  for (int e = threadIdx.x; e < kQo3 * kKo3; e += blockDim.x) (&t.H[0][0])[e] = a.H[e];
-  for (int e = threadIdx.x; e < kQo3 * 4; e += blockDim.x) (&t.c[0][0])[e] = a.c[e];
-  for (int e = threadIdx.x; e < kQo3 * 3; e += blockDim.x) (&t.v[0][0])[e] = a.v[e];
-  for (int e = threadIdx.x; e < kQo3; e += blockDim.x) t.off[e] = a.off[e];
-  __syncthreads();
-  const int lane = threadIdx.x & 3, cell = threadIdx.x >> 2;
-  const int nxs = (s.nx + 31) / 32;
-  const long long nseg = (long long)nxs * s.ny * s.nz;
-  for (long long seg = blockIdx.x; seg < nseg; seg += gridDim.x) {
-    const int xs = (int)(seg % nxs);
-    const int y = (int)((seg / nxs) % s.ny), z = (int)(seg / ((long long)nxs * s.ny));
-    const int x = xs * 32 + cell;
-    const bool active = x < s.nx;
-    const long long si = sidx3(s, active ? x : s.nx - 1, y, z);   // inactive lanes read a valid cell
-    const S* __restrict__ base = a.fin + si;
-    // moments: partial sums over this thread's populations, then across the quad
-    S N[4] = {S(0), S(0), S(0), S(0)}, Tm[4][4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int w = 0; w < 4; ++w) Tm[u][w] = S(0);
-#pragma unroll 4
-    for (int j = 0; j < kPer; ++j) {
-      const int i = lane + 4 * j;
-      const S g = __ldg(base + (long long)i * s.plane + t.off[i]);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const S gu = g * t.c[i][u];
-        N[u] += gu;
-#pragma unroll
-        for (int w = u; w < 4; ++w) Tm[u][w] = fma(gu, t.c[i][w], Tm[u][w]);
-      }
-    }
-#pragma unroll
-    for (int m = 1; m <= 2; m <<= 1) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        N[u] += __shfl_xor_sync(0xffffffffu, N[u], m);
-#pragma unroll
-        for (int w = u; w < 4; ++w) Tm[u][w] += __shfl_xor_sync(0xffffffffu, Tm[u][w], m);
-      }
-    }
-    // Landau frame, equilibrium moments
-    S Mk[kKo3];
-    bool ok;
-    S U0, Ux, Uy, Uz, kt;
-    if constexpr (sizeof(S) == 8) {
-      double Nd[4], Td[4][4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        Nd[u] = N[u];
-#pragma unroll
-        for (int w = 0; w < 4; ++w) Td[u][w] = u <= w ? Tm[u][w] : Tm[w][u];
-      }
-      const Macro3 M = landau3(Nd, Td);
-      ok = M.ok;
-      double Md[kKo3];
-      mj_full3<kKo3>(M.n, M.T, M.U, Md);
-#pragma unroll
-      for (int k = 0; k < kKo3; ++k) Mk[k] = Md[k];
-      U0 = M.U[0]; Ux = M.U[1]; Uy = M.U[2]; Uz = M.U[3];
-    } else {
-      const Macro3f M = landau3f(N, Tm, s);
-      ok = M.ok;
-      mj_delta3<kKo3>(M, (float)s.n_ref, (float)s.T_ref, Mk);
-      U0 = M.U0; Ux = M.Ux; Uy = M.Uy; Uz = M.Uz;
-    }
-    if (active && lane == 0 && !ok) atomicAdd(a.status, 1ULL);
-    kt = ok ? (S)(1.0 / s.tau) : S(0);
-    long long img[26];
-    const int nimg = active ? cell_images(s, x, y, z, img) : 0;
-    // equilibrium, relaxation and store of this thread's populations
-#pragma unroll 2
-    for (int j = 0; j < kPer; ++j) {
-      const int i = lane + 4 * j;
-      const long long pl = (long long)i * s.plane;
-      const S g = __ldg(base + pl + t.off[i]);
-      S geq = S(0);
-#pragma unroll
-      for (int k = 0; k < kKo3; ++k) geq = fma(t.H[i][k], Mk[k], geq);
-      const S om = kt * (U0 - t.v[i][0] * Ux - t.v[i][1] * Uy - t.v[i][2] * Uz);
-      const S gn = fma(om, geq - g, g);
-      if (active) {
-        a.fout[pl + si] = gn;
-        for (int m = 0; m < nimg; ++m) a.fout[pl + img[m]] = gn;
-      }
-    }
-  }
-}
+constexpr int kQo3 = 288, kKo3 = 30;
 
 // FP32 storage: one thread per cell, a warp per row segment of 32 cells.
-// The four threads per cell of k_step3q would each repeat the FP64 polish of
-// the Landau root and read one table entry per FMA; here every thread of a
-// warp reads the same table row, so a 16-byte shared load broadcasts four
+// With four threads per cell each thread would repeat the FP64 polish of the
+// Landau root and read one table entry per FMA; here every thread of a warp
+// reads the same table row, so a 16-byte shared load broadcasts four
 // entries of H (rows padded to 32 with zero columns, Mk[30..31] = 0) and the
 // Landau solve runs once per cell.  The populations are read twice (moments,
 // then relaxation); the second read mostly finds them in L2.
@@ -429,23 +324,9 @@ cudaError_t launch_cell(const Step3qArgs<float>& a, cudaStream_t st) {
 // 192^3 the fastest of 8-40 warps per SM and load batches of 4-16 (fewer
 // warps hide less latency, more of them push the second read of the
 // populations out of L2).
-cudaError_t launch_step3q_cell(const Step3qArgs<float>& a, cudaStream_t st) { return launch_cell<5, 8, 4>(a, st); }
-
-template <typename S>
-cudaError_t launch_step3q(const Step3qArgs<S>& a, cudaStream_t st) {
+cudaError_t launch_step3q_cell(const Step3qArgs<float>& a, cudaStream_t st) {
   if (a.s.Q != kQo3) return cudaErrorInvalidValue;
-  if constexpr (sizeof(S) == 4) return launch_step3q_cell(a, st);
-  const int smem = (int)sizeof(SharedTables3<S>);
-  cudaError_t e = cudaFuncSetAttribute(k_step3q<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0, per = 0;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step3q<S>, 128, smem)) != cudaSuccess) return e;
-  const long long nseg = (long long)((a.s.nx + 31) / 32) * a.s.ny * a.s.nz;
-  const long long grid = std::min<long long>(nseg, (long long)sms * (per > 0 ? per : 1));
-  k_step3q<S><<<(unsigned)grid, 128, smem, st>>>(a);
-  return cudaGetLastError();
+  return launch_cell<5, 8, 4>(a, st);
 }
 
 template <typename S>
@@ -468,8 +349,6 @@ cudaError_t launch_fields3q(const Fields3qArgs<S>& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template cudaError_t launch_step3q<float>(const Step3qArgs<float>&, cudaStream_t);
-template cudaError_t launch_step3q<double>(const Step3qArgs<double>&, cudaStream_t);
 template cudaError_t launch_init3q<float>(const Init3qArgs<float>&, cudaStream_t);
 template cudaError_t launch_init3q<double>(const Init3qArgs<double>&, cudaStream_t);
 template cudaError_t launch_fields3q<float>(const Fields3qArgs<float>&, cudaStream_t);
