@@ -280,6 +280,72 @@ def test_d3_tables_come_in_sign_orbits(rl, order):
         assert masks == [7] * 9 + [1, 2, 4]
 
 
+def _cuda_int_table(path, name):
+    """The integers of a brace-initialised constant table in a CUDA source."""
+    import re as _re
+    src = open(path).read()
+    m = _re.search(name + r"\[[^=]*=\s*\{(.*?)\};", src, _re.S)
+    body = _re.sub(r"//[^\n]*", "", m.group(1))
+    return [int(t) for t in _re.findall(r"-?\d+", body)]
+
+
+def test_sign_orbit_tables_of_the_kernels_match_the_basis():
+    """The parity tables compiled into the (3+1)-d sign-orbit kernels are the
+    parities of the basis members' x, y, z exponents."""
+    csrc = os.path.join(os.path.dirname(__file__), "..", "paper_1909_04502_gb300", "csrc")
+    par = _cuda_int_table(os.path.join(csrc, "step3q.cu"), "kBasis3o3Par")
+    want = [(b[1] & 1) | ((b[2] & 1) << 1) | ((b[3] & 1) << 2) for b in _D3_BASIS]
+    assert par == want
+    exp2 = _cuda_int_table(os.path.join(csrc, "step3.cu"), "kBasis3Exp")
+    assert exp2 == [e for b in _D3_BASIS[:14] for e in b[1:]]
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_sign_orbit_evaluation_equals_row_by_row(rl, order):
+    """The sign-orbit kernels' algebra on the library's tables: per run, the
+    Walsh-Hadamard transform of the populations times the first member's
+    monomials gives the moments N^a, T^ab, and the transformed parity-class
+    sums of the first H row give every member's f^eq; both agree with the
+    row-by-row sums to rounding."""
+    d = rl.plan3(order)
+    n, p, H, K = d["n"], d["p"], d["H"], d["K"]
+    basis = np.array(_D3_BASIS[:K])
+    cls = (basis[:, 1] & 1) | ((basis[:, 2] & 1) << 1) | ((basis[:, 3] & 1) << 2)
+    rng = np.random.default_rng(order)
+    f = rng.uniform(0.1, 1.0, d["Q"])
+    M = rng.normal(size=K)
+    N_row = p.T @ f
+    T_row = np.einsum("qa,qb,q->ab", p, p, f)
+    feq_row = H @ M
+    N_orb, T_orb, feq_orb = np.zeros(4), np.zeros((4, 4)), np.zeros(d["Q"])
+    i = 0
+    while i < d["Q"]:
+        mask = sum(1 << k for k in range(3) if n[i][k])
+        members = [sg for sg in range(8) if not (sg & ~mask)]
+        L = len(members)
+        # characters chi_c(s) = (-1)^popcount(c & s) over the run's members
+        chi = np.array([[(-1) ** bin(c & sg).count("1") for sg in members] for c in members], dtype=float)
+        F = chi @ f[i:i + L]
+        Fc = dict(zip(members, F))
+        p0 = p[i]
+        for a in range(4):
+            ca = 0 if a == 0 else 1 << (a - 1)
+            N_orb[a] += p0[a] * Fc.get(ca, 0.0)
+            for b in range(4):
+                cb = 0 if b == 0 else 1 << (b - 1)
+                T_orb[a, b] += p0[a] * p0[b] * Fc.get(ca ^ cb, 0.0)
+        C = {c: 0.0 for c in members}
+        for k in range(K):
+            c = cls[k] & mask
+            C[c] += H[i, k] * M[k]
+        for j, sg in enumerate(members):
+            feq_orb[i + j] = sum((-1) ** bin(c & sg).count("1") * C[c] for c in members)
+        i += L
+    assert np.allclose(N_orb, N_row, rtol=1e-13, atol=1e-13 * np.abs(N_row).max())
+    assert np.allclose(T_orb, T_row, rtol=1e-13, atol=1e-13 * np.abs(T_row).max())
+    assert np.allclose(feq_orb, feq_row, rtol=1e-12, atol=1e-13 * np.abs(feq_row).max())
+
+
 def test_d3_plan_rejects_other_orders(rl):
     with pytest.raises(rl.RLBMError):
         rl.plan3(4)
