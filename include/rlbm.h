@@ -359,7 +359,10 @@ int rlbm3_plan(int order, int* Q, int* K, int* nvec, double* p, double* w, doubl
  * f_ref the equilibrium at n = T = 1 at rest; the Landau root is corrected,
  * and n, its difference from 1, eps and T are evaluated, in FP64).  Each side
  * at least the halo width (3, or 6 at order 3) and nx*ny*nz <= 2^28.
- * Synchronous. */
+ * The FP64 step evaluates the table in sign-orbit form (runs of sign
+ * variants whose equilibrium rows differ only by the basis members' signs);
+ * RLBM_ERR_QUADRATURE if that identity does not hold exactly (the built-in
+ * tables satisfy it).  Synchronous. */
 int rlbm3_create(int nx, int ny, int nz, double tau, int order, int precision, void* stream,
                  rlbm3_handle** out);
 void rlbm3_destroy(rlbm3_handle* h);
