@@ -18,7 +18,7 @@ def rl():
     return rlbm
 
 
-CONFIGS = [
+INSTANCES = [
     dict(nx=37, ny=23, tau=0.7),
     dict(nx=64, ny=64, tau=1.3, m=1.0),
     dict(nx=50, ny=70, tau=1.9, m=10.0),
@@ -36,13 +36,13 @@ def _fields(c, seed):
 
 
 def test_batched_step_is_bitwise_equal_to_plain(rl):
-    batch = rl.Batch([dict(c, precision="fp32") for c in CONFIGS])
+    batch = rl.Batch([dict(c, precision="fp32") for c in INSTANCES])
     plain = []
-    for i, c in enumerate(CONFIGS):
+    for i, c in enumerate(INSTANCES):
         c = dict(c)
         nx, ny = c.pop("nx"), c.pop("ny")
         lat = rl.Lattice(nx, ny, precision="fp32", **c)
-        f = _fields(CONFIGS[i], seed=100 + i)
+        f = _fields(INSTANCES[i], seed=100 + i)
         lat.init(*f)
         batch[i].init(*f)
         plain.append(lat)
@@ -68,9 +68,9 @@ def test_batched_step_is_bitwise_equal_to_plain(rl):
 
 
 def test_mixed_batch_and_handle_steps_stay_consistent(rl):
-    batch = rl.Batch([dict(c, precision="fp32") for c in CONFIGS[:3]])
+    batch = rl.Batch([dict(c, precision="fp32") for c in INSTANCES[:3]])
     ref = []
-    for i, c in enumerate(CONFIGS[:3]):
+    for i, c in enumerate(INSTANCES[:3]):
         f = _fields(c, seed=7 + i)
         batch[i].init(*f)
         cc = dict(c)
@@ -112,7 +112,7 @@ def test_barrier_timeout_is_reported_not_hung(rl):
 
 
 def test_autotuner_picks_a_valid_configuration(rl):
-    batch = rl.Batch([dict(c, precision="fp32") for c in CONFIGS])
+    batch = rl.Batch([dict(c, precision="fp32") for c in INSTANCES])
     shape, grid, ms = batch.tune(trial_steps=2)
     info = batch.info()
     assert shape in (0, 1) and 0 < grid <= info["grid_max"][shape] and ms > 0
