@@ -460,6 +460,93 @@ def test_bilinear_streaming_conserves_global_sums():
     assert np.abs(S.stream_bilinear(c, 1.0 * q.velocity()) - 1.0).max() < 1e-15
 
 
+# Displacements lambda * v_i of the massless order-2 stencil (|v_i| = 1) at
+# lambda = 0.5, 1 and 2.5, and two massive-like short vectors: fractional
+# parts 0.1 ... 0.9 in both directions, none of them 1/2 in both axes (where
+# phi and 1 - phi coincide).
+def _fractional_displacements():
+    q = L.massless_quadrature(2)
+    out = [lam * v for lam in (0.5, 1.0, 2.5) for v in q.velocity()]
+    out += [np.array([0.37, -1.71]), np.array([-2.26, 0.13])]
+    return out
+
+
+@pytest.mark.parametrize("k", range(0, 86, 5))
+def test_bilinear_streaming_reproduces_linear_fields_exactly(k):
+    """Bilinear interpolation is exact on fields linear in x and y: a field
+    F = a + b x + c y streamed by a displacement d must equal F(x - d) at every
+    cell whose two tap columns and rows lie inside the grid (no periodic
+    wrap).  A swap of phi and 1 - phi, or a wrong rounding of the departure
+    point, moves the result by a non-zero multiple of b or c."""
+    d = _fractional_displacements()[k % len(_fractional_displacements())]
+    ny, nx = 17, 23
+    a, b, c = 0.7, 0.013, -0.021
+    yy, xx = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    F = a + b * xx + c * yy
+    out = S.stream_bilinear(F[None], d[None])[0]
+    src = -d
+    o = np.floor(src)
+    lo_x, hi_x = max(0, -int(o[0])), min(nx, nx - int(o[0]) - 1)
+    lo_y, hi_y = max(0, -int(o[1])), min(ny, ny - int(o[1]) - 1)
+    assert hi_x - lo_x >= 5 and hi_y - lo_y >= 5
+    want = a + b * (xx - d[0]) + c * (yy - d[1])
+    sl = (slice(lo_y, hi_y), slice(lo_x, hi_x))
+    assert np.abs(out[sl] - want[sl]).max() < 1e-14
+
+
+@pytest.mark.parametrize("k", range(0, 86, 5))
+def test_bilinear_streaming_moves_an_impulse_by_exactly_its_displacement(k):
+    """A unit impulse streamed by d keeps its mass, its centre moves by exactly
+    d, and its variance along each axis is phi (1 - phi) -- the numerical
+    diffusion of one interpolation, phi the fractional part of the departure
+    point x - d.  (Grid large enough that no tap wraps.)"""
+    d = _fractional_displacements()[k % len(_fractional_displacements())]
+    ny, nx = 15, 15
+    y0, x0 = 7, 7
+    f = np.zeros((1, ny, nx))
+    f[0, y0, x0] = 1.0
+    out = S.stream_bilinear(f, d[None])[0]
+    yy, xx = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    mass = out.sum()
+    assert abs(mass - 1.0) < 1e-15
+    cx, cy = (out * xx).sum(), (out * yy).sum()
+    assert abs(cx - (x0 + d[0])) < 1e-13 and abs(cy - (y0 + d[1])) < 1e-13
+    phi = -d - np.floor(-d)
+    vx, vy = (out * (xx - cx) ** 2).sum(), (out * (yy - cy) ** 2).sum()
+    assert abs(vx - phi[0] * (1 - phi[0])) < 1e-13 and abs(vy - phi[1] * (1 - phi[1])) < 1e-13
+
+
+def test_bilinear_taps_are_non_negative_and_bracket_the_departure_point():
+    """All four weights lie in [0, 1] and sum to one, and the taps are the
+    corners of the unit cell that contains x - d."""
+    for d in _fractional_displacements():
+        taps = S.bilinear_taps(d)
+        w = np.array([t[2] for t in taps])
+        assert (w >= 0).all() and (w <= 1).all() and abs(w.sum() - 1) < 1e-15
+        xs = sorted({t[0] for t in taps})
+        ys = sorted({t[1] for t in taps})
+        # (a departure point within 1e-12 of a whole cell is that cell)
+        assert xs[0] - 1e-12 <= -d[0] <= xs[-1] + 1e-12 and xs[-1] - xs[0] == 1
+        assert ys[0] - 1e-12 <= -d[1] <= ys[-1] + 1e-12 and ys[-1] - ys[0] == 1
+
+
+def test_tau_from_eta_over_s_reproduces_eta_over_s():
+    """Step 7 with eta/s fixed.  With the independent App. C coefficient
+    eta = c P tau (c = ce_shear_viscosity_coeff(0) = 3/4 for a massless d = 2
+    gas), P = n T and the entropy density s = (d + 1) n, the ratio
+    eta / s = c T tau / (d + 1) in lattice units, times 1/kappa to convert
+    hbar/k_B units, must give back the prescribed eta/s for every (n, T)."""
+    rng = np.random.default_rng(7)
+    c = P.ce_shear_viscosity_coeff(0.0)
+    for _ in range(20):
+        n, T = rng.uniform(0.2, 3.0, 2)
+        target, kappa = rng.uniform(0.01, 1.0), rng.uniform(1.0, 30.0)
+        tau = S.tau_from_eta_over_s(T, target, kappa)
+        eta = c * (n * T) * tau
+        s = 3.0 * n
+        assert abs(eta / s / kappa - target) < 1e-14 * target
+
+
 def test_freeflow_streaming_clamps_sources():
     q = L.massless_quadrature(2)
     fs = np.zeros((q.Q, 1, 20))
