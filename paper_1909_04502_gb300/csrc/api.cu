@@ -344,6 +344,35 @@ const char* rlbm_strerror(int code) {
 
 const char* rlbm_last_error(const rlbm_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
+// Dimension of the stencils and of the gas they carry: d = 1 problems run on
+// a d = 2 stencil over an nx x 1 grid (the paper's own practice for its
+// one-dimensional tests), so the EOS and eta/s -> tau use d = 2.
+constexpr int kStencilDim = 2;
+
+// Checks shared by rlbm_create and the allocation-free step.
+static int validate_params(const rlbm_params* p, std::string* err) {
+  auto bad = [err](int code, const char* msg) { *err = msg; return code; };
+  if (p->d == 3) return bad(RLBM_ERR_UNSUPPORTED, "d = 3 runs through rlbm3_create");
+  if (p->d != 1 && p->d != 2) return bad(RLBM_ERR_INVALID_ARG, "d must be 1 or 2");
+  if (p->order != 2 && p->order != 3) return bad(RLBM_ERR_INVALID_ARG, "order must be 2 or 3");
+  if (p->nx <= 0 || p->ny <= 0 || (long long)p->nx * p->ny > (1LL << 30))
+    return bad(RLBM_ERR_INVALID_ARG, "grid size out of range");
+  if (p->d == 1 && p->ny != 1) return bad(RLBM_ERR_INVALID_ARG, "d = 1 needs ny = 1");
+  if (p->precision != RLBM_FP64 && p->precision != RLBM_FP32_STORE) return bad(RLBM_ERR_INVALID_ARG, "precision");
+  if (p->boundary != RLBM_BC_PERIODIC && p->boundary != RLBM_BC_FREEFLOW_X && p->boundary != RLBM_BC_EQWALL_X)
+    return bad(RLBM_ERR_INVALID_ARG, "boundary");
+  if (p->stream_mode != RLBM_ONLATTICE && p->stream_mode != RLBM_BILINEAR)
+    return bad(RLBM_ERR_INVALID_ARG, "stream_mode");
+  if (p->stream_mode == RLBM_BILINEAR && !(p->lambda > 0.0))
+    return bad(RLBM_ERR_INVALID_ARG, "bilinear streaming needs lambda > 0");
+  if (p->tau_mode < 0 || p->tau_mode > 2) return bad(RLBM_ERR_INVALID_ARG, "tau_mode");
+  if (p->tau_mode == RLBM_TAU_CONST && !(p->tau > 0.5)) return bad(RLBM_ERR_INVALID_ARG, "tau must exceed 1/2");
+  if (p->tau_mode == RLBM_TAU_ETA_OVER_S && !(p->eta_over_s > 0.0 && p->kappa > 0.0))
+    return bad(RLBM_ERR_INVALID_ARG, "eta_over_s and kappa must be positive");
+  if (!(p->T_ref > 0.0) || !(p->n_ref >= 0.0)) return bad(RLBM_ERR_INVALID_ARG, "reference state");
+  return RLBM_OK;
+}
+
 int rlbm_plan(const rlbm_params* p, int* Q, int* K, int* nvec, double* pmom, double* w, double* H,
               double* v0) {
   if (!p || !Q || !K) return fail(nullptr, RLBM_ERR_INVALID_ARG, "null argument");
@@ -370,24 +399,11 @@ int rlbm_plan(const rlbm_params* p, int* Q, int* K, int* nvec, double* pmom, dou
 int rlbm_create(const rlbm_params* p, rlbm_handle** out) {
   if (!p || !out) return fail(nullptr, RLBM_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
-  if (p->d != 2) return fail(nullptr, p->d == 3 ? RLBM_ERR_UNSUPPORTED : RLBM_ERR_INVALID_ARG, "d must be 2");
-  if (p->order != 2 && p->order != 3) return fail(nullptr, RLBM_ERR_INVALID_ARG, "order must be 2 or 3");
-  if (p->nx <= 0 || p->ny <= 0 || (long long)p->nx * p->ny > (1LL << 30))
-    return fail(nullptr, RLBM_ERR_INVALID_ARG, "grid size out of range");
-  if (p->precision != RLBM_FP64 && p->precision != RLBM_FP32_STORE)
-    return fail(nullptr, RLBM_ERR_INVALID_ARG, "precision");
-  if (p->boundary != RLBM_BC_PERIODIC && p->boundary != RLBM_BC_FREEFLOW_X && p->boundary != RLBM_BC_EQWALL_X)
-    return fail(nullptr, RLBM_ERR_INVALID_ARG, "boundary");
-  if (p->stream_mode != RLBM_ONLATTICE && p->stream_mode != RLBM_BILINEAR)
-    return fail(nullptr, RLBM_ERR_INVALID_ARG, "stream_mode");
-  if (p->stream_mode == RLBM_BILINEAR && !(p->lambda > 0.0))
-    return fail(nullptr, RLBM_ERR_INVALID_ARG, "bilinear streaming needs lambda > 0");
-  if (p->tau_mode == RLBM_TAU_CONST && !(p->tau > 0.5))
-    return fail(nullptr, RLBM_ERR_INVALID_ARG, "tau must exceed 1/2");
-  if (p->tau_mode == RLBM_TAU_ETA_OVER_S && !(p->eta_over_s > 0.0 && p->kappa > 0.0))
-    return fail(nullptr, RLBM_ERR_INVALID_ARG, "eta_over_s and kappa must be positive");
-  if (p->tau_mode < 0 || p->tau_mode > 2) return fail(nullptr, RLBM_ERR_INVALID_ARG, "tau_mode");
-  if (!(p->T_ref > 0.0) || !(p->n_ref >= 0.0)) return fail(nullptr, RLBM_ERR_INVALID_ARG, "reference state");
+  {
+    std::string verr;
+    const int vrc = validate_params(p, &verr);
+    if (vrc != RLBM_OK) return fail(nullptr, vrc, verr);
+  }
 
   std::unique_ptr<rlbm_handle> h(new rlbm_handle());
   h->p = *p;
@@ -416,7 +432,7 @@ int rlbm_create(const rlbm_params* p, rlbm_handle** out) {
   s.boundary = p->boundary;
   s.tau_mode = p->tau_mode;
   s.tau = p->tau;
-  s.tau_coef = p->eta_over_s * (p->d + 2) * p->kappa;
+  s.tau_coef = p->eta_over_s * (kStencilDim + 2) * p->kappa;
   s.m = m;
   s.n_ref = nr;
   s.T_ref = Tr;
@@ -711,23 +727,10 @@ void rlbm_internal_set_error(const std::string& msg) { g_create_error = msg; }
 
 int rlbm_internal_prepare(const rlbm_params* p, Scalars* sc, Tables<float>* tf, Tables<double>* td,
                           std::string* err) {
-  if (p->d != 2) { *err = "d must be 2"; return p->d == 3 ? RLBM_ERR_UNSUPPORTED : RLBM_ERR_INVALID_ARG; }
-  if (p->order != 2 && p->order != 3) { *err = "order must be 2 or 3"; return RLBM_ERR_INVALID_ARG; }
-  if (p->nx <= 0 || p->ny <= 0 || (long long)p->nx * p->ny > (1LL << 30)) {
-    *err = "grid size out of range";
-    return RLBM_ERR_INVALID_ARG;
+  {
+    const int vrc = validate_params(p, err);
+    if (vrc != RLBM_OK) return vrc;
   }
-  if (p->precision != RLBM_FP64 && p->precision != RLBM_FP32_STORE) { *err = "precision"; return RLBM_ERR_INVALID_ARG; }
-  if (p->boundary != RLBM_BC_PERIODIC && p->boundary != RLBM_BC_FREEFLOW_X && p->boundary != RLBM_BC_EQWALL_X) { *err = "boundary"; return RLBM_ERR_INVALID_ARG; }
-  if (p->stream_mode != RLBM_ONLATTICE && p->stream_mode != RLBM_BILINEAR) { *err = "stream_mode"; return RLBM_ERR_INVALID_ARG; }
-  if (p->stream_mode == RLBM_BILINEAR && !(p->lambda > 0.0)) { *err = "bilinear streaming needs lambda > 0"; return RLBM_ERR_INVALID_ARG; }
-  if (p->tau_mode == RLBM_TAU_CONST && !(p->tau > 0.5)) { *err = "tau must exceed 1/2"; return RLBM_ERR_INVALID_ARG; }
-  if (p->tau_mode == RLBM_TAU_ETA_OVER_S && !(p->eta_over_s > 0.0 && p->kappa > 0.0)) {
-    *err = "eta_over_s and kappa must be positive";
-    return RLBM_ERR_INVALID_ARG;
-  }
-  if (p->tau_mode < 0 || p->tau_mode > 2) { *err = "tau_mode"; return RLBM_ERR_INVALID_ARG; }
-  if (!(p->T_ref > 0.0) || !(p->n_ref >= 0.0)) { *err = "reference state"; return RLBM_ERR_INVALID_ARG; }
   rlbm_handle h;                      // host-side description only: no device buffers
   h.p = *p;
   h.p.groups = nullptr;
@@ -752,7 +755,7 @@ int rlbm_internal_prepare(const rlbm_params* p, Scalars* sc, Tables<float>* tf, 
   s.boundary = p->boundary;
   s.tau_mode = p->tau_mode;
   s.tau = p->tau;
-  s.tau_coef = p->eta_over_s * (p->d + 2) * p->kappa;
+  s.tau_coef = p->eta_over_s * (kStencilDim + 2) * p->kappa;
   s.m = m;
   s.n_ref = nr;
   s.T_ref = Tr;

@@ -133,12 +133,13 @@ def _check(rc, handle=None):
 def make_params(nx, ny, m=0.0, order=2, quadrature=None, groups=None, v0=0.0, custom=None,
                 tau=1.0, tau_mode="const", eta_over_s=0.0, kappa=0.0, boundary="periodic",
                 precision="fp32", stream="onlattice", lam=0.0, n_ref=1.0, T_ref=1.0,
-                cuda_stream=None, g=(0.0, 0.0), wall_T=(0.0, 0.0)):
+                cuda_stream=None, g=(0.0, 0.0), wall_T=(0.0, 0.0), d=2):
     """Fill an rlbm_params struct; returns (params, keepalive) -- the second
-    item holds arrays the struct points to."""
+    item holds arrays the struct points to.  d = 1 runs a one-dimensional
+    problem on the d = 2 stencil over an nx x 1 grid (ny must be 1)."""
     p = Params()
     lib().rlbm_default_params(ctypes.byref(p))
-    p.d = 2
+    p.d = int(d)
     p.m = float(m)
     p.order = int(order)
     if quadrature is None:

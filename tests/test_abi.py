@@ -52,6 +52,19 @@ def test_strerror_and_invalid_create(rl):
     p, keep = rl.make_params(8, 8)
     p.d = 3
     assert L.rlbm_create(ctypes.byref(p), ctypes.byref(h)) == -2
+    # d = 1 is a one-dimensional problem on an nx x 1 grid
+    p, keep = rl.make_params(8, 2, d=1)
+    assert L.rlbm_create(ctypes.byref(p), ctypes.byref(h)) == -1
+    assert "ny = 1" in L.rlbm_last_error(None).decode()
+    p, keep = rl.make_params(8, 1, d=4)
+    assert L.rlbm_create(ctypes.byref(p), ctypes.byref(h)) == -1
+
+
+def test_one_dimensional_plan_uses_the_two_dimensional_stencil(rl):
+    a = rl.plan(nx=64, ny=1, d=1)
+    b = rl.plan(nx=64, ny=1, d=2)
+    assert a["Q"] == b["Q"] == 28
+    assert np.array_equal(a["p"], b["p"]) and np.array_equal(a["H"], b["H"])
 
 
 def _key(n, p0):
