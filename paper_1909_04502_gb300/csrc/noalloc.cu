@@ -71,6 +71,12 @@ int scratch_address(unsigned long long** out) {
   return RLBM_OK;
 }
 
+// The key holds every field of rlbm_params that rlbm_internal_prepare reads
+// (all of them but the stream), and the arrays that groups and custom_table
+// point to.  The size check below fails to compile when a field is added to
+// rlbm_params, so that the key is extended with it.
+static_assert(sizeof(rlbm_params) == 176, "rlbm_params changed: extend config_key with the new field");
+
 std::string config_key(const rlbm_params* p) {
   std::string k;
   auto add = [&k](const void* d, size_t n) { k.append((const char*)d, n); };
@@ -95,6 +101,9 @@ std::string config_key(const rlbm_params* p) {
   add(&p->lambda, sizeof(p->lambda));
   add(&p->n_ref, sizeof(p->n_ref));
   add(&p->T_ref, sizeof(p->T_ref));
+  add(&p->gx, sizeof(p->gx));             // the force decides Scalars::force and the kernel
+  add(&p->gy, sizeof(p->gy));
+  add(&p->wall_T[0], sizeof(p->wall_T));  // both wall temperatures
   return k;
 }
 

@@ -101,3 +101,62 @@ def test_noalloc_multi_step_and_limits(rl):
     rc = rl.lib().rlbm_step_noalloc(ctypes.byref(params), a.data_ptr(), b.data_ptr(), None, 1025, None)
     assert rc == -1
     assert "1024" in rl.lib().rlbm_last_error(None).decode()
+
+
+def _noalloc_vs_handle(rl, nx, ny, fields, kw, nsteps=2, tau=None):
+    """Relative L-inf gap between rlbm_step_noalloc and rlbm_step of a handle
+    created with the same parameters, over the whole buffer (halo included),
+    after nsteps steps from the handle's initial state."""
+    import torch
+    stream = torch.cuda.current_stream().cuda_stream
+    lat = rl.Lattice(nx, ny, cuda_stream=stream, **kw)
+    lat.init(*fields)
+    if tau is not None:
+        lat.set_tau_field(tau)
+    torch.cuda.synchronize()
+    a, elem = _copy_of_handle_buffer(lat)
+    b = torch.zeros_like(a)
+    params, keep = rl.make_params(nx, ny, cuda_stream=stream, **kw)
+    dt = torch.float64 if elem == 8 else torch.float32
+    tau_dev = None
+    if tau is not None:
+        tau_dev = torch.as_tensor(tau, device="cuda", dtype=dt).contiguous()
+    rc, counts = _noalloc(rl, params, a, b, nsteps, tau_dev)
+    assert rc == 0 and counts == [0] * nsteps
+    lat.step(nsteps)
+    torch.cuda.synchronize()
+    ref, _ = _copy_of_handle_buffer(lat)
+    got = (b if nsteps % 2 else a).view(dt).double()
+    want = ref.view(dt).double()
+    lat.close()
+    return float((got - want).abs().max() / want.abs().max())
+
+
+def test_noalloc_tables_follow_force_and_wall_temperatures(rl):
+    """Calls in one process whose parameters differ only in the force or in
+    the wall temperatures must each run with their own tables: every call is
+    compared with a handle created with the same parameters."""
+    nx, ny = 36, 20
+    fields = [np.ascontiguousarray(a) for a in inputs.random_smooth(nx, ny, seed=23, umax=0.2)]
+    base = dict(m=5.0, order=2, precision="fp64", tau=0.9)
+    for extra in (dict(),
+                  dict(g=(0.0, 1e-6)),
+                  dict(g=(2e-6, -1e-6)),
+                  dict(boundary="eqwall_x", wall_T=(1.01, 0.99)),
+                  dict(boundary="eqwall_x", wall_T=(1.03, 0.97)),
+                  dict()):
+        err = _noalloc_vs_handle(rl, nx, ny, fields, dict(base, **extra))
+        assert err <= 1e-12, (extra, err)
+
+
+def test_noalloc_order3_tau_field(rl):
+    """Order-3 massless stencil (Q = 44) with a per-cell relaxation time, in
+    both precisions, against the handle path."""
+    nx, ny = 30, 18
+    fields = [np.ascontiguousarray(a) for a in inputs.random_smooth(nx, ny, seed=24, umax=0.2)]
+    rng = np.random.default_rng(24)
+    tau = np.ascontiguousarray(0.7 + 0.6 * rng.random((ny, nx)))
+    for precision, tol in (("fp64", 1e-12), ("fp32", 1e-5)):
+        kw = dict(order=3, precision=precision, tau_mode="field")
+        err = _noalloc_vs_handle(rl, nx, ny, fields, kw, nsteps=3, tau=tau)
+        assert err <= tol, (precision, err)
