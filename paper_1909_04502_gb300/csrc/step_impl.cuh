@@ -149,15 +149,24 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 }
 
 // FP32 storage: the solve runs in FP32, then one Newton correction whose
-// residuals are evaluated in FP64: p(l) at the FP32 root, the eigenvector v
-// there, its Minkowski norm nu^2 = v.v and w = v.N (so that n = w / nu).  The
-// outputs the FP32 equilibrium needs are formed from accurate differences:
-//   dn = n - n_ref = (w^2 - n_ref^2 nu^2) / (nu (w + n_ref nu))   (numerator in FP64),
-//   d_eps = eps - eps_ref (the FP32 Newton unknown plus its correction),
-//   dT = T - T_ref from the EOS written for differences (FP32),
-// and U = v / nu only needs FP32 accuracy.  About 24 FP64 operations per
-// cell.  The moments are reference + FP32 sums of g, and the eigenvalue is
-// written l = eps_ref + delta.
+// residual p(l) is evaluated in FP64 at the FP32 root (the eigenvalue, and
+// with it eps, carries FP64 accuracy: it decides energy conservation).  The
+// rest is formed in FP32 from quantities accurate relative to the deviation
+// from the reference state, so that every FP32 rounding is proportional to
+// that deviation, like the storage of g = f - f_ref itself:
+//   v = (D, vx, vy), the eigenvector, shifted to the corrected root to first
+//     order (v is quadratic in l: the remainder is O(dl^2));
+//   U = v / nu, nu^2 = v.v;
+//   dn = n - n_ref = (w - n_ref nu) / nu with w = v.N (n = U.N, step 3), in
+//     the difference form
+//       w - n_ref nu = D dN0 - vx Nx - vy Ny + n_ref (vx^2 + vy^2) / (D + nu),
+//     dN0 = N0 - n_ref (the FP32 moment of g), whose terms are all of the
+//     size of the deviation (D - nu = (vx^2 + vy^2)/(D + nu) without
+//     cancellation);
+//   d_eps = eps - eps_ref (the FP32 Newton unknown plus its correction);
+//   dT = T - T_ref from the EOS written for differences.
+// 13 FP64 operations per cell.  The moments are reference + FP32 sums of g,
+// and the eigenvalue is written l = eps_ref + delta.
 // ML: 1 massless, 0 massive (known at compile time), -1 decided by sc.massless.
 template <int ML = -1>
 __device__ __forceinline__ Macro landau_fp32(const Scalars& sc, const float (&mm)[9]) {
@@ -183,47 +192,41 @@ __device__ __forceinline__ Macro landau_fp32(const Scalars& sc, const float (&mm
     dp = -D + a * (b + c) - M2;
     del -= __fdividef(p, dp);
   }
-  // FP64 residuals at l = eps_ref + del
-  const double dd = f2d(del);
-  const double s = f2d(fs), t = f2d(ft), r = f2d(fr);
-  const double base = sc.PE_ref + dd;
-  const double ad = f2d(mm[3]) - dd;
-  const double bd = base + f2d(mm[6]);
-  const double cd = base + f2d(mm[8]);
-  const double D = fma(bd, cd, -r * r);
-  const double vx = fma(s, cd, -r * t);
-  const double vy = fma(t, bd, -r * s);
-  const double p = fma(ad, D, -fma(s, vx, t * vy));
-  const float dl = -__fdividef(d2f(p), dp);          // Newton correction (FP32 is enough)
+  // FP64 residual p(l) at l = eps_ref + del
+  {
+    const double dd = f2d(del);
+    const double s = f2d(fs), t = f2d(ft), r = f2d(fr);
+    const double base = sc.PE_ref + dd;
+    const double ad = f2d(mm[3]) - dd;
+    const double bd = base + f2d(mm[6]);
+    const double cd = base + f2d(mm[8]);
+    const double D = fma(bd, cd, -r * r);
+    const double vx = fma(s, cd, -r * t);
+    const double vy = fma(t, bd, -r * s);
+    const double p = fma(ad, D, -fma(s, vx, t * vy));
+    dp = -__fdividef(d2f(p), dp);     // Newton correction dl (FP32 is enough)
+  }
+  const float dl = dp;
   const float fNx = mm[1], fNy = mm[2];
-  const double N0 = sc.N0_ref + f2d(mm[0]);
-  const double nu2 = fma(D, D, -fma(vx, vx, vy * vy));
-  const double w = fma(D, N0, -fma(vx, f2d(fNx), vy * f2d(fNy)));
-  // first-order shift of v, w, nu^2 to the corrected root (v is quadratic in l
-  // with a unit second derivative in v0 only: the remainder is O(dl^2))
-  const float bc = b + c;
-  // FP32 copies of v and N^0 for the FP32 outputs, evaluated in FP32 at the
-  // same root (D ~ (P + eps)^2 and the leading terms of vx, vy do not cancel)
+  // the eigenvector at the corrected root, in FP32 (D ~ (P + eps)^2 and the
+  // leading terms of vx, vy do not cancel)
   const float fb = PE + mm[6] + del, fc = PE + mm[8] + del;
-  const float fD = fb * fc - fr * fr, fvx = fs * fc - fr * ft, fvy = ft * fb - fr * fs;
-  const float fN0 = sc.f_n_ref + mm[0];
-  const float dw = dl * (bc * fN0 - fs * fNx - ft * fNy);
-  const float dnu2 = 2.f * dl * (fD * bc - fvx * fs - fvy * ft);
-  const double wc = w + f2d(dw);
-  const double nu2c = nu2 + f2d(dnu2);
-  const float fnu2 = d2f(nu2c);
+  const float bc = fb + fc;
+  const float fD = fmaf(dl, bc, fb * fc - fr * fr);
+  const float fvx = fmaf(dl, fs, fs * fc - fr * ft);
+  const float fvy = fmaf(dl, ft, ft * fb - fr * fs);
+  const float vv = fvx * fvx + fvy * fvy;
+  const float fnu2 = fD * fD - vv;
   const float inu = rsqrtf(fnu2);
   const float fnu = fnu2 * inu;
-  const float fw = d2f(wc);
-  Macro M;
-  M.fU0 = (fD + dl * bc) * inu;
-  M.fUx = (fvx + dl * fs) * inu;
-  M.fUy = (fvy + dl * ft) * inu;
-  M.fn = fw * inu;
-  // dn = (w^2 - n_ref^2 nu^2) / (nu (w + n_ref nu))
   const float nr = sc.f_n_ref;
-  const double num = fma(wc, wc, -sc.n_ref2 * nu2c);
-  M.fdn = __fdividef(d2f(num), fnu * (fw + nr * fnu));
+  const float X = fD * mm[0] - fvx * fNx - fvy * fNy + __fdividef(nr * vv, fD + fnu);
+  Macro M;
+  M.fU0 = fD * inu;
+  M.fUx = fvx * inu;
+  M.fUy = fvy * inu;
+  M.fdn = X * inu;
+  M.fn = nr + M.fdn;
   const float deps = del + dl;                          // eps - eps_ref
   const float fn = M.fn, fm = sc.f_m, fTr = sc.f_T_ref;
   if (ML == 1 || (ML == -1 && sc.massless)) {
@@ -250,10 +253,10 @@ __device__ __forceinline__ Macro landau_fp32(const Scalars& sc, const float (&mm
   M.U0 = f2d(M.fU0);
   M.Ux = f2d(M.fUx);
   M.Uy = f2d(M.fUy);
-  // positivity tests on the sign / exponent bits (integer pipe); FP32 tests
+  // a timelike eigenvector with v^0 > 0, n > 0, T > 0; the FP32 tests also
   // catch non-finite values
-  M.ok = (__double2hiint(D) > 0) && (__double2hiint(nu2c) > 0) && (__double2hiint(wc) > 0) && (M.fT > 0.f) &&
-         isfinite(M.fT) && isfinite(M.fU0) && isfinite(M.fn) && isfinite(M.fdn);
+  M.ok = (fD > 0.f) && (fnu2 > 0.f) && (fn > 0.f) && (M.fT > 0.f) && isfinite(M.fT) && isfinite(M.fU0) &&
+         isfinite(M.fn) && isfinite(M.fdn);
   return M;
 }
 
@@ -456,6 +459,12 @@ struct Orbits<49> {   // built-in order 3, App. H column C (m~ = 5)
 template <>
 struct Orbits<53> {   // built-in order 3, App. H column D (m~ = 7 ... 20)
   static constexpr int n8 = 4, n4 = 3, nd = 2, n1 = 1;
+  static constexpr bool massless = false;
+};
+template <>
+struct Orbits<45> {   // order 3, the paper's performance-table stencil (Sec. 6.3): (2,1), (3,2)
+                      // eight-member orbits, four axis, three diagonal quartets, rest
+  static constexpr int n8 = 2, n4 = 4, nd = 3, n1 = 1;
   static constexpr bool massless = false;
 };
 template <int QT>
