@@ -304,6 +304,22 @@ def A_ratio(j, zeta, d=2):
     return zeta ** (j - 1) * special.kve(j + h, zeta) / special.kve(1 + h, zeta)
 
 
+def A_ratio_half_integer(j, zeta):
+    """A_j / A_1 for d = 2 (Bessel orders j + 1/2 and 3/2), evaluated in
+    whatever float type zeta carries: K_{n+1/2}(z) = sqrt(pi/(2z)) e^{-z}
+    R_n(z) with the terminating series R_n(z) = sum_{k<=n} (n+k)!/(k!(n-k)!)
+    (2z)^{-k} (textbook closed form of the half-integer modified Bessel
+    function), so A_j/A_1 = zeta^{j-1} R_j(zeta) / R_1(zeta) without special
+    functions.  zeta > 0."""
+    def R(nu):
+        tot = zeta * 0 + 1
+        for k in range(1, nu + 1):
+            c = math.factorial(nu + k) // (math.factorial(k) * math.factorial(nu - k))
+            tot = tot + c / (2 * zeta) ** k
+        return tot
+    return zeta ** (j - 1) * R(j) / R(1)
+
+
 def _pairings(idx):
     """All ways to choose k disjoint index pairs from positions, for every k.
     Yields (pairs, singles)."""
@@ -322,6 +338,24 @@ def _pairings(idx):
 
 
 ETA = np.diag([1.0, -1.0, -1.0])
+
+
+def mj_moment_ld(alphas, n, U, T, m):
+    """mj_moment for d = 2 and m > 0 in np.longdouble (the same App. B
+    formula, with A_j/A_1 from A_ratio_half_integer)."""
+    r = len(alphas)
+    T = np.asarray(T, dtype=np.longdouble)
+    zeta = np.longdouble(m) / T
+    total = np.longdouble(0)
+    for pairs, singles in _pairings(range(r)):
+        k = len(pairs)
+        term = (-1) ** k * A_ratio_half_integer(r - k, zeta)
+        for (i, j) in pairs:
+            term = term * np.longdouble(ETA[alphas[i], alphas[j]])
+        for s_ in singles:
+            term = term * U[alphas[s_]]
+        total = total + term
+    return np.asarray(n, dtype=np.longdouble) * T ** (r - 1) * total
 
 
 def mj_moment(alphas, n, U, T, m, d=2):
@@ -361,7 +395,10 @@ class Expansion:
     order <= 2: App. F polynomials and App. G projections (closed forms).
     order == 3: Gram-Schmidt basis and projections a_k = int f_MJ J_k d^2p/p0
     assembled from the App. B moments (the order-3 formulas are in the
-    paper's missing supplement).
+    paper's missing supplement).  For m > 0 the projections and the sum
+    f^eq = w sum_k a_k J_k run in np.longdouble: the Gram-Schmidt
+    coefficients of p0 ~ m~ monomials are large and cancel, and in double
+    the equilibrium loses 7.5e-13 of max |f| at m~ = 15.
     """
 
     def __init__(self, quad: Quadrature, order=None, source=None):
@@ -371,6 +408,7 @@ class Expansion:
         if source is None:
             source = "appFG" if self.order == 2 else "gram_schmidt"
         self.source = source
+        self.extended = False
         if source == "appFG":
             if self.order != 2:
                 raise ValueError("App. F/G closed forms are printed up to order 2")
@@ -383,13 +421,16 @@ class Expansion:
                 ctx.prec = 50
                 rows, self.mons = _gram_schmidt_decimal(self.order, self.m)
                 self.C = np.array([[float(x) for x in r] for r in rows])
+                self.C_ld = np.array([[np.longdouble(str(x)) for x in r] for r in rows])
                 pw = lambda x, k: math.prod([x] * k, start=Decimal(1))
                 J = []
                 for p0, px, py in quad.p:
                     phi = [pw(Decimal(p0), c) * pw(Decimal(px), a) * pw(Decimal(py), b)
                            for (c, a, b) in self.mons]
-                    J.append([float(sum(r[q] * phi[q] for q in range(len(phi)))) for r in rows])
-            self.J = np.array(J).T                                  # (K, Q)
+                    J.append([sum(r[q] * phi[q] for q in range(len(phi))) for r in rows])
+            self.J = np.array([[float(x) for x in row] for row in J]).T              # (K, Q)
+            self.J_ld = np.array([[np.longdouble(str(x)) for x in row] for row in J]).T
+        self.extended = source == "gram_schmidt" and self.m > 0.0
 
     def projections(self, n, U, T):
         """a^(k) = n b^(k), shape (K, ...)."""
@@ -401,6 +442,15 @@ class Expansion:
 
     def feq(self, n, U, T):
         """Eq. mj-discrete-feq: f^eq_i = w_i sum_k a^(k) J^(k)(p_i), shape (Q, ...)."""
+        if self.extended:
+            ld = np.longdouble
+            n_, T_ = np.asarray(n, dtype=ld), np.asarray(T, dtype=ld)
+            U_ = np.asarray(U, dtype=ld)
+            Mm = np.stack([mj_moment_ld((0,) * c + (1,) * a + (2,) * b, n_, U_, T_, self.m) * np.ones_like(T_)
+                           for (c, a, b) in self.mons], axis=0)
+            a_ = np.tensordot(self.C_ld, Mm, axes=1)
+            w = np.asarray(self.quad.w, dtype=ld).reshape((-1,) + (1,) * np.ndim(T))
+            return (w * np.tensordot(self.J_ld.T, a_, axes=1)).astype(np.float64)
         a = self.projections(n, U, T)
         return self.quad.w.reshape((-1,) + (1,) * np.ndim(T)) * np.tensordot(self.J.T, a, axes=1)
 

@@ -131,7 +131,8 @@ void compute_layout(const Quadrature& q, const rlbm_params& p, size_t elem, Scal
 // every step and drifts the global sums of N^0 and T^{0a}.
 // True when the kernels' orbit-symmetric evaluation applies: the stencil has
 // one of the compiled orbit compositions (massless Q = 28, 44; the built-in
-// massive Q = 33, 29, 25 at order 2 and 65, 57, 49, 53 at order 3) in orbit
+// massive Q = 33, 29, 25 at order 2 and 65, 57, 49, 53 at order 3; the
+// 45-vector stencil of the paper's performance table at order 3) in orbit
 // order (setup.cpp), every member's momentum
 // and weight are the signed / swapped image of its orbit's first member, and
 // every row of H is exactly the first row with the matching column signs and
@@ -149,6 +150,7 @@ bool orbit_symmetric(const rlbm_handle* h) {
   else if (q.Q == 57 && h->K == 16 && q.m > 0.0) { n8 = 5; n4 = 1; nd = 3; n1 = 1; }
   else if (q.Q == 49 && h->K == 16 && q.m > 0.0) { n8 = 3; n4 = 4; nd = 2; n1 = 1; }
   else if (q.Q == 53 && h->K == 16 && q.m > 0.0) { n8 = 4; n4 = 3; nd = 2; n1 = 1; }
+  else if (q.Q == 45 && h->K == 16 && q.m > 0.0) { n8 = 2; n4 = 4; nd = 3; n1 = 1; }
   else return false;
   const int K = h->K;
   auto row = [&](int i, int k) { return h->H[(size_t)i * K + k]; };

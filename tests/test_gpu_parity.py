@@ -25,10 +25,12 @@ def rl():
 
 
 def make_pair(rl, nx, ny, fields, m=0.0, order=2, tau=1.0, boundary="periodic", stream="onlattice",
-              lam=0.0, precision="fp64", tau_mode="const", eta_over_s=0.0, kappa=0.0, tau_field=None):
+              lam=0.0, precision="fp64", tau_mode="const", eta_over_s=0.0, kappa=0.0, tau_field=None,
+              groups=None, T_ref=1.0):
     lat = rl.Lattice(nx, ny, m=m, order=order, tau=tau, boundary=boundary, stream=stream, lam=lam,
-                     precision=precision, tau_mode=tau_mode, eta_over_s=eta_over_s, kappa=kappa)
-    d = rl.plan(nx=nx, ny=ny, m=m, order=order)
+                     precision=precision, tau_mode=tau_mode, eta_over_s=eta_over_s, kappa=kappa,
+                     groups=groups, T_ref=T_ref)
+    d = rl.plan(nx=nx, ny=ny, m=m, order=order, groups=groups)
     quad = oracle_quadrature(m, order, d["n"], d["v0"])
     idx = permutation(lat.n, lat.p, quad)
     if tau_mode == "const":
@@ -70,6 +72,9 @@ def compare(lat, sim, idx, tol):
     return errs
 
 
+# Sec. 6.3: the 2-d stencil of the paper's performance table (45 vectors)
+PAPER_STENCIL_45 = [(0, 0), (1, 0), (1, 1), (2, 0), (2, 1), (2, 2), (3, 0), (3, 2), (3, 3), (4, 0)]
+
 CASES_FP64 = [
     # name, nx, ny, kwargs, steps
     ("onlattice_periodic_N2", 37, 23, dict(), 12),
@@ -84,6 +89,9 @@ CASES_FP64 = [
     ("massive_m2_N3", 35, 21, dict(m=2.0, order=3), 8),
     ("massive_m3_N3", 33, 18, dict(m=3.0, order=3), 8),
     ("massive_m5_N3", 34, 22, dict(m=5.0, order=3), 8),
+    # the 45-vector stencil of the paper's performance table (Sec. 6.3), order
+    # 3: non-negative weights from m~ = 14.75 on (none at m~ = 5)
+    ("paper_stencil45_m15_N3", 36, 20, dict(m=15.0, order=3, groups=PAPER_STENCIL_45), 8),
 ]
 
 

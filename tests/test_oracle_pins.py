@@ -904,3 +904,51 @@ def test_equilibrium_walls_leave_the_wall_columns_at_rest():
         assert np.allclose(after.n[:, 0], fl.n[:, col], rtol=1e-12)
         assert np.allclose(after.T[:, 0], fl.T[:, col], rtol=1e-12)
     assert np.array_equal(fs[:, :, 1:7], fs0[:, :, 1:7])
+
+
+@pytest.mark.parametrize("m,groups", [(15.0, [(0, 0), (1, 0), (1, 1), (2, 0), (2, 1), (2, 2), (3, 0), (3, 2),
+                                              (3, 3), (4, 0)]),
+                                      (20.0, [(0, 0), (1, 0), (1, 1), (2, 0), (2, 1), (3, 1), (3, 2), (3, 3),
+                                              (4, 0), (4, 2)])])
+def test_order3_massive_equilibrium_matches_arbitrary_precision_evaluation(m, groups):
+    """The order-3 massive equilibrium (Sec. 5.2, Gram-Schmidt basis, App. B
+    moments) against the same definition evaluated with mpmath at 40 digits
+    (Bessel functions K_{n+1/2} from mpmath, not the closed form the oracle
+    uses): the extended-precision evaluation keeps 1e-15 of max |f| where
+    plain double loses up to 1e-12 at these masses.  Stencils: the paper's
+    45-vector performance stencil (Sec. 6.3) at m~ = 15, App. H column D
+    at m~ = 20; v0 from the oracle's own Sec. 5.3 search."""
+    mp = pytest.importorskip("mpmath")
+    from decimal import localcontext
+    mp.mp.dps = 40
+    win = L.search_v0(groups, m, order=3, npts=800)
+    assert win, "no non-negative v0"
+    v0 = 0.5 * (min(win) + max(win))
+    q, res = L.massive_quadrature(groups, m, v0, 3)
+    e = L.Expansion(q)
+    n, T, ux, uy = 1.07, 0.93, 0.21, -0.13
+    g = 1 / math.sqrt(1 - ux * ux - uy * uy)
+    U = np.array([g, g * ux, g * uy])
+    f = e.feq(np.array([n]), U.reshape(3, 1), np.array([T]))[:, 0]
+
+    def mj(alphas):
+        zeta = mp.mpf(m) / mp.mpf(T)
+        tot = mp.mpf(0)
+        for pairs, singles in L._pairings(range(len(alphas))):
+            r = len(alphas) - len(pairs)
+            term = (-1) ** len(pairs) * zeta ** (r - 1) * mp.besselk(r + 0.5, zeta) / mp.besselk(1.5, zeta)
+            for (i, j) in pairs:
+                term *= L.ETA[alphas[i], alphas[j]]
+            for s in singles:
+                term *= mp.mpf(float(U[alphas[s]]))
+            tot += term
+        return mp.mpf(n) * mp.mpf(T) ** (len(alphas) - 1) * tot
+
+    with localcontext() as ctx:
+        ctx.prec = 50
+        rows, mons = L._gram_schmidt_decimal(3, m)
+    M = [mj((0,) * c + (1,) * a + (2,) * b) for (c, a, b) in mons]
+    a = [sum(mp.mpf(str(r[k])) * M[k] for k in range(len(mons))) for r in rows]
+    want = np.array([float(mp.mpf(float(q.w[i])) * sum(a[k] * mp.mpf(str(e.J_ld[k, i])) for k in range(len(a))))
+                     for i in range(q.Q)])
+    assert np.abs(f - want).max() <= 1e-15 * np.abs(want).max()
