@@ -79,7 +79,10 @@ enum { RLBM_KERNEL_AUTO = 0, RLBM_KERNEL_DIRECT = 1, RLBM_KERNEL_TMA_32X8 = 2, R
 enum { RLBM_TAU_CONST = 0, RLBM_TAU_FIELD = 1, RLBM_TAU_ETA_OVER_S = 2 };
 
 typedef struct rlbm_params {
-  int d;              /* spatial dimensions; must be 2 (a 1-D problem runs as nx x 1) */
+  int d;              /* spatial dimensions: 2, or 1 for a one-dimensional problem run
+                         on the d = 2 stencil over an nx x 1 grid (ny must be 1; the
+                         gas stays two-dimensional: EOS and eta/s -> tau of d = 2).
+                         The native (1+1)-d gas is rlbm1_*, d = 3 is rlbm3_*     */
   double m;           /* rest mass m~ = m c^2/(k_B T0); zeta = m~/T~ (Sec. 5.2)      */
   int order;          /* expansion order N of Eq. mj-discrete-feq: 2 or 3           */
   int quadrature;     /* RLBM_QUAD_*                                                 */
@@ -323,6 +326,20 @@ const char* rlbm_adjoint_last_error(const rlbm_adjoint* A);
  * No counterpart in the paper. */
 int rlbm_adjoint_step(rlbm_handle* h, const void* x_prev, const void* a_next, void* a_out, double* grad_tau);
 
+/* The FP32 <-> FP64 conversions of the FP32-storage kernels, element by
+ * element on device arrays (asynchronous on `stream`): out_d[i] = in_f[i]
+ * converted exactly to FP64 (i < nf), out_f[i] = in_d[i] rounded to FP32
+ * (i < nd).  The kernels do these on the integer pipe from the IEEE-754 bit
+ * layouts (a hardware conversion costs about an FP64 multiply on this part);
+ * they differ from the hardware's in three documented ways: FP64 -> FP32
+ * rounds a value exactly halfway between two floats away from zero (the
+ * hardware rounds it to even), results below the smallest normal float
+ * become signed zero, and FP32 denormal inputs convert to signed zero.
+ * Infinities and NaNs keep their class.  No counterpart in the paper: a
+ * check of the library's own arithmetic. */
+int rlbm_convert_f32_f64(const float* in_f, double* out_d, int nf, const double* in_d, float* out_f, int nd,
+                         void* stream);
+
 /* Message of the last error on this handle (or of the last failed
  * rlbm_create when h is NULL).  Never NULL. */
 const char* rlbm_last_error(const rlbm_handle* h);
@@ -331,12 +348,13 @@ const char* rlbm_last_error(const rlbm_handle* h);
 const char* rlbm_strerror(int code);
 
 /* ------------------------------------------------------------------------
- * (3+1) dimensions: massless particles, expansion order 2 (Sec. 5-6 with
- * d = 3).  Stencil and weights: App. H, "(3+1) dimensions", order 2, read
- * with the group (+-2, +-2, +-1) (the printed (+-2, +-1, +-1) does not have
- * the common length 3 of a massless stencil) and the weights shell by shell
- * (per shell the (2, 2, 1) group, then (3, 0, 0)): Q = 78.  On-lattice
- * streaming, periodic in x, y and z, constant tau.
+ * (3+1) dimensions: massless particles, expansion orders 2 and 3 (Sec. 5-6
+ * with d = 3).  Stencils and weights: App. H, "(3+1) dimensions".  Order 2
+ * is read with the group (+-2, +-2, +-1) (the printed (+-2, +-1, +-1) does
+ * not have the common length 3 of a massless stencil) and the weights shell
+ * by shell (per shell the (2, 2, 1) group, then (3, 0, 0)): Q = 78.  Order 3
+ * (v0 = 1/sqrt(41)) reads as printed, weights shell by shell: Q = 288.
+ * On-lattice streaming, periodic in x, y and z, constant tau.
  * EOS eps = 3 n T.  Fields are row-major [z][y][x] arrays of nx*ny*nz doubles.
  * ------------------------------------------------------------------------ */
 typedef struct rlbm3_handle rlbm3_handle;
@@ -356,8 +374,10 @@ int rlbm3_plan(int order, int* Q, int* K, int* nvec, double* p, double* w, doubl
  * order-2 stencil, Q = 78, halo 3) or 3 (App. H order-3 stencil, v0 =
  * 1/sqrt(41), Q = 288, halo 6).  precision: RLBM_FP64 (f stored and collided
  * in FP64) or RLBM_FP32_STORE (g = f - f_ref stored and collided in FP32,
- * f_ref the equilibrium at n = T = 1 at rest; the Landau root is corrected,
- * and n, its difference from 1, eps and T are evaluated, in FP64).  Each side
+ * f_ref the equilibrium at n = T = 1 at rest; the Landau root is found in
+ * FP32 and corrected by one Newton step whose residual, eigenvector, norm
+ * nu^2, w = v.N and the numerator of n - 1 are evaluated in FP64; n, n - 1,
+ * T - 1 and U are then FP32 quotients of those FP64 values).  Each side
  * at least the halo width (3, or 6 at order 3) and nx*ny*nz <= 2^28.
  * The FP64 step evaluates the table in sign-orbit form (runs of sign
  * variants whose equilibrium rows differ only by the basis members' signs);
@@ -397,6 +417,76 @@ int rlbm3_sync_status(rlbm3_handle* h, long long* count);
 /* Message of the last error on this handle (or of the last failed
  * rlbm3_create when h is NULL).  Never NULL. */
 const char* rlbm3_last_error(const rlbm3_handle* h);
+
+/* ------------------------------------------------------------------------
+ * (1+1) dimensions: a one-dimensional massless gas on the App. H "(1+1)
+ * dimensions" quadratures (Sec. 5-6 with d = 1).  Populations
+ * p_{j,s} = p0_j (1, s), s = +-1, on the N shells of the order-N table
+ * (order 4 read with its two printed columns exchanged: the printed weights
+ * are the roots of L_4); each moves one cell per step in direction s.
+ * Equilibrium: the massless limit of the order-N expansion (Sec. 5.2, Eq.
+ * mj-expanded-1D-massless; the weight normalised with C = 1/(2 m K_1(m)),
+ * whose constant member has no finite norm as m -> 0).  On these tables the
+ * 2N populations and the 2N members (p0)^a sign(p^x)^b (a = 1..N, b = 0, 1)
+ * of the limit basis form a square system that the quadrature integrates
+ * exactly, so f^eq is the discrete distribution whose moments of those
+ * members are the Maxwell-Juttner ones, n (a-1)! T^(a-1) {cosh, sinh}(a th)
+ * with U = (cosh th, sinh th).  Landau frame of the 2 x 2 mixed tensor
+ * (Sec. 4); EOS eps = P = n T (d = 1, m = 0).  The moments, the Landau solve
+ * and the equilibrium moments run in FP64 in both precisions.
+ * A d = 2 stencil on an nx x 1 grid (rlbm_params.d = 1) is the other way to
+ * run a one-dimensional problem: a two-dimensional gas with a 1-d flow.
+ * Fields are arrays of nx doubles.
+ * ------------------------------------------------------------------------ */
+typedef struct rlbm1_handle rlbm1_handle;
+
+/* Host-only tables for expansion order `order` (2 ... 5): Q = 2 order,
+ * directions nvec (Q ints, +-1), momenta p (2Q: p0, px), weights w (Q; half
+ * the printed per-direction value, the weight exp(-p0)/2 of dp/p0 spread
+ * over both directions), H (Q x Q row-major, f^eq_i = sum_k H_ik M_k,
+ * k = 2 (a - 1) + b).  Outputs but Q nullable. */
+int rlbm1_plan(int order, int* Q, int* nvec, double* p, double* w, double* H);
+
+/* nx cells; tau > 1/2 (units of Delta t); boundary RLBM_BC_PERIODIC,
+ * RLBM_BC_FREEFLOW_X (pulls from beyond an end read the end cell) or
+ * RLBM_BC_EQWALL_X (the end cells hold f^eq(n, rest, T_w) after each
+ * collision, T_w = wall_T[0] / wall_T[1] or, where 0 or wall_T is NULL,
+ * the cell's own T); precision RLBM_FP64 or RLBM_FP32_STORE (populations
+ * stored as f - f_ref in FP32, f_ref the equilibrium of n = T = 1 at rest);
+ * stream: the cudaStream_t work is issued on.  Allocates two population
+ * buffers of 2 order (nx + 2) elements and field buffers.  Synchronous. */
+int rlbm1_create(int nx, int order, double tau, int boundary, const double* wall_T, int precision,
+                 void* stream, rlbm1_handle** out);
+void rlbm1_destroy(rlbm1_handle* h);
+
+/* Q, directions (Q ints), momenta (2Q) and weights (Q); outputs but Q nullable. */
+int rlbm1_stencil(const rlbm1_handle* h, int* Q, int* nvec, double* p, double* w);
+
+/* f*(0) = f^eq(n, U(ux), T): nx doubles each, host (on_device = 0:
+ * copied, synchronous) or device (borrowed, asynchronous). */
+int rlbm1_init(rlbm1_handle* h, const double* n, const double* ux, const double* T, int on_device);
+
+/* nsteps fused steps (pull, moments, Landau frame, equilibrium, relaxation),
+ * asynchronous.  Cells without a Landau frame are left unrelaxed and
+ * counted (rlbm1_sync_status). */
+int rlbm1_step(rlbm1_handle* h, int nsteps);
+
+/* Fields of f(t) (f*(t-1) streamed; at t = 0 the initial equilibrium):
+ * out = [8][nx] doubles n, ux, T, eps, N^0, N^x, T^00, T^0x (n NaN without a
+ * Landau frame), host (synchronous) or device (asynchronous). */
+int rlbm1_moments(rlbm1_handle* h, double* out, int on_device);
+
+/* Post-collision populations f*(t) (f_ref added back for FP32 storage),
+ * host array [Q][nx] of doubles.  Synchronous. */
+int rlbm1_get_populations(rlbm1_handle* h, double* f);
+
+/* Synchronise; RLBM_ERR_NONPHYSICAL if cell updates were left unrelaxed
+ * since the last call (their number in *count, nullable), else RLBM_OK. */
+int rlbm1_sync_status(rlbm1_handle* h, long long* count);
+
+/* Message of the last error on this handle (or of the last failed
+ * rlbm1_create / rlbm1_plan when h is NULL).  Never NULL. */
+const char* rlbm1_last_error(const rlbm1_handle* h);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,531 @@
+// (1+1)-dimensional massless RLBM step (include/rlbm.h, rlbm1_*): the d = 1
+// case of Sec. 5-6.2 of arXiv:1909.04502 on the App. H "(1+1) dimensions"
+// quadratures.
+//
+// Populations p_{j,s} = p0_j (1, s), s = +-1, on the N shells of the order-N
+// table; every population moves one cell per step in direction s.  The
+// equilibrium is the massless limit of the order-N expansion (Sec. 5.2, Eq.
+// mj-expanded-1D-massless).  On these quadratures the Q = 2N populations and
+// the 2N members phi_{a,s} = (p0)^a sign(p^x)^s (a = 1..N) of the limit basis
+// form a square system, and the quadrature integrates every product the
+// expansion needs exactly, so the discrete equilibrium is the unique f with
+//   sum_i f_i phi_{a,s}(p_i) = M_{a,s} = int f_MJ phi_{a,s} dp/p0
+//     = n (a-1)! T^(a-1) {cosh, sinh}(a theta),   U = (cosh theta, sinh theta),
+// i.e. f^eq = H M with H the inverse of the matrix phi_{a,s}(p_i) (built on
+// the host in double-double).  Landau frame: the largest eigenvalue of the
+// 2 x 2 mixed tensor, in closed form; EOS eps = P = n T (d = 1, m = 0).
+//
+// Layout: one plane per population, nx interior cells with one halo cell on
+// each side (a periodic image or, for free-flow ends and equilibrium walls,
+// a copy of the end cell), so the pull reads base + x - s.  FP32 storage
+// holds g = f - f_ref (f_ref the equilibrium of (n_ref, rest, T_ref)); the
+// moments, the Landau solve, the EOS and the equilibrium moments are FP64 in
+// both precisions (Q <= 10 populations per cell).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/rlbm.h"
+#include "dd.h"
+
+namespace rlbm1 {
+
+constexpr int kMaxN = 5;               // App. H tables: orders 2 ... 5
+constexpr int kMaxQ = 2 * kMaxN;
+constexpr int kThreads = 128;
+
+// App. H, (1+1) dimensions: shells and per-direction weights.  Order 4 is
+// printed with its columns exchanged (the printed weights are the roots of
+// L_4); it is stored here read back.
+struct Table1 {
+  int N;
+  double p0[kMaxN];
+  double w[kMaxN];
+};
+const Table1 kTables[] = {
+    {2, {3.414213562373095048, 0.585786437626904951}, {0.042893218813452475, 1.457106781186547524}},
+    {3, {6.289945082937479196, 0.415774556783479083, 2.294280360279041719},
+     {0.001651724516604877, 1.710285053107483686, 0.121396555709244769}},
+    {4, {0.322547689619392311, 4.536620296921127983, 9.395070912301133129, 1.745761101158346575},
+     {1.869968763544262523, 0.008571999852268322, 0.000057401877068880, 0.204735168059733606}},
+    {5, {0.26356031971814091020, 3.59642577104072208122, 1.41340305910651679221, 7.08581000585883755692,
+         12.6408008442757826594},
+     {1.97964401902679930651, 0.02111608983931054815, 0.28206165857260368669, 0.00050971712153383997,
+      0.00000184877308595198}},
+};
+
+template <typename S>
+struct Tab {
+  double p0[kMaxQ];       // shell energy of population i
+  int s[kMaxQ];           // direction (+1 / -1)
+  double H[kMaxQ][kMaxQ]; // f^eq_i - f_ref,i = sum_k H_ik dM_k  (k = 2 (a - 1) + b)
+  S Hs[kMaxQ][kMaxQ];     // the same in the storage type
+};
+
+struct Sc {
+  int Q, N, nx, P;         // populations, order, cells, plane stride (nx + 2)
+  int boundary;            // RLBM_BC_*
+  double tau;
+  double wall_T[2];        // equilibrium walls: first / last cell temperature (0: own T)
+  double n_ref, T_ref;     // reference state of FP32 storage (n_ref = 0: none)
+  double N0_ref, T00_ref;  // its moments: N^0 = n_ref, T^00 = T^xx = n_ref T_ref (eps = P)
+};
+
+// M_{a,b} - M_{a,b}(n_ref, rest, T_ref) for a = 1..N, b = 0, 1.
+__host__ __device__ inline void moments_dM(const Sc& s, double n, double U0, double Ux, double T,
+                                           double* dM) {
+  const double E = U0 + Ux;               // exp(theta)
+  const double Ei = 1.0 / E;              // exp(-theta) = U0 - Ux, without cancellation
+  double Ea = 1.0, Eia = 1.0, fact = 1.0, Tp = 1.0, Trp = 1.0;
+  for (int a = 1; a <= s.N; ++a) {
+    Ea *= E;
+    Eia *= Ei;
+    if (a > 1) {
+      fact *= (double)(a - 1);
+      Tp *= T;
+      Trp *= s.T_ref;
+    }
+    const double c = n * fact * Tp;
+    dM[2 * (a - 1)] = 0.5 * c * (Ea + Eia) - s.n_ref * fact * Trp;
+    dM[2 * (a - 1) + 1] = 0.5 * c * (Ea - Eia);
+  }
+}
+
+struct Macro1 {
+  double n, U0, Ux, T, eps, N0, Nx, T00, T0x;
+  bool ok;
+};
+
+// Steps 1-4 of Sec. 6.2 from the streamed populations (shifted by f_ref in
+// FP32 storage): moments, the Landau frame of the 2 x 2 mixed tensor
+// A = [[T00, -T0x], [T0x, -Txx]] (largest root of
+// l^2 - (T00 - Txx) l + T0x^2 - T00 Txx, eigenvector (Txx + l, T0x)),
+// n = U.N and T = eps / n.
+template <typename S>
+__device__ inline Macro1 macro1(const Tab<S>& tb, const Sc& s, const S* g) {
+  double N0 = 0.0, Nx = 0.0, T00 = 0.0, T0x = 0.0;
+  for (int i = 0; i < s.Q; ++i) {
+    const double f = (double)g[i], p = tb.p0[i];
+    const double fp = f * p;
+    N0 += fp;
+    T00 += fp * p;
+    if (tb.s[i] > 0) { Nx += fp; T0x += fp * p; }
+    else { Nx -= fp; T0x -= fp * p; }
+  }
+  Macro1 M;
+  M.N0 = s.N0_ref + N0;
+  M.Nx = Nx;
+  M.T00 = s.T00_ref + T00;
+  M.T0x = T0x;
+  const double Txx = M.T00;               // p^x p^x = p0 p0 on every population
+  const double disc = (M.T00 + Txx) * (M.T00 + Txx) - 4.0 * M.T0x * M.T0x;
+  const double l = 0.5 * ((M.T00 - Txx) + sqrt(fmax(disc, 0.0)));
+  const double v0 = Txx + l, v1 = M.T0x;
+  const double nu2 = v0 * v0 - v1 * v1;
+  const double inu = nu2 > 0.0 ? rsqrt(nu2) : 0.0;
+  M.U0 = v0 * inu;
+  M.Ux = v1 * inu;
+  M.eps = l;
+  M.n = M.U0 * M.N0 - M.Ux * M.Nx;
+  M.T = l / M.n;
+  M.ok = disc > 0.0 && nu2 > 0.0 && v0 > 0.0 && l > 0.0 && M.n > 0.0 && isfinite(M.T);
+  return M;
+}
+
+template <typename S>
+__device__ inline S feq_i(const Tab<S>& tb, const Sc& s, int i, const double* dM) {
+  if constexpr (sizeof(S) == 8) {
+    double f = 0.0;
+    for (int k = 0; k < s.Q; ++k) f = fma(tb.H[i][k], dM[k], f);
+    return f;
+  } else {
+    float f = 0.f;
+    for (int k = 0; k < s.Q; ++k) f = fmaf(tb.Hs[i][k], (float)dM[k], f);
+    return f;
+  }
+}
+
+// Store cell x of plane i and its halo image (periodic: the opposite halo
+// cell; free-flow / walls: the halo cell beside an end cell).
+template <typename S>
+__device__ inline void store1(const Sc& s, S* out, int i, int x, S v) {
+  S* row = out + (long long)i * s.P;
+  row[x + 1] = v;
+  if (s.boundary == RLBM_BC_PERIODIC) {
+    if (x == 0) row[s.nx + 1] = v;
+    if (x == s.nx - 1) row[0] = v;
+  } else {
+    if (x == 0) row[0] = v;
+    if (x == s.nx - 1) row[s.nx + 1] = v;
+  }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kThreads) k_step1(const __grid_constant__ Tab<S> tb, const __grid_constant__ Sc s,
+                                                    const S* __restrict__ fin, S* __restrict__ fout,
+                                                    unsigned long long* status) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= s.nx) return;
+  S g[kMaxQ];
+  for (int i = 0; i < s.Q; ++i) g[i] = fin[(long long)i * s.P + x + 1 - tb.s[i]];   // pull
+  const Macro1 M = macro1<S>(tb, s, g);
+  if (!M.ok) {
+    atomicAdd(status, 1ULL);                                 // left unrelaxed (Omega = 0)
+    for (int i = 0; i < s.Q; ++i) store1<S>(s, fout, i, x, g[i]);
+    return;
+  }
+  double dM[kMaxQ];
+  const bool wall = s.boundary == RLBM_BC_EQWALL_X && (x == 0 || x == s.nx - 1);
+  if (wall) {
+    const double Tw = s.wall_T[x == 0 ? 0 : 1] > 0.0 ? s.wall_T[x == 0 ? 0 : 1] : M.T;
+    moments_dM(s, M.n, 1.0, 0.0, Tw, dM);
+    for (int i = 0; i < s.Q; ++i) store1<S>(s, fout, i, x, feq_i<S>(tb, s, i, dM));
+    return;
+  }
+  moments_dM(s, M.n, M.U0, M.Ux, M.T, dM);
+  const double itau = 1.0 / s.tau;
+  for (int i = 0; i < s.Q; ++i) {
+    const S om = (S)((M.U0 - (double)tb.s[i] * M.Ux) * itau);   // p.U / (p0 tau)
+    const S fe = feq_i<S>(tb, s, i, dM);
+    store1<S>(s, fout, i, x, g[i] + om * (fe - g[i]));
+  }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kThreads) k_init1(const __grid_constant__ Tab<S> tb, const __grid_constant__ Sc s,
+                                                    const double* n, const double* ux, const double* T, S* fout,
+                                                    unsigned long long* status) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= s.nx) return;
+  const double u = ux[x];
+  const bool ok = u * u < 1.0 && n[x] > 0.0 && T[x] > 0.0;
+  if (!ok) atomicAdd(status, 1ULL);
+  const double gam = ok ? rsqrt(1.0 - u * u) : 1.0;
+  double dM[kMaxQ];
+  moments_dM(s, n[x], gam, gam * u, T[x], dM);
+  for (int i = 0; i < s.Q; ++i) store1<S>(s, fout, i, x, feq_i<S>(tb, s, i, dM));
+}
+
+// Fields of the streamed populations (pull = 1) or of the stored ones:
+// out[8][nx] = n, ux, T, eps, N0, Nx, T00, T0x (n NaN without a Landau frame).
+template <typename S>
+__global__ void __launch_bounds__(kThreads) k_fields1(const __grid_constant__ Tab<S> tb, const __grid_constant__ Sc s,
+                                                      const S* __restrict__ fin, int pull, double* out) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= s.nx) return;
+  S g[kMaxQ];
+  for (int i = 0; i < s.Q; ++i) g[i] = fin[(long long)i * s.P + x + 1 - (pull ? tb.s[i] : 0)];
+  const Macro1 M = macro1<S>(tb, s, g);
+  const int nx = s.nx;
+  out[x] = M.ok ? M.n : __longlong_as_double(0x7ff8000000000000LL);
+  out[nx + x] = M.Ux / M.U0;
+  out[2 * nx + x] = M.T;
+  out[3 * nx + x] = M.eps;
+  out[4 * nx + x] = M.N0;
+  out[5 * nx + x] = M.Nx;
+  out[6 * nx + x] = M.T00;
+  out[7 * nx + x] = M.T0x;
+}
+
+// Host: the order-N table and H = inverse of phi_{a,b}(p_i) in double-double.
+bool build_tables(int order, std::vector<double>* p0, std::vector<int>* sgn, std::vector<double>* w,
+                  std::vector<double>* H) {
+  const Table1* t = nullptr;
+  for (const auto& tt : kTables)
+    if (tt.N == order) t = &tt;
+  if (!t) return false;
+  const int Q = 2 * order;
+  p0->clear();
+  sgn->clear();
+  w->clear();
+  for (int j = 0; j < order; ++j)
+    for (int s : {1, -1}) {
+      p0->push_back(t->p0[j]);
+      sgn->push_back(s);
+      w->push_back(0.5 * t->w[j]);
+    }
+  // A[k][i] = phi_k(p_i), k = 2 (a - 1) + b; H = A^-1 by Gauss-Jordan with
+  // partial pivoting
+  using rlbm::dd;
+  std::vector<dd> A((size_t)Q * 2 * Q);
+  for (int k = 0; k < Q; ++k) {
+    const int a = k / 2 + 1, b = k % 2;
+    for (int i = 0; i < Q; ++i) {
+      dd v(1.0);
+      for (int e = 0; e < a; ++e) v = v * dd((*p0)[i]);
+      if (b && (*sgn)[i] < 0) v = -v;
+      A[(size_t)k * 2 * Q + i] = v;
+    }
+    for (int i = 0; i < Q; ++i) A[(size_t)k * 2 * Q + Q + i] = dd(i == k ? 1.0 : 0.0);
+  }
+  for (int c = 0; c < Q; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < Q; ++r)
+      if (std::fabs(A[(size_t)r * 2 * Q + c].hi) > std::fabs(A[(size_t)piv * 2 * Q + c].hi)) piv = r;
+    if (A[(size_t)piv * 2 * Q + c].hi == 0.0) return false;
+    if (piv != c)
+      for (int j = 0; j < 2 * Q; ++j) std::swap(A[(size_t)c * 2 * Q + j], A[(size_t)piv * 2 * Q + j]);
+    const dd d = A[(size_t)c * 2 * Q + c];
+    for (int j = 0; j < 2 * Q; ++j) A[(size_t)c * 2 * Q + j] = A[(size_t)c * 2 * Q + j] / d;
+    for (int r = 0; r < Q; ++r) {
+      if (r == c) continue;
+      const dd f = A[(size_t)r * 2 * Q + c];
+      if (f.hi == 0.0) continue;
+      for (int j = 0; j < 2 * Q; ++j) A[(size_t)r * 2 * Q + j] = A[(size_t)r * 2 * Q + j] - f * A[(size_t)c * 2 * Q + j];
+    }
+  }
+  // A = [I | Phi^-1] with Phi[k][i]; f = Phi^-1 M, so H[i][k] = (Phi^-1)[i][k]
+  H->assign((size_t)Q * Q, 0.0);
+  for (int i = 0; i < Q; ++i)
+    for (int k = 0; k < Q; ++k) (*H)[(size_t)i * Q + k] = A[(size_t)i * 2 * Q + Q + k].to_double();
+  return true;
+}
+
+}  // namespace rlbm1
+
+using namespace rlbm1;
+
+struct rlbm1_handle {
+  Sc sc{};
+  std::unique_ptr<Tab<float>> tf;
+  std::unique_ptr<Tab<double>> td;
+  std::vector<double> p0, w, fref;
+  std::vector<int> sgn;
+  size_t elem = 8;
+  void* buf[2] = {nullptr, nullptr};
+  int cur = 0;
+  bool have_prev = false;
+  double* fields = nullptr;          // [8][nx]
+  double* staging = nullptr;         // [3][nx] init input from host
+  unsigned long long* status = nullptr;
+  cudaStream_t stream = nullptr;
+  std::string err = "no error";
+  ~rlbm1_handle() {
+    for (void* b : buf) cudaFree(b);
+    cudaFree(fields);
+    cudaFree(staging);
+    cudaFree(status);
+  }
+};
+
+namespace {
+
+thread_local std::string g_err1 = "no error";
+
+int fail1(rlbm1_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_err1 = msg;
+  return code;
+}
+
+int cuda_fail1(rlbm1_handle* h, cudaError_t e, const char* what) {
+  return fail1(h, RLBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <typename S>
+void fill(const rlbm1_handle* h, const std::vector<double>& H, Tab<S>* t) {
+  std::memset(t, 0, sizeof(Tab<S>));
+  const int Q = h->sc.Q;
+  for (int i = 0; i < Q; ++i) {
+    t->p0[i] = h->p0[i];
+    t->s[i] = h->sgn[i];
+    for (int k = 0; k < Q; ++k) {
+      t->H[i][k] = H[(size_t)i * Q + k];
+      t->Hs[i][k] = (S)H[(size_t)i * Q + k];
+    }
+  }
+}
+
+dim3 grid1(int nx) { return dim3((nx + kThreads - 1) / kThreads); }
+
+}  // namespace
+
+extern "C" {
+
+const char* rlbm1_last_error(const rlbm1_handle* h) { return h ? h->err.c_str() : g_err1.c_str(); }
+
+int rlbm1_plan(int order, int* Q, int* nvec, double* p, double* w, double* H) {
+  if (!Q) return fail1(nullptr, RLBM_ERR_INVALID_ARG, "null argument");
+  std::vector<double> p0, wv, Hm;
+  std::vector<int> sg;
+  if (!build_tables(order, &p0, &sg, &wv, &Hm)) return fail1(nullptr, RLBM_ERR_INVALID_ARG, "order must be 2 ... 5");
+  const int q = 2 * order;
+  *Q = q;
+  for (int i = 0; i < q; ++i) {
+    if (nvec) nvec[i] = sg[i];
+    if (p) { p[2 * i] = p0[i]; p[2 * i + 1] = sg[i] * p0[i]; }
+    if (w) w[i] = wv[i];
+  }
+  if (H) std::memcpy(H, Hm.data(), sizeof(double) * q * q);
+  return RLBM_OK;
+}
+
+int rlbm1_create(int nx, int order, double tau, int boundary, const double* wall_T, int precision, void* stream,
+                 rlbm1_handle** out) {
+  if (!out) return fail1(nullptr, RLBM_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (nx < 1 || nx > (1 << 28)) return fail1(nullptr, RLBM_ERR_INVALID_ARG, "nx out of range");
+  if (!(tau > 0.5)) return fail1(nullptr, RLBM_ERR_INVALID_ARG, "tau must exceed 1/2");
+  if (boundary != RLBM_BC_PERIODIC && boundary != RLBM_BC_FREEFLOW_X && boundary != RLBM_BC_EQWALL_X)
+    return fail1(nullptr, RLBM_ERR_INVALID_ARG, "boundary");
+  if (precision != RLBM_FP64 && precision != RLBM_FP32_STORE) return fail1(nullptr, RLBM_ERR_INVALID_ARG, "precision");
+  std::unique_ptr<rlbm1_handle> h(new rlbm1_handle());
+  std::vector<double> H;
+  if (!build_tables(order, &h->p0, &h->sgn, &h->w, &H)) return fail1(nullptr, RLBM_ERR_INVALID_ARG, "order must be 2 ... 5");
+  Sc& s = h->sc;
+  s.N = order;
+  s.Q = 2 * order;
+  s.nx = nx;
+  s.P = nx + 2;
+  s.boundary = boundary;
+  s.tau = tau;
+  s.wall_T[0] = wall_T ? wall_T[0] : 0.0;
+  s.wall_T[1] = wall_T ? wall_T[1] : 0.0;
+  s.n_ref = precision == RLBM_FP32_STORE ? 1.0 : 0.0;
+  s.T_ref = 1.0;
+  s.N0_ref = s.n_ref;
+  s.T00_ref = s.n_ref * s.T_ref;
+  h->elem = precision == RLBM_FP32_STORE ? 4 : 8;
+  h->stream = (cudaStream_t)stream;
+  // reference populations f_ref = H M(n_ref, rest, T_ref) (the shift of FP32 storage)
+  h->fref.assign(s.Q, 0.0);
+  if (s.n_ref > 0.0) {
+    Sc z = s;
+    z.n_ref = 0.0;
+    double M[kMaxQ];
+    moments_dM(z, s.n_ref, 1.0, 0.0, s.T_ref, M);
+    for (int i = 0; i < s.Q; ++i)
+      for (int k = 0; k < s.Q; ++k) h->fref[i] += H[(size_t)i * s.Q + k] * M[k];
+  }
+  if (h->elem == 4) { h->tf.reset(new Tab<float>()); fill(h.get(), H, h->tf.get()); }
+  else { h->td.reset(new Tab<double>()); fill(h.get(), H, h->td.get()); }
+  const size_t bytes = (size_t)s.Q * s.P * h->elem;
+  for (int b = 0; b < 2; ++b)
+    if (cudaMalloc(&h->buf[b], bytes) != cudaSuccess) { cudaGetLastError(); return fail1(nullptr, RLBM_ERR_OOM, "population buffers"); }
+  if (cudaMalloc(&h->fields, sizeof(double) * 8 * nx) != cudaSuccess ||
+      cudaMalloc(&h->staging, sizeof(double) * 3 * nx) != cudaSuccess ||
+      cudaMalloc(&h->status, sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail1(nullptr, RLBM_ERR_OOM, "field buffers");
+  }
+  cudaError_t e = cudaMemsetAsync(h->status, 0, sizeof(unsigned long long), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[0], 0, bytes, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[1], 0, bytes, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail1(nullptr, e, "rlbm1_create");
+  *out = h.release();
+  return RLBM_OK;
+}
+
+void rlbm1_destroy(rlbm1_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  delete h;
+}
+
+int rlbm1_stencil(const rlbm1_handle* h, int* Q, int* nvec, double* p, double* w) {
+  if (!h || !Q) return RLBM_ERR_INVALID_ARG;
+  *Q = h->sc.Q;
+  for (int i = 0; i < h->sc.Q; ++i) {
+    if (nvec) nvec[i] = h->sgn[i];
+    if (p) { p[2 * i] = h->p0[i]; p[2 * i + 1] = h->sgn[i] * h->p0[i]; }
+    if (w) w[i] = h->w[i];
+  }
+  return RLBM_OK;
+}
+
+int rlbm1_init(rlbm1_handle* h, const double* n, const double* ux, const double* T, int on_device) {
+  if (!h || !n || !ux || !T) return RLBM_ERR_INVALID_ARG;
+  const int nx = h->sc.nx;
+  const double* dn = n;
+  const double* du = ux;
+  const double* dT = T;
+  cudaError_t e = cudaSuccess;
+  if (!on_device) {
+    e = cudaMemcpyAsync(h->staging, n, sizeof(double) * nx, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->staging + nx, ux, sizeof(double) * nx, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->staging + 2 * nx, T, sizeof(double) * nx, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail1(h, e, "rlbm1_init copy");
+    dn = h->staging;
+    du = h->staging + nx;
+    dT = h->staging + 2 * nx;
+  }
+  if (h->elem == 4)
+    k_init1<float><<<grid1(nx), kThreads, 0, h->stream>>>(*h->tf, h->sc, dn, du, dT, (float*)h->buf[h->cur], h->status);
+  else
+    k_init1<double><<<grid1(nx), kThreads, 0, h->stream>>>(*h->td, h->sc, dn, du, dT, (double*)h->buf[h->cur], h->status);
+  e = cudaGetLastError();
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail1(h, e, "rlbm1_init");
+  h->have_prev = false;
+  return RLBM_OK;
+}
+
+int rlbm1_step(rlbm1_handle* h, int nsteps) {
+  if (!h || nsteps < 0) return RLBM_ERR_INVALID_ARG;
+  for (int it = 0; it < nsteps; ++it) {
+    if (h->elem == 4)
+      k_step1<float><<<grid1(h->sc.nx), kThreads, 0, h->stream>>>(*h->tf, h->sc, (const float*)h->buf[h->cur],
+                                                                   (float*)h->buf[h->cur ^ 1], h->status);
+    else
+      k_step1<double><<<grid1(h->sc.nx), kThreads, 0, h->stream>>>(*h->td, h->sc, (const double*)h->buf[h->cur],
+                                                                    (double*)h->buf[h->cur ^ 1], h->status);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail1(h, e, "rlbm1_step");
+    h->cur ^= 1;
+    h->have_prev = true;
+  }
+  return RLBM_OK;
+}
+
+int rlbm1_moments(rlbm1_handle* h, double* out, int on_device) {
+  if (!h || !out) return RLBM_ERR_INVALID_ARG;
+  const int nx = h->sc.nx;
+  const void* src = h->have_prev ? h->buf[h->cur ^ 1] : h->buf[h->cur];
+  const int pull = h->have_prev ? 1 : 0;
+  double* dst = on_device ? out : h->fields;
+  if (h->elem == 4)
+    k_fields1<float><<<grid1(nx), kThreads, 0, h->stream>>>(*h->tf, h->sc, (const float*)src, pull, dst);
+  else
+    k_fields1<double><<<grid1(nx), kThreads, 0, h->stream>>>(*h->td, h->sc, (const double*)src, pull, dst);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && !on_device) {
+    e = cudaMemcpyAsync(out, h->fields, sizeof(double) * 8 * nx, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail1(h, e, "rlbm1_moments");
+  return RLBM_OK;
+}
+
+int rlbm1_get_populations(rlbm1_handle* h, double* f) {
+  if (!h || !f) return RLBM_ERR_INVALID_ARG;
+  const Sc& s = h->sc;
+  std::vector<unsigned char> raw((size_t)s.Q * s.P * h->elem);
+  cudaError_t e = cudaMemcpyAsync(raw.data(), h->buf[h->cur], raw.size(), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail1(h, e, "rlbm1_get_populations");
+  for (int i = 0; i < s.Q; ++i)
+    for (int x = 0; x < s.nx; ++x) {
+      const size_t at = (size_t)i * s.P + x + 1;
+      const double v = h->elem == 4 ? (double)((const float*)raw.data())[at] : ((const double*)raw.data())[at];
+      f[(size_t)i * s.nx + x] = v + h->fref[i];
+    }
+  return RLBM_OK;
+}
+
+int rlbm1_sync_status(rlbm1_handle* h, long long* count) {
+  if (!h) return RLBM_ERR_INVALID_ARG;
+  unsigned long long c = 0;
+  cudaError_t e = cudaMemcpyAsync(&c, h->status, sizeof(c), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(c), h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail1(h, e, "rlbm1_sync_status");
+  if (count) *count = (long long)c;
+  return c ? fail1(h, RLBM_ERR_NONPHYSICAL, "non-physical cell updates") : RLBM_OK;
+}
+
+}  // extern "C"

@@ -67,6 +67,17 @@ SIGNATURES = {
     "rlbm3_get_populations": (ctypes.c_int, [_H, _DP]),
     "rlbm3_sync_status": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_longlong)]),
     "rlbm3_last_error": (ctypes.c_char_p, [_H]),
+    "rlbm1_plan": (ctypes.c_int, [ctypes.c_int, _IP, _IP, _DP, _DP, _DP]),
+    "rlbm1_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, _DP, ctypes.c_int,
+                                    _VP, ctypes.POINTER(_H)]),
+    "rlbm1_destroy": (None, [_H]),
+    "rlbm1_stencil": (ctypes.c_int, [_H, _IP, _IP, _DP, _DP]),
+    "rlbm1_init": (ctypes.c_int, [_H, _VP, _VP, _VP, ctypes.c_int]),
+    "rlbm1_step": (ctypes.c_int, [_H, ctypes.c_int]),
+    "rlbm1_moments": (ctypes.c_int, [_H, _VP, ctypes.c_int]),
+    "rlbm1_get_populations": (ctypes.c_int, [_H, _DP]),
+    "rlbm1_sync_status": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_longlong)]),
+    "rlbm1_last_error": (ctypes.c_char_p, [_H]),
     "rlbm_destroy": (None, [_H]),
     "rlbm_init": (ctypes.c_int, [_H, _VP, _VP, _VP, _VP, ctypes.c_int]),
     "rlbm_set_tau_field": (ctypes.c_int, [_H, _VP, ctypes.c_int]),
@@ -101,6 +112,7 @@ SIGNATURES = {
     "rlbm_adjoint_forward": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_int]),
     "rlbm_adjoint_backward": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, ctypes.c_int]),
     "rlbm_adjoint_last_error": (ctypes.c_char_p, [_VP]),
+    "rlbm_convert_f32_f64": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP]),
     "rlbm_last_error": (ctypes.c_char_p, [_H]),
     "rlbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -568,6 +580,99 @@ class Lattice3:
     def close(self):
         if getattr(self, "h", None):
             lib().rlbm3_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plan1(order=2):
+    """Host-only (1+1)-d tables (no GPU): dict with Q, n (Q,), p (Q, 2), w, H (Q, Q)."""
+    Q = ctypes.c_int()
+    nvec = np.zeros(10, dtype=np.int32)
+    pm = np.zeros(20)
+    w = np.zeros(10)
+    H = np.zeros(100)
+    rc = lib().rlbm1_plan(int(order), ctypes.byref(Q), nvec.ctypes.data_as(_IP), pm.ctypes.data_as(_DP),
+                          w.ctypes.data_as(_DP), H.ctypes.data_as(_DP))
+    if rc != RLBM_OK:
+        raise RLBMError(rc, lib().rlbm1_last_error(None).decode())
+    q = Q.value
+    return dict(Q=q, n=nvec[:q].copy(), p=pm[:2 * q].reshape(q, 2).copy(), w=w[:q].copy(),
+                H=H[:q * q].reshape(q, q).copy())
+
+
+class Lattice1:
+    """A (1+1)-d massless gas (App. H (1+1)-d table of expansion order 2 ... 5;
+    FP64 or FP32 storage) behind the rlbm1_* calls; fields are numpy (nx,)
+    arrays or CUDA float64 tensors."""
+
+    FIELDS = ("n", "ux", "T", "eps", "N0", "Nx", "T00", "T0x")
+
+    def __init__(self, nx, order=2, tau=1.0, boundary="periodic", wall_T=None, precision="fp64",
+                 cuda_stream=None):
+        if cuda_stream is None:
+            cuda_stream = _current_stream()
+        self.nx = int(nx)
+        h = _H()
+        wt = None
+        if wall_T is not None:
+            self._wall = np.ascontiguousarray(wall_T, dtype=np.float64)
+            wt = self._wall.ctypes.data_as(_DP)
+        rc = lib().rlbm1_create(self.nx, int(order), float(tau), BC[boundary], wt, PREC[precision], cuda_stream,
+                                ctypes.byref(h))
+        if rc != RLBM_OK:
+            raise RLBMError(rc, lib().rlbm1_last_error(None).decode())
+        self.h = h
+        Q = ctypes.c_int()
+        nvec = np.zeros(10, dtype=np.int32)
+        pm = np.zeros(20)
+        w = np.zeros(10)
+        self._chk(lib().rlbm1_stencil(self.h, ctypes.byref(Q), nvec.ctypes.data_as(_IP), pm.ctypes.data_as(_DP),
+                                      w.ctypes.data_as(_DP)))
+        self.Q = Q.value
+        self.n = nvec[:self.Q].copy()
+        self.p = pm[:2 * self.Q].reshape(self.Q, 2).copy()
+        self.w = w[:self.Q].copy()
+
+    def _chk(self, rc):
+        if rc != RLBM_OK:
+            raise RLBMError(rc, lib().rlbm1_last_error(self.h).decode())
+
+    def init(self, n, ux, T):
+        ptrs = [_ptr(a) for a in (n, ux, T)]
+        dev = {d for _, d in ptrs}
+        if len(dev) != 1:
+            raise ValueError("fields must all live on the host or all on the device")
+        self._chk(lib().rlbm1_init(self.h, *[p for p, _ in ptrs], dev.pop()))
+
+    def step(self, k=1):
+        self._chk(lib().rlbm1_step(self.h, int(k)))
+
+    def moments(self):
+        """dict n, ux, T, eps, N0, Nx, T00, T0x of f(t) as (nx,) host arrays."""
+        out = np.empty((8, self.nx))
+        self._chk(lib().rlbm1_moments(self.h, out.ctypes.data, 0))
+        return dict(zip(self.FIELDS, out))
+
+    def populations(self):
+        f = np.empty((self.Q, self.nx))
+        self._chk(lib().rlbm1_get_populations(self.h, f.ctypes.data_as(_DP)))
+        return f
+
+    def sync_status(self):
+        c = ctypes.c_longlong()
+        rc = lib().rlbm1_sync_status(self.h, ctypes.byref(c))
+        if rc not in (RLBM_OK, -4):             # -4: NONPHYSICAL, reported with the count
+            self._chk(rc)
+        return rc, c.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().rlbm1_destroy(self.h)
             self.h = None
 
     def __del__(self):

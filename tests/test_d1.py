@@ -1,0 +1,171 @@
+"""(1+1)-d massless gas (rlbm1_*): host tables against the oracle (CPU), GPU
+parity against the FP64 oracle (oracle/d1.py), and the heated rod of Sec.
+7.2 in one dimension against the Chapman-Enskog thermal conductivity of
+App. C (d = 1, massless: lambda = 2 n tau)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import d1 as O1
+
+ORDERS = [2, 3, 4, 5]
+
+
+@pytest.fixture(scope="module")
+def rl():
+    from paper_1909_04502_gb300 import build, rlbm
+    build.build()
+    return rlbm
+
+
+@pytest.mark.parametrize("order", ORDERS)
+def test_host_tables_reproduce_the_oracle_equilibrium(rl, order):
+    """The library's H (inverse of the basis at the populations) applied to the
+    closed-form Maxwell-Juttner moments gives the oracle's massless-limit
+    equilibrium (the oracle builds it as c0 + projection, Sec. 5.2)."""
+    d = rl.plan1(order)
+    q = O1.massless_quadrature_1d(order)
+    assert d["Q"] == q.Q
+    assert np.array_equal(d["p"], q.p) and np.array_equal(d["w"], q.w) and np.array_equal(d["n"], q.n)
+    e = O1.Expansion1(q)
+    rng = np.random.default_rng(order)
+    n, T, u = rng.uniform(0.6, 1.4, 8), rng.uniform(0.7, 1.5, 8), rng.uniform(-0.6, 0.6, 8)
+    U = O1.four_velocity1(u)
+    M = np.array([O1.mj_moment_1d(a, s, n, U[0], U[1], T) for a in range(1, order + 1) for s in (0, 1)])
+    f_lib = d["H"] @ M
+    f_orc = e.feq(n, U, T)
+    assert np.abs(f_lib - f_orc).max() <= 1e-13 * np.abs(f_orc).max()
+
+
+def test_invalid_arguments_are_refused(rl):
+    import ctypes
+    h = ctypes.c_void_p()
+    L = rl.lib()
+    assert L.rlbm1_create(16, 6, 1.0, 0, None, 0, None, ctypes.byref(h)) == -1
+    assert "order" in L.rlbm1_last_error(None).decode()
+    assert L.rlbm1_create(16, 2, 0.5, 0, None, 0, None, ctypes.byref(h)) == -1
+    assert L.rlbm1_create(0, 2, 1.0, 0, None, 0, None, ctypes.byref(h)) == -1
+    assert L.rlbm1_create(16, 2, 1.0, 7, None, 0, None, ctypes.byref(h)) == -1
+
+
+def _fields(nx, seed, umax=0.4):
+    rng = np.random.default_rng(seed)
+    x = 2 * np.pi * np.arange(nx) / nx
+    ph = rng.uniform(0, 2 * np.pi, 3)
+    n = 1 + 0.2 * np.sin(x + ph[0])
+    u = umax * np.sin(2 * x + ph[1])
+    T = 1 + 0.15 * np.cos(x + ph[2])
+    return [np.ascontiguousarray(a) for a in (n, u, T)]
+
+
+def _pair(rl, nx, order, fields, precision="fp64", tau=0.9, boundary="periodic", wall_T=None):
+    lat = rl.Lattice1(nx, order=order, tau=tau, boundary=boundary, wall_T=wall_T, precision=precision)
+    sim = O1.Simulation1(O1.massless_quadrature_1d(order), nx, tau=tau, boundary=boundary,
+                         wall_T=tuple(wall_T) if wall_T is not None else (0.0, 0.0))
+    lat.init(*fields)
+    sim.init(*fields)
+    sim.u0max = float(np.abs(fields[1]).max())
+    return lat, sim
+
+
+def _compare(lat, sim, tol):
+    """Relative L-inf of f, n, T (by max |reference|) and of u (by the largest
+    speed of the reference, initial or current)."""
+    f = lat.populations()
+    err = float(np.abs(f - sim.fs).max() / np.abs(sim.fs).max())
+    m = lat.moments()
+    fl = sim.fields
+    umax = max(sim.u0max, np.abs(fl.ux).max(), 1e-300)
+    errs = {"f": err, "n": float(np.abs(m["n"] - fl.n).max() / np.abs(fl.n).max()),
+            "T": float(np.abs(m["T"] - fl.T).max() / np.abs(fl.T).max()),
+            "ux": float(np.abs(m["ux"] - fl.ux).max() / umax)}
+    for k, v in errs.items():
+        assert v <= tol, errs
+    return errs
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("order", ORDERS)
+def test_fp64_parity_periodic(rl, order):
+    """A ragged grid (173 cells, two blocks), flows up to 0.4 c: FP64 against
+    the oracle, element by element, at t = 0, 10 and 20."""
+    lat, sim = _pair(rl, 173, order, _fields(173, order))
+    _compare(lat, sim, 1e-12)
+    for _ in range(2):
+        lat.step(10)
+        sim.step(10)
+        _compare(lat, sim, 1e-12)
+    assert lat.sync_status()[0] == 0
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("order", [2, 3])
+def test_fp32_storage_parity(rl, order):
+    lat, sim = _pair(rl, 300, order, _fields(300, 10 + order), precision="fp32")
+    for _ in range(4):
+        lat.step(25)
+        sim.step(25)
+        _compare(lat, sim, 1e-5)
+    assert lat.sync_status()[0] == 0
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_shock_tube_with_free_flow_ends(rl, precision, tol):
+    """A Riemann problem (pressure ratio 2.5 across the middle, at rest) with
+    free-flow ends, 60 steps: the waves run at c and leave through the ends."""
+    nx = 200
+    x = np.arange(nx)
+    n = np.where(x < nx // 2, 1.0, 0.5)
+    T = np.where(x < nx // 2, 1.0, 0.8)
+    fields = [np.ascontiguousarray(a) for a in (n, np.zeros(nx), T)]
+    lat, sim = _pair(rl, nx, 3, fields, precision=precision, tau=1.2, boundary="freeflow_x")
+    for _ in range(3):
+        lat.step(20)
+        sim.step(20)
+        m = lat.moments()
+        assert np.abs(lat.populations() - sim.fs).max() <= tol * np.abs(sim.fs).max()
+        assert np.abs(m["n"] - sim.fields.n).max() <= tol
+    assert lat.sync_status()[0] == 0
+
+
+@pytest.mark.gpu
+def test_equilibrium_walls_at_prescribed_temperatures(rl):
+    lat, sim = _pair(rl, 64, 3, _fields(64, 5, umax=0.2), boundary="eqwall_x", wall_T=np.array([1.02, 0.97]))
+    lat.step(30)
+    sim.step(30)
+    _compare(lat, sim, 1e-12)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("tau", [0.8, 1.5])
+def test_heated_rod_thermal_conductivity(rl, tau):
+    """Sec. 7.2 in d = 1: a rod between equilibrium walls at T = 1.005 and
+    0.995, relaxed to its steady state.  The heat flux q = h_e (N_E - N)
+    (h_e = (eps + P)/n = 2T) over the gradient of T gives lambda; App. C's
+    first-order Chapman-Enskog value for a massless d = 1 gas is
+    lambda = (d+1)/d n tau = 2 n tau.  For a massless lattice gas the
+    first-order particle current of the pre-collision populations is
+    -tau d_x sum sign p^x f^eq = -tau d_x n exactly (p^x = sign p0 on every
+    population), so the quadrature adds no error to this coefficient; the
+    flux is read from the pre-collision state (the fields rlbm1_moments
+    returns), whose coefficient is tau (not tau - 1/2).  The 20 cells next to
+    each wall are excluded."""
+    nx = 400
+    lat = rl.Lattice1(nx, order=3, tau=tau, boundary="eqwall_x", wall_T=np.array([1.005, 0.995]))
+    lat.init(np.ones(nx), np.zeros(nx), np.ones(nx))
+    steps = int(8 * nx * nx / (math.pi ** 2 * tau))           # ~8 decay times of the slowest mode
+    lat.step(steps)
+    m = lat.moments()
+    assert lat.sync_status()[0] == 0
+    n, T, ux = m["n"], m["T"], m["ux"]
+    g = 1 / np.sqrt(1 - ux * ux)
+    qx = 2 * T * (n * g * ux - m["Nx"])                       # h_e (N_E^x - N^x)
+    sl = slice(20, nx - 20)
+    dT = (T[2:] - T[:-2])[sl.start - 1:sl.stop - 1] / 2
+    lam = -qx[sl] / dT
+    want = 2 * n[sl] * tau
+    assert np.abs(lam / want - 1).max() < 2e-3, np.abs(lam / want - 1).max()
+    # the steady flux is uniform along the rod
+    assert np.abs(qx[sl] / qx[sl].mean() - 1).max() < 2e-3
