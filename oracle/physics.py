@@ -100,11 +100,30 @@ def _exp_e1(z):
     return np.where(z <= 500.0, special.exp1(small) * np.exp(small), special.hyperu(1.0, 1.0, z))
 
 
+def bickley_ki1(z):
+    """Ki_1(z) = int_z^inf K_0(t) dt (the Bickley function of App. C), by
+    adaptive quadrature."""
+    from scipy import integrate
+    z = np.atleast_1d(np.asarray(z, dtype=np.float64))
+    return np.array([integrate.quad(lambda t: special.k0(t), v, np.inf, epsabs=0, epsrel=1e-13, limit=200)[0]
+                     for v in z])
+
+
 def ce_shear_viscosity_coeff(zeta, d=2):
     """f(zeta) in eta = f(zeta) P tau, Chapman-Enskog (App. C, "To give a few
-    examples"): d = 2: (2 G_2 - zeta^2 + e^zeta zeta^4 Gamma(0, zeta)/(zeta + 1))/8.
+    examples"): d = 2: (2 G_2 - zeta^2 + e^zeta zeta^4 Gamma(0, zeta)/(zeta + 1))/8;
+    d = 3: (3 G_3 - 5 zeta^2 + G_3 zeta^2 - zeta^3 Ki_1(zeta)/K_2(zeta))/15.
     Gamma(0, z) = E_1(z) (e^z E_1(z) by _exp_e1).  UR limit (d+1)/(d+2)
     (Eq. ce-ur-limit)."""
+    if d == 3:
+        z = np.atleast_1d(np.asarray(zeta, dtype=np.float64))
+        g = G_d(z, 3)
+        out = np.full(z.shape, 4.0 / 5.0)
+        nz = z > 0
+        if np.any(nz):
+            zn = z[nz]
+            out[nz] = (3 * g[nz] - 5 * zn * zn + g[nz] * zn * zn - zn ** 3 * bickley_ki1(zn) / special.kv(2, zn)) / 15
+        return out if np.ndim(zeta) else float(out[0])
     if d != 2:
         raise NotImplementedError
     z = np.asarray(zeta, dtype=np.float64)
