@@ -23,6 +23,24 @@
 
 namespace rlbm {
 
+// Reference scalars and tau in the working precision: the FP32 path reads
+// the FP32 copies, since a conversion from double runs on the FP64 pipe.
+template <typename S>
+__device__ __forceinline__ void ref_scalars(const Scalars& sc, S& T00, S& Tii, S& N0, S& m) {
+  if constexpr (sizeof(S) == 4) { T00 = sc.f_T00_ref; Tii = sc.f_Tii_ref; N0 = sc.f_n_ref; m = sc.f_m; }
+  else { T00 = (S)sc.T00_ref; Tii = (S)sc.Tii_ref; N0 = (S)sc.N0_ref; m = (S)sc.m; }
+}
+template <typename S>
+__device__ __forceinline__ S const_tau(const Scalars& sc) {
+  if constexpr (sizeof(S) == 4) return sc.f_tau;
+  else return sc.tau;
+}
+template <typename S>
+__device__ __forceinline__ S inv_sqrt(S x) {
+  if constexpr (sizeof(S) == 4) return rsqrtf(x);
+  else return S(1) / sqrt(x);
+}
+
 // Transposed streaming: lambda_i(x) = (S^T a)_i(x).
 template <typename S, int QT, bool EX, int MODE>
 __device__ __forceinline__ void gather_rev(const Tables<S>& tb, const Scalars& s, const S* __restrict__ a,
@@ -56,11 +74,12 @@ template <typename S>
 __device__ __forceinline__ void dM_vjp(const S (&h)[9], S n, S T, S U0, S Ux, S Uy, S m, S& gn, S& gT,
                                        S& gU0, S& gUx, S& gUy) {
   const S mT = m + T;
-  const S r2 = (m * m + S(3) * m * T + S(3) * T * T) / mT;
-  const S dr2 = (S(3) * m + S(6) * T) / mT - r2 / mT;
+  const S imT = qdiv(S(1), mT);
+  const S r2 = (m * m + S(3) * m * T + S(3) * T * T) * imT;
+  const S dr2 = (S(3) * m + S(6) * T) * imT - r2 * imT;
   const S A = h[4] * U0 * Ux + h[5] * U0 * Uy + h[6] * Ux * Ux + h[7] * Ux * Uy + h[8] * Uy * Uy;
-  gn += h[0] / mT + h[1] * U0 + h[2] * Ux + h[3] * Uy + r2 * A + (h[6] + h[8]) * T;
-  gT += -h[0] * n / (mT * mT) + n * dr2 * A + (h[6] + h[8]) * n;
+  gn += h[0] * imT + h[1] * U0 + h[2] * Ux + h[3] * Uy + r2 * A + (h[6] + h[8]) * T;
+  gT += -h[0] * n * imT * imT + n * dr2 * A + (h[6] + h[8]) * n;
   const S nr2 = n * r2;
   gU0 += h[1] * n + nr2 * (h[4] * Ux + h[5] * Uy);
   gUx += h[2] * n + nr2 * (h[4] * U0 + S(2) * h[6] * Ux + h[7] * Uy);
@@ -70,17 +89,18 @@ __device__ __forceinline__ void dM_vjp(const S (&h)[9], S n, S T, S U0, S Ux, S 
 // ds/dmoments from ds/d(eps, U) through the Landau eigen-solve (Sec. 4).
 // mm: the 9 stored-population moment sums; the totals add the reference.
 template <typename S>
-__device__ __forceinline__ void landau_vjp(const Scalars& sc, const S (&mm)[9], double epsd, S gE, S gU0, S gUx,
+__device__ __forceinline__ void landau_vjp(const Scalars& sc, const S (&mm)[9], S eps, S gE, S gU0, S gUx,
                                            S gUy, S (&gm)[9]) {
-  const S eps = (S)epsd;
-  const S T00 = (S)sc.T00_ref + mm[3], s = mm[4], t = mm[5];
-  const S Txx = (S)sc.Tii_ref + mm[6], r = mm[7], Tyy = (S)sc.Tii_ref + mm[8];
+  S T00r, Tiir, N0r, mr;
+  ref_scalars<S>(sc, T00r, Tiir, N0r, mr);
+  const S T00 = T00r + mm[3], s = mm[4], t = mm[5];
+  const S Txx = Tiir + mm[6], r = mm[7], Tyy = Tiir + mm[8];
   // the reference parts must be added in the working precision
   const S a = T00 - eps, b = Txx + eps, c = Tyy + eps;
   const S D = b * c - r * r;
   const S vx = s * c - r * t, vy = t * b - r * s;
   const S nu2 = D * D - vx * vx - vy * vy;
-  const S inu = S(1) / sqrt(nu2);
+  const S inu = inv_sqrt(nu2);
   // U = v / nu, nu^2 = v0^2 - vx^2 - vy^2
   const S gdot = (gU0 * D + gUx * vx + gUy * vy) * inu * inu * inu;
   const S gv0 = gU0 * inu - gdot * D;
@@ -89,7 +109,7 @@ __device__ __forceinline__ void landau_vjp(const Scalars& sc, const S (&mm)[9], 
   // eigenvalue: p(eps) = a D - s vx - t vy = 0
   const S dp = -D + a * (b + c) - s * s - t * t;
   const S gEt = gE + gv0 * (b + c) + gvx * s + gvy * t;
-  const S k = gEt / dp;
+  const S k = qdiv(gEt, dp);
   gm[3] = -k * D;                                                              // T00
   gm[6] = gv0 * c + gvy * t - k * (a * c - t * t);                             // Txx
   gm[8] = gv0 * b + gvx * s - k * (a * b - s * s);                             // Tyy
@@ -173,6 +193,7 @@ __device__ __forceinline__ void collide_vjp(const Tables<S>& tb, const Scalars& 
   if constexpr (SYM) moments_sym<S, QT>(tb, g, mm);
   else moments9<S, QT, EX>(tb, sc.Q, g, mm);
   Macro M;
+  S eps;
   if constexpr (MIN && sizeof(S) == 4) {
     const int nc = sc.ncell;
     M.fn = __ldg(mac + cell);
@@ -182,7 +203,7 @@ __device__ __forceinline__ void collide_vjp(const Tables<S>& tb, const Scalars& 
     M.fUy = __ldg(mac + 4 * nc + cell);
     M.fdn = __ldg(mac + 5 * nc + cell);
     M.fdT = __ldg(mac + 6 * nc + cell);
-    M.eps = (double)__ldg(mac + 7 * nc + cell);
+    eps = __ldg(mac + 7 * nc + cell);
     M.ok = !isnan(M.fn);
     if (!M.ok) {
 #pragma unroll
@@ -193,13 +214,16 @@ __device__ __forceinline__ void collide_vjp(const Tables<S>& tb, const Scalars& 
   } else {
     M = landau<S, SYM ? (Orbits<QT>::massless ? 1 : 0) : -1>(sc, mm);
     if (!M.ok) atomicAdd(status, 1ULL);
+    eps = (S)M.eps;
   }
+  S T00r, Tiir, N0r, mr;
+  ref_scalars<S>(sc, T00r, Tiir, N0r, mr);
   S dM[9];
   eq_moments_of<S, 9>(sc, M, dM);
   S n, T, U0, Ux, Uy;
   if constexpr (sizeof(S) == 4) { n = M.fn; T = M.fT; U0 = M.fU0; Ux = M.fUx; Uy = M.fUy; }
   else { n = M.n; T = M.T; U0 = M.U0; Ux = M.Ux; Uy = M.Uy; }
-  const S inv_tau = S(1) / tau;
+  const S inv_tau = qdiv(S(1), tau);
   S h[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) h[k] = S(0);
@@ -252,21 +276,21 @@ __device__ __forceinline__ void collide_vjp(const Tables<S>& tb, const Scalars& 
   }
   gtau = -sr * inv_tau;
   S gn = 0, gT = 0, gU0 = q0, gUx = qx, gUy = qy;
-  dM_vjp<S>(h, n, T, U0, Ux, Uy, (S)sc.m, gn, gT, gU0, gUx, gUy);
+  dM_vjp<S>(h, n, T, U0, Ux, Uy, mr, gn, gT, gU0, gUx, gUy);
   // temperature from eps/n (d = 2 closed form)
   S gE;
-  const S eps = (S)M.eps;
+  const S in_ = qdiv(S(1), n);
   if (sc.massless) {
-    gE = gT / (S(2) * n);
-    gn += -gT * T / n;
+    gE = S(0.5) * gT * in_;
+    gn += -gT * T * in_;
   } else {
-    const S m = (S)sc.m, e = eps / n;
-    const S dTde = (T + m) / (S(4) * T + S(2) * m - e);
-    gE = gT * dTde / n;
-    gn += -gT * dTde * e / n;
+    const S m = mr, e = eps * in_;
+    const S dTde = qdiv(T + m, S(4) * T + S(2) * m - e);
+    gE = gT * dTde * in_;
+    gn += -gT * dTde * e * in_;
   }
   // n = U0 N0 - Ux Nx - Uy Ny
-  const S N0 = (S)sc.N0_ref + mm[0], Nx = mm[1], Ny = mm[2];
+  const S N0 = N0r + mm[0], Nx = mm[1], Ny = mm[2];
   gU0 += gn * N0;
   gUx -= gn * Nx;
   gUy -= gn * Ny;
@@ -274,7 +298,7 @@ __device__ __forceinline__ void collide_vjp(const Tables<S>& tb, const Scalars& 
   gm[0] = gn * U0;
   gm[1] = -gn * Ux;
   gm[2] = -gn * Uy;
-  landau_vjp<S>(sc, mm, M.eps, gE, gU0, gUx, gUy, gm);
+  landau_vjp<S>(sc, mm, eps, gE, gU0, gUx, gUy, gm);
   if constexpr (SYM) {
     moments_sym_transpose<S, QT>(tb, gm, a);
   } else {
@@ -314,10 +338,11 @@ __global__ void __launch_bounds__(kThreads, (sizeof(S) == 4 ? 512 : 256) / kThre
   S g[QT], lam[QT], out[QT];
   gather<S, QT, EX, MODE>(tb, a.s, a.xprev, si, g);
   gather_rev<S, QT, EX, MODE>(tb, a.s, a.anext, si, lam);
-  const S tau = (a.s.tau_mode == 1) ? a.tau_field[cell] : (S)a.s.tau;
+  const S tau = (a.s.tau_mode == 1) ? a.tau_field[cell] : const_tau<S>(a.s);
   S gt;
   collide_vjp<S, QT, EX, SYM, MIN>(tb, a.s, g, lam, tau, out, gt, a.status, a.macro, cell);
-  a.gtau[cell] += (double)gt;
+  if constexpr (sizeof(S) == 4) a.gtau[cell] += f2d(gt);   // exact conversion on the integer pipe
+  else a.gtau[cell] += gt;
   S* __restrict__ ob = a.aout + si;
 #pragma unroll
   for (int i = 0; i < QT; ++i)
@@ -370,7 +395,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_loss(const __grid_constant__ T
     const S gUx = ex / U0, gUy = ey / U0, gU0 = -(ex * ux + ey * uy) / U0;
     S gm[9];
     gm[0] = gm[1] = gm[2] = S(0);
-    landau_vjp<S>(a.s, mm, M.eps, S(0), gU0, gUx, gUy, gm);
+    landau_vjp<S>(a.s, mm, (S)M.eps, S(0), gU0, gUx, gUy, gm);
     S out[QT];
 #pragma unroll
     for (int i = 0; i < QT; ++i) {

@@ -130,7 +130,7 @@ struct InitArgs {
 // the FP32 equilibrium (dn = n - n_ref and dT = T - T_ref carry FP64 accuracy).
 struct Macro {
   double eps, U0, Ux, Uy, n, T;
-  float fU0, fUx, fUy, fn, fT, fdn, fdT;
+  float fU0, fUx, fUy, fn, fT, fdn, fdT, feps;
   bool ok;
 };
 

@@ -247,6 +247,7 @@ __device__ __forceinline__ Macro landau_fp32(const Scalars& sc, const float (&mm
     M.fdT = T0 - fTr;
   }
   M.fT = fTr + M.fdT;
+  M.feps = epsr + deps;
   M.eps = sc.T00_ref + f2d(deps);
   M.n = f2d(fn);
   M.T = f2d(M.fT);
@@ -628,7 +629,7 @@ __device__ __forceinline__ void collide_store(const Tables<S>& tb, const Scalars
     macro[4 * nc + cell] = M.fUy;
     macro[5 * nc + cell] = M.fdn;
     macro[6 * nc + cell] = M.fdT;
-    macro[7 * nc + cell] = (float)M.eps;
+    macro[7 * nc + cell] = M.feps;
   }
   S dM[KT];
   eq_moments_of<S, KT>(s, M, dM);
