@@ -546,10 +546,26 @@ def bench_adjoint(torch, rlbm, inputs, stream, L=512, nsteps=2000, K=100):
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     cells = L * L * nsteps
+    Q = lat.Q
+    # algorithmic bytes per cell and step (FP32 storage, per-cell tau):
+    # forward: populations read and written, tau read; backward: the
+    # recomputing forward step (the same plus the 32-byte macroscopic state
+    # written) and the adjoint step (x(t-1) and a(t+1) read, a(t) written,
+    # tau and the state read, the FP64 tau gradient read and written)
+    fwd_b = 2 * Q * 4 + 4
+    bwd_b = (2 * Q * 4 + 4 + 32) + (3 * Q * 4 + 4 + 32 + 16)
+    peak, _ = _peaks()
+    fwd_gbs = fwd_b * cells / (t1 - t0) / 1e9
+    bwd_gbs = bwd_b * cells / (t2 - t1) / 1e9
     res = {"workload": "calibration_shear_%d_%dsteps_ckpt%d" % (L, nsteps, K), "forward_s": round(t1 - t0, 4),
            "backward_s": round(t2 - t1, 4), "backward_over_forward": round((t2 - t1) / (t1 - t0), 3),
            "mlups_forward": round(cells / (t1 - t0) / 1e6, 1),
            "mlups_adjoint_incl_recompute": round(cells / (t2 - t1) / 1e6, 1),
+           "roofline": {"bound": "hbm", "unit": "GB/s", "peak": peak,
+                        "forward": {"bytes_per_cell": fwd_b, "achieved": round(fwd_gbs, 1),
+                                    "frac": round(fwd_gbs / peak, 4)},
+                        "backward": {"bytes_per_cell": bwd_b, "achieved": round(bwd_gbs, 1),
+                                     "frac": round(bwd_gbs / peak, 4)}},
            "loss": float(out["loss"].item()), "grad_tau_norm": float(out["tau"].norm().item())}
     adj.close()
     lat.close()

@@ -51,7 +51,7 @@ __device__ __forceinline__ void gather_rev(const Tables<S>& tb, const Scalars& s
   for (int i = 0; i < QT; ++i) {
     lam[i] = S(0);
     if (i < Qn) {
-      const int o = i * s.iplane + tb.roff[i];
+      const int o = tb.roff[i];
       if constexpr (MODE == kOnLattice) {
         lam[i] = __ldg(base + o);
       } else {
@@ -327,7 +327,7 @@ struct AdjArgs {
 };
 
 template <typename S, int QT, bool EX, int MODE, bool SYM, bool MIN>
-__global__ void __launch_bounds__(kThreads, (sizeof(S) == 4 ? 512 : 256) / kThreads) k_adj_step(const __grid_constant__ Tables<S> tb,
+__global__ void __launch_bounds__(kThreads, (sizeof(S) == 4 ? 640 : 256) / kThreads) k_adj_step(const __grid_constant__ Tables<S> tb,
                                                        const __grid_constant__ AdjArgs<S> a) {
   const int x = blockIdx.x * kBX + threadIdx.x;
   const int y = blockIdx.y * kBY + threadIdx.y;
@@ -346,12 +346,12 @@ __global__ void __launch_bounds__(kThreads, (sizeof(S) == 4 ? 512 : 256) / kThre
   S* __restrict__ ob = a.aout + si;
 #pragma unroll
   for (int i = 0; i < QT; ++i)
-    if (i < Qn) ob[i * a.s.iplane] = out[i];
+    if (i < Qn) ob[tb.pl[i]] = out[i];
   for_each_halo_image(a.s, x, y, [&](long long hi) {
     S* __restrict__ hb = a.aout + hi;
 #pragma unroll
     for (int i = 0; i < QT; ++i)
-      if (i < Qn) hb[i * a.s.iplane] = out[i];
+      if (i < Qn) hb[tb.pl[i]] = out[i];
   });
 }
 

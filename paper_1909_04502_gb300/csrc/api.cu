@@ -260,6 +260,7 @@ void fill_tables(const rlbm_handle* h, const Scalars& s, Tables<R>* t) {
     t->pl[i] = i * (int)s.plane;
     t->offp[i] = t->pl[i] + t->off[i];
     t->offr[i] = t->offp[i] + s.pitch;
+    t->roff[i] += t->pl[i];
     t->fref[i] = (R)(i < (int)h->fref.size() ? h->fref[i] : 0.0);
   }
 }

@@ -97,7 +97,10 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_step3q_cell(const __grid_c
     const float kt = M.ok ? (float)(1.0 / s.tau) : 0.f;
     long long img[26];
     const int nimg = cell_images(s, x, y, z, img);
-    for (int i0 = 0; i0 < kQo3; i0 += BATCH) {
+    // pass 2 in reverse order of the batches: the populations pass 1 read
+    // last are the most likely to be still in L2
+    static_assert(kQo3 % BATCH == 0, "whole batches");
+    for (int i0 = kQo3 - BATCH; i0 >= 0; i0 -= BATCH) {
       float g[BATCH];
 #pragma unroll
       for (int j = 0; j < BATCH; ++j) g[j] = __ldg(base + (long long)(i0 + j) * s.plane + t.off[i0 + j]);
