@@ -34,8 +34,9 @@ struct Tables {
   int off[kMaxQ];          // pull source offset in elements: on-lattice -n_iy*pitch - n_ix;
                            // bilinear o_iy*pitch + o_ix (tap (0,0))
   short dx[kMaxQ], dy[kMaxQ];   // the same offset before the pitch is applied: off = dy*pitch + dx
-  int roff[kMaxQ];         // transposed streaming (adjoint pull): on-lattice +n_iy*pitch + n_ix;
-                           // bilinear (-o_iy-1)*pitch + (-o_ix-1), tap weights bw[i][3-k]
+  int roff[kMaxQ];         // transposed streaming (adjoint pull) relative to the cell, plane
+                           // included: pl[i] + n_iy*pitch + n_ix on-lattice; bilinear
+                           // pl[i] + (-o_iy-1)*pitch + (-o_ix-1), tap weights bw[i][3-k]
   int pl[kMaxQ];           // i * plane: start of population plane i
   int offp[kMaxQ];         // pl[i] + off[i]: pull source of population i relative to the cell
   int offr[kMaxQ];         // offp[i] + pitch: the bilinear taps' second row
