@@ -229,7 +229,10 @@ def collide1(f, quad: Quadrature1, exp: Expansion1, tau, eqwall=False, wall_T=(0
         for side, col in enumerate((0, f.shape[1] - 1)):
             T = wall_T[side] if wall_T[side] > 0 else fl.T[col]
             fs[:, col] = exp.feq(np.array([fl.n[col]]), np.array([[1.0], [0.0]]), np.array([T]))[:, 0]
-    return fs, fl
+    # a cell without a physical Landau frame is left unrelaxed
+    with np.errstate(invalid="ignore"):
+        good = fl.ok & (fl.n > 0) & (fl.T > 0) & np.isfinite(fl.T)
+    return np.where(good[None], fs, f), fl
 
 
 def stream1(fs, shifts, boundary="periodic"):

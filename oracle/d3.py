@@ -240,8 +240,10 @@ def collide3(f, quad: Quadrature3, exp: Expansion3, tau):
     feq = exp.feq(fl.n, fl.U, fl.T)
     pU = np.tensordot(quad.p * np.array([1.0, -1.0, -1.0, -1.0]), fl.U, axes=([1], [0]))
     om = pU / (quad.p[:, 0].reshape((-1,) + (1,) * (f.ndim - 1)) * tau)
-    om = np.where(fl.ok[None], om, 0.0)
-    return f - om * (f - feq), fl
+    with np.errstate(invalid="ignore"):
+        good = fl.ok & (fl.n > 0) & (fl.T > 0) & np.isfinite(fl.n) & np.isfinite(fl.T)
+    # (selected, not multiplied by zero: the frame of a bad cell may be NaN)
+    return np.where(good[None], f - om * (f - feq), f), fl
 
 
 def stream3(fs, shifts):

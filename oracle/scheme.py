@@ -185,7 +185,20 @@ def collide(f, quad: Quadrature, exp: Expansion, tau, g=None, eqwall=False, wall
             rest = np.zeros((3,) + n.shape)
             rest[0] = 1.0
             fs[:, :, col] = exp.feq(n, rest, T)
+    # a cell without a physical Landau frame (no timelike eigenvector, n or T
+    # not positive, non-finite moments) is left unrelaxed (reading of the
+    # states the paper does not discuss)
+    bad = ~physical(fl)
+    if np.any(bad):
+        fs = np.where(bad[None], f, fs)
     return fs, fl
+
+
+def physical(fl):
+    """Cells whose Landau frame exists: a timelike eigenvector with a real
+    positive eigenvalue, n > 0, T > 0, all finite."""
+    with np.errstate(invalid="ignore"):
+        return fl.ok & (fl.n > 0) & (fl.T > 0) & np.isfinite(fl.n) & np.isfinite(fl.T)
 
 
 class Simulation:

@@ -213,7 +213,14 @@ __device__ __forceinline__ void collide_vjp(const Tables<S>& tb, const Scalars& 
     }
   } else {
     M = landau<S, SYM ? (Orbits<QT>::massless ? 1 : 0) : -1>(sc, mm);
-    if (!M.ok) atomicAdd(status, 1ULL);
+    if (!M.ok) {
+      // the forward step left this cell unrelaxed: its collision is the identity
+      atomicAdd(status, 1ULL);
+#pragma unroll
+      for (int i = 0; i < QT; ++i) a[i] = lam[i];
+      gtau = S(0);
+      return;
+    }
     eps = (S)M.eps;
   }
   S T00r, Tiir, N0r, mr;

@@ -324,6 +324,24 @@ __device__ __forceinline__ void mj_delta3(const Macro3f& M, float nr, float Tr, 
 // needs (full moments in FP64, differences from the reference in FP32), and
 // tau^-1 U (zero where the cell has no Landau frame, which leaves it
 // unrelaxed).  Returns whether the frame exists.
+// A cell without a physical Landau frame is left unrelaxed (Omega = 0); its
+// frame is replaced by the reference state (rest, n_ref or 1, T_ref) so
+// that the equilibrium and Omega stay finite (0 * NaN is not 0).
+__device__ __forceinline__ void unphysical_to_reference3(const Scalars3& s, Macro3& M) {
+  M.n = s.n_ref > 0.0 ? s.n_ref : 1.0;
+  M.T = s.T_ref;
+  M.eps = 3.0 * M.n * M.T;
+  M.U[0] = 1.0;
+  M.U[1] = M.U[2] = M.U[3] = 0.0;
+}
+__device__ __forceinline__ void unphysical_to_reference3(const Scalars3& s, Macro3f& M) {
+  M.n = (float)(s.n_ref > 0.0 ? s.n_ref : 1.0);
+  M.T = (float)s.T_ref;
+  M.dn = M.dT = 0.f;
+  M.U0 = 1.f;
+  M.Ux = M.Uy = M.Uz = 0.f;
+}
+
 template <typename S, int K>
 __device__ __forceinline__ bool frame3(const S (&m)[14], const Scalars3& s, S (&Mk)[K], S& kU0, S (&kU)[3]) {
   if constexpr (sizeof(S) == 8) {
@@ -332,7 +350,8 @@ __device__ __forceinline__ bool frame3(const S (&m)[14], const Scalars3& s, S (&
                              {m[5], m[8], m[9], m[10]},
                              {m[6], m[9], m[11], m[12]},
                              {m[7], m[10], m[12], m[13]}};
-    const Macro3 M = landau3(N, Tm);
+    Macro3 M = landau3(N, Tm);
+    if (!M.ok) unphysical_to_reference3(s, M);
     mj_full3<K>(M.n, M.T, M.U, Mk);
     const double kt = M.ok ? 1.0 / s.tau : 0.0;
     kU0 = kt * M.U[0];
@@ -346,7 +365,8 @@ __device__ __forceinline__ bool frame3(const S (&m)[14], const Scalars3& s, S (&
                             {m[5], m[8], m[9], m[10]},
                             {m[6], m[9], m[11], m[12]},
                             {m[7], m[10], m[12], m[13]}};
-    const Macro3f M = landau3f(N, Tm, s);
+    Macro3f M = landau3f(N, Tm, s);
+    if (!M.ok) unphysical_to_reference3(s, M);
     mj_delta3<K>(M, (float)s.n_ref, (float)s.T_ref, Mk);
     const float kt = M.ok ? (float)(1.0 / s.tau) : 0.f;
     kU0 = kt * M.U0;

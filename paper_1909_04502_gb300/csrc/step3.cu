@@ -185,9 +185,12 @@ __global__ void __launch_bounds__(128, 8) k_step3f(const __grid_constant__ Table
       for (int v = u; v < 4; ++v) Tm[u][v] = fmaf(gu, tb.cf[i][v], Tm[u][v]);
     }
   }
-  const Macro3f M = landau3f(N, Tm, s);
+  Macro3f M = landau3f(N, Tm, s);
   const bool ok = M.ok;
-  if (!ok) atomicAdd(a.status, 1ULL);
+  if (!ok) {
+    atomicAdd(a.status, 1ULL);
+    unphysical_to_reference3(s, M);      // left unrelaxed below (kt = 0)
+  }
   const float U0 = M.U0, Ux = M.Ux, Uy = M.Uy, Uz = M.Uz;
   float dM[14];
   mj_delta3<14>(M, (float)s.n_ref, (float)s.T_ref, dM);

@@ -84,7 +84,8 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_step3q_cell(const __grid_c
         }
       }
     }
-    const Macro3f M = landau3f(N, Tm, s);
+    Macro3f M = landau3f(N, Tm, s);
+    if (!M.ok) unphysical_to_reference3(s, M);     // left unrelaxed below (kt = 0)
     float Mk[32];
     {
       float Md[kKo3];

@@ -344,6 +344,31 @@ __device__ __forceinline__ void eq_moments_of(const Scalars& sc, const Macro& M,
   }
 }
 
+// The reference state (rest, n_ref, T_ref; n = 1 without the storage
+// shift) in place of a cell's non-physical frame, as selects on the members
+// the step of storage type S reads; ok stays false.
+template <typename S>
+__device__ __forceinline__ void unphysical_to_reference(const Scalars& sc, Macro& M) {
+  const bool bad = !M.ok;
+  if constexpr (sizeof(S) == 4) {
+    const float n = sc.f_n_ref > 0.f ? sc.f_n_ref : 1.f;
+    M.fU0 = bad ? 1.f : M.fU0;
+    M.fUx = bad ? 0.f : M.fUx;
+    M.fUy = bad ? 0.f : M.fUy;
+    M.fn = bad ? n : M.fn;
+    M.fT = bad ? sc.f_T_ref : M.fT;
+    M.fdn = bad ? 0.f : M.fdn;
+    M.fdT = bad ? 0.f : M.fdT;
+  } else {
+    const double n = sc.n_ref > 0.0 ? sc.n_ref : 1.0;
+    M.U0 = bad ? 1.0 : M.U0;
+    M.Ux = bad ? 0.0 : M.Ux;
+    M.Uy = bad ? 0.0 : M.Uy;
+    M.n = bad ? n : M.n;
+    M.T = bad ? sc.T_ref : M.T;
+  }
+}
+
 template <typename S, int ML = -1>
 __device__ __forceinline__ Macro landau(const Scalars& sc, const S (&mm)[9]) {
   if constexpr (sizeof(S) == 4) return landau_fp32<ML>(sc, mm);
@@ -617,8 +642,12 @@ __device__ __forceinline__ void collide_store(const Tables<S>& tb, const Scalars
   S mm[9];
   if constexpr (SYM) moments_sym<S, QT>(tb, g, mm);
   else moments9<S, QT, EX>(tb, s.Q, g, mm);
-  const Macro M = landau<S, SYM ? (Orbits<QT>::massless ? 1 : 0) : -1>(s, mm);
+  Macro M = landau<S, SYM ? (Orbits<QT>::massless ? 1 : 0) : -1>(s, mm);
+  // no physical Landau frame: counted, and left unrelaxed (Omega = 0); the
+  // frame is replaced by the reference state so that the equilibrium and
+  // Omega stay finite (0 * NaN would not leave the populations unchanged)
   if (!M.ok) atomicAdd(status, 1ULL);
+  unphysical_to_reference<S>(s, M);
   if constexpr (MOUT && sizeof(S) == 4) {
     const int cell = y * s.nx + x;
     const int nc = s.ncell;

@@ -952,3 +952,23 @@ def test_order3_massive_equilibrium_matches_arbitrary_precision_evaluation(m, gr
     want = np.array([float(mp.mpf(float(q.w[i])) * sum(a[k] * mp.mpf(str(e.J_ld[k, i])) for k in range(len(a))))
                      for i in range(q.Q)])
     assert np.abs(f - want).max() <= 1e-15 * np.abs(want).max()
+
+
+def test_non_physical_cells_are_left_unrelaxed():
+    """A cell without a physical Landau frame (here its populations negated:
+    no positive density) keeps its populations through the collision, and
+    every other cell is relaxed as usual (reading of states the paper does
+    not discuss)."""
+    q = L.massless_quadrature(2)
+    e = L.Expansion(q)
+    n, ux, uy, T = _random_state((6, 7), umax=0.2)
+    f = e.feq(n, P.four_velocity(ux, uy), T)
+    f = f * (1 + 0.05 * RNG.standard_normal(f.shape))
+    f[:, 2, 3] = -f[:, 2, 3]
+    with np.errstate(invalid="ignore", divide="ignore"):
+        fs, fl = S.collide(f, q, e, 0.9)
+    assert not S.physical(fl)[2, 3] and S.physical(fl).sum() == 41
+    assert np.array_equal(fs[:, 2, 3], f[:, 2, 3])
+    assert np.all(np.isfinite(fs))
+    good = S.physical(fl)
+    assert np.abs(fs - f)[:, good].max() > 1e-6                 # the others do relax
