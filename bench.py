@@ -479,7 +479,7 @@ def bench_batched(torch, rlbm, inputs, stream, steps=10, count=64, seed=1909, si
     runs = inputs.sweep(count=count, seed=seed, side_lo=side_lo, side_hi=side_hi, zetas=zetas)
     cfgs = [dict(nx=r["side"], ny=r["side"], tau=r["tau"], m=r["zeta"], precision="fp32") for r in runs]
     batch = rlbm.Batch(cfgs, cuda_stream=stream.cuda_stream)
-    shape, grid, _ = batch.tune(trial_steps=2)
+    shape, grid, _ = batch.tune(trial_steps=4)
     cells = 0
     for i, r in enumerate(runs):
         f = [np.ascontiguousarray(a) for a in inputs.shear_wave(r["side"], r["side"], amp=0.05)]

@@ -264,9 +264,10 @@ int rlbm_batch_step(rlbm_batch* b, int nsteps);
  * grid = persistent blocks (at most the co-resident limit; a kind with fewer
  * tiles runs with one block per tile). */
 int rlbm_batch_config(rlbm_batch* b, int tile_shape, int grid);
-/* Autotuner: times trial_steps steps for each tile shape and three grid
- * sizes and keeps the fastest.  It advances every instance by
- * 12 * trial_steps steps; call it before rlbm_init of the instances.
+/* Autotuner: times trial_steps steps for each tile shape and five grid
+ * sizes (1, 3/4, 1/2, 1/3 and 1/4 of the co-resident limit) and keeps the
+ * fastest.  It advances every instance by 20 * trial_steps steps; call it
+ * before rlbm_init of the instances.
  * Outputs are nullable. */
 int rlbm_batch_tune(rlbm_batch* b, int trial_steps, int* tile_shape, int* grid, float* ms_per_step);
 /* Current configuration, co-resident limits {32x8, 32x4} (the smallest over

@@ -553,8 +553,8 @@ int rlbm_batch_tune(rlbm_batch* b, int trial_steps, int* tile_shape, int* grid, 
   int rc = RLBM_OK;
   for (int shape = 0; shape < 2 && rc == RLBM_OK; ++shape) {
     const int gmax = b->grid_max[shape];
-    const int cands[3] = {gmax, (gmax * 3) / 4, gmax / 2};
-    for (int c = 0; c < 3 && rc == RLBM_OK; ++c) {
+    const int cands[5] = {gmax, (gmax * 3) / 4, gmax / 2, gmax / 3, gmax / 4};
+    for (int c = 0; c < 5 && rc == RLBM_OK; ++c) {
       if (cands[c] <= 0) continue;
       rc = rlbm_batch_config(b, shape, cands[c]);
       if (rc == RLBM_OK) rc = rlbm_batch_step(b, trial_steps);   // capture + warm-up
