@@ -407,7 +407,7 @@ def main():
         "config": {"workload": wl["workload"], "nx": L, "ny": L, "Q": Q, "order": wl["order"],
                    "quadrature": "App. H massless order 2", "stream": wl["stream"], "lambda": wl["lam"],
                    "tau": wl["tau"], "u0": wl["u0"],
-                   "landau": "FP32 Newton, FP64 residual correction of the eigenvalue" if elem == 4 else "FP64",
+                   "landau": "FP32 Newton, float-float (48-bit) residual correction of the eigenvalue" if elem == 4 else "FP64",
                    "l2": "flushed before every timed step (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,

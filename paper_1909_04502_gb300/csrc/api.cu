@@ -99,6 +99,8 @@ void finish_scalars(Scalars* s) {
   s->f_T_ref = (float)s->T_ref;
   s->f_T00_ref = (float)s->T00_ref;
   s->f_Tii_ref = (float)s->Tii_ref;
+  s->f_PE_hi = (float)s->PE_ref;
+  s->f_PE_lo = (float)(s->PE_ref - (double)s->f_PE_hi);
 }
 
 // Halo widths and padded layout of the population planes (kernels.cuh).

@@ -2,7 +2,8 @@
 // pipe (IEEE-754 bit layouts), keeping the FP64 pipe for arithmetic (a
 // hardware conversion costs about as much as an FP64 multiply on this part).
 // Zero and FP32 denormals map to signed zero; infinities and NaNs keep their
-// class.  Shared by the (2+1)-d and (3+1)-d kernels.
+// class.  Also float-float arithmetic on the FP32 pipe.  Shared by the
+// (2+1)-d and (3+1)-d kernels.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -38,6 +39,54 @@ __device__ __forceinline__ float d2f(double d) {
   const unsigned special = is_nan ? 0x7FC00000u : (sgn | 0x7F800000u);
   b = (e <= 0) ? sgn : ((e >= 255 || ed == 0x7FFu) ? special : b);
   return __uint_as_float(b);
+}
+
+// Float-float arithmetic: a value is the unevaluated sum hi + lo of two FP32
+// numbers (about 48 significant bits), built on error-free transformations
+// (Knuth's two-sum, the FMA two-product).  It runs on the FP32 pipe, whose
+// rate is 64 times the FP64 rate on this part.  ff_add and ff_sub are the
+// "sloppy" sums: their error is a few units of 2^-48 of the larger operand,
+// also under cancellation.  Valid while no intermediate over- or underflows.
+struct ff {
+  float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_sum(float a, float b) {       // exact a + b
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+
+__device__ __forceinline__ ff ff_fast(float a, float b) {      // exact a + b for |a| >= |b|
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+
+__device__ __forceinline__ ff ff_prod(float a, float b) {      // exact a * b
+  const float p = a * b;
+  return {p, fmaf(a, b, -p)};
+}
+
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const ff s = ff_sum(a.hi, b.hi);
+  return ff_fast(s.hi, s.lo + (a.lo + b.lo));
+}
+
+__device__ __forceinline__ ff ff_sub(ff a, ff b) {
+  const ff s = ff_sum(a.hi, -b.hi);
+  return ff_fast(s.hi, s.lo + (a.lo - b.lo));
+}
+
+// The products are left unnormalised (|lo| may exceed half an ulp of hi by a
+// few units of 2^-24 |lo|); the sums above accept such operands.
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  const ff p = ff_prod(a.hi, b.hi);
+  return {p.hi, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo))};
+}
+
+__device__ __forceinline__ ff ff_mulf(float a, ff b) {
+  const ff p = ff_prod(a, b.hi);
+  return {p.hi, fmaf(a, b.lo, p.lo)};
 }
 
 }  // namespace rlbm

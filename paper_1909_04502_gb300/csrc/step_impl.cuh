@@ -149,8 +149,9 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 }
 
 // FP32 storage: the solve runs in FP32, then one Newton correction whose
-// residual p(l) is evaluated in FP64 at the FP32 root (the eigenvalue, and
-// with it eps, carries FP64 accuracy: it decides energy conservation).  The
+// residual p(l) is evaluated in float-float arithmetic (about 48 bits) at
+// the FP32 root (the eigenvalue, and with it eps, carries that accuracy: it
+// decides energy conservation).  The
 // rest is formed in FP32 from quantities accurate relative to the deviation
 // from the reference state, so that every FP32 rounding is proportional to
 // that deviation, like the storage of g = f - f_ref itself:
@@ -165,7 +166,7 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 //     cancellation);
 //   d_eps = eps - eps_ref (the FP32 Newton unknown plus its correction);
 //   dT = T - T_ref from the EOS written for differences.
-// 13 FP64 operations per cell.  The moments are reference + FP32 sums of g,
+// No FP64 operation.  The moments are reference + FP32 sums of g,
 // and the eigenvalue is written l = eps_ref + delta.
 // ML: 1 massless, 0 massive (known at compile time), -1 decided by sc.massless.
 template <int ML = -1>
@@ -192,19 +193,17 @@ __device__ __forceinline__ Macro landau_fp32(const Scalars& sc, const float (&mm
     dp = -D + a * (b + c) - M2;
     del -= __fdividef(p, dp);
   }
-  // FP64 residual p(l) at l = eps_ref + del
+  // residual p(l) at l = eps_ref + del in float-float arithmetic; every
+  // input but P_ref + eps_ref is an FP32 number
   {
-    const double dd = f2d(del);
-    const double s = f2d(fs), t = f2d(ft), r = f2d(fr);
-    const double base = sc.PE_ref + dd;
-    const double ad = f2d(mm[3]) - dd;
-    const double bd = base + f2d(mm[6]);
-    const double cd = base + f2d(mm[8]);
-    const double D = fma(bd, cd, -r * r);
-    const double vx = fma(s, cd, -r * t);
-    const double vy = fma(t, bd, -r * s);
-    const double p = fma(ad, D, -fma(s, vx, t * vy));
-    dp = -__fdividef(d2f(p), dp);     // Newton correction dl (FP32 is enough)
+    const ff PE = {sc.f_PE_hi, sc.f_PE_lo};
+    const ff cd = ff_add(PE, ff_sum(mm[8], del));             // Tyy + l
+    ff acc = ff_mulf(fs, ff_sub(ff_mulf(fs, cd), ff_prod(fr, ft)));       // s vx
+    const ff bd = ff_add(PE, ff_sum(mm[6], del));             // Txx + l
+    acc = ff_add(acc, ff_mulf(ft, ff_sub(ff_mulf(ft, bd), ff_prod(fr, fs))));   // + t vy
+    const ff D = ff_sub(ff_mul(bd, cd), ff_prod(fr, fr));
+    const ff p = ff_sub(ff_mul(ff_sum(mm[3], -del), D), acc);   // (T00 - l) D - s vx - t vy
+    dp = -__fdividef(p.hi + p.lo, dp);     // Newton correction dl (FP32 is enough)
   }
   const float dl = dp;
   const float fNx = mm[1], fNy = mm[2];
