@@ -297,8 +297,10 @@ const char* rlbm_batch_last_error(const rlbm_batch* b);
 typedef struct rlbm_adjoint rlbm_adjoint;
 
 /* Allocate checkpoints (ceil(nsteps / checkpoint_every) population buffers),
- * one segment of checkpoint_every buffers, two adjoint buffers and per-cell
- * accumulators for a run of nsteps steps of handle h (borrowed). */
+ * two segments of checkpoint_every + 1 buffers (the backward pass recomputes
+ * one segment on a second, lowest-priority stream while it runs the adjoint
+ * steps of the other), two adjoint buffers and per-cell accumulators for a
+ * run of nsteps steps of handle h (borrowed). */
 int rlbm_adjoint_create(rlbm_handle* h, int nsteps, int checkpoint_every, rlbm_adjoint** out);
 void rlbm_adjoint_destroy(rlbm_adjoint* A);
 /* Forward pass: rlbm_init(n, u, T) then nsteps steps, saving checkpoints.

@@ -543,8 +543,16 @@ struct rlbm_adjoint {
   int T = 0;                              // forward steps of the run
   int K = 0;                              // checkpoint interval
   void* ckpt = nullptr;                   // checkpoints x(0), x(K), x(2K), ...
-  void* seg = nullptr;                    // recomputed states of one segment (K + 1 buffers)
-  float* macro = nullptr;                 // FP32 storage: macroscopic states of the segment [K + 1][planes][ncell]
+  // recomputed states of a segment (K + 1 buffers) and, FP32 storage, their
+  // macroscopic states [K + 1][planes][ncell]: two sets, so that the
+  // recomputation of segment s - 1 (on stream st2) overlaps the adjoint
+  // steps of segment s (on the handle's stream)
+  void* seg[2] = {nullptr, nullptr};
+  float* macro[2] = {nullptr, nullptr};
+  cudaStream_t st2 = nullptr;             // recomputation stream (lowest priority)
+  cudaEvent_t ev_start = nullptr;         // work before the backward pass (handle's stream)
+  cudaEvent_t ev_rec[2] = {nullptr, nullptr};   // segment set b recomputed
+  cudaEvent_t ev_adj[2] = {nullptr, nullptr};   // adjoint steps on segment set b done
   void* adj[2] = {nullptr, nullptr};      // adjoint populations (ping-pong)
   double* gtau = nullptr;                 // dL/dtau per cell
   double* init_fields = nullptr;          // n0, ux0, uy0, T0 of the run [4][ncell]
@@ -564,20 +572,37 @@ int adj_fail(rlbm_adjoint* A, int code, const std::string& msg) {
 
 void* state_ptr(void* base, size_t bytes, int k) { return (char*)base + bytes * (size_t)k; }
 
-float* macro_ptr(rlbm_adjoint* A, int j) {
-  return A->macro + (size_t)j * kMacroPlanes * (size_t)A->h->sc.ncell;
+float* macro_ptr(rlbm_adjoint* A, int b, int j) {
+  return A->macro[b] + (size_t)j * kMacroPlanes * (size_t)A->h->sc.ncell;
 }
 
 // One forward step from src into dst using the handle's tables; with macro
 // (FP32 storage) the step also writes the macroscopic state of its cells.
-cudaError_t fwd_step(rlbm_handle* h, const void* src, void* dst, float* macro = nullptr) {
+cudaError_t fwd_step(rlbm_handle* h, const void* src, void* dst, float* macro, cudaStream_t st) {
   const int mode = h->p.stream_mode == RLBM_BILINEAR ? kBilinear : kOnLattice;
   if (h->elem == 4) {
     StepArgs<float> a{h->sc, (const float*)src, (float*)dst, (const float*)h->tau_field, h->status, macro};
-    return launch_step<float>(*h->tf, a, mode, h->stream);
+    return launch_step<float>(*h->tf, a, mode, st);
   }
   StepArgs<double> a{h->sc, (const double*)src, (double*)dst, (const double*)h->tau_field, h->status};
-  return launch_step<double>(*h->td, a, mode, h->stream);
+  return launch_step<double>(*h->td, a, mode, st);
+}
+
+void free_adjoint(rlbm_adjoint* A) {
+  cudaFree(A->ckpt);
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(A->seg[b]);
+    cudaFree(A->macro[b]);
+    if (A->ev_rec[b]) cudaEventDestroy(A->ev_rec[b]);
+    if (A->ev_adj[b]) cudaEventDestroy(A->ev_adj[b]);
+  }
+  if (A->ev_start) cudaEventDestroy(A->ev_start);
+  if (A->st2) cudaStreamDestroy(A->st2);
+  cudaFree(A->adj[0]);
+  cudaFree(A->adj[1]);
+  cudaFree(A->gtau);
+  cudaFree(A->init_fields);
+  cudaFree(A->loss);
 }
 
 }  // namespace
@@ -598,9 +623,11 @@ int rlbm_adjoint_create(rlbm_handle* h, int nsteps, int checkpoint_every, rlbm_a
   A->nckpt = (nsteps + A->K - 1) / A->K;
   const size_t nc = (size_t)h->sc.ncell;
   cudaError_t e = cudaMalloc(&A->ckpt, A->buf_bytes * A->nckpt);
-  if (e == cudaSuccess) e = cudaMalloc(&A->seg, A->buf_bytes * (A->K + 1));
-  if (e == cudaSuccess && h->elem == 4 && h->sc.sym && h->q.Q == 28)
-    e = cudaMalloc(&A->macro, sizeof(float) * kMacroPlanes * nc * (A->K + 1));
+  const bool with_macro = h->elem == 4 && h->sc.sym && h->q.Q == 28;
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+    e = cudaMalloc(&A->seg[b], A->buf_bytes * (A->K + 1));
+    if (e == cudaSuccess && with_macro) e = cudaMalloc(&A->macro[b], sizeof(float) * kMacroPlanes * nc * (A->K + 1));
+  }
   if (e == cudaSuccess) e = cudaMalloc(&A->adj[0], A->buf_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&A->adj[1], A->buf_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&A->gtau, nc * sizeof(double));
@@ -608,9 +635,21 @@ int rlbm_adjoint_create(rlbm_handle* h, int nsteps, int checkpoint_every, rlbm_a
   if (e == cudaSuccess) e = cudaMalloc(&A->loss, sizeof(double));
   if (e != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(A->ckpt); cudaFree(A->seg); cudaFree(A->macro); cudaFree(A->adj[0]); cudaFree(A->adj[1]);
-    cudaFree(A->gtau); cudaFree(A->init_fields); cudaFree(A->loss);
+    free_adjoint(A.get());
     return RLBM_ERR_OOM;
+  }
+  int prio_lo = 0, prio_hi = 0;
+  e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&A->st2, cudaStreamNonBlocking, prio_lo);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&A->ev_start, cudaEventDisableTiming);
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+    e = cudaEventCreateWithFlags(&A->ev_rec[b], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&A->ev_adj[b], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_adjoint(A.get());
+    return RLBM_ERR_CUDA;
   }
   cudaMemset(A->adj[0], 0, A->buf_bytes);
   cudaMemset(A->adj[1], 0, A->buf_bytes);
@@ -621,14 +660,8 @@ int rlbm_adjoint_create(rlbm_handle* h, int nsteps, int checkpoint_every, rlbm_a
 void rlbm_adjoint_destroy(rlbm_adjoint* A) {
   if (!A) return;
   cudaStreamSynchronize(A->h->stream);
-  cudaFree(A->ckpt);
-  cudaFree(A->seg);
-  cudaFree(A->macro);
-  cudaFree(A->adj[0]);
-  cudaFree(A->adj[1]);
-  cudaFree(A->gtau);
-  cudaFree(A->init_fields);
-  cudaFree(A->loss);
+  if (A->st2) cudaStreamSynchronize(A->st2);
+  free_adjoint(A);
   delete A;
 }
 
@@ -683,32 +716,54 @@ int rlbm_adjoint_backward(rlbm_adjoint* A, const double* ux_target, const double
   cudaMemsetAsync(A->loss, 0, sizeof(double), st);
   int an = 0;                  // adj[an] holds a(t+1)
   bool have_a = false;
+  // Segment sgi covers the states x(c) .. x(last), c = sgi K.  Its adjoint
+  // steps t (x(t-1) in the segment: t = t_hi .. c+1, t_hi = min(last+1, T-1);
+  // t = T is the loss) read segment set sgi & 1.  The recomputation of
+  // segment sgi - 1 runs on st2 while they execute; it waits for the
+  // adjoint steps of segment sgi + 1, the last readers of its set.
+  auto seg_bounds = [&](int sgi, int& c, int& last, int& t_hi) {
+    c = sgi * A->K;
+    last = std::min(c + A->K, A->T) - 1;
+    t_hi = std::min(last + 1, A->T - 1);
+  };
+  // recompute the segment: seg[j] = x(c + j).  With stored macroscopic
+  // states, macro[j] is that of f(c + j), which adjoint step t = c + j needs,
+  // so the recompute runs up to j = t_hi - c (<= K)
+  auto recompute = [&](int sgi) -> cudaError_t {
+    const int b = sgi & 1;
+    int c, last, t_hi;
+    seg_bounds(sgi, c, last, t_hi);
+    cudaError_t r = cudaMemcpyAsync(state_ptr(A->seg[b], A->buf_bytes, 0), state_ptr(A->ckpt, A->buf_bytes, sgi),
+                                    A->buf_bytes, cudaMemcpyDeviceToDevice, A->st2);
+    const int jmax = A->macro[b] ? std::max(t_hi - c, last - c) : last - c;
+    for (int j = 1; j <= jmax && r == cudaSuccess; ++j)
+      r = fwd_step(h, state_ptr(A->seg[b], A->buf_bytes, j - 1), state_ptr(A->seg[b], A->buf_bytes, j),
+                   A->macro[b] ? macro_ptr(A, b, j) : nullptr, A->st2);
+    if (r == cudaSuccess) r = cudaEventRecord(A->ev_rec[b], A->st2);
+    return r;
+  };
+  e = cudaEventRecord(A->ev_start, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(A->st2, A->ev_start, 0);
+  if (e == cudaSuccess) e = recompute(A->nckpt - 1);
+  if (e != cudaSuccess) return adj_fail(A, RLBM_ERR_CUDA, cudaGetErrorString(e));
   for (int sgi = A->nckpt - 1; sgi >= 0; --sgi) {
-    const int c = sgi * A->K;
-    const int last = std::min(c + A->K, A->T) - 1;        // states x(c) .. x(last) of this segment
-    // adjoint steps t whose x(t-1) lies in this segment: t = last+1 .. c+1
-    // (t >= 1), except that t = T is the loss (done first) -- t runs below T
-    const int t_hi = std::min(last + 1, A->T - 1);
-    // recompute the segment: seg[j] = x(c + j).  With stored macroscopic
-    // states, macro[j] is that of f(c + j), which adjoint step t = c + j
-    // needs, so the recompute runs up to j = t_hi - c (<= K)
-    e = cudaMemcpyAsync(state_ptr(A->seg, A->buf_bytes, 0), state_ptr(A->ckpt, A->buf_bytes, sgi), A->buf_bytes,
-                        cudaMemcpyDeviceToDevice, st);
-    if (e != cudaSuccess) return adj_fail(A, RLBM_ERR_CUDA, cudaGetErrorString(e));
-    const int jmax = A->macro ? std::max(t_hi - c, last - c) : last - c;
-    for (int j = 1; j <= jmax; ++j) {
-      e = fwd_step(h, state_ptr(A->seg, A->buf_bytes, j - 1), state_ptr(A->seg, A->buf_bytes, j),
-                   A->macro ? macro_ptr(A, j) : nullptr);
-      if (e != cudaSuccess) return adj_fail(A, RLBM_ERR_CUDA, cudaGetErrorString(e));
+    const int b = sgi & 1;
+    int c, last, t_hi;
+    seg_bounds(sgi, c, last, t_hi);
+    if (sgi >= 1) {
+      if (sgi + 1 <= A->nckpt - 1) e = cudaStreamWaitEvent(A->st2, A->ev_adj[b ^ 1], 0);
+      if (e == cudaSuccess) e = recompute(sgi - 1);
     }
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, A->ev_rec[b], 0);
+    if (e != cudaSuccess) return adj_fail(A, RLBM_ERR_CUDA, cudaGetErrorString(e));
     if (!have_a) {
       // a(T) from the loss on f(T) = S x(T-1), x(T-1) = seg[last - c]
       if (h->elem == 4) {
-        AdjLossArgs<float> la{s, (const float*)state_ptr(A->seg, A->buf_bytes, last - c), uxt, uyt,
+        AdjLossArgs<float> la{s, (const float*)state_ptr(A->seg[b], A->buf_bytes, last - c), uxt, uyt,
                               (float*)A->adj[an], A->loss, h->status};
         e = adj_loss<float>(*h->tf, la, mode, st);
       } else {
-        AdjLossArgs<double> la{s, (const double*)state_ptr(A->seg, A->buf_bytes, last - c), uxt, uyt,
+        AdjLossArgs<double> la{s, (const double*)state_ptr(A->seg[b], A->buf_bytes, last - c), uxt, uyt,
                                (double*)A->adj[an], A->loss, h->status};
         e = adj_loss<double>(*h->td, la, mode, st);
       }
@@ -716,11 +771,11 @@ int rlbm_adjoint_backward(rlbm_adjoint* A, const double* ux_target, const double
       have_a = true;
     }
     for (int t = t_hi; t >= c + 1; --t) {
-      const void* xprev = state_ptr(A->seg, A->buf_bytes, t - 1 - c);
+      const void* xprev = state_ptr(A->seg[b], A->buf_bytes, t - 1 - c);
       if (h->elem == 4) {
         AdjArgs<float> aa{s, (const float*)xprev, (const float*)A->adj[an], (float*)A->adj[an ^ 1],
                           (const float*)h->tau_field, A->gtau, h->status,
-                          A->macro ? macro_ptr(A, t - c) : nullptr};
+                          A->macro[b] ? macro_ptr(A, b, t - c) : nullptr};
         e = adj_step<float>(*h->tf, aa, mode, st);
       } else {
         AdjArgs<double> aa{s, (const double*)xprev, (const double*)A->adj[an], (double*)A->adj[an ^ 1],
@@ -730,6 +785,8 @@ int rlbm_adjoint_backward(rlbm_adjoint* A, const double* ux_target, const double
       if (e != cudaSuccess) return adj_fail(A, RLBM_ERR_CUDA, cudaGetErrorString(e));
       an ^= 1;
     }
+    e = cudaEventRecord(A->ev_adj[b], st);
+    if (e != cudaSuccess) return adj_fail(A, RLBM_ERR_CUDA, cudaGetErrorString(e));
   }
   // dL/du0 from lambda(0) = S^T a(1)
   double* gux = h->fields + 2 * nc;
