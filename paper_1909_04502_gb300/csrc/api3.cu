@@ -170,6 +170,9 @@ int rlbm3_create(int nx, int ny, int nz, double tau, int order, int precision, v
   h->elem = precision == RLBM_FP32_STORE ? 4 : 8;
   s.n_ref = h->elem == 4 ? 1.0 : 0.0;
   s.T_ref = h->elem == 4 ? 1.0 : 0.0;
+  s.f_n_ref = (float)s.n_ref;
+  s.f_T_ref = (float)s.T_ref;
+  s.f_inv_tau = (float)(1.0 / s.tau);
   // order 2 keeps 32-bit pull offsets i * plane - shift; order 3 adds the
   // plane offset in 64 bits and keeps only the shift
   if (order == 2 && (long long)s.Q * s.plane >= (1LL << 31))

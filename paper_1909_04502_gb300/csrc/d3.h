@@ -29,6 +29,7 @@ struct Scalars3 {
   long long slab, plane;  // elements per z-slab and per population plane
   double tau;
   double n_ref, T_ref;    // FP32 storage reference state (0, 0 for FP64 storage)
+  float f_n_ref, f_T_ref, f_inv_tau;   // FP32 copies of n_ref, T_ref and 1 / tau
 };
 
 // S: storage type (double: f; float: g = f - f_ref)

@@ -336,7 +336,7 @@ __device__ __forceinline__ void unphysical_to_reference3(const Scalars3& s, Macr
 }
 __device__ __forceinline__ void unphysical_to_reference3(const Scalars3& s, Macro3f& M) {
   M.n = (float)(s.n_ref > 0.0 ? s.n_ref : 1.0);
-  M.T = (float)s.T_ref;
+  M.T = s.f_T_ref;
   M.dn = M.dT = 0.f;
   M.U0 = 1.f;
   M.Ux = M.Uy = M.Uz = 0.f;
@@ -367,8 +367,8 @@ __device__ __forceinline__ bool frame3(const S (&m)[14], const Scalars3& s, S (&
                             {m[7], m[10], m[12], m[13]}};
     Macro3f M = landau3f(N, Tm, s);
     if (!M.ok) unphysical_to_reference3(s, M);
-    mj_delta3<K>(M, (float)s.n_ref, (float)s.T_ref, Mk);
-    const float kt = M.ok ? (float)(1.0 / s.tau) : 0.f;
+    mj_delta3<K>(M, s.f_n_ref, s.f_T_ref, Mk);
+    const float kt = M.ok ? s.f_inv_tau : 0.f;
     kU0 = kt * M.U0;
     kU[0] = kt * M.Ux;
     kU[1] = kt * M.Uy;

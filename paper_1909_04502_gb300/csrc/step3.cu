@@ -193,8 +193,8 @@ __global__ void __launch_bounds__(128, 8) k_step3f(const __grid_constant__ Table
   }
   const float U0 = M.U0, Ux = M.Ux, Uy = M.Uy, Uz = M.Uz;
   float dM[14];
-  mj_delta3<14>(M, (float)s.n_ref, (float)s.T_ref, dM);
-  const float kt = ok ? (float)(1.0 / s.tau) : 0.f;
+  mj_delta3<14>(M, s.f_n_ref, s.f_T_ref, dM);
+  const float kt = ok ? s.f_inv_tau : 0.f;
   int ix[2], iy[2], iz[2];
   const int nx2 = images1(x, s.nx, s.h, ix), ny2 = images1(y, s.ny, s.h, iy), nz2 = images1(z, s.nz, s.h, iz);
   long long img[26];

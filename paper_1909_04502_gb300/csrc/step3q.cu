@@ -89,13 +89,13 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_step3q_cell(const __grid_c
     float Mk[32];
     {
       float Md[kKo3];
-      mj_delta3<kKo3>(M, (float)s.n_ref, (float)s.T_ref, Md);
+      mj_delta3<kKo3>(M, s.f_n_ref, s.f_T_ref, Md);
 #pragma unroll
       for (int k = 0; k < kKo3; ++k) Mk[k] = Md[k];
       Mk[30] = Mk[31] = 0.f;
     }
     if (!M.ok) atomicAdd(a.status, 1ULL);
-    const float kt = M.ok ? (float)(1.0 / s.tau) : 0.f;
+    const float kt = M.ok ? s.f_inv_tau : 0.f;
     long long img[26];
     const int nimg = cell_images(s, x, y, z, img);
     // pass 2 in reverse order of the batches: the populations pass 1 read
