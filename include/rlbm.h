@@ -99,8 +99,13 @@ typedef struct rlbm_params {
   double kappa;       /*   kappa = hbar/(k_B T0 dt)                                  */
   int boundary;       /* RLBM_BC_*                                                   */
   int nx, ny;         /* grid size in cells                                          */
-  int precision;      /* RLBM_FP64 | RLBM_FP32_STORE (FP32 populations, FP64 Landau
-                         solve and EOS inversion)                                    */
+  int precision;      /* RLBM_FP64 | RLBM_FP32_STORE: FP32 populations g = f - f_ref
+                         with an FP32 Landau solve whose eigenvalue gets one Newton
+                         correction from a float-float (about 48-bit) residual; at
+                         order 3 with m~ >= 6 on an orbit-symmetric stencil (App. H
+                         columns A-D, the Sec. 6.3 stencil) the equilibrium moments
+                         are float-float and H dM a compensated sum as well, since
+                         FP32 moments lose the 1e-5 bar there                      */
   int stream_mode;    /* RLBM_ONLATTICE | RLBM_BILINEAR                              */
   double lambda;      /* RLBM_BILINEAR: displacement per step = lambda * v_i cells
                          (lambda = 1/dx in units of c dt; the on-lattice value is

@@ -267,6 +267,36 @@ void fill_tables(const rlbm_handle* h, const Scalars& s, Tables<R>* t) {
   }
 }
 
+// FP32 storage at order 3 with m~ >= kXeqMinMass on an orbit-symmetric
+// table runs the extended-precision equilibrium of step_xeq.cu: there the
+// contraction H dM cancels so strongly that FP32 moments lose the 1e-5 bar
+// (at m~ = 10-20 by 10-55 %; at m~ = 7 they keep 3-4e-6).
+constexpr double kXeqMinMass = 6.0;
+
+bool use_xeq(const rlbm_handle* h, const Scalars& s) {
+  return h->p.precision == RLBM_FP32_STORE && h->p.order == 3 && h->p.m >= kXeqMinMass && s.sym &&
+         xeq_supported_q(h->q.Q);
+}
+
+void split_pair(double v, float (&out)[2]) {
+  out[0] = (float)v;
+  out[1] = (float)(v - (double)out[0]);
+}
+
+// The low parts of the FP32 equilibrium matrix (fill_tables rounds H to
+// FP32) and the reference scalars as pairs.
+void fill_xeq_tables(const rlbm_handle* h, const Scalars& s, XeqTables* t) {
+  std::memset(t, 0, sizeof(XeqTables));
+  for (int i = 0; i < h->q.Q; ++i)
+    for (int k = 0; k < h->K; ++k) {
+      const double v = h->H[(size_t)i * h->K + k];
+      t->Hl[i][k] = (float)(v - (double)(float)v);
+    }
+  split_pair(s.m, t->m);
+  split_pair(s.n_ref, t->n_ref);
+  split_pair(s.T_ref, t->T_ref);
+}
+
 int build_quadrature(const rlbm_params* p, Quadrature* q, std::string* err) {
   if (p->quadrature == RLBM_QUAD_MASSLESS) {
     if (p->m != 0.0) { *err = "RLBM_QUAD_MASSLESS needs m = 0"; return RLBM_ERR_INVALID_ARG; }
@@ -460,6 +490,10 @@ int rlbm_create(const rlbm_params* p, rlbm_handle** out) {
   if (h->elem == 4) {
     h->tf.reset(new Tables<float>());
     fill_tables(h.get(), s, h->tf.get());
+    if (use_xeq(h.get(), s)) {
+      h->txq.reset(new XeqTables());
+      fill_xeq_tables(h.get(), s, h->txq.get());
+    }
   } else {
     h->td.reset(new Tables<double>());
     fill_tables(h.get(), s, h->td.get());
@@ -551,7 +585,7 @@ int rlbm_init(rlbm_handle* h, const double* n, const double* ux, const double* u
   cudaError_t e;
   if (h->elem == 4) {
     InitArgs<float> a{s, dev[0], dev[1], dev[2], dev[3], (float*)h->buf[h->cur], h->status};
-    e = launch_init<float>(*h->tf, a, h->stream);
+    e = h->txq ? launch_init_xeq(*h->tf, *h->txq, a, h->stream) : launch_init<float>(*h->tf, a, h->stream);
   } else {
     InitArgs<double> a{s, dev[0], dev[1], dev[2], dev[3], (double*)h->buf[h->cur], h->status};
     e = launch_init<double>(*h->td, a, h->stream);
@@ -600,7 +634,9 @@ int rlbm_step(rlbm_handle* h, int nsteps) {
       StepArgs<float> a{h->sc, (const float*)h->buf[h->cur], (float*)h->buf[h->cur ^ 1],
                         (const float*)h->tau_field, h->status};
       const int k = effective_step_kernel(h);
-      if (k == RLBM_KERNEL_TMA_32X8 || k == RLBM_KERNEL_TMA_32X4)
+      if (h->txq)
+        e = launch_step_xeq(*h->tf, *h->txq, a, mode, h->stream);
+      else if (k == RLBM_KERNEL_TMA_32X8 || k == RLBM_KERNEL_TMA_32X4)
         e = launch_step_tma(*h->tf, a, mode, k == RLBM_KERNEL_TMA_32X8 ? 8 : 4,
                             h->tma->m[h->cur][k == RLBM_KERNEL_TMA_32X8 ? 0 : 1], h->stream);
       else
@@ -731,7 +767,7 @@ int rlbm_buffers(rlbm_handle* h, void** cur, void** prev, int* elem_size, long l
 void rlbm_internal_set_error(const std::string& msg) { g_create_error = msg; }
 
 int rlbm_internal_prepare(const rlbm_params* p, Scalars* sc, Tables<float>* tf, Tables<double>* td,
-                          std::string* err) {
+                          std::unique_ptr<XeqTables>* txq, std::string* err) {
   {
     const int vrc = validate_params(p, err);
     if (vrc != RLBM_OK) return vrc;
@@ -780,7 +816,14 @@ int rlbm_internal_prepare(const rlbm_params* p, Scalars* sc, Tables<float>* tf, 
     return RLBM_ERR_UNSUPPORTED;
   }
   reference_populations(&h, p->order, m, nr, Tr);
-  if (p->precision == RLBM_FP32_STORE) fill_tables(&h, s, tf);
-  else fill_tables(&h, s, td);
+  if (p->precision == RLBM_FP32_STORE) {
+    fill_tables(&h, s, tf);
+    if (use_xeq(&h, s)) {
+      txq->reset(new XeqTables());
+      fill_xeq_tables(&h, s, txq->get());
+    }
+  } else {
+    fill_tables(&h, s, td);
+  }
   return RLBM_OK;
 }

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/rlbm.h"
+#include "dispatch.h"
 #include "kernels.cuh"
 #include "setup.h"
 #include "step_tma.h"
@@ -20,6 +21,8 @@ struct rlbm_handle {
   rlbm::Scalars sc;              // kernel scalars
   std::unique_ptr<rlbm::Tables<float>> tf;    // kernel tables, FP32 storage
   std::unique_ptr<rlbm::Tables<double>> td;   // kernel tables, FP64
+  std::unique_ptr<rlbm::XeqTables> txq;       // FP32 storage at order 3, m~ >= 6: extended-precision
+                                              // equilibrium tables (step_xeq.cu), else null
   size_t elem = 4;               // bytes per stored population
   void* buf[2] = {nullptr, nullptr};   // ping-pong population buffers
   int cur = 0;                   // buf[cur] holds f*(t)

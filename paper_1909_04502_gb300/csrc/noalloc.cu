@@ -22,7 +22,7 @@
 // Provided by api.cu (host only, no device work): kernel tables and scalars
 // for a parameter set, and the thread's error message of rlbm_last_error(NULL).
 int rlbm_internal_prepare(const rlbm_params* p, rlbm::Scalars* sc, rlbm::Tables<float>* tf,
-                          rlbm::Tables<double>* td, std::string* err);
+                          rlbm::Tables<double>* td, std::unique_ptr<rlbm::XeqTables>* txq, std::string* err);
 void rlbm_internal_set_error(const std::string& msg);
 
 namespace rlbm {
@@ -43,6 +43,7 @@ struct Prepared {
   Scalars sc;
   std::unique_ptr<Tables<float>> tf;
   std::unique_ptr<Tables<double>> td;
+  std::unique_ptr<XeqTables> txq;   // extended-precision equilibrium (order 3, m~ >= 6, FP32), or null
 };
 std::map<std::string, std::shared_ptr<Prepared>> g_prepared;   // host-side tables per configuration
 
@@ -124,7 +125,7 @@ int prepare(const rlbm_params* p, std::shared_ptr<Prepared>* out) {
   if (p->precision == RLBM_FP32_STORE) pr->tf.reset(new Tables<float>());
   else pr->td.reset(new Tables<double>());
   std::string err;
-  int rc = rlbm_internal_prepare(p, &pr->sc, pr->tf.get(), pr->td.get(), &err);
+  int rc = rlbm_internal_prepare(p, &pr->sc, pr->tf.get(), pr->td.get(), &pr->txq, &err);
   if (rc != RLBM_OK) return set_error(rc, err);
   std::lock_guard<std::mutex> lock(g_mutex);
   g_prepared[key] = pr;
@@ -159,7 +160,7 @@ extern "C" int rlbm_step_noalloc(const rlbm_params* p, void* f_a, void* f_b, con
     void* outp = buf[(s + 1) & 1];
     if (pr->tf) {
       StepArgs<float> a{pr->sc, (const float*)in, (float*)outp, (const float*)tau_field, scratch + s};
-      e = launch_step<float>(*pr->tf, a, mode, st);
+      e = pr->txq ? launch_step_xeq(*pr->tf, *pr->txq, a, mode, st) : launch_step<float>(*pr->tf, a, mode, st);
     } else {
       StepArgs<double> a{pr->sc, (const double*)in, (double*)outp, (const double*)tau_field, scratch + s};
       e = launch_step<double>(*pr->td, a, mode, st);

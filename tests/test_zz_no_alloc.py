@@ -160,3 +160,12 @@ def test_noalloc_order3_tau_field(rl):
         kw = dict(order=3, precision=precision, tau_mode="field")
         err = _noalloc_vs_handle(rl, nx, ny, fields, kw, nsteps=3, tau=tau)
         assert err <= tol, (precision, err)
+
+
+def test_noalloc_high_mass_order3_extended_equilibrium(rl):
+    """Order 3, FP32 storage, m~ = 10: both paths run the extended-precision
+    equilibrium and agree bit for bit."""
+    nx, ny = 34, 22
+    fields = [np.ascontiguousarray(a) for a in inputs.random_smooth(nx, ny, seed=25, umax=0.2)]
+    err = _noalloc_vs_handle(rl, nx, ny, fields, dict(m=10.0, order=3, precision="fp32"), nsteps=3)
+    assert err == 0.0, err
