@@ -260,6 +260,37 @@ def test_fp32_high_mass_order3_parity(rl, case):
     assert lat.sync_status()[0] == 0
 
 
+def test_fp32_landau_eigenvalue_carries_the_float_float_residual(rl):
+    """FP32 storage: the eigenvalue eps reported for each cell agrees with an
+    FP64 eigen-solve (the oracle's LAPACK Landau frame, Sec. 4) of the very
+    moment sums the library solved (rlbm_moments reports them), to the FP32
+    rounding of d_eps = eps - eps_ref alone.  The FP32 Newton root is
+    corrected once with a float-float residual; with an FP32 residual the
+    error would be about 1e-8 here, set by the momentum terms of p(l) in a
+    bulk flow at |u| = 0.49 rather than by d_eps (a few 1e-4: n and T vary
+    by 1e-4 over long wavelengths, the flow is uniform, so streaming barely
+    moves the Landau-frame energy)."""
+    from oracle import physics
+    nx, ny = 64, 48
+    X, Y = np.meshgrid(2 * np.pi * np.arange(nx) / nx, 2 * np.pi * np.arange(ny) / ny)
+    fields = [np.ascontiguousarray(a) for a in
+              (1 + 1e-4 * np.sin(X + Y), np.full((ny, nx), 0.45), np.full((ny, nx), 0.2),
+               1 + 1e-4 * np.cos(2 * X - Y))]
+    lat = rl.Lattice(nx, ny, precision="fp32", tau=0.8)
+    lat.init(*fields)
+    lat.step(3)
+    m = lat.moments(full=True)
+    t = m["Tab"]        # T00, T0x, T0y, Txx, Txy, Tyy
+    Tab = np.array([[t[0], t[1], t[2]], [t[1], t[3], t[4]], [t[2], t[4], t[5]]])
+    eps_o, _, _, ok = physics.landau(m["N"], Tab)
+    assert ok.all()
+    deps = np.abs(eps_o - 2.0)          # eps_ref = 2 n_ref T_ref (massless, n_ref = T_ref = 1)
+    err = np.abs(m["eps"] - eps_o)
+    assert deps.max() < 1e-3
+    assert np.all(err <= 1.2e-7 * deps + 1e-12), float((err / (deps + 1e-30)).max())
+    assert lat.sync_status()[0] == 0
+
+
 def test_init_reports_input_fields(rl):
     nx, ny = 50, 30
     n, ux, uy, T = inputs.random_smooth(nx, ny, seed=2, umax=0.6)
