@@ -266,10 +266,8 @@ rlbm_handle* rlbm_batch_handle(rlbm_batch* b, int i);
  * kernel per stencil kind; asynchronous). */
 int rlbm_batch_step(rlbm_batch* b, int nsteps);
 /* Launch configuration: tile_shape 0 (32 x 8 cells per block) or 1 (32 x 4);
- * grid = persistent blocks, at most the co-resident limit of the kind with
- * the fewest co-resident blocks per SM (rlbm_batch_info); a kind whose
- * kernel fits more blocks per SM runs proportionally more, and a kind with
- * fewer tiles runs with one block per tile. */
+ * grid = persistent blocks (at most the co-resident limit; a kind with fewer
+ * tiles runs with one block per tile). */
 int rlbm_batch_config(rlbm_batch* b, int tile_shape, int grid);
 /* Autotuner: times trial_steps steps for each tile shape and five grid
  * sizes (1, 3/4, 1/2, 1/3 and 1/4 of the co-resident limit) and keeps the

@@ -120,20 +120,13 @@ __device__ __forceinline__ void batch_tile(const BatchInst& I, int tile, int ste
 
 // One persistent kernel per stencil kind: a kernel compiled for a single
 // population count keeps a per-kind register budget (a kernel holding every
-// kind's cell update spills).  The massless kinds and Q = 25 fit 64
-// registers without spilling and run 1024 resident threads per SM; Q = 33
-// and Q = 29 run 768 (80 registers), since the run-time offsets and the loop
-// state need more registers than the single-grid kernel and their spills at
-// 64 cost more than the lost occupancy.  The tiles of the kind's instances
+// kind's cell update spills).  768 resident threads per SM (80 registers):
+// the run-time offsets and the loop state need more registers than the
+// single-grid kernel's 64, and at 1024 threads the spills cost more than the
+// lost occupancy (measured 3-10 % slower).  The tiles of the kind's instances
 // are the contiguous range [tile_lo, tile_hi).
-template <int KIND>
-constexpr int batch_threads_per_sm() {
-  return (KIND == kKindQ33 || KIND == kKindQ29) ? 768 : 1024;
-}
-
 template <int BX, int BY, int KIND>
-__global__ void __launch_bounds__(BX * BY, batch_threads_per_sm<KIND>() / (BX * BY))
-    k_batch(const __grid_constant__ BatchArgs a) {
+__global__ void __launch_bounds__(BX * BY, 768 / (BX * BY)) k_batch(const __grid_constant__ BatchArgs a) {
   __shared__ BatchInst s_inst;
   constexpr int kWords = (int)(sizeof(BatchInst) / sizeof(int));
   static_assert(sizeof(BatchInst) % sizeof(int) == 0, "descriptor copied as words");
@@ -190,8 +183,6 @@ struct rlbm_batch {
   int tile_shape = 0;                     // 0: 32 x 8, 1: 32 x 4 (autotuned)
   int grid = 0;                           // persistent grid size (autotuned)
   int grid_max[2] = {0, 0};               // co-resident limit per tile shape (smallest over the kinds present)
-  int nb[2][kNumKinds] = {};              // co-resident blocks per SM of each kind's kernel, per tile shape
-  int nb_min[2] = {0, 0};                 // the smallest of them over the kinds present
   std::map<long long, cudaGraphExec_t> graphs;
   std::string err = "no error";
 };
@@ -269,21 +260,15 @@ int blocks_per_sm(int kind) {
 }
 
 // The kinds run one after another (each a cooperative launch of its own
-// tiles).  b->grid is counted in blocks of the kind with the fewest
-// co-resident blocks per SM; a kind that fits more runs proportionally more
-// (never more than its co-resident limit), and a kind with fewer tiles than
-// that gets a grid of its tile count.
+// tiles); a kind with fewer tiles than the grid gets a grid of its tile count.
 cudaError_t enqueue(rlbm_batch* b, int nsteps, cudaStream_t st) {
   cudaError_t e = cudaMemcpyToSymbolAsync(c_btab, b->tab_host, sizeof(Tables<float>) * kNumKinds, 0,
                                           cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return e;
-  const int sh = b->tile_shape;
   for (int k = 0; k < kNumKinds; ++k) {
     const int tiles = b->kind_hi[k] - b->kind_lo[k];
     if (tiles <= 0) continue;
-    const int sms = b->grid_max[sh] / b->nb_min[sh];
-    const int scaled = (int)std::min((long long)b->grid * b->nb[sh][k] / b->nb_min[sh], (long long)b->nb[sh][k] * sms);
-    const int grid = std::min(scaled, tiles);
+    const int grid = std::min(b->grid, tiles);
     e = (b->tile_shape == 0) ? launch_batch<32, 8>(b, k, nsteps, grid, st) : launch_batch<32, 4>(b, k, nsteps, grid, st);
     if (e != cudaSuccess) return e;
   }
@@ -424,13 +409,9 @@ int rlbm_batch_create(const rlbm_params* params, int count, rlbm_batch** out) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   for (int k = 0; k < kNumKinds; ++k) {
     if (!kind_owner[k]) continue;
-    b->nb[0][k] = blocks_per_sm<32, 8>(k);
-    b->nb[1][k] = blocks_per_sm<32, 4>(k);
-    nb8 = std::min(nb8, b->nb[0][k]);
-    nb4 = std::min(nb4, b->nb[1][k]);
+    nb8 = std::min(nb8, blocks_per_sm<32, 8>(k));
+    nb4 = std::min(nb4, blocks_per_sm<32, 4>(k));
   }
-  b->nb_min[0] = nb8;
-  b->nb_min[1] = nb4;
   b->grid_max[0] = nb8 * sms;
   b->grid_max[1] = nb4 * sms;
   b->grid = b->grid_max[0];
