@@ -231,7 +231,7 @@ __device__ __forceinline__ Macro landau_fp32(const Scalars& sc, const float (&mm
   if (ML == 1 || (ML == -1 && sc.massless)) {
     // eps = 2 n T with eps_ref = 2 n_ref T_ref:  dT = (d_eps - 2 T_ref dn) / (2 n)
     M.fdT = __fdividef(deps - 2.f * fTr * M.fdn, 2.f * fn);
-  } else if (sc.n_ref > 0.0) {
+  } else if (sc.f_n_ref > 0.f) {
     // 2T^2 + (2m - e) T + m (m - e) = 0 for (T, e) and (T_ref, e_ref):
     // dT (2 (T + T_ref + m) - e) = de (T_ref + m),  e = eps/n
     // with T = T_ref + dT:  2 dT^2 + B dT - de (T_ref + m) = 0,  B = 4 T_ref + 2m - e
@@ -787,20 +787,26 @@ __device__ __forceinline__ void cell_update(const Tables<S>& tb, const Scalars& 
 }
 
 // FP32 storage: 1024 resident threads per SM (eight 32 x 4 blocks, at most
-// 64 registers per thread) -- the FP64 polish and the gather latency need
-// the resident warps; 32 x 4 blocks measured 3-7 % faster than 32 x 8.
+// 64 registers per thread) for the on-lattice pull -- the gather latency
+// needs the resident warps; 32 x 4 blocks measured 3-7 % faster than 32 x 8.
+// The bilinear pull (four taps per population) runs seven blocks at up to
+// 72 registers: no spill, 1-2 % faster at 512^2 to 4096^2.  The generic
+// (not orbit-symmetric) on-lattice kernels, which carry the force and wall
+// terms, run six blocks at up to 80 registers instead of spilling 1.6 KB at
+// 64.
 // FP64 storage with more than 56 populations: 256 threads per SM, so that a
 // cell's 64-72 doubles stay in registers (12 % faster at Q = 65); up to 56
 // populations the spills of 512 threads cost less than the lost warps (3 %).
 // SYM: orbit-symmetric moments and equilibrium (built-in massless stencils).
 // MOUT: also write the macroscopic state (a.macro).
-template <typename S, int QT>
+template <typename S, int QT, int MODE, bool SYM>
 constexpr int step_threads_per_sm() {
-  return sizeof(S) == 4 ? (QT <= 40 ? 1024 : 512) : (QT <= 56 ? 512 : 256);
+  return sizeof(S) == 4 ? (QT <= 40 ? (MODE == kBilinear ? 896 : (SYM ? 1024 : 768)) : 512)
+                        : (QT <= 56 ? 512 : 256);
 }
 
 template <typename S, int QT, bool EX, int KT, int MODE, bool SYM, bool MOUT = false>
-__global__ void __launch_bounds__(kThreads, step_threads_per_sm<S, QT>() / kThreads) k_step(const __grid_constant__ Tables<S> tb,
+__global__ void __launch_bounds__(kThreads, step_threads_per_sm<S, QT, MODE, SYM>() / kThreads) k_step(const __grid_constant__ Tables<S> tb,
                                                    const __grid_constant__ StepArgs<S> a) {
   const int x = blockIdx.x * kBX + threadIdx.x;
   const int y = blockIdx.y * kBY + threadIdx.y;
