@@ -4,7 +4,8 @@
 Default workload (the 2-d massless Taylor-Green configuration): 512 x 512
 doubly periodic grid, order-2 massless quadrature (Q = 28), off-lattice
 bilinear streaming with lambda = 1, tau = 1, u0 = 0.1 c, uniform n = T = 1,
-FP32 populations with the FP64 Landau solve.  A bench step is one RLBM time
+FP32 populations with an FP32 Landau solve whose eigenvalue gets a
+float-float (48-bit) Newton correction.  A bench step is one RLBM time
 step (one fused kernel launch over the whole grid); the L2 cache is flushed
 (a 256 MiB write) before every timed step, so each step reads its inputs
 from HBM.  Each launch is timed with CUDA events on the stream it runs on.
@@ -470,7 +471,7 @@ def bench_batched(torch, rlbm, inputs, stream, steps=10, count=64, seed=1909, si
                   zetas=(0.0, 1.0, 10.0)):
     """Batched tau-sweep: `count` shear-wave runs, side ~ U{side_lo..side_hi},
     tau ~ U[0.6, 2.0], zeta round-robin over {0, 1, 10}, amplitude 0.05 c,
-    FP32 storage with the FP64 Landau solve, on-lattice order-2 stencils.  One
+    FP32 storage (float-float Landau correction), on-lattice order-2 stencils.  One
     graph launch per call (one persistent cooperative kernel per stencil
     kind) against the same instances stepped one handle at a time
     (back-to-back launches).  The working set of all instances exceeds L2 for

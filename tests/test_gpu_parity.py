@@ -1,7 +1,8 @@
 """GPU parity of the fused RLBM step (C ABI) against the FP64 oracle.
 
 Bars: relative L-infinity <= 1e-12 in FP64 mode and <= 1e-5 in FP32-storage
-mode (FP64 Landau solve), normalised by max |reference| of the compared
+mode (FP32 Landau solve with an extended-precision eigenvalue correction),
+normalised by max |reference| of the compared
 field.  Grids are ragged (cell counts not multiples of the 256-thread block)
 and span several blocks.
 """
@@ -125,8 +126,8 @@ def test_fast_bulk_flow_parity(rl, kw, ub, precision, tol):
     steps (0.5c at massless N = 3; 0.4c at m~ = 1, N = 2 and m~ = 2, N = 3;
     faster flows drive the truncated equilibrium negative and the cells
     non-physical within a few steps, in the oracle as well), where the Landau
-    solve is least well conditioned: the FP32 mode's FP64 polish keeps
-    1e-5."""
+    solve is least well conditioned: the FP32 mode's float-float eigenvalue
+    correction keeps 1e-5."""
     nx, ny = 40, 24
     lat, sim, idx = make_pair(rl, nx, ny, _fast_flow(nx, ny, ub), precision=precision, **kw)
     for _ in range(2):

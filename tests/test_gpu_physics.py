@@ -93,7 +93,7 @@ def test_tg512_bilinear_5000_steps_conserve_N0_and_T0a(rl):
 
 def test_tg_bilinear_fp32_5000_step_parity_small_grid(rl):
     """The config-2 configuration (bilinear lambda = 1, tau = 1, u0 = 0.1,
-    FP32 storage with the FP64 Landau polish) on a 40 x 40 grid (two tiles
+    FP32 storage with the float-float Landau correction) on a 40 x 40 grid (two tiles
     wide with a ragged tail) for the full 5000 steps against the FP64 oracle:
     populations within 1e-5 relative, velocities within 1e-5 of the initial
     speed."""
