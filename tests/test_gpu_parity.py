@@ -261,6 +261,26 @@ def test_fp32_high_mass_order3_parity(rl, case):
     assert lat.sync_status()[0] == 0
 
 
+@pytest.mark.parametrize("tau_mode", ["field", "eta_over_s"])
+def test_fp32_high_mass_order3_local_tau_free_flow(rl, tau_mode):
+    """The extended-precision equilibrium with a local relaxation time (a
+    per-cell field, or tau from eta/s and the local T) and free-flow ends
+    (m~ = 10, order 3, FP32 storage): 60 steps within 1e-5."""
+    nx, ny = 48, 20
+    n, ux, uy, T = inputs.random_smooth(nx, ny, seed=13, umax=0.2)
+    rng = np.random.default_rng(13)
+    tau = np.ascontiguousarray(0.7 + 0.8 * rng.random((ny, nx)))
+    kw = dict(tau_mode="field", tau_field=tau) if tau_mode == "field" else \
+        dict(tau_mode="eta_over_s", eta_over_s=0.1, kappa=2.5)
+    lat, sim, idx = make_pair(rl, nx, ny, (n, ux, uy, T), m=10.0, order=3, precision="fp32",
+                              boundary="freeflow_x", **kw)
+    for _ in range(3):
+        lat.step(20)
+        sim.step(20)
+        compare(lat, sim, idx, 1e-5)
+    assert lat.sync_status()[0] == 0
+
+
 def test_fp32_landau_eigenvalue_carries_the_float_float_residual(rl):
     """FP32 storage: the eigenvalue eps reported for each cell agrees with an
     FP64 eigen-solve (the oracle's LAPACK Landau frame, Sec. 4) of the very
