@@ -195,17 +195,11 @@ __global__ void __launch_bounds__(128, 8) k_step3f(const __grid_constant__ Table
   float dM[14];
   mj_delta3<14>(M, s.f_n_ref, s.f_T_ref, dM);
   const float kt = ok ? s.f_inv_tau : 0.f;
-  int ix[2], iy[2], iz[2];
-  const int nx2 = images1(x, s.nx, s.h, ix), ny2 = images1(y, s.ny, s.h, iy), nz2 = images1(z, s.nz, s.h, iz);
-  long long img[26];
-  int nimg = 0;
-  for (int cz = -1; cz < nz2; ++cz)
-    for (int cy = -1; cy < ny2; ++cy)
-      for (int cx = -1; cx < nx2; ++cx) {
-        if (cx < 0 && cy < 0 && cz < 0) continue;
-        img[nimg++] = sidx3(s, cx < 0 ? x : ix[cx], cy < 0 ? y : iy[cy], cz < 0 ? z : iz[cz]);
-      }
-  float* __restrict__ out = a.fout;
+  // interior stores (order 2 keeps Q * plane below 2^31), then the periodic
+  // images of cells next to a face from the just-written values (the thread
+  // reads back its own stores), so that interior cells run no image loop
+  const int ipl = (int)s.plane;
+  float* ob = a.fout + si;
 #pragma unroll 2
   for (int i = 0; i < QT; ++i) {
     const float g = __ldg(base + tb.off[i]);
@@ -213,10 +207,24 @@ __global__ void __launch_bounds__(128, 8) k_step3f(const __grid_constant__ Table
 #pragma unroll
     for (int kk = 0; kk < 14; ++kk) geq = fmaf(tb.Hf[i][kk], dM[kk], geq);
     const float om = kt * (U0 - tb.vf[i][0] * Ux - tb.vf[i][1] * Uy - tb.vf[i][2] * Uz);
-    const float gn = fmaf(om, geq - g, g);
-    const long long pl = (long long)i * s.plane;
-    out[pl + si] = gn;
-    for (int m = 0; m < nimg; ++m) out[pl + img[m]] = gn;
+    ob[i * ipl] = fmaf(om, geq - g, g);
+  }
+  int ix[2], iy[2], iz[2];
+  const int nx2 = images1(x, s.nx, s.h, ix), ny2 = images1(y, s.ny, s.h, iy), nz2 = images1(z, s.nz, s.h, iz);
+  if (nx2 + ny2 + nz2 > 0) {
+    long long img[26];
+    int nimg = 0;
+    for (int cz = -1; cz < nz2; ++cz)
+      for (int cy = -1; cy < ny2; ++cy)
+        for (int cx = -1; cx < nx2; ++cx) {
+          if (cx < 0 && cy < 0 && cz < 0) continue;
+          img[nimg++] = sidx3(s, cx < 0 ? x : ix[cx], cy < 0 ? y : iy[cy], cz < 0 ? z : iz[cz]);
+        }
+    for (int i = 0; i < QT; ++i) {
+      const float gn = ob[i * ipl];
+      float* oi = a.fout + (long long)i * s.plane;
+      for (int m = 0; m < nimg; ++m) oi[img[m]] = gn;
+    }
   }
 }
 
