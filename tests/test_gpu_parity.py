@@ -241,6 +241,9 @@ XEQ_CASES = [
     ("massive_m20_N3", 38, 34, dict(m=20.0, order=3)),
     ("paper_stencil45_m15_N3", 40, 36, dict(m=15.0, order=3, groups=PAPER_STENCIL_45)),
     ("massive_m10_N3_bilinear", 36, 30, dict(m=10.0, order=3, stream="bilinear", lam=1.5)),
+    # a mass and a reference temperature that FP32 does not hold exactly
+    # (the kernel takes m and T_ref as float-float pairs)
+    ("massive_m7.3_N3_Tref1.1", 36, 30, dict(m=7.3, order=3, T_ref=1.1)),
 ]
 
 
