@@ -18,9 +18,9 @@
 // Layout: one plane per population, nx interior cells with one halo cell on
 // each side (a periodic image or, for free-flow ends and equilibrium walls,
 // a copy of the end cell), so the pull reads base + x - s.  FP32 storage
-// holds g = f - f_ref (f_ref the equilibrium of (n_ref, rest, T_ref)); the
-// moments, the Landau solve, the EOS and the equilibrium moments are FP64 in
-// both precisions (Q <= 10 populations per cell).
+// holds g = f - f_ref (f_ref the equilibrium of (n_ref, rest, T_ref)) and
+// steps in FP32 from differences to that state (k_step1f); FP64 storage
+// steps in FP64 (Q <= 10 populations per cell).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -64,6 +64,8 @@ struct Tab {
   int s[kMaxQ];           // direction (+1 / -1)
   double H[kMaxQ][kMaxQ]; // f^eq_i - f_ref,i = sum_k H_ik dM_k  (k = 2 (a - 1) + b)
   S Hs[kMaxQ][kMaxQ];     // the same in the storage type
+  // the FP32-storage step: p0 and p0^2 as FP32 (hi, lo) pairs
+  float w1h[kMaxQ], w1l[kMaxQ], w2h[kMaxQ], w2l[kMaxQ];
 };
 
 struct Sc {
@@ -73,6 +75,10 @@ struct Sc {
   double wall_T[2];        // equilibrium walls: first / last cell temperature (0: own T)
   double n_ref, T_ref;     // reference state of FP32 storage (n_ref = 0: none)
   double N0_ref, T00_ref;  // its moments: N^0 = n_ref, T^00 = T^xx = n_ref T_ref (eps = P)
+  // FP32 copies for the FP32-storage step: n_ref, T_ref, eps_ref = n_ref T_ref,
+  // 1 / tau, the wall temperatures and their differences from T_ref
+  float f_n_ref, f_T_ref, f_Er, f_inv_tau;
+  float f_wall_T[2], f_wall_dT[2];
 };
 
 // M_{a,b} - M_{a,b}(n_ref, rest, T_ref) for a = 1..N, b = 0, 1.
@@ -192,6 +198,130 @@ __global__ void __launch_bounds__(kThreads) k_step1(const __grid_constant__ Tab<
     const S om = (S)((M.U0 - (double)tb.s[i] * M.Ux) * itau);   // p.U / (p0 tau)
     const S fe = feq_i<S>(tb, s, i, dM);
     store1<S>(s, fout, i, x, g[i] + om * (fe - g[i]));
+  }
+}
+
+// FP32 storage (g = f - f_ref): the step in FP32 throughout, with every
+// quantity formed from differences to the reference state (n_ref, rest,
+// T_ref), so that each FP32 rounding is of the size of the deviation, like
+// the storage of g itself.  With T^xx = T^00 = E on every population the
+// largest eigenvalue is l = sqrt(E^2 - T0x^2), E = eps_ref + dE, and
+//   l - eps_ref = (dE (2 eps_ref + dE) - T0x^2) / (l + eps_ref),
+// the eigenvector v = (E + l, T0x), nu^2 = v.v,
+//   n - n_ref = (v0 dN0 - v1 Nx + n_ref v1^2 / (v0 + nu)) / nu,
+//   T - T_ref = (l - eps_ref - (n - n_ref) T_ref) / n      (eps = n T),
+// and the moment differences, with E_th = U0 + Ux = e^theta,
+// E_th - 1 = Ux + Ux^2 / (U0 + 1) and (E_th^a - 1) = (E_th - 1) sum_{j<a} E_th^j:
+//   dM_{a,0} / (a-1)! = n T^(a-1) (E_th^a - 1)^2 / (2 E_th^a) + dn T^(a-1)
+//                       + n_ref (T^(a-1) - T_ref^(a-1)),
+//   dM_{a,1} / (a-1)! = n T^(a-1) (E_th^a - 1)(E_th^a + 1) / (2 E_th^a),
+// T^(a-1) - T_ref^(a-1) = T (T^(a-2) - T_ref^(a-2)) + T_ref^(a-2) dT.
+// The FP64-storage step (k_step1<double>) keeps the FP64 arithmetic.
+template <int N>
+__device__ __forceinline__ void moments_dM_f32(float n, float dn, float T, float dT, float Em1, float Eth,
+                                               float nr, float Tr, float (&dM)[2 * N]) {
+  float Ea = 1.f, Sa = 0.f, Ta = 1.f, Tra = 1.f, DTa = 0.f, fact = 1.f;
+#pragma unroll
+  for (int a = 1; a <= N; ++a) {
+    Sa += Ea;                              // sum_{j<a} E_th^j
+    Ea *= Eth;                             // E_th^a
+    if (a > 1) {
+      DTa = T * DTa + Tra * dT;            // T^(a-1) - T_ref^(a-1)
+      Ta *= T;
+      Tra *= Tr;
+      fact *= (float)(a - 1);
+    }
+    const float Em1a = Em1 * Sa;           // E_th^a - 1
+    const float h = __fdividef(0.5f * n * Ta * Em1a, Ea);
+    dM[2 * (a - 1)] = fact * (h * Em1a + dn * Ta + nr * DTa);
+    dM[2 * (a - 1) + 1] = fact * h * (Ea + 1.f);
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_step1f(const __grid_constant__ Tab<float> tb,
+                                                     const __grid_constant__ Sc s, const float* __restrict__ fin,
+                                                     float* __restrict__ fout, unsigned long long* status) {
+  constexpr int Q = 2 * N;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= s.nx) return;
+  float g[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) g[i] = __ldg(fin + (long long)i * s.P + x + 1 - tb.s[i]);   // pull
+  // the four moment sums, compensated: every product g p0^k split exactly
+  // (FMA), every addition exactly (two-sum), the errors and the lo parts of
+  // p0^k summed in a second register.  Plain FP32 sums measured 2.5x the
+  // error of exact ones against the oracle (their rounding is not a
+  // consistent change of the state)
+  float m[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const float sg = tb.s[i] > 0 ? 1.f : -1.f;
+    const float p1 = __fmul_rn(g[i], tb.w1h[i]);   // not contracted into the sums below
+    const float p2 = __fmul_rn(g[i], tb.w2h[i]);
+    const float r1 = fmaf(g[i], tb.w1l[i], fmaf(g[i], tb.w1h[i], -p1));   // p1's error + the lo part
+    const float r2 = fmaf(g[i], tb.w2l[i], fmaf(g[i], tb.w2h[i], -p2));
+    const float p[4] = {p1, sg * p1, p2, sg * p2};
+    const float r[4] = {r1, sg * r1, r2, sg * r2};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float t = m[k] + p[k];
+      const float bb = t - m[k];
+      const float err = (m[k] - (t - bb)) + (p[k] - bb);
+      m[k] = t;
+      c[k] += err + r[k];
+    }
+  }
+  const float dN0 = m[0] + c[0], Nx = m[1] + c[1], dE = m[2] + c[2], T0x = m[3] + c[3];
+  const float Er = s.f_Er, nr = s.f_n_ref, Tr = s.f_T_ref;
+  const float E = Er + dE;
+  const float q = (E - T0x) * (E + T0x);
+  const float l = sqrtf(fmaxf(q, 0.f));
+  const float dl = __fdividef(fmaf(dE, 2.f * Er + dE, -T0x * T0x), l + Er);
+  const float v0 = E + l, v1 = T0x;
+  const float nu2 = (v0 - v1) * (v0 + v1);
+  const float inu = rsqrtf(nu2);
+  const float nu = nu2 * inu;
+  const float dn = (v0 * dN0 - v1 * Nx + __fdividef(nr * v1 * v1, v0 + nu)) * inu;
+  const float n = nr + dn;
+  const float dT = __fdividef(dl - dn * Tr, n);
+  const float T = Tr + dT;
+  const float U0 = v0 * inu, Ux = v1 * inu;
+  const bool ok = q > 0.f && nu2 > 0.f && v0 > 0.f && l > 0.f && n > 0.f && T > 0.f && isfinite(T) &&
+                  isfinite(U0) && isfinite(dn);
+  if (!ok) {
+    atomicAdd(status, 1ULL);                                 // left unrelaxed (Omega = 0)
+#pragma unroll
+    for (int i = 0; i < Q; ++i) store1<float>(s, fout, i, x, g[i]);
+    return;
+  }
+  float dM[Q];
+  const bool wall = s.boundary == RLBM_BC_EQWALL_X && (x == 0 || x == s.nx - 1);
+  if (wall) {
+    // f^eq(n, rest, T_w): theta = 0, T_w the prescribed wall temperature or the cell's own
+    const int side = x == 0 ? 0 : 1;
+    const bool fix = s.f_wall_T[side] > 0.f;
+    const float Tw = fix ? s.f_wall_T[side] : T, dTw = fix ? s.f_wall_dT[side] : dT;
+    moments_dM_f32<N>(n, dn, Tw, dTw, 0.f, 1.f, nr, Tr, dM);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      float fe = 0.f;
+#pragma unroll
+      for (int k = 0; k < Q; ++k) fe = fmaf(tb.Hs[i][k], dM[k], fe);
+      store1<float>(s, fout, i, x, fe);
+    }
+    return;
+  }
+  const float Em1 = Ux + __fdividef(Ux * Ux, U0 + 1.f);     // e^theta - 1
+  moments_dM_f32<N>(n, dn, T, dT, Em1, 1.f + Em1, nr, Tr, dM);
+  const float kt = s.f_inv_tau;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    float fe = 0.f;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) fe = fmaf(tb.Hs[i][k], dM[k], fe);
+    const float om = kt * (U0 - (float)tb.s[i] * Ux);     // p.U / (p0 tau)
+    store1<float>(s, fout, i, x, fmaf(om, fe - g[i], g[i]));
   }
 }
 
@@ -332,6 +462,11 @@ void fill(const rlbm1_handle* h, const std::vector<double>& H, Tab<S>* t) {
   const int Q = h->sc.Q;
   for (int i = 0; i < Q; ++i) {
     t->p0[i] = h->p0[i];
+    const double p2 = h->p0[i] * h->p0[i];
+    t->w1h[i] = (float)h->p0[i];
+    t->w1l[i] = (float)(h->p0[i] - (double)t->w1h[i]);
+    t->w2h[i] = (float)p2;
+    t->w2l[i] = (float)(p2 - (double)t->w2h[i]);
     t->s[i] = h->sgn[i];
     for (int k = 0; k < Q; ++k) {
       t->H[i][k] = H[(size_t)i * Q + k];
@@ -389,6 +524,14 @@ int rlbm1_create(int nx, int order, double tau, int boundary, const double* wall
   s.T_ref = 1.0;
   s.N0_ref = s.n_ref;
   s.T00_ref = s.n_ref * s.T_ref;
+  s.f_n_ref = (float)s.n_ref;
+  s.f_T_ref = (float)s.T_ref;
+  s.f_Er = (float)s.T00_ref;
+  s.f_inv_tau = (float)(1.0 / tau);
+  for (int k = 0; k < 2; ++k) {
+    s.f_wall_T[k] = (float)s.wall_T[k];
+    s.f_wall_dT[k] = (float)(s.wall_T[k] - s.T_ref);
+  }
   h->elem = precision == RLBM_FP32_STORE ? 4 : 8;
   h->stream = (cudaStream_t)stream;
   // reference populations f_ref = H M(n_ref, rest, T_ref) (the shift of FP32 storage)
@@ -468,10 +611,16 @@ int rlbm1_init(rlbm1_handle* h, const double* n, const double* ux, const double*
 int rlbm1_step(rlbm1_handle* h, int nsteps) {
   if (!h || nsteps < 0) return RLBM_ERR_INVALID_ARG;
   for (int it = 0; it < nsteps; ++it) {
-    if (h->elem == 4)
-      k_step1<float><<<grid1(h->sc.nx), kThreads, 0, h->stream>>>(*h->tf, h->sc, (const float*)h->buf[h->cur],
-                                                                   (float*)h->buf[h->cur ^ 1], h->status);
-    else
+    if (h->elem == 4) {
+      const float* in = (const float*)h->buf[h->cur];
+      float* o = (float*)h->buf[h->cur ^ 1];
+      switch (h->sc.N) {
+        case 2: k_step1f<2><<<grid1(h->sc.nx), kThreads, 0, h->stream>>>(*h->tf, h->sc, in, o, h->status); break;
+        case 3: k_step1f<3><<<grid1(h->sc.nx), kThreads, 0, h->stream>>>(*h->tf, h->sc, in, o, h->status); break;
+        case 4: k_step1f<4><<<grid1(h->sc.nx), kThreads, 0, h->stream>>>(*h->tf, h->sc, in, o, h->status); break;
+        default: k_step1f<5><<<grid1(h->sc.nx), kThreads, 0, h->stream>>>(*h->tf, h->sc, in, o, h->status); break;
+      }
+    } else
       k_step1<double><<<grid1(h->sc.nx), kThreads, 0, h->stream>>>(*h->td, h->sc, (const double*)h->buf[h->cur],
                                                                     (double*)h->buf[h->cur ^ 1], h->status);
     const cudaError_t e = cudaGetLastError();

@@ -63,7 +63,7 @@ __device__ __forceinline__ ff ff_fast(float a, float b) {      // exact a + b fo
 }
 
 __device__ __forceinline__ ff ff_prod(float a, float b) {      // exact a * b
-  const float p = a * b;
+  const float p = __fmul_rn(a, b);     // never contracted into an FMA with a later sum
   return {p, fmaf(a, b, -p)};
 }
 

@@ -100,8 +100,13 @@ def test_fp64_parity_periodic(rl, order):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("order", [2, 3])
+@pytest.mark.parametrize("order", [2, 3, 4])
 def test_fp32_storage_parity(rl, order):
+    """FP32 storage at flows up to 0.4c over 100 steps, within 1e-5.  Order 5
+    misses the bar (about 1.3e-5 in u): its equilibrium matrix, applied in
+    FP32, amplifies the rounding of dM; an FP64 Landau state and FP64
+    moments on the host replay miss it alike, so FP64 storage is the order-5
+    precision."""
     lat, sim = _pair(rl, 300, order, _fields(300, 10 + order), precision="fp32")
     for _ in range(4):
         lat.step(25)
@@ -131,11 +136,15 @@ def test_shock_tube_with_free_flow_ends(rl, precision, tol):
 
 
 @pytest.mark.gpu
-def test_equilibrium_walls_at_prescribed_temperatures(rl):
-    lat, sim = _pair(rl, 64, 3, _fields(64, 5, umax=0.2), boundary="eqwall_x", wall_T=np.array([1.02, 0.97]))
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+@pytest.mark.parametrize("wall_T", [(1.02, 0.97), (0.0, 1.03)])
+def test_equilibrium_walls_at_prescribed_temperatures(rl, precision, tol, wall_T):
+    """Equilibrium walls at prescribed temperatures, or (0) at the cell's own."""
+    lat, sim = _pair(rl, 64, 3, _fields(64, 5, umax=0.2), precision=precision, boundary="eqwall_x",
+                     wall_T=np.array(wall_T))
     lat.step(30)
     sim.step(30)
-    _compare(lat, sim, 1e-12)
+    _compare(lat, sim, tol)
 
 
 @pytest.mark.gpu
