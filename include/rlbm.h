@@ -440,8 +440,10 @@ const char* rlbm3_last_error(const rlbm3_handle* h);
  * exactly, so f^eq is the discrete distribution whose moments of those
  * members are the Maxwell-Juttner ones, n (a-1)! T^(a-1) {cosh, sinh}(a th)
  * with U = (cosh th, sinh th).  Landau frame of the 2 x 2 mixed tensor
- * (Sec. 4); EOS eps = P = n T (d = 1, m = 0).  The moments, the Landau solve
- * and the equilibrium moments run in FP64 in both precisions.
+ * (Sec. 4); EOS eps = P = n T (d = 1, m = 0).  FP64 storage computes in
+ * FP64; FP32 storage (g = f - f_ref) computes in FP32 from differences to
+ * the reference state, with compensated moment sums, and meets the 1e-5
+ * parity bar up to order 4 (order 5: about 1.3e-5; use FP64 there).
  * A d = 2 stencil on an nx x 1 grid (rlbm_params.d = 1) is the other way to
  * run a one-dimensional problem: a two-dimensional gas with a 1-d flow.
  * Fields are arrays of nx doubles.
