@@ -234,7 +234,7 @@ def main():
     ap.add_argument("--workload", default="tg512", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint measurements")
-    ap.add_argument("--only", default=None, choices=["batched", "adjoint", "paper", "kh", "d3"],
+    ap.add_argument("--only", default=None, choices=["batched", "adjoint", "paper", "kh", "d3", "forcing", "d1"],
                     help="run only this extra measurement and print its JSON object")
     ap.add_argument("--side", type=int, default=None,
                     help="grid side for --only kh / d3 (default 2048 / 192); smaller sides serve profiling")
@@ -288,6 +288,10 @@ def main():
             res = {"kelvin_helmholtz": bench_kh(torch, rlbm, inputs, stream, L=args.side or 2048)}
         elif args.only == "d3":
             res = {"d3_taylor_green": bench_d3(torch, rlbm, inputs, stream, L=args.side or 192)}
+        elif args.only == "forcing":
+            res = {"forcing_walls": bench_forcing_walls(torch, rlbm, inputs, stream)}
+        elif args.only == "d1":
+            res = {"d1_wave": bench_d1(torch, rlbm, inputs, stream)}
         else:
             res = {"adjoint": bench_adjoint(torch, rlbm, inputs, stream)}
         if rank == 0:
@@ -396,6 +400,8 @@ def main():
                                                                groups=PAPER_STENCIL_45)
         extras["kelvin_helmholtz_2048"] = bench_kh(torch, rlbm, inputs, stream)
         extras["d3_taylor_green_192"] = bench_d3(torch, rlbm, inputs, stream)
+        extras["forcing_walls"] = bench_forcing_walls(torch, rlbm, inputs, stream)
+        extras["d1_wave"] = bench_d1(torch, rlbm, inputs, stream)
         if wl["workload"] == "tg512_bilinear_fp32":
             extras["viscosity"] = bench_tg_viscosity(rlbm, inputs)
 
@@ -679,6 +685,68 @@ def bench_d3(torch, rlbm, inputs, stream, L=192, steps=10, warmup=3):
         rc, bad = lat.sync_status()
         gbs = 2 * lat.Q * elem * L ** 3 / (ms * 1e-3) / 1e9
         out[key] = {"Q": lat.Q, "ms_per_step": round(ms, 3), "mlups": round(L ** 3 / (ms * 1e-3) / 1e6, 1),
+                     "algorithmic_gbs": round(gbs, 1), "frac_of_hbm": round(gbs / peak, 4), "nonphysical": bad}
+        lat.close()
+    return out
+
+
+def _time_steps(torch, lat, stream, steps, warmup):
+    """Mean CUDA-event time of one step (ms), each step timed on its own."""
+    lat.step(warmup)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for a, b in ev:
+        a.record(stream)
+        lat.step(1)
+        b.record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / steps
+
+
+def bench_forcing_walls(torch, rlbm, inputs, stream, nx=4096, ny=1024, m=5.0, steps=10, warmup=3):
+    """The forcing-validation setup of Sec. 8.1 at a size that exercises the
+    bandwidth: a massive gas (m~ = 5, order 2, Q = 29) between equilibrium
+    walls at the first and last column, periodic in y, driven by the
+    gravity-like force g = (0, 1e-8) (forcing scheme B), FP64 and FP32
+    storage.  These run the generic (not orbit-symmetric) kernel, which
+    carries the force and wall terms.  Each buffer holds 3.9 (FP64) or
+    1.9 GB (FP32), more than L2."""
+    import numpy as np
+    peak, _ = _peaks()
+    out = {"workload": f"channel{nx}x{ny}_m{m:g}_eqwalls_force"}
+    one = np.ones((ny, nx))
+    z = np.zeros((ny, nx))
+    for prec, elem in (("fp64", 8), ("fp32", 4)):
+        lat = rlbm.Lattice(nx, ny, m=m, tau=1.0, boundary="eqwall_x", precision=prec, g=(0.0, 1e-8),
+                           cuda_stream=stream.cuda_stream)
+        lat.init(one, z, z.copy(), one)
+        ms = _time_steps(torch, lat, stream, steps, warmup)
+        rc, bad = lat.sync_status(raise_on_error=False)
+        gbs = 2 * lat.Q * elem * nx * ny / (ms * 1e-3) / 1e9
+        out[prec] = {"Q": lat.Q, "ms_per_step": round(ms, 4), "mlups": round(nx * ny / (ms * 1e-3) / 1e6, 1),
+                     "algorithmic_gbs": round(gbs, 1), "frac_of_hbm": round(gbs / peak, 4), "nonphysical": bad}
+        lat.close()
+    return out
+
+
+def bench_d1(torch, rlbm, inputs, stream, nx=1 << 24, order=3, steps=10, warmup=3):
+    """The native (1+1)-d massless gas (App. H (1+1)-d table, order 3,
+    Q = 6) on 2^24 cells with a smooth density and temperature wave and a
+    flow of 0.2c, FP64 and FP32 storage.  Each buffer holds 0.8 (FP64) or
+    0.4 GB (FP32), more than L2."""
+    import numpy as np
+    peak, _ = _peaks()
+    x = 2 * np.pi * np.arange(nx) / nx
+    fields = [np.ascontiguousarray(a) for a in (1 + 0.1 * np.sin(x), 0.2 * np.cos(x), 1 + 0.1 * np.cos(x))]
+    out = {"workload": f"d1_wave_{nx}_order{order}"}
+    Q = 2 * order
+    for prec, elem in (("fp64", 8), ("fp32", 4)):
+        lat = rlbm.Lattice1(nx, order=order, tau=0.9, precision=prec, cuda_stream=stream.cuda_stream)
+        lat.init(*fields)
+        ms = _time_steps(torch, lat, stream, steps, warmup)
+        rc, bad = lat.sync_status()
+        gbs = 2 * Q * elem * nx / (ms * 1e-3) / 1e9
+        out[prec] = {"Q": Q, "ms_per_step": round(ms, 4), "mlups": round(nx / (ms * 1e-3) / 1e6, 1),
                      "algorithmic_gbs": round(gbs, 1), "frac_of_hbm": round(gbs / peak, 4), "nonphysical": bad}
         lat.close()
     return out
