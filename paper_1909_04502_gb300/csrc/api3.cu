@@ -25,9 +25,10 @@ struct rlbm3_handle {
   unsigned long long* status = nullptr;
   cudaStream_t stream = nullptr;
   std::vector<double> fref;       // reference populations (FP32 storage)
-  bool sym = false;               // order 2 in sign-orbit form (the FP64 step needs it)
+  bool sym = false;               // order 2 in sign-orbit form (the FP64 step needs it; FP32 storage uses it)
   // order 3 in sign-orbit form (the FP64 step needs it), or null
   std::unique_ptr<Tables3s3<double>> ts3d;
+  std::unique_ptr<Tables3s3<float>> ts3f;    // order 3, FP32 storage, sign-orbit form (null: row by row)
   // order 3: tables in device memory
   void* dH = nullptr;             // Q x 30, storage precision
   void* dc = nullptr;             // Q x 4
@@ -117,6 +118,10 @@ std::unique_ptr<Tables3s3<S>> order3_runs(const Quadrature3& q, const std::vecto
   }
   if (n8 != kRuns8o3 || n4 != kRuns4o3 || i0 != q.Q || (int)offs.size() != q.Q) return nullptr;
   for (int i = 0; i < q.Q; ++i) t->off[i] = offs[i];
+  for (int r = 0; r < kRuns8o3; ++r)
+    for (int k = 0; k < 8; ++k) t->off8[r][k] = offs[t->start8[r] + k];
+  for (int r = 0; r < kRuns4o3; ++r)
+    for (int k = 0; k < 4; ++k) t->off4[r][k] = offs[t->start4[r] + k];
   return t;
 }
 
@@ -212,6 +217,7 @@ int rlbm3_create(int nx, int ny, int nz, double tau, int order, int precision, v
     if (rc) return fail3(nullptr, rc, "order-3 tables");
   }
   if (order == 3 && h->q.sym && h->elem == 8) h->ts3d = order3_runs<double>(h->q, offs);
+  if (order == 3 && h->q.sym && h->elem == 4) h->ts3f = order3_runs<float>(h->q, offs);
   if (order == 2) {
     // sign-orbit form: 9 runs of 8, then the axis pairs along x, y and z
     static const int kMasks[kRuns3] = {7, 7, 7, 7, 7, 7, 7, 7, 7, 1, 2, 4};
@@ -223,6 +229,7 @@ int rlbm3_create(int nx, int ny, int nz, double tau, int order, int precision, v
                                p[0] * p[3], p[1] * p[1], p[1] * p[2], p[1] * p[3], p[2] * p[2],
                                p[2] * p[3], p[3] * p[3]};
       for (int k = 0; k < 14; ++k) h->tb->mono[r][k] = mono[k];
+      for (int k = 0; k < 14; ++k) h->tb->monof[r][k] = (float)mono[k];
     }
   }
   // the FP64 kernels take the table in sign-orbit form (checked exactly above)
@@ -324,7 +331,7 @@ int rlbm3_step(rlbm3_handle* h, int nsteps) {
       if (h->elem == 4) {
         Step3qArgs<float> a{(const float*)h->buf[h->cur], (float*)h->buf[h->cur ^ 1], h->status, h->sc,
                             (const float*)h->dH, (const float*)h->dc, (const float*)h->dv, h->doff};
-        e = launch_step3q_cell(a, h->stream);
+        e = h->ts3f ? launch_step3q_symf(*h->ts3f, a, h->stream) : launch_step3q_cell(a, h->stream);
       } else {
         Step3qArgs<double> a{(const double*)h->buf[h->cur], (double*)h->buf[h->cur ^ 1], h->status, h->sc,
                              (const double*)h->dH, (const double*)h->dc, (const double*)h->dv, h->doff};
@@ -332,7 +339,7 @@ int rlbm3_step(rlbm3_handle* h, int nsteps) {
       }
     } else if (h->elem == 4) {
       Step3Args<float> a{(const float*)h->buf[h->cur], (float*)h->buf[h->cur ^ 1], h->status, h->sc};
-      e = launch_step3f(*h->tb, a, h->stream);
+      e = h->sym ? launch_step3f_sym(*h->tb, a, h->stream) : launch_step3f(*h->tb, a, h->stream);
     } else {
       Step3Args<double> a{(const double*)h->buf[h->cur], (double*)h->buf[h->cur ^ 1], h->status, h->sc};
       e = launch_step3_sym(*h->tb, a, h->stream);

@@ -19,8 +19,10 @@ struct Tables3 {
   int off[kMaxQ3];        // pull source of population i relative to the cell: i * plane - n_i . strides
   // sign-orbit form (order 2: 9 runs of 8, then the axis pairs along x, y, z):
   // the moment monomials p0, px, py, pz, p0p0, p0px, p0py, p0pz, pxpx, pxpy,
-  // pxpz, pypy, pypz, pzpz of each run's first member (all components >= 0)
+  // pxpz, pypy, pypz, pzpz of each run's first member (all components >= 0),
+  // in FP64 and rounded to FP32
   double mono[kRuns3][14];
+  float monof[kRuns3][14];
 };
 
 struct Scalars3 {
@@ -96,8 +98,10 @@ cudaError_t launch_init3q(const Init3qArgs<S>& a, cudaStream_t st);
 template <typename S>
 cudaError_t launch_fields3q(const Fields3qArgs<S>& a, cudaStream_t st);
 
-// order 2, FP32 storage (k_step3f)
+// order 2, FP32 storage: row by row (k_step3f), or in sign-orbit form
+// (k_step3fs, Tables3::monof filled)
 cudaError_t launch_step3f(const Tables3& tb, const Step3Args<float>& a, cudaStream_t st);
+cudaError_t launch_step3f_sym(const Tables3& tb, const Step3Args<float>& a, cudaStream_t st);
 // The order-3 table in sign-orbit form: 33 runs of 8 and 6 runs of 4 (the
 // (5, 4, 0) patterns, non-zero components x y, x z, x y, x z, y z, y z), each
 // run's first member's equilibrium row, moment monomials (as Tables3::mono)
@@ -109,9 +113,12 @@ struct Tables3s3 {
   S H4[kRuns4o3][30], mono4[kRuns4o3][14], v4[kRuns4o3][3];
   int start8[kRuns8o3], start4[kRuns4o3];
   int off[288];           // pull shifts -n_i . strides (i * plane added in 64 bits)
+  int off8[kRuns8o3][8], off4[kRuns4o3][4];   // the same shifts by run and member
 };
+// order 3 in sign-orbit form: FP64 (k_step3qs) and FP32 storage (k_step3qsf)
 template <typename S>
 cudaError_t launch_step3q_sym(const Tables3s3<S>& tb, const Step3qArgs<S>& a, cudaStream_t st);
+cudaError_t launch_step3q_symf(const Tables3s3<float>& tb, const Step3qArgs<float>& a, cudaStream_t st);
 
 // FP64 step of the order-2 table in sign-orbit form (Tables3::mono filled)
 template <typename S>

@@ -411,6 +411,37 @@ __device__ __forceinline__ void moments_run8(const S (&F)[8], const C* c, S (&m)
   m[13] = fma((S)c[13], F[0], m[13]);
 }
 
+// FP32 storage: the periodic images of a cell next to a face, copied from the
+// values the thread has just stored for the cell itself, B populations at a
+// time so that B loads are in flight (one at a time, each waits on the L2
+// round trip of the one before, as the stores in between may alias them).
+template <int QT, int B>
+__device__ __forceinline__ void images_from_stored(const Scalars3& s, float* out, long long si, int x, int y, int z) {
+  int ix[2], iy[2], iz[2];
+  const int nx2 = images1(x, s.nx, s.h, ix), ny2 = images1(y, s.ny, s.h, iy), nz2 = images1(z, s.nz, s.h, iz);
+  if (nx2 + ny2 + nz2 == 0) return;
+  long long img[26];
+  int nimg = 0;
+  for (int cz = -1; cz < nz2; ++cz)
+    for (int cy = -1; cy < ny2; ++cy)
+      for (int cx = -1; cx < nx2; ++cx) {
+        if (cx < 0 && cy < 0 && cz < 0) continue;
+        img[nimg++] = sidx3(s, cx < 0 ? x : ix[cx], cy < 0 ? y : iy[cy], cz < 0 ? z : iz[cz]);
+      }
+  static_assert(QT % B == 0, "whole batches");
+  const long long P = s.plane;
+  for (int i0 = 0; i0 < QT; i0 += B) {
+    float v[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j) v[j] = out[(long long)(i0 + j) * P + si];
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      float* oi = out + (long long)(i0 + j) * P;
+      for (int m = 0; m < nimg; ++m) oi[img[m]] = v[j];
+    }
+  }
+}
+
 // periodic images of a cell (every side at least h: at most 26)
 __device__ __forceinline__ int cell_images(const Scalars3& s, int x, int y, int z, long long (&img)[26]) {
   int ix[2], iy[2], iz[2];

@@ -2,8 +2,10 @@
 // on-lattice pull, the moments N^a and T^ab, the Landau frame of the 4 x 4
 // mixed tensor (Sec. 4), n = U.N, T = eps / (3n) (Eq. ultra-relativistic-eos,
 // d = 3), f^eq = H M(n, U, T) (Eq. mj-discrete-feq), Anderson-Witting
-// relaxation, store with the periodic halo images.  Kernels: k_step3s (FP64,
-// the table in sign-orbit form) and k_step3f (FP32 storage of g = f - f_ref).
+// relaxation, store with the periodic halo images.  Kernels: k_step3s (FP64)
+// and k_step3fs (FP32 storage of g = f - f_ref), both with the table in
+// sign-orbit form, and k_step3f (FP32 storage, row by row, for a table
+// without that form).
 //
 // Layout: one plane per population, cell (x, y, z) at
 //   (z + h) * slab + (y + h) * pitch + (x + px),  slab = (ny + 2h) * pitch,
@@ -23,9 +25,7 @@ __device__ constexpr int kBasis3Exp[14][3] = {{0, 0, 0}, {0, 0, 0}, {1, 0, 0}, {
                                               {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0}, {1, 1, 0},
                                               {1, 0, 1}, {0, 2, 0}, {0, 1, 1}, {0, 0, 2}};
 
-// The FP64 step in sign-orbit form (the kernel is written for either storage
-// type; with FP32 storage it measured 7 % slower than k_step3f, which is
-// bound by load latency rather than arithmetic, so only FP64 uses it).
+// The FP64 step in sign-orbit form (k_step3fs is its FP32-storage form).
 // Populations come in runs whose members share p0 and |p| componentwise:
 // 9 runs of 8 (member s negates the components whose bit is set in s) and
 // the pairs (+-3, 0, 0), (0, +-3, 0), (0, 0, +-3).  Per run of 8, a
@@ -158,9 +158,9 @@ __global__ void __launch_bounds__(128) k_step3s(const __grid_constant__ Tables3 
 // differences dM = M(n, U, T) - M_ref are written so that each is accurate
 // relative to itself, and the equilibrium, the relaxation and the store are
 // FP32.
-// Eight blocks of 128 threads per SM (64 registers): at 192^3 this is 20 %
-// faster than the 82-register build, which fits six; unrolling the pulls 13
-// or 26 deep instead of 6 gained 4-9 % at 82 registers and spilled at 64.
+// Eight blocks of 128 threads per SM (64 registers).  The handles run
+// k_step3fs, which evaluates the same arithmetic in sign-orbit form; this
+// kernel serves a table without that form.
 template <int QT>
 __global__ void __launch_bounds__(128, 8) k_step3f(const __grid_constant__ Tables3 tb,
                                                    const __grid_constant__ Step3Args<float> a) {
@@ -209,23 +209,100 @@ __global__ void __launch_bounds__(128, 8) k_step3f(const __grid_constant__ Table
     const float om = kt * (U0 - tb.vf[i][0] * Ux - tb.vf[i][1] * Uy - tb.vf[i][2] * Uz);
     ob[i * ipl] = fmaf(om, geq - g, g);
   }
-  int ix[2], iy[2], iz[2];
-  const int nx2 = images1(x, s.nx, s.h, ix), ny2 = images1(y, s.ny, s.h, iy), nz2 = images1(z, s.nz, s.h, iz);
-  if (nx2 + ny2 + nz2 > 0) {
-    long long img[26];
-    int nimg = 0;
-    for (int cz = -1; cz < nz2; ++cz)
-      for (int cy = -1; cy < ny2; ++cy)
-        for (int cx = -1; cx < nx2; ++cx) {
-          if (cx < 0 && cy < 0 && cz < 0) continue;
-          img[nimg++] = sidx3(s, cx < 0 ? x : ix[cx], cy < 0 ? y : iy[cy], cz < 0 ? z : iz[cz]);
-        }
-    for (int i = 0; i < QT; ++i) {
-      const float gn = ob[i * ipl];
-      float* oi = a.fout + (long long)i * s.plane;
-      for (int m = 0; m < nimg; ++m) oi[img[m]] = gn;
+  images_from_stored<QT, 6>(s, a.fout, si, x, y, z);
+}
+
+// FP32 storage in sign-orbit form: the arithmetic of k_step3s on g = f -
+// f_ref in FP32, with the Landau frame of k_step3f (frame3).  Every run is
+// unrolled, so each table entry (pull shift, monomial, H row, velocity) is an
+// immediate constant operand rather than a load by run-time index (with the
+// runs in a loop this form was slower than k_step3f).  At 192^3: 1.52 ms per
+// step against 2.20 ms for k_step3f.  The interior is stored in the
+// relaxation pass; cells next to a face then copy their values to the
+// periodic images, six at a time.
+__global__ void __launch_bounds__(128, 8) k_step3fs(const __grid_constant__ Tables3 tb,
+                                                    const __grid_constant__ Step3Args<float> a) {
+  const Scalars3& s = a.s;
+  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y, z = blockIdx.z;
+  if (x >= s.nx || y >= s.ny || z >= s.nz) return;
+  const long long si = sidx3(s, x, y, z);
+  const float* __restrict__ base = a.fin + si;
+  // pass 1: m = N0 Nx Ny Nz T00 T0x T0y T0z Txx Txy Txz Tyy Tyz Tzz of g
+  float m[14];
+#pragma unroll
+  for (int k = 0; k < 14; ++k) m[k] = 0.f;
+#pragma unroll
+  for (int r = 0; r < 9; ++r) {
+    float f[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) f[q] = __ldg(base + tb.off[8 * r + q]);
+    fwht(f);
+    moments_run8(f, tb.monof[r], m);
+  }
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const float fp = __ldg(base + tb.off[72 + 2 * ax]), fm = __ldg(base + tb.off[73 + 2 * ax]);
+    const float Sm = fp + fm, D = fp - fm;
+    const float* c = tb.monof[9 + ax];
+    const int taa = ax == 0 ? 8 : (ax == 1 ? 11 : 13);
+    m[0] = fmaf(c[0], Sm, m[0]);
+    m[4] = fmaf(c[4], Sm, m[4]);
+    m[1 + ax] = fmaf(c[1 + ax], D, m[1 + ax]);
+    m[5 + ax] = fmaf(c[5 + ax], D, m[5 + ax]);
+    m[taa] = fmaf(c[taa], Sm, m[taa]);
+  }
+  float Mm[14], kU0, kU[3];
+  if (!frame3(m, s, Mm, kU0, kU)) atomicAdd(a.status, 1ULL);
+  // pass 2: equilibrium differences, relaxation, interior store (order 2
+  // keeps Q * plane below 2^31)
+  const int ipl = (int)s.plane;
+  float* ob = a.fout + si;
+#pragma unroll
+  for (int r = 0; r < 9; ++r) {
+    const float* H0 = tb.Hf[8 * r];
+    float C[8];
+    C[0] = fmaf(H0[0], Mm[0], fmaf(H0[1], Mm[1], fmaf(H0[8], Mm[8], fmaf(H0[11], Mm[11], H0[13] * Mm[13]))));
+    C[1] = fmaf(H0[2], Mm[2], H0[5] * Mm[5]);
+    C[2] = fmaf(H0[3], Mm[3], H0[6] * Mm[6]);
+    C[4] = fmaf(H0[4], Mm[4], H0[7] * Mm[7]);
+    C[3] = H0[9] * Mm[9];
+    C[5] = H0[10] * Mm[10];
+    C[6] = H0[12] * Mm[12];
+    C[7] = 0.f;
+    fwht(C);
+    const float* vb = tb.vf[8 * r];
+    const float X = vb[0] * kU[0], Y = vb[1] * kU[1], Z = vb[2] * kU[2];
+    const float r0 = kU0 - X, r1 = kU0 + X;
+    const float R[4] = {r0 - Y, r1 - Y, r0 + Y, r1 + Y};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int i = 8 * r + q;
+      const float om = (q & 4) ? R[q & 3] + Z : R[q & 3] - Z;
+      const float g = __ldg(base + tb.off[i]);
+      ob[i * ipl] = fmaf(om, C[q] - g, g);
     }
   }
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const int i0 = 72 + 2 * ax;
+    const float* H0 = tb.Hf[i0];
+    float Ce = 0.f, Co = 0.f;
+#pragma unroll
+    for (int k = 0; k < 14; ++k) {
+      if (kBasis3Exp[k][ax] & 1) Co = fmaf(H0[k], Mm[k], Co);
+      else Ce = fmaf(H0[k], Mm[k], Ce);
+    }
+    const float va = tb.vf[i0][ax] * kU[ax];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int i = i0 + q;
+      const float feq = q ? Ce - Co : Ce + Co;
+      const float om = q ? kU0 + va : kU0 - va;
+      const float g = __ldg(base + tb.off[i]);
+      ob[i * ipl] = fmaf(om, feq - g, g);
+    }
+  }
+  images_from_stored<78, 6>(s, a.fout, si, x, y, z);
 }
 
 // f*(0) = f^eq(n, U, T) of device fields (row-major [z][y][x]), stored as f
@@ -305,6 +382,12 @@ template cudaError_t launch_step3_sym<double>(const Tables3&, const Step3Args<do
 cudaError_t launch_step3f(const Tables3& tb, const Step3Args<float>& a, cudaStream_t st) {
   if (a.s.Q != 78) return cudaErrorInvalidValue;
   k_step3f<78><<<grid3(a.s), dim3(32, 4), 0, st>>>(tb, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step3f_sym(const Tables3& tb, const Step3Args<float>& a, cudaStream_t st) {
+  if (a.s.Q != 78) return cudaErrorInvalidValue;
+  k_step3fs<<<grid3(a.s), dim3(32, 4), 0, st>>>(tb, a);
   return cudaGetLastError();
 }
 

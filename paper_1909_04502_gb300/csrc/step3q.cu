@@ -1,12 +1,13 @@
 // (3+1)-dimensional massless RLBM step at order 3 (App. H, v0 = 1/sqrt(41),
 // Q = 288, K = 30), the order-2 step of step3.cu with the 30-member basis.
-// Two kernels:
+// Three kernels:
 // - k_step3qs (FP64, the table in sign-orbit form): one thread per cell over
 //   33 runs of 8 and 6 runs of 4 sign variants, the run tables as kernel
 //   parameters;
-// - k_step3q_cell (FP32 storage of g = f - f_ref): one thread per cell, a warp
-//   per 32-cell row segment, the 288 x 30 table in shared memory read by
-//   broadcast 16-byte loads.
+// - k_step3qsf (FP32 storage of g = f - f_ref), the same form in FP32;
+// - k_step3q_cell (FP32 storage, row by row, for a table without that form):
+//   one thread per cell, a warp per 32-cell row segment, the 288 x 30 table in
+//   shared memory read by broadcast 16-byte loads.
 // (An earlier form with four threads per cell, 72 populations each and the
 // moment sums combined by warp shuffles, ran 3-6x slower than these.)
 // Pull offsets are the plane offset i * plane (64-bit) plus a per-population
@@ -129,9 +130,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_step3q_cell(const __grid_c
 }
 
 // Sign-orbit form, one thread per cell: the order-2 scheme of k_step3s with
-// the 30-member basis (written for either storage type; with FP32 storage it
-// measured 29 % slower than k_step3q_cell, whose bound is the latency of the
-// population loads, so only FP64 uses it).  Runs of
+// the 30-member basis (k_step3qsf is its FP32-storage form).  Runs of
 // 8: a Walsh-Hadamard transform of the pulled values gives the moment sums;
 // the first H row's partial sums over the eight parity classes of the basis
 // (class of member k: the parities of its x, y, z exponents), transformed
@@ -247,6 +246,104 @@ __global__ void __launch_bounds__(128) k_step3qs(const __grid_constant__ Tables3
   }
 }
 
+// FP32 storage in sign-orbit form: the arithmetic of k_step3qs on g = f -
+// f_ref in FP32 with the Landau frame of k_step3q_cell (frame3).  The moment
+// pass is unrolled three runs deep and takes each run's pull shifts by run
+// and member (off8, off4); the relaxation pass starts with the runs of 4 and
+// takes the runs of 8 in reverse, the order opposite to the moment pass, so
+// that it first rereads what is most likely still in L2.  Six blocks of 128
+// threads per SM (80 registers).  At 192^3: 6.6 ms per step against
+// 10.2 ms for k_step3q_cell; unrolling the relaxation pass too, or the moment
+// pass completely, made it slower (instruction-cache misses).
+__global__ void __launch_bounds__(128, 6) k_step3qsf(const __grid_constant__ Tables3s3<float> tb,
+                                                     const __grid_constant__ Step3qArgs<float> a) {
+  const Scalars3& s = a.s;
+  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y, z = blockIdx.z;
+  if (x >= s.nx || y >= s.ny || z >= s.nz) return;
+  const long long si = sidx3(s, x, y, z);
+  const float* __restrict__ base = a.fin + si;
+  const long long P = s.plane;
+  float m[14];
+#pragma unroll
+  for (int k = 0; k < 14; ++k) m[k] = 0.f;
+#pragma unroll 3
+  for (int r = 0; r < kRuns8o3; ++r) {
+    const float* b = base + (long long)tb.start8[r] * P;
+    float f[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) f[q] = __ldg(b + q * P + tb.off8[r][q]);
+    fwht(f);
+    moments_run8(f, tb.mono8[r], m);
+  }
+#pragma unroll
+  for (int r = 0; r < kRuns4o3; ++r) {
+    const int j = kMask4o3[r] & 1 ? 0 : 1, k = kMask4o3[r] & 4 ? 2 : 1;   // the non-zero components, j < k
+    const float* b = base + (long long)tb.start4[r] * P;
+    float f[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) f[q] = __ldg(b + q * P + tb.off4[r][q]);
+    fwht(f);                      // f = (sum, sum s_j, sum s_k, sum s_j s_k)
+    const float* c = tb.mono4[r];
+    const int djj = j == 0 ? 8 : 11, dkk = k == 1 ? 11 : 13, djk = j == 0 ? (k == 1 ? 9 : 10) : 12;
+    m[0] = fmaf(c[0], f[0], m[0]);
+    m[4] = fmaf(c[4], f[0], m[4]);
+    m[1 + j] = fmaf(c[1 + j], f[1], m[1 + j]);
+    m[1 + k] = fmaf(c[1 + k], f[2], m[1 + k]);
+    m[5 + j] = fmaf(c[5 + j], f[1], m[5 + j]);
+    m[5 + k] = fmaf(c[5 + k], f[2], m[5 + k]);
+    m[djj] = fmaf(c[djj], f[0], m[djj]);
+    m[dkk] = fmaf(c[dkk], f[0], m[dkk]);
+    m[djk] = fmaf(c[djk], f[3], m[djk]);
+  }
+  float Mm[kKo3], kU0, kU[3];
+  if (!frame3(m, s, Mm, kU0, kU)) atomicAdd(a.status, 1ULL);
+  float* ob = a.fout + si;
+#pragma unroll
+  for (int r = kRuns4o3 - 1; r >= 0; --r) {
+    const int j = kMask4o3[r] & 1 ? 0 : 1, k = kMask4o3[r] & 4 ? 2 : 1;
+    const long long p0 = (long long)tb.start4[r] * P;
+    const float* H0 = tb.H4[r];
+    float C[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int kk = 0; kk < kKo3; ++kk) {
+      const int par = kBasis3o3Par[kk];
+      const int c = ((par >> j) & 1) | (((par >> k) & 1) << 1);
+      C[c] = fmaf(H0[kk], Mm[kk], C[c]);
+    }
+    fwht(C);                      // C[q] = f^eq of member q (bit 0: j negated, bit 1: k negated)
+    const float* vb = tb.v4[r];
+    const float Xj = vb[j] * kU[j], Xk = vb[k] * kU[k];
+    const float om[4] = {kU0 - Xj - Xk, kU0 + Xj - Xk, kU0 - Xj + Xk, kU0 + Xj + Xk};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float g = __ldg(base + p0 + q * P + tb.off4[r][q]);
+      ob[p0 + q * P] = fmaf(om[q], C[q] - g, g);
+    }
+  }
+#pragma unroll 1
+  for (int r = kRuns8o3 - 1; r >= 0; --r) {
+    const long long p0 = (long long)tb.start8[r] * P;
+    const float* H0 = tb.H8[r];
+    float C[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) C[c] = 0.f;
+#pragma unroll
+    for (int k = 0; k < kKo3; ++k) C[kBasis3o3Par[k]] = fmaf(H0[k], Mm[k], C[kBasis3o3Par[k]]);
+    fwht(C);                      // C[q] = f^eq of member q
+    const float* vb = tb.v8[r];
+    const float X = vb[0] * kU[0], Y = vb[1] * kU[1], Z = vb[2] * kU[2];
+    const float r0 = kU0 - X, r1 = kU0 + X;
+    const float R[4] = {r0 - Y, r1 - Y, r0 + Y, r1 + Y};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float om = (q & 4) ? R[q & 3] + Z : R[q & 3] - Z;
+      const float g = __ldg(base + p0 + q * P + tb.off8[r][q]);
+      ob[p0 + q * P] = fmaf(om, C[q] - g, g);
+    }
+  }
+  images_from_stored<kQo3, 8>(s, a.fout, si, x, y, z);
+}
+
 // f*(0) = f^eq(n, U, T) (stored f, or f - f_ref for FP32), one thread per cell.
 template <typename S>
 __global__ void __launch_bounds__(128) k_init3q(const __grid_constant__ Init3qArgs<S> a) {
@@ -340,6 +437,11 @@ cudaError_t launch_step3q_sym(const Tables3s3<S>& tb, const Step3qArgs<S>& a, cu
   return cudaGetLastError();
 }
 template cudaError_t launch_step3q_sym<double>(const Tables3s3<double>&, const Step3qArgs<double>&, cudaStream_t);
+cudaError_t launch_step3q_symf(const Tables3s3<float>& tb, const Step3qArgs<float>& a, cudaStream_t st) {
+  if (a.s.Q != kQo3) return cudaErrorInvalidValue;
+  k_step3qsf<<<grid3q(a.s), dim3(32, 4), 0, st>>>(tb, a);
+  return cudaGetLastError();
+}
 
 template <typename S>
 cudaError_t launch_init3q(const Init3qArgs<S>& a, cudaStream_t st) {
