@@ -249,12 +249,16 @@ __global__ void __launch_bounds__(128) k_step3qs(const __grid_constant__ Tables3
 // FP32 storage in sign-orbit form: the arithmetic of k_step3qs on g = f -
 // f_ref in FP32 with the Landau frame of k_step3q_cell (frame3).  The moment
 // pass is unrolled three runs deep and takes each run's pull shifts by run
-// and member (off8, off4); the relaxation pass starts with the runs of 4 and
-// takes the runs of 8 in reverse, the order opposite to the moment pass, so
-// that it first rereads what is most likely still in L2.  Six blocks of 128
-// threads per SM (80 registers).  At 192^3: 6.6 ms per step against
-// 10.2 ms for k_step3q_cell; unrolling the relaxation pass too, or the moment
-// pass completely, made it slower (instruction-cache misses).
+// and member (off8, off4); the relaxation pass, unrolled two runs deep,
+// starts with the runs of 4 and takes the runs of 8 in reverse, the order
+// opposite to the moment pass, so that it first rereads what is most likely
+// still in L2.  Six blocks of 128 threads per SM (80 registers).  At 192^3:
+// 6.4 ms per step against 10.2 ms for k_step3q_cell.  Measured and not kept:
+// the moment pass unrolled completely (5 % slower) or not at all (8 %), the
+// relaxation pass unrolled completely (1.4x slower; the code grows
+// several-fold), five or seven blocks per SM (1-8 % slower), the relaxation
+// pass in the moment pass's order (5 % slower), image copies 4 or 16 at a
+// time (3 % slower).
 __global__ void __launch_bounds__(128, 6) k_step3qsf(const __grid_constant__ Tables3s3<float> tb,
                                                      const __grid_constant__ Step3qArgs<float> a) {
   const Scalars3& s = a.s;
@@ -320,7 +324,7 @@ __global__ void __launch_bounds__(128, 6) k_step3qsf(const __grid_constant__ Tab
       ob[p0 + q * P] = fmaf(om[q], C[q] - g, g);
     }
   }
-#pragma unroll 1
+#pragma unroll 2
   for (int r = kRuns8o3 - 1; r >= 0; --r) {
     const long long p0 = (long long)tb.start8[r] * P;
     const float* H0 = tb.H8[r];
