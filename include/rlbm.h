@@ -388,9 +388,8 @@ int rlbm3_plan(int order, int* Q, int* K, int* nvec, double* p, double* w, doubl
  * T - 1 and U are then FP32 quotients of those FP64 values).  Each side
  * at least the halo width (3, or 6 at order 3) and nx*ny*nz <= 2^28.
  * The steps evaluate the table in sign-orbit form (runs of sign variants
- * whose equilibrium rows differ only by the basis members' signs); an FP64
- * handle fails with RLBM_ERR_QUADRATURE if that identity does not hold
- * exactly, an FP32-storage handle then runs a row-by-row kernel (the built-in
+ * whose equilibrium rows differ only by the basis members' signs);
+ * RLBM_ERR_QUADRATURE if that identity does not hold exactly (the built-in
  * tables satisfy it).  Synchronous. */
 int rlbm3_create(int nx, int ny, int nz, double tau, int order, int precision, void* stream,
                  rlbm3_handle** out);

@@ -25,14 +25,11 @@ struct rlbm3_handle {
   unsigned long long* status = nullptr;
   cudaStream_t stream = nullptr;
   std::vector<double> fref;       // reference populations (FP32 storage)
-  bool sym = false;               // order 2 in sign-orbit form (the FP64 step needs it; FP32 storage uses it)
-  // order 3 in sign-orbit form (the FP64 step needs it), or null
+  bool sym = false;               // order 2 in sign-orbit form (the steps need it)
+  // order 3 run tables in sign-orbit form for the FP64 or the FP32-storage step, or null
   std::unique_ptr<Tables3s3<double>> ts3d;
-  std::unique_ptr<Tables3s3<float>> ts3f;    // order 3, FP32 storage, sign-orbit form (null: row by row)
-  // order 3: tables in device memory
-  void* dH = nullptr;             // Q x 30, storage precision
-  void* dc = nullptr;             // Q x 4
-  void* dv = nullptr;             // Q x 3
+  std::unique_ptr<Tables3s3<float>> ts3f;
+  // order 3: tables in device memory (init, fields)
   double* dHd = nullptr;          // Q x 30 FP64 (init)
   double* dcd = nullptr;          // Q x 4 FP64 (fields)
   double* dfref = nullptr;        // Q
@@ -43,7 +40,6 @@ struct rlbm3_handle {
     cudaFree(fields);
     cudaFree(staging);
     cudaFree(status);
-    for (void* d : {dH, dc, dv}) cudaFree(d);
     cudaFree(dHd);
     cudaFree(dcd);
     cudaFree(dfref);
@@ -198,18 +194,10 @@ int rlbm3_create(int nx, int ny, int nz, double tau, int order, int precision, v
   h->tb.reset(new Tables3());
   std::memset(h->tb.get(), 0, sizeof(Tables3));
   if (order == 3) {
-    std::vector<double> c(4 * s.Q), v(3 * s.Q);
-    for (int i = 0; i < s.Q; ++i) {
+    std::vector<double> c(4 * s.Q);
+    for (int i = 0; i < s.Q; ++i)
       for (int u = 0; u < 4; ++u) c[4 * i + u] = h->q.p[4 * i + u];
-      for (int u = 0; u < 3; ++u) v[3 * i + u] = h->q.p[4 * i + 1 + u] / h->q.p[4 * i];
-    }
-    int rc = RLBM_OK;
-    if (h->elem == 4) {         // the FP32 step's tables (the FP64 step takes its run tables as parameters)
-      std::vector<float> Hf(h->q.H.begin(), h->q.H.end()), cf(c.begin(), c.end()), vf(v.begin(), v.end());
-      if (!rc) rc = upload(&h->dH, Hf);
-      if (!rc) rc = upload(&h->dc, cf);
-      if (!rc) rc = upload(&h->dv, vf);
-    }
+    int rc = RLBM_OK;           // (the steps take their run tables as kernel parameters)
     if (!rc) rc = upload((void**)&h->dHd, h->q.H);
     if (!rc) rc = upload((void**)&h->dcd, c);
     if (!rc) rc = upload((void**)&h->dfref, h->fref);
@@ -232,14 +220,13 @@ int rlbm3_create(int nx, int ny, int nz, double tau, int order, int precision, v
       for (int k = 0; k < 14; ++k) h->tb->monof[r][k] = (float)mono[k];
     }
   }
-  // the FP64 kernels take the table in sign-orbit form (checked exactly above)
-  if (h->elem == 8 && (order == 2 ? !h->sym : !h->ts3d))
+  // the steps take the table in sign-orbit form (checked exactly above)
+  if (order == 2 ? !h->sym : !(h->elem == 8 ? (bool)h->ts3d : (bool)h->ts3f))
     return fail3(nullptr, RLBM_ERR_QUADRATURE, "3-d table not in sign-orbit form");
   for (int i = 0; i < s.Q && order == 2; ++i) {
     for (int u = 0; u < 4; ++u) h->tb->c[i][u] = h->q.p[4 * i + u];
     for (int u = 0; u < 3; ++u) h->tb->v[i][u] = h->q.p[4 * i + 1 + u] / h->q.p[4 * i];
     for (int k = 0; k < 14; ++k) h->tb->H[i][k] = h->q.H[(size_t)i * 14 + k];
-    for (int u = 0; u < 4; ++u) h->tb->cf[i][u] = (float)h->tb->c[i][u];
     for (int u = 0; u < 3; ++u) h->tb->vf[i][u] = (float)h->tb->v[i][u];
     for (int k = 0; k < 14; ++k) h->tb->Hf[i][k] = (float)h->tb->H[i][k];
     h->tb->fref[i] = h->fref[i];
@@ -329,17 +316,15 @@ int rlbm3_step(rlbm3_handle* h, int nsteps) {
     cudaError_t e;
     if (h->q.order == 3) {
       if (h->elem == 4) {
-        Step3qArgs<float> a{(const float*)h->buf[h->cur], (float*)h->buf[h->cur ^ 1], h->status, h->sc,
-                            (const float*)h->dH, (const float*)h->dc, (const float*)h->dv, h->doff};
-        e = h->ts3f ? launch_step3q_symf(*h->ts3f, a, h->stream) : launch_step3q_cell(a, h->stream);
+        Step3qArgs<float> a{(const float*)h->buf[h->cur], (float*)h->buf[h->cur ^ 1], h->status, h->sc};
+        e = launch_step3q_symf(*h->ts3f, a, h->stream);
       } else {
-        Step3qArgs<double> a{(const double*)h->buf[h->cur], (double*)h->buf[h->cur ^ 1], h->status, h->sc,
-                             (const double*)h->dH, (const double*)h->dc, (const double*)h->dv, h->doff};
+        Step3qArgs<double> a{(const double*)h->buf[h->cur], (double*)h->buf[h->cur ^ 1], h->status, h->sc};
         e = launch_step3q_sym(*h->ts3d, a, h->stream);
       }
     } else if (h->elem == 4) {
       Step3Args<float> a{(const float*)h->buf[h->cur], (float*)h->buf[h->cur ^ 1], h->status, h->sc};
-      e = h->sym ? launch_step3f_sym(*h->tb, a, h->stream) : launch_step3f(*h->tb, a, h->stream);
+      e = launch_step3f_sym(*h->tb, a, h->stream);
     } else {
       Step3Args<double> a{(const double*)h->buf[h->cur], (double*)h->buf[h->cur ^ 1], h->status, h->sc};
       e = launch_step3_sym(*h->tb, a, h->stream);

@@ -13,8 +13,7 @@ struct Tables3 {
   double v[kMaxQ3][3];    // microscopic velocity p / p0
   double H[kMaxQ3][14];   // equilibrium matrix: f^eq_i = sum_k H_ik M_k
   double fref[kMaxQ3];    // FP32 storage: f_ref,i = f^eq_i(n_ref, rest, T_ref) (stored g = f - f_ref)
-  float cf[kMaxQ3][4];    // FP32 copies of c, v, H
-  float vf[kMaxQ3][3];
+  float vf[kMaxQ3][3];    // FP32 copies of v and H
   float Hf[kMaxQ3][14];
   int off[kMaxQ3];        // pull source of population i relative to the cell: i * plane - n_i . strides
   // sign-orbit form (order 2: 9 runs of 8, then the axis pairs along x, y, z):
@@ -58,17 +57,14 @@ struct Fields3Args {
   Scalars3 s;
 };
 
-// Order 3 (Q = 288, K = 30): tables in global memory (device arrays).
+// Order 3 (Q = 288, K = 30): the step takes its tables as Tables3s3; init
+// and fields read device arrays.
 template <typename S>
 struct Step3qArgs {
   const S* fin;
   S* fout;
   unsigned long long* status;
   Scalars3 s;
-  const S* H;      // Q x 30 in the storage precision
-  const S* c;      // Q x 4
-  const S* v;      // Q x 3
-  const int* off;  // Q pull shifts -n_i . strides (the plane offset i * plane is added in 64 bits)
 };
 
 template <typename S>
@@ -91,16 +87,12 @@ struct Fields3qArgs {
   const double* fref;   // Q
 };
 
-// order 3, FP32 storage (k_step3q_cell)
-cudaError_t launch_step3q_cell(const Step3qArgs<float>& a, cudaStream_t st);
 template <typename S>
 cudaError_t launch_init3q(const Init3qArgs<S>& a, cudaStream_t st);
 template <typename S>
 cudaError_t launch_fields3q(const Fields3qArgs<S>& a, cudaStream_t st);
 
-// order 2, FP32 storage: row by row (k_step3f), or in sign-orbit form
-// (k_step3fs, Tables3::monof filled)
-cudaError_t launch_step3f(const Tables3& tb, const Step3Args<float>& a, cudaStream_t st);
+// order 2, FP32 storage, in sign-orbit form (k_step3fs, Tables3::monof filled)
 cudaError_t launch_step3f_sym(const Tables3& tb, const Step3Args<float>& a, cudaStream_t st);
 // The order-3 table in sign-orbit form: 33 runs of 8 and 6 runs of 4 (the
 // (5, 4, 0) patterns, non-zero components x y, x z, x y, x z, y z, y z), each

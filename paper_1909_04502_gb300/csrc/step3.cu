@@ -4,8 +4,7 @@
 // d = 3), f^eq = H M(n, U, T) (Eq. mj-discrete-feq), Anderson-Witting
 // relaxation, store with the periodic halo images.  Kernels: k_step3s (FP64)
 // and k_step3fs (FP32 storage of g = f - f_ref), both with the table in
-// sign-orbit form, and k_step3f (FP32 storage, row by row, for a table
-// without that form).
+// sign-orbit form.
 //
 // Layout: one plane per population, cell (x, y, z) at
 //   (z + h) * slab + (y + h) * pitch + (x + px),  slab = (ny + 2h) * pitch,
@@ -150,76 +149,21 @@ __global__ void __launch_bounds__(128) k_step3s(const __grid_constant__ Tables3 
   }
 }
 
-// FP32 storage: g = f - f_ref is stored and collided in FP32; the moments are
-// FP32 sums of g (the reference moments enter in FP64); the Landau root is
-// found in FP32 (Newton on det(A - l I)) and corrected by one Newton step
-// whose residual, the eigenvector's nu^2 = v.v, w = v.N and the numerator of
-// dn = n - n_ref are evaluated in FP64 (landau3f); the equilibrium
+// FP32 storage in sign-orbit form: g = f - f_ref is stored and collided in
+// FP32 with the run arithmetic of k_step3s; the moments are FP32 sums of g
+// (the reference moments enter in FP64); the Landau root is found in FP32
+// (Newton on det(A - l I)) and corrected by one Newton step whose residual,
+// the eigenvector's nu^2 = v.v, w = v.N and the numerator of dn = n - n_ref
+// are evaluated in FP64 (landau3f, through frame3); the equilibrium
 // differences dM = M(n, U, T) - M_ref are written so that each is accurate
 // relative to itself, and the equilibrium, the relaxation and the store are
-// FP32.
-// Eight blocks of 128 threads per SM (64 registers).  The handles run
-// k_step3fs, which evaluates the same arithmetic in sign-orbit form; this
-// kernel serves a table without that form.
-template <int QT>
-__global__ void __launch_bounds__(128, 8) k_step3f(const __grid_constant__ Tables3 tb,
-                                                   const __grid_constant__ Step3Args<float> a) {
-  const Scalars3& s = a.s;
-  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y, z = blockIdx.z;
-  if (x >= s.nx || y >= s.ny || z >= s.nz) return;
-  const long long si = sidx3(s, x, y, z);
-  const float* __restrict__ base = a.fin + si;
-  float N[4] = {0.f, 0.f, 0.f, 0.f}, Tm[4][4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) Tm[u][v] = 0.f;
-#pragma unroll 6
-  for (int i = 0; i < QT; ++i) {
-    const float g = __ldg(base + tb.off[i]);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const float gu = g * tb.cf[i][u];
-      N[u] += gu;
-#pragma unroll
-      for (int v = u; v < 4; ++v) Tm[u][v] = fmaf(gu, tb.cf[i][v], Tm[u][v]);
-    }
-  }
-  Macro3f M = landau3f(N, Tm, s);
-  const bool ok = M.ok;
-  if (!ok) {
-    atomicAdd(a.status, 1ULL);
-    unphysical_to_reference3(s, M);      // left unrelaxed below (kt = 0)
-  }
-  const float U0 = M.U0, Ux = M.Ux, Uy = M.Uy, Uz = M.Uz;
-  float dM[14];
-  mj_delta3<14>(M, s.f_n_ref, s.f_T_ref, dM);
-  const float kt = ok ? s.f_inv_tau : 0.f;
-  // interior stores (order 2 keeps Q * plane below 2^31), then the periodic
-  // images of cells next to a face from the just-written values (the thread
-  // reads back its own stores), so that interior cells run no image loop
-  const int ipl = (int)s.plane;
-  float* ob = a.fout + si;
-#pragma unroll 2
-  for (int i = 0; i < QT; ++i) {
-    const float g = __ldg(base + tb.off[i]);
-    float geq = 0.f;
-#pragma unroll
-    for (int kk = 0; kk < 14; ++kk) geq = fmaf(tb.Hf[i][kk], dM[kk], geq);
-    const float om = kt * (U0 - tb.vf[i][0] * Ux - tb.vf[i][1] * Uy - tb.vf[i][2] * Uz);
-    ob[i * ipl] = fmaf(om, geq - g, g);
-  }
-  images_from_stored<QT, 6>(s, a.fout, si, x, y, z);
-}
-
-// FP32 storage in sign-orbit form: the arithmetic of k_step3s on g = f -
-// f_ref in FP32, with the Landau frame of k_step3f (frame3).  Every run is
-// unrolled, so each table entry (pull shift, monomial, H row, velocity) is an
-// immediate constant operand rather than a load by run-time index (with the
-// runs in a loop this form was slower than k_step3f).  At 192^3: 1.52 ms per
-// step against 2.20 ms for k_step3f.  The interior is stored in the
-// relaxation pass; cells next to a face then copy their values to the
-// periodic images, six at a time.
+// FP32.  Every run is unrolled, so each table entry (pull shift, monomial, H
+// row, velocity) is an immediate constant operand rather than a load by
+// run-time index (with the runs in a loop this form was slower than the
+// row-by-row kernel it replaced).  Eight blocks of 128 threads per SM
+// (64 registers).  At 192^3: 1.51 ms per step against 2.20 ms row by row.
+// The interior is stored in the relaxation pass; cells next to a face then
+// copy their values to the periodic images, six at a time.
 __global__ void __launch_bounds__(128, 8) k_step3fs(const __grid_constant__ Tables3 tb,
                                                     const __grid_constant__ Step3Args<float> a) {
   const Scalars3& s = a.s;
@@ -378,12 +322,6 @@ cudaError_t launch_step3_sym(const Tables3& tb, const Step3Args<S>& a, cudaStrea
   return cudaGetLastError();
 }
 template cudaError_t launch_step3_sym<double>(const Tables3&, const Step3Args<double>&, cudaStream_t);
-
-cudaError_t launch_step3f(const Tables3& tb, const Step3Args<float>& a, cudaStream_t st) {
-  if (a.s.Q != 78) return cudaErrorInvalidValue;
-  k_step3f<78><<<grid3(a.s), dim3(32, 4), 0, st>>>(tb, a);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_step3f_sym(const Tables3& tb, const Step3Args<float>& a, cudaStream_t st) {
   if (a.s.Q != 78) return cudaErrorInvalidValue;

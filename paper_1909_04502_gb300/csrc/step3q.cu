@@ -1,20 +1,13 @@
 // (3+1)-dimensional massless RLBM step at order 3 (App. H, v0 = 1/sqrt(41),
 // Q = 288, K = 30), the order-2 step of step3.cu with the 30-member basis.
-// Three kernels:
-// - k_step3qs (FP64, the table in sign-orbit form): one thread per cell over
-//   33 runs of 8 and 6 runs of 4 sign variants, the run tables as kernel
-//   parameters;
-// - k_step3qsf (FP32 storage of g = f - f_ref), the same form in FP32;
-// - k_step3q_cell (FP32 storage, row by row, for a table without that form):
-//   one thread per cell, a warp per 32-cell row segment, the 288 x 30 table in
-//   shared memory read by broadcast 16-byte loads.
-// (An earlier form with four threads per cell, 72 populations each and the
-// moment sums combined by warp shuffles, ran 3-6x slower than these.)
+// Two kernels, one thread per cell over 33 runs of 8 and 6 runs of 4 sign
+// variants, the run tables as kernel parameters: k_step3qs (FP64) and
+// k_step3qsf (FP32 storage of g = f - f_ref).  (Earlier forms, row by row
+// with four threads per cell or with the table in shared memory, ran
+// 1.6-5x slower.)
 // Pull offsets are the plane offset i * plane (64-bit) plus a per-population
 // shift, since 288 planes of a large grid exceed 2^31 elements.
 #include <cuda_runtime.h>
-
-#include <algorithm>
 
 #include "d3_impl.cuh"
 
@@ -23,111 +16,6 @@ namespace rlbm {
 namespace {
 
 constexpr int kQo3 = 288, kKo3 = 30;
-
-// FP32 storage: one thread per cell, a warp per row segment of 32 cells.
-// With four threads per cell each thread would repeat the FP64 polish of the
-// Landau root and read one table entry per FMA; here every thread of a warp
-// reads the same table row, so a 16-byte shared load broadcasts four
-// entries of H (rows padded to 32 with zero columns, Mk[30..31] = 0) and the
-// Landau solve runs once per cell.  The populations are read twice (moments,
-// then relaxation); the second read mostly finds them in L2.
-struct SharedTables3f {
-  float4 H[kQo3][8];
-  float4 c[kQo3];
-  float4 v[kQo3];
-  int off[kQo3];
-};
-
-template <int WARPS, int BATCH, int MINB>
-__global__ void __launch_bounds__(32 * WARPS, MINB) k_step3q_cell(const __grid_constant__ Step3qArgs<float> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  SharedTables3f& t = *reinterpret_cast<SharedTables3f*>(smem_raw);
-  const Scalars3& s = a.s;
-  for (int e = threadIdx.x; e < kQo3 * 32; e += blockDim.x) {
-    const int i = e >> 5, k = e & 31;
-    reinterpret_cast<float*>(&t.H[i][0])[k] = k < kKo3 ? a.H[i * kKo3 + k] : 0.f;
-  }
-  for (int i = threadIdx.x; i < kQo3; i += blockDim.x) {
-    t.c[i] = make_float4(a.c[4 * i], a.c[4 * i + 1], a.c[4 * i + 2], a.c[4 * i + 3]);
-    t.v[i] = make_float4(a.v[3 * i], a.v[3 * i + 1], a.v[3 * i + 2], 0.f);
-    t.off[i] = a.off[i];
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nxs = (s.nx + 31) / 32;
-  const long long nseg = (long long)nxs * s.ny * s.nz;
-  for (long long seg = (long long)blockIdx.x * WARPS + warp; seg < nseg; seg += (long long)gridDim.x * WARPS) {
-    const int xs = (int)(seg % nxs);
-    const int y = (int)((seg / nxs) % s.ny), z = (int)(seg / ((long long)nxs * s.ny));
-    const int x = xs * 32 + lane;
-    if (x >= s.nx) continue;
-    const long long si = sidx3(s, x, y, z);
-    const float* __restrict__ base = a.fin + si;
-    float N[4] = {0.f, 0.f, 0.f, 0.f}, Tm[4][4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int w = 0; w < 4; ++w) Tm[u][w] = 0.f;
-    for (int i0 = 0; i0 < kQo3; i0 += BATCH) {
-      float g[BATCH];
-#pragma unroll
-      for (int j = 0; j < BATCH; ++j) g[j] = __ldg(base + (long long)(i0 + j) * s.plane + t.off[i0 + j]);
-#pragma unroll
-      for (int j = 0; j < BATCH; ++j) {
-        const float4 c = t.c[i0 + j];
-        const float cu[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float gu = g[j] * cu[u];
-          N[u] += gu;
-#pragma unroll
-          for (int w = u; w < 4; ++w) Tm[u][w] = fmaf(gu, cu[w], Tm[u][w]);
-        }
-      }
-    }
-    Macro3f M = landau3f(N, Tm, s);
-    if (!M.ok) unphysical_to_reference3(s, M);     // left unrelaxed below (kt = 0)
-    float Mk[32];
-    {
-      float Md[kKo3];
-      mj_delta3<kKo3>(M, s.f_n_ref, s.f_T_ref, Md);
-#pragma unroll
-      for (int k = 0; k < kKo3; ++k) Mk[k] = Md[k];
-      Mk[30] = Mk[31] = 0.f;
-    }
-    if (!M.ok) atomicAdd(a.status, 1ULL);
-    const float kt = M.ok ? s.f_inv_tau : 0.f;
-    long long img[26];
-    const int nimg = cell_images(s, x, y, z, img);
-    // pass 2 in reverse order of the batches: the populations pass 1 read
-    // last are the most likely to be still in L2
-    static_assert(kQo3 % BATCH == 0, "whole batches");
-    for (int i0 = kQo3 - BATCH; i0 >= 0; i0 -= BATCH) {
-      float g[BATCH];
-#pragma unroll
-      for (int j = 0; j < BATCH; ++j) g[j] = __ldg(base + (long long)(i0 + j) * s.plane + t.off[i0 + j]);
-#pragma unroll
-      for (int j = 0; j < BATCH; ++j) {
-        const int i = i0 + j;
-        float geq = 0.f;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const float4 h = t.H[i][q];
-          geq = fmaf(h.x, Mk[4 * q], geq);
-          geq = fmaf(h.y, Mk[4 * q + 1], geq);
-          geq = fmaf(h.z, Mk[4 * q + 2], geq);
-          geq = fmaf(h.w, Mk[4 * q + 3], geq);
-        }
-        const float4 v = t.v[i];
-        const float om = kt * (M.U0 - v.x * M.Ux - v.y * M.Uy - v.z * M.Uz);
-        const float gn = fmaf(om, geq - g[j], g[j]);
-        const long long pl = (long long)i * s.plane;
-        a.fout[pl + si] = gn;
-        for (int m = 0; m < nimg; ++m) a.fout[pl + img[m]] = gn;
-      }
-    }
-  }
-}
 
 // Sign-orbit form, one thread per cell: the order-2 scheme of k_step3s with
 // the 30-member basis (k_step3qsf is its FP32-storage form).  Runs of
@@ -247,13 +135,16 @@ __global__ void __launch_bounds__(128) k_step3qs(const __grid_constant__ Tables3
 }
 
 // FP32 storage in sign-orbit form: the arithmetic of k_step3qs on g = f -
-// f_ref in FP32 with the Landau frame of k_step3q_cell (frame3).  The moment
+// f_ref in FP32 with the FP32 Landau frame and FP64 polish of the order-2
+// step (frame3).  The moment
 // pass is unrolled three runs deep and takes each run's pull shifts by run
 // and member (off8, off4); the relaxation pass, unrolled two runs deep,
 // starts with the runs of 4 and takes the runs of 8 in reverse, the order
 // opposite to the moment pass, so that it first rereads what is most likely
 // still in L2.  Six blocks of 128 threads per SM (80 registers).  At 192^3:
-// 6.4 ms per step against 10.2 ms for k_step3q_cell.  Measured and not kept:
+// 6.4 ms per step against 10.2 ms for the row-by-row kernel it replaced (the
+// 288 x 30 table in shared memory, read by broadcast 16-byte loads).
+// Measured and not kept:
 // the moment pass unrolled completely (5 % slower) or not at all (8 %), the
 // relaxation pass unrolled completely (1.4x slower; the code grows
 // several-fold), five or seven blocks per SM (1-8 % slower), the relaxation
@@ -407,32 +298,6 @@ __global__ void __launch_bounds__(128) k_fields3q(const __grid_constant__ Fields
 dim3 grid3q(const Scalars3& s) { return dim3((s.nx + 31) / 32, (s.ny + 3) / 4, s.nz); }
 
 }  // namespace
-
-template <int WARPS, int BATCH, int MINB>
-cudaError_t launch_cell(const Step3qArgs<float>& a, cudaStream_t st) {
-  auto kern = k_step3q_cell<WARPS, BATCH, MINB>;
-  const int smem = (int)sizeof(SharedTables3f);
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0, per = 0;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 32 * WARPS, smem)) != cudaSuccess) return e;
-  const long long nseg = (long long)((a.s.nx + 31) / 32) * a.s.ny * a.s.nz;
-  const long long blocks = (nseg + WARPS - 1) / WARPS;
-  const long long grid = std::min<long long>(blocks, (long long)sms * (per > 0 ? per : 1));
-  kern<<<(unsigned)grid, 32 * WARPS, smem, st>>>(a);
-  return cudaGetLastError();
-}
-
-// 5 warps per block, 4 blocks per SM (80 registers, 189 KB of tables): at
-// 192^3 the fastest of 8-40 warps per SM and load batches of 4-16 (fewer
-// warps hide less latency, more of them push the second read of the
-// populations out of L2).
-cudaError_t launch_step3q_cell(const Step3qArgs<float>& a, cudaStream_t st) {
-  if (a.s.Q != kQo3) return cudaErrorInvalidValue;
-  return launch_cell<5, 8, 4>(a, st);
-}
 
 template <typename S>
 cudaError_t launch_step3q_sym(const Tables3s3<S>& tb, const Step3qArgs<S>& a, cudaStream_t st) {

@@ -269,7 +269,7 @@ def test_d3_tables_come_in_sign_orbits(rl, order):
     set in s (over the non-zero components), and its equilibrium rows are the
     first row times the sign each basis member takes, exactly; at order 2 the
     runs are nine of eight, then the axis pairs along x, y and z (the layout
-    the sign-orbit FP64 kernel takes)."""
+    the sign-orbit kernels take)."""
     d = rl.plan3(order)
     n, p, w, H = d["n"], d["p"], d["w"], d["H"]
     basis = np.array(_D3_BASIS[:d["K"]])
