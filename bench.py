@@ -478,8 +478,9 @@ def bench_batched(torch, rlbm, inputs, stream, steps=10, count=64, seed=1909, si
     """Batched tau-sweep: `count` shear-wave runs, side ~ U{side_lo..side_hi},
     tau ~ U[0.6, 2.0], zeta round-robin over {0, 1, 10}, amplitude 0.05 c,
     FP32 storage (float-float Landau correction), on-lattice order-2 stencils.  One
-    graph launch per call (one persistent cooperative kernel per stencil
-    kind) against the same instances stepped one handle at a time
+    graph launch per call (the tuner's choice of persistent cooperative
+    kernels, one per stencil kind, or independent per-instance chains of
+    step kernels) against the same instances stepped one handle at a time
     (back-to-back launches).  The working set of all instances exceeds L2 for
     both sweeps the bench runs (about 5 GB and 0.4 GB), so L2 is not flushed."""
     import numpy as np
@@ -521,7 +522,8 @@ def bench_batched(torch, rlbm, inputs, stream, steps=10, count=64, seed=1909, si
            "speedup_vs_plain_loop": round(tp / tb, 3),
            "roofline": {"bound": "hbm", "achieved": round(alg_bytes / (tb * 1e-3) / 1e9, 1), "peak": peak,
                         "unit": "GB/s", "frac": round(alg_bytes / (tb * 1e-3) / 1e9 / peak, 4)},
-           "tuned": {"tile_shape": ["32x8", "32x4"][shape], "grid": grid}, "status": rc,
+           "tuned": {"schedule": ["persistent 32x8", "persistent 32x4", "per-instance chains"][shape],
+                     "grid": grid}, "status": rc,
            "nonphysical": nonphys}
     batch.close()
     return out

@@ -241,9 +241,12 @@ int rlbm_step_noalloc(const rlbm_params* p, void* f_a, void* f_b, const void* ta
 /* ------------------------------------------------------------------------
  * Batched simulations: many independent grids (different sizes, tau and
  * stencils; FP32 storage, order 2, built-in stencils, constant or eta/s tau)
- * advanced together by persistent cooperative kernels replayed from one
- * captured CUDA graph per call: one kernel per stencil kind present (the
- * kinds run one after another, each over all its instances' tiles).  Not in the paper: it serves the paper's
+ * advanced together from one captured CUDA graph per call, under one of two
+ * schedules: persistent cooperative kernels, one per stencil kind present
+ * (the kinds run one after another, each over all its instances' tiles, with
+ * a grid-wide barrier between steps), or independent chains of each
+ * instance's single-grid step kernels (each instance waits only on its own
+ * previous step; the chains run concurrently).  Not in the paper: it serves the paper's
  * calibration of tau against transport coefficients (Sec. 7), which runs many
  * independent simulations.  Each instance stays an ordinary handle
  * (rlbm_batch_handle) for init / moments / populations; the batched step is
@@ -262,21 +265,22 @@ void rlbm_batch_destroy(rlbm_batch* b);
 int rlbm_batch_size(const rlbm_batch* b);
 /* The i-th instance (borrowed; owned by the batch). */
 rlbm_handle* rlbm_batch_handle(rlbm_batch* b, int i);
-/* Advance every instance by nsteps (one graph launch holding one cooperative
- * kernel per stencil kind; asynchronous). */
+/* Advance every instance by nsteps (one graph launch; asynchronous). */
 int rlbm_batch_step(rlbm_batch* b, int nsteps);
-/* Launch configuration: tile_shape 0 (32 x 8 cells per block) or 1 (32 x 4);
- * grid = persistent blocks (at most the co-resident limit; a kind with fewer
- * tiles runs with one block per tile). */
+/* Schedule: tile_shape 0 or 1 runs the persistent kernels with 32 x 8 or
+ * 32 x 4 cells per block and grid = persistent blocks (at most the
+ * co-resident limit; a kind with fewer tiles runs with one block per tile);
+ * tile_shape 2 runs the per-instance chains (grid ignored). */
 int rlbm_batch_config(rlbm_batch* b, int tile_shape, int grid);
 /* Autotuner: times trial_steps steps for each tile shape and five grid
- * sizes (1, 3/4, 1/2, 1/3 and 1/4 of the co-resident limit) and keeps the
- * fastest.  It advances every instance by 20 * trial_steps steps; call it
- * before rlbm_init of the instances.
+ * sizes (1, 3/4, 1/2, 1/3 and 1/4 of the co-resident limit) and for the
+ * per-instance chains (tile_shape 2, grid 0), and keeps the fastest.  It
+ * advances every instance by 23 * trial_steps steps; call it before
+ * rlbm_init of the instances.
  * Outputs are nullable. */
 int rlbm_batch_tune(rlbm_batch* b, int trial_steps, int* tile_shape, int* grid, float* ms_per_step);
-/* Current configuration, co-resident limits {32x8, 32x4} (the smallest over
- * the kinds present) and tile count. */
+/* Current configuration (grid 0 for the per-instance chains), co-resident
+ * limits {32x8, 32x4} (the smallest over the kinds present) and tile count. */
 int rlbm_batch_info(const rlbm_batch* b, int* tile_shape, int* grid, int* grid_max, long long* total_tiles);
 /* Iteration limit of the bounded grid-barrier wait (default 2^24 polls of
  * about 64 ns).  A wait that runs out sets the batch error flag; every block

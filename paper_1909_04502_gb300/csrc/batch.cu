@@ -10,6 +10,12 @@
 // then waits at a grid-wide barrier before the next step.  The barrier spins a
 // bounded number of times; on timeout it records RLBM_ERR_TIMEOUT and every
 // block leaves.
+//
+// Second schedule (kChains): each instance's own single-grid step kernels,
+// nsteps in a row, captured on one stream per instance so that the graph holds
+// independent chains: an instance waits only on its own previous step, never
+// on a grid-wide barrier, and the chains of different instances run
+// concurrently.  The tuner picks whichever schedule is faster.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -17,6 +23,7 @@
 #include <map>
 #include <memory>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/rlbm.h"
@@ -180,10 +187,14 @@ struct rlbm_batch {
   BarrierState* bar = nullptr;
   unsigned long long* timeouts = nullptr;
   long long spin_limit = 1LL << 24;
-  int tile_shape = 0;                     // 0: 32 x 8, 1: 32 x 4 (autotuned)
+  int tile_shape = 0;                     // 0: 32 x 8, 1: 32 x 4, 2: per-instance chains (autotuned)
   int grid = 0;                           // persistent grid size (autotuned)
   int grid_max[2] = {0, 0};               // co-resident limit per tile shape (smallest over the kinds present)
-  std::map<long long, cudaGraphExec_t> graphs;
+  // graphs by (nsteps, schedule, and for chains the buffer parity of every
+  // instance, which the captured launches bake in)
+  std::map<std::pair<long long, std::string>, cudaGraphExec_t> graphs;
+  std::vector<cudaStream_t> chain_streams;  // one per instance (kChains capture)
+  std::vector<cudaEvent_t> chain_events;    // fork, then one join per instance
   std::string err = "no error";
 };
 
@@ -259,9 +270,45 @@ int blocks_per_sm(int kind) {
   return nb;
 }
 
+constexpr int kChains = 2;
+
+// kChains: fork from st into one stream per instance, enqueue each instance's
+// nsteps single-grid steps there (rlbm_step on a borrowed stream; the handle's
+// host state is restored, rlbm_batch_step advances it after the launch), join.
+cudaError_t enqueue_chains(rlbm_batch* b, int nsteps, cudaStream_t st) {
+  cudaError_t e = cudaEventRecord(b->chain_events[0], st);
+  for (size_t i = 0; i < b->h.size() && e == cudaSuccess; ++i) {
+    rlbm_handle* h = b->h[i];
+    cudaStream_t ws = b->chain_streams[i];
+    e = cudaStreamWaitEvent(ws, b->chain_events[0], 0);
+    if (e != cudaSuccess) break;
+    const cudaStream_t own = h->stream;
+    const int cur = h->cur;
+    const long long t = h->t;
+    const bool have_prev = h->have_prev;
+    h->stream = ws;
+    const int rc = rlbm_step(h, nsteps);
+    h->stream = own;
+    h->cur = cur;
+    h->t = t;
+    h->have_prev = have_prev;
+    if (rc != RLBM_OK) return cudaErrorLaunchFailure;
+    e = cudaEventRecord(b->chain_events[1 + i], ws);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->chain_events[1 + i], 0);
+  }
+  return e;
+}
+
 // The kinds run one after another (each a cooperative launch of its own
 // tiles); a kind with fewer tiles than the grid gets a grid of its tile count.
+// The descriptors' buffer parity flips at the end under both schedules.
 cudaError_t enqueue(rlbm_batch* b, int nsteps, cudaStream_t st) {
+  if (b->tile_shape == kChains) {
+    cudaError_t e = enqueue_chains(b, nsteps, st);
+    if (e != cudaSuccess) return e;
+    k_batch_flip<<<(int)((b->h.size() + 127) / 128), 128, 0, st>>>(b->inst_dev, (int)b->h.size(), nsteps);
+    return cudaGetLastError();
+  }
   cudaError_t e = cudaMemcpyToSymbolAsync(c_btab, b->tab_host, sizeof(Tables<float>) * kNumKinds, 0,
                                           cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return e;
@@ -368,7 +415,21 @@ int rlbm_batch_create(const rlbm_params* params, int count, rlbm_batch** out) {
   if (e == cudaSuccess) e = cudaMalloc(&b->inst_dev, sizeof(BatchInst) * count);
   if (e == cudaSuccess) e = cudaMalloc(&b->bar, sizeof(BarrierState));
   if (e == cudaSuccess) e = cudaMalloc(&b->timeouts, sizeof(unsigned long long));
+  for (int i = 0; i < count && e == cudaSuccess; ++i) {
+    cudaStream_t cs = nullptr;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) b->chain_streams.push_back(cs);
+  }
+  for (int i = 0; i <= count && e == cudaSuccess; ++i) {
+    cudaEvent_t ev = nullptr;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->chain_events.push_back(ev);
+  }
   if (e != cudaSuccess) {
+    for (cudaStream_t cs : b->chain_streams) cudaStreamDestroy(cs);
+    for (cudaEvent_t ev : b->chain_events) cudaEventDestroy(ev);
+    b->chain_streams.clear();
+    b->chain_events.clear();
     cleanup();
     return RLBM_ERR_OOM;
   }
@@ -436,6 +497,8 @@ void rlbm_batch_destroy(rlbm_batch* b) {
   cudaFree(b->bar);
   cudaFree(b->timeouts);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  for (cudaStream_t cs : b->chain_streams) cudaStreamDestroy(cs);
+  for (cudaEvent_t ev : b->chain_events) cudaEventDestroy(ev);
   delete b;
 }
 
@@ -447,7 +510,12 @@ rlbm_handle* rlbm_batch_handle(rlbm_batch* b, int i) {
 }
 
 int rlbm_batch_config(rlbm_batch* b, int tile_shape, int grid) {
-  if (!b || (tile_shape != 0 && tile_shape != 1)) return RLBM_ERR_INVALID_ARG;
+  if (!b || tile_shape < 0 || tile_shape > kChains) return RLBM_ERR_INVALID_ARG;
+  if (tile_shape == kChains) {          // the grid does not apply
+    b->tile_shape = kChains;
+    drop_graphs(b);
+    return RLBM_OK;
+  }
   const int gmax = b->grid_max[tile_shape];
   if (grid <= 0 || grid > gmax) return batch_fail(b, RLBM_ERR_INVALID_ARG, "grid exceeds co-resident blocks");
   if (tile_shape != b->tile_shape) {
@@ -471,7 +539,10 @@ int rlbm_batch_step(rlbm_batch* b, int nsteps) {
   if (nsteps == 0) return RLBM_OK;
   int rc = sync_descriptors(b);
   if (rc != RLBM_OK) return rc;
-  const long long key = (long long)nsteps * 4 + b->tile_shape * 2;
+  std::string parity;
+  if (b->tile_shape == kChains)
+    for (const rlbm_handle* h : b->h) parity.push_back(h->cur ? '1' : '0');
+  const std::pair<long long, std::string> key((long long)nsteps * 4 + b->tile_shape, parity);
   cudaGraphExec_t exec = nullptr;
   auto it = b->graphs.find(key);
   if (it != b->graphs.end()) {
@@ -537,7 +608,7 @@ int rlbm_batch_set_spin_limit(rlbm_batch* b, long long limit) {
 int rlbm_batch_info(const rlbm_batch* b, int* tile_shape, int* grid, int* grid_max, long long* total_tiles) {
   if (!b) return RLBM_ERR_INVALID_ARG;
   if (tile_shape) *tile_shape = b->tile_shape;
-  if (grid) *grid = b->grid;
+  if (grid) *grid = b->tile_shape == kChains ? 0 : b->grid;
   if (grid_max) { grid_max[0] = b->grid_max[0]; grid_max[1] = b->grid_max[1]; }
   if (total_tiles) *total_tiles = b->total_tiles;
   return RLBM_OK;
@@ -569,10 +640,27 @@ int rlbm_batch_tune(rlbm_batch* b, int trial_steps, int* tile_shape, int* grid, 
       if (ms < best) { best = ms; best_shape = shape; best_grid = cands[c]; }
     }
   }
+  // the per-instance chains (no grid): two untimed runs capture the graphs of
+  // both buffer parities, the third is timed
+  if (rc == RLBM_OK) rc = rlbm_batch_config(b, kChains, 0);
+  for (int rep = 0; rep < 3 && rc == RLBM_OK; ++rep) {
+    if (rep < 2) {
+      rc = rlbm_batch_step(b, trial_steps);
+      continue;
+    }
+    cudaEventRecord(e0, b->stream);
+    rc = rlbm_batch_step(b, trial_steps);
+    cudaEventRecord(e1, b->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) rc = batch_fail(b, RLBM_ERR_CUDA, "tuning run failed");
+    if (rc != RLBM_OK) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) { best = ms; best_shape = kChains; best_grid = 0; }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != RLBM_OK) return rc;
-  rc = rlbm_batch_config(b, best_shape, best_grid);
+  rc = rlbm_batch_config(b, best_shape, best_shape == kChains ? 0 : best_grid);
   if (tile_shape) *tile_shape = best_shape;
   if (grid) *grid = best_grid;
   if (ms_per_step) *ms_per_step = best / trial_steps;

@@ -371,8 +371,10 @@ class _BorrowedLattice(Lattice):
 
 
 class Batch:
-    """Many independent simulations stepped by persistent kernels (one per
-    stencil kind) replayed from a CUDA graph (rlbm_batch_* in include/rlbm.h).  ``configs`` is a list of keyword dicts
+    """Many independent simulations stepped together from a CUDA graph, by
+    persistent kernels (one per stencil kind; tile_shape 0 or 1) or by
+    independent per-instance chains of step kernels (tile_shape 2)
+    (rlbm_batch_* in include/rlbm.h).  ``configs`` is a list of keyword dicts
     for ``make_params`` (each with nx and ny)."""
 
     def __init__(self, configs, cuda_stream=None):

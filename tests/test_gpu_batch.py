@@ -1,5 +1,6 @@
-"""Batched persistent kernel (rlbm_batch_*): bitwise equality with the plain
-step on every instance, bounded grid-barrier timeout, autotuner."""
+"""Batched steps (rlbm_batch_*), persistent kernels and per-instance chains:
+bitwise equality with the plain step on every instance, bounded grid-barrier
+timeout, autotuner."""
 import numpy as np
 import pytest
 
@@ -46,8 +47,8 @@ def test_batched_step_is_bitwise_equal_to_plain(rl):
         lat.init(*f)
         batch[i].init(*f)
         plain.append(lat)
-    for shape in (0, 1):
-        gmax = batch.info()["grid_max"][shape]
+    for shape in (0, 1, 2, 0):
+        gmax = batch.info()["grid_max"][shape] if shape < 2 else 0
         batch.config(shape, max(1, gmax // 3))
         batch.step(7)
         for lat in plain:
@@ -67,8 +68,13 @@ def test_batched_step_is_bitwise_equal_to_plain(rl):
     batch.close()
 
 
-def test_mixed_batch_and_handle_steps_stay_consistent(rl):
+@pytest.mark.parametrize("shape", [0, 2])
+def test_mixed_batch_and_handle_steps_stay_consistent(rl, shape):
+    """An instance stepped through its own handle between batched steps: the
+    persistent kernels read its buffer parity from the descriptors, the
+    chains take a graph captured for the new parities."""
     batch = rl.Batch([dict(c, precision="fp32") for c in INSTANCES[:3]])
+    batch.config(shape, max(1, batch.info()["grid_max"][0] // 2))
     ref = []
     for i, c in enumerate(INSTANCES[:3]):
         f = _fields(c, seed=7 + i)
@@ -81,8 +87,9 @@ def test_mixed_batch_and_handle_steps_stay_consistent(rl):
     batch.step(2)
     batch[1].step(1)          # one instance stepped through its own handle
     batch.step(3)
+    batch.step(3)
     for i, lat in enumerate(ref):
-        lat.step(5 + (1 if i == 1 else 0))
+        lat.step(8 + (1 if i == 1 else 0))
         assert np.array_equal(batch[i].populations(), lat.populations())
     batch.close()
 
@@ -115,7 +122,8 @@ def test_autotuner_picks_a_valid_configuration(rl):
     batch = rl.Batch([dict(c, precision="fp32") for c in INSTANCES])
     shape, grid, ms = batch.tune(trial_steps=2)
     info = batch.info()
-    assert shape in (0, 1) and 0 < grid <= info["grid_max"][shape] and ms > 0
+    assert shape in (0, 1, 2) and ms > 0
+    assert (0 < grid <= info["grid_max"][shape]) if shape < 2 else grid == 0
     assert info["tile_shape"] == shape and info["grid"] == grid
     batch.close()
 
