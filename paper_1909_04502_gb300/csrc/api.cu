@@ -480,8 +480,14 @@ int rlbm_create(const rlbm_params* p, rlbm_handle** out) {
   s.wall_T[0] = p->wall_T[0];
   s.wall_T[1] = p->wall_T[1];
   finish_scalars(&s);
-  // the orbit-symmetric kernels carry neither the force term nor the walls
-  s.sym = (orbit_symmetric(h.get()) && !s.force && s.boundary != RLBM_BC_EQWALL_X) ? 1 : 0;
+  // sym: the orbit-symmetric kernels without force or walls (the batched,
+  // adjoint and extended-precision kernels take only these); sym_fw: the
+  // order-2 orbit-symmetric kernels with the force term or the walls
+  {
+    const bool orb = orbit_symmetric(h.get()), fw = s.force || s.boundary == RLBM_BC_EQWALL_X;
+    s.sym = (orb && !fw) ? 1 : 0;
+    s.sym_fw = (orb && fw && s.K == 9) ? 1 : 0;
+  }
   if ((long long)h->q.Q * s.plane >= (1LL << 31))
     return fail(nullptr, RLBM_ERR_UNSUPPORTED, "grid too large: Q * plane must stay below 2^31 elements");
   reference_populations(h.get(), p->order, m, nr, Tr);
@@ -809,8 +815,12 @@ int rlbm_internal_prepare(const rlbm_params* p, Scalars* sc, Tables<float>* tf, 
   s.wall_T[0] = p->wall_T[0];
   s.wall_T[1] = p->wall_T[1];
   finish_scalars(&s);
-  // the orbit-symmetric kernels carry neither the force term nor the walls
-  s.sym = (orbit_symmetric(&h) && !s.force && s.boundary != RLBM_BC_EQWALL_X) ? 1 : 0;
+  // as in rlbm_create
+  {
+    const bool orb = orbit_symmetric(&h), fw = s.force || s.boundary == RLBM_BC_EQWALL_X;
+    s.sym = (orb && !fw) ? 1 : 0;
+    s.sym_fw = (orb && fw && s.K == 9) ? 1 : 0;
+  }
   if ((long long)h.q.Q * s.plane >= (1LL << 31)) {
     *err = "grid too large: Q * plane must stay below 2^31 elements";
     return RLBM_ERR_UNSUPPORTED;

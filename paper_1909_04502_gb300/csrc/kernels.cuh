@@ -71,6 +71,7 @@ struct Scalars {
   // FP32 copies of the scalars used by the FP32-storage kernels
   float f_tau, f_tau_coef, f_m, f_n_ref, f_T_ref, f_T00_ref, f_Tii_ref;
   float f_PE_hi, f_PE_lo;  // P_ref + eps_ref as a float-float pair (hi + lo)
+  int sym_fw;              // orbit-ordered stencil with exactly symmetric H, with a force or walls
 };
 
 // Parity of the px and py exponents of basis monomial k of setup.h

@@ -631,7 +631,9 @@ __device__ __forceinline__ void feq_orbit4(const S (&h)[kMaxK], const S (&dM)[KT
 // of different sizes), otherwise from the per-handle table tb.pl.
 // MOUT (FP32 storage): also write the cell's macroscopic state to macro
 // (planes of kMacroPlanes; n is NaN where the update was non-physical).
-template <typename S, int QT, bool EX, int KT, bool SYM = false, bool DYN = false, bool MOUT = false>
+// FW (with SYM): the orbit-symmetric evaluation with the force term and the
+// equilibrium walls of the generic path.
+template <typename S, int QT, bool EX, int KT, bool SYM = false, bool DYN = false, bool MOUT = false, bool FW = false>
 __device__ __forceinline__ void collide_store(const Tables<S>& tb, const Scalars& s, S (&g)[QT],
                                               S* __restrict__ fout, const S* __restrict__ tau_field,
                                               unsigned long long* status, int x, int y,
@@ -673,9 +675,58 @@ __device__ __forceinline__ void collide_store(const Tables<S>& tb, const Scalars
     g[i] = fma(om, feq - g[i], g[i]);
     obase[plane_of(i)] = g[i];
   };
+  // Forcing scheme B (Sec. 4.4), gravity-like force K = (g.p, p^0 g):
+  // F_i = (m/T) f^eq_i (U^0 g.v_i - g.U), with the full f^eq (the stored
+  // shift f_ref added back).  Equilibrium walls (first and last column):
+  // the cell keeps f^eq(n, U = (1, 0, 0), T_w) instead, T_w the prescribed
+  // wall temperature or the cell's own T.
+  S cf = S(0), gx = S(0), gy = S(0), gU = S(0);
+  bool wall = false;
+  S dMw[KT];
+  if (!SYM || FW) {
+    if (s.force && M.ok) {
+      if constexpr (sizeof(S) == 4) { cf = __fdividef(s.f_m, M.fT); gx = s.f_gx; gy = s.f_gy; }
+      else { cf = s.m / M.T; gx = s.gx; gy = s.gy; }
+      gU = gx * Ux + gy * Uy;
+    }
+    wall = s.boundary == 2 && (x == 0 || x == s.nx - 1) && M.ok;
+    if (wall) {
+      const int side = x == 0 ? 0 : 1;
+      if constexpr (sizeof(S) == 4) {
+        const bool fix = s.f_wall_T[side] > 0.f;
+        const float Tw = fix ? s.f_wall_T[side] : M.fT;
+        const float dTw = fix ? (float)(s.wall_T[side] - s.T_ref) : M.fdT;
+        eq_moments<S, KT>(M.fdn, dTw, M.fn, Tw, S(1), S(0), S(0), s.f_m, s.f_n_ref, s.f_T_ref, dMw);
+      } else {
+        const double Tw = s.wall_T[side] > 0.0 ? s.wall_T[side] : M.T;
+        eq_moments<S, KT>(M.n - s.n_ref, Tw - s.T_ref, M.n, Tw, S(1), S(0), S(0), s.m, s.n_ref, s.T_ref, dMw);
+      }
+    }
+  }
   if constexpr (SYM) {
     using O = Orbits<QT>;
     const S U0k = U0 * kt, Uxk = Ux * kt, Uyk = Uy * kt;
+    if constexpr (FW) {
+      // a wall cell evaluates the orbits at the wall state and stores f^eq
+      // unrelaxed; elsewhere the force term follows the relaxation
+      if (wall) {
+#pragma unroll
+        for (int k = 0; k < KT; ++k) dM[k] = dMw[k];
+      }
+    }
+    auto relax_sym = [&](int i, S feq, S om) {
+      if constexpr (FW) {
+        if (wall) {
+          g[i] = feq;
+        } else {
+          g[i] = fma(om, feq - g[i], g[i]);
+          if (cf != S(0)) g[i] = fma(cf * (feq + tb.fref[i]), U0 * (gx * tb.vx[i] + gy * tb.vy[i]) - gU, g[i]);
+        }
+        obase[plane_of(i)] = g[i];
+      } else {
+        relax(i, feq, om);
+      }
+    };
     // Omega of a sign quartet with base velocity (va, vb), members (+,+), (-,+), (+,-), (-,-)
     auto quartet_om = [&](S va, S vb, S (&om)[4]) {
       const S X = Uxk * va, Y = Uyk * vb;
@@ -690,9 +741,9 @@ __device__ __forceinline__ void collide_store(const Tables<S>& tb, const Scalars
       quartet_om(tb.vx[i0], tb.vy[i0], oa);
       quartet_om(tb.vx[i0 + 4], tb.vy[i0 + 4], ob);
 #pragma unroll
-      for (int m = 0; m < 4; ++m) relax(i0 + m, f[m], oa[m]);
+      for (int m = 0; m < 4; ++m) relax_sym(i0 + m, f[m], oa[m]);
 #pragma unroll
-      for (int m = 0; m < 4; ++m) relax(i0 + 4 + m, f[4 + m], ob[m]);
+      for (int m = 0; m < 4; ++m) relax_sym(i0 + 4 + m, f[4 + m], ob[m]);
     }
 #pragma unroll
     for (int o = 0; o < O::n4; ++o) {
@@ -700,10 +751,10 @@ __device__ __forceinline__ void collide_store(const Tables<S>& tb, const Scalars
       S f[4];
       feq_orbit4<S, KT>(tb.H[i0], dM, f);
       const S X = Uxk * tb.vx[i0], Y = Uyk * tb.vx[i0];   // members (v,0), (-v,0), (0,v), (0,-v)
-      relax(i0, f[0], U0k - X);
-      relax(i0 + 1, f[1], U0k + X);
-      relax(i0 + 2, f[2], U0k - Y);
-      relax(i0 + 3, f[3], U0k + Y);
+      relax_sym(i0, f[0], U0k - X);
+      relax_sym(i0 + 1, f[1], U0k + X);
+      relax_sym(i0 + 2, f[2], U0k - Y);
+      relax_sym(i0 + 3, f[3], U0k + Y);
     }
 #pragma unroll
     for (int o = 0; o < O::nd; ++o) {
@@ -712,39 +763,14 @@ __device__ __forceinline__ void collide_store(const Tables<S>& tb, const Scalars
       feq_diag4<S, KT>(tb.H[i0], dM, f);
       quartet_om(tb.vx[i0], tb.vy[i0], om);
 #pragma unroll
-      for (int m = 0; m < 4; ++m) relax(i0 + m, f[m], om[m]);
+      for (int m = 0; m < 4; ++m) relax_sym(i0 + m, f[m], om[m]);
     }
 #pragma unroll
     for (int o = 0; o < O::n1; ++o) {
       const int i0 = OrbitStart<QT>::rest + o;
-      relax(i0, feq_rest<S, KT>(tb.H[i0], dM), U0k);
+      relax_sym(i0, feq_rest<S, KT>(tb.H[i0], dM), U0k);
     }
   } else {
-    // Forcing scheme B (Sec. 4.4), gravity-like force K = (g.p, p^0 g):
-    // F_i = (m/T) f^eq_i (U^0 g.v_i - g.U), with the full f^eq (the stored
-    // shift f_ref added back).  Equilibrium walls (first and last column):
-    // the cell keeps f^eq(n, U = (1, 0, 0), T_w) instead, T_w the prescribed
-    // wall temperature or the cell's own T.
-    S cf = S(0), gx = S(0), gy = S(0), gU = S(0);
-    if (s.force && M.ok) {
-      if constexpr (sizeof(S) == 4) { cf = __fdividef(s.f_m, M.fT); gx = s.f_gx; gy = s.f_gy; }
-      else { cf = s.m / M.T; gx = s.gx; gy = s.gy; }
-      gU = gx * Ux + gy * Uy;
-    }
-    const bool wall = s.boundary == 2 && (x == 0 || x == s.nx - 1) && M.ok;
-    S dMw[KT];
-    if (wall) {
-      const int side = x == 0 ? 0 : 1;
-      if constexpr (sizeof(S) == 4) {
-        const bool fix = s.f_wall_T[side] > 0.f;
-        const float Tw = fix ? s.f_wall_T[side] : M.fT;
-        const float dTw = fix ? (float)(s.wall_T[side] - s.T_ref) : M.fdT;
-        eq_moments<S, KT>(M.fdn, dTw, M.fn, Tw, S(1), S(0), S(0), s.f_m, s.f_n_ref, s.f_T_ref, dMw);
-      } else {
-        const double Tw = s.wall_T[side] > 0.0 ? s.wall_T[side] : M.T;
-        eq_moments<S, KT>(M.n - s.n_ref, Tw - s.T_ref, M.n, Tw, S(1), S(0), S(0), s.m, s.n_ref, s.T_ref, dMw);
-      }
-    }
 #pragma unroll
     for (int i = 0; i < QT; ++i) {
       if (i < Qn) {
@@ -777,13 +803,14 @@ __device__ __forceinline__ void collide_store(const Tables<S>& tb, const Scalars
 
 // One cell of the fused step (Sec. 6.2, steps 1-8): pull-gather from global
 // memory, then collide_store.
-template <typename S, int QT, bool EX, int KT, int MODE, bool DYN = false, bool NC = true, bool SYM = false>
+template <typename S, int QT, bool EX, int KT, int MODE, bool DYN = false, bool NC = true, bool SYM = false,
+          bool FW = false>
 __device__ __forceinline__ void cell_update(const Tables<S>& tb, const Scalars& s, const S* __restrict__ fin,
                                             S* __restrict__ fout, const S* __restrict__ tau_field,
                                             unsigned long long* status, int x, int y) {
   S g[QT];
   gather<S, QT, EX, MODE, DYN, NC>(tb, s, fin, sidx(s, x, y), g);
-  collide_store<S, QT, EX, KT, SYM, DYN>(tb, s, g, fout, tau_field, status, x, y);
+  collide_store<S, QT, EX, KT, SYM, DYN, false, FW>(tb, s, g, fout, tau_field, status, x, y);
 }
 
 // FP32 storage: 1024 resident threads per SM (eight 32 x 4 blocks, at most
@@ -799,14 +826,16 @@ __device__ __forceinline__ void cell_update(const Tables<S>& tb, const Scalars& 
 // populations the spills of 512 threads cost less than the lost warps (3 %).
 // SYM: orbit-symmetric moments and equilibrium (built-in massless stencils).
 // MOUT: also write the macroscopic state (a.macro).
-template <typename S, int QT, int MODE, bool SYM>
+// FW: SYM with the force term and the equilibrium walls (six blocks, as the
+// generic kernels that otherwise carry them).
+template <typename S, int QT, int MODE, bool SYM, bool FW = false>
 constexpr int step_threads_per_sm() {
-  return sizeof(S) == 4 ? (QT <= 40 ? (MODE == kBilinear ? 896 : (SYM ? 1024 : 768)) : 512)
+  return sizeof(S) == 4 ? (QT <= 40 ? (MODE == kBilinear ? 896 : (SYM && !FW ? 1024 : 768)) : 512)
                         : (QT <= 56 ? 512 : 256);
 }
 
-template <typename S, int QT, bool EX, int KT, int MODE, bool SYM, bool MOUT = false>
-__global__ void __launch_bounds__(kThreads, step_threads_per_sm<S, QT, MODE, SYM>() / kThreads) k_step(const __grid_constant__ Tables<S> tb,
+template <typename S, int QT, bool EX, int KT, int MODE, bool SYM, bool MOUT = false, bool FW = false>
+__global__ void __launch_bounds__(kThreads, step_threads_per_sm<S, QT, MODE, SYM, FW>() / kThreads) k_step(const __grid_constant__ Tables<S> tb,
                                                    const __grid_constant__ StepArgs<S> a) {
   const int x = blockIdx.x * kBX + threadIdx.x;
   const int y = blockIdx.y * kBY + threadIdx.y;
@@ -816,7 +845,7 @@ __global__ void __launch_bounds__(kThreads, step_threads_per_sm<S, QT, MODE, SYM
     gather<S, QT, EX, MODE>(tb, a.s, a.fin, sidx(a.s, x, y), g);
     collide_store<S, QT, EX, KT, SYM, false, true>(tb, a.s, g, a.fout, a.tau_field, a.status, x, y, a.macro);
   } else {
-    cell_update<S, QT, EX, KT, MODE, false, true, SYM>(tb, a.s, a.fin, a.fout, a.tau_field, a.status, x, y);
+    cell_update<S, QT, EX, KT, MODE, false, true, SYM, FW>(tb, a.s, a.fin, a.fout, a.tau_field, a.status, x, y);
   }
 }
 
@@ -895,10 +924,10 @@ inline dim3 block_dim() { return dim3(kBX, kBY); }
 
 // QT: population count of the instantiation; EX: the stencil has exactly QT
 // populations (no per-population bounds test), otherwise Q <= QT at run time.
-template <typename S, int QT, bool EX, int KT, bool SYM = false, bool MOUT = false>
+template <typename S, int QT, bool EX, int KT, bool SYM = false, bool MOUT = false, bool FW = false>
 cudaError_t launch_step_q(const Tables<S>& tb, const StepArgs<S>& a, int mode, cudaStream_t st) {
-  if (mode == kOnLattice) k_step<S, QT, EX, KT, kOnLattice, SYM, MOUT><<<grid_for(a.s), block_dim(), 0, st>>>(tb, a);
-  else k_step<S, QT, EX, KT, kBilinear, SYM, MOUT><<<grid_for(a.s), block_dim(), 0, st>>>(tb, a);
+  if (mode == kOnLattice) k_step<S, QT, EX, KT, kOnLattice, SYM, MOUT, FW><<<grid_for(a.s), block_dim(), 0, st>>>(tb, a);
+  else k_step<S, QT, EX, KT, kBilinear, SYM, MOUT, FW><<<grid_for(a.s), block_dim(), 0, st>>>(tb, a);
   return cudaGetLastError();
 }
 

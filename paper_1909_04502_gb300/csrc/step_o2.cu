@@ -15,6 +15,15 @@ cudaError_t launch_step_k9(const Tables<S>& tb, const StepArgs<S>& a, int mode, 
     return launch_step_q<S, 28, true, 9, true>(tb, a, mode, st);
   }
   if (a.macro) return cudaErrorInvalidValue;   // macroscopic output: built-in massless FP32 stencil only
+  if (a.s.sym_fw) {                             // the same with the force term or equilibrium walls
+    switch (a.s.Q) {
+      case 28: return launch_step_q<S, 28, true, 9, true, false, true>(tb, a, mode, st);
+      case 25: return launch_step_q<S, 25, true, 9, true, false, true>(tb, a, mode, st);
+      case 29: return launch_step_q<S, 29, true, 9, true, false, true>(tb, a, mode, st);
+      case 33: return launch_step_q<S, 33, true, 9, true, false, true>(tb, a, mode, st);
+      default: break;
+    }
+  }
   if (a.s.sym) {
     switch (a.s.Q) {
       case 25: return launch_step_q<S, 25, true, 9, true>(tb, a, mode, st);
