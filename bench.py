@@ -710,9 +710,8 @@ def bench_forcing_walls(torch, rlbm, inputs, stream, nx=4096, ny=1024, m=5.0, st
     bandwidth: a massive gas (m~ = 5, order 2, Q = 29) between equilibrium
     walls at the first and last column, periodic in y, driven by the
     gravity-like force g = (0, 1e-8) (forcing scheme B), FP64 and FP32
-    storage.  These run the generic (not orbit-symmetric) kernel, which
-    carries the force and wall terms.  Each buffer holds 3.9 (FP64) or
-    1.9 GB (FP32), more than L2."""
+    storage, on the orbit-symmetric kernel with the force and wall terms.
+    Each buffer holds 3.9 (FP64) or 1.9 GB (FP32), more than L2."""
     import numpy as np
     peak, _ = _peaks()
     out = {"workload": f"channel{nx}x{ny}_m{m:g}_eqwalls_force"}
