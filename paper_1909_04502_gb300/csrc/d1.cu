@@ -37,6 +37,7 @@ namespace rlbm1 {
 constexpr int kMaxN = 5;               // App. H tables: orders 2 ... 5
 constexpr int kMaxQ = 2 * kMaxN;
 constexpr int kThreads = 128;
+constexpr int kStep1CPT = 2;           // cells per thread of the FP32-storage step
 
 // App. H, (1+1) dimensions: shells and per-direction weights.  Order 4 is
 // printed with its columns exchanged (the printed weights are the roots of
@@ -238,16 +239,11 @@ __device__ __forceinline__ void moments_dM_f32(float n, float dn, float T, float
   }
 }
 
+// One cell of the FP32-storage step from its pulled populations g.
 template <int N>
-__global__ void __launch_bounds__(kThreads) k_step1f(const __grid_constant__ Tab<float> tb,
-                                                     const __grid_constant__ Sc s, const float* __restrict__ fin,
-                                                     float* __restrict__ fout, unsigned long long* status) {
+__device__ __forceinline__ void cell1f(const Tab<float>& tb, const Sc& s, const float (&g)[2 * N], int x,
+                                       float* __restrict__ fout, unsigned long long* status) {
   constexpr int Q = 2 * N;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= s.nx) return;
-  float g[Q];
-#pragma unroll
-  for (int i = 0; i < Q; ++i) g[i] = __ldg(fin + (long long)i * s.P + x + 1 - tb.s[i]);   // pull
   // the four moment sums, compensated: every product g p0^k split exactly
   // (FMA), every addition exactly (two-sum), the errors and the lo parts of
   // p0^k summed in a second register.  Plain FP32 sums measured 2.5x the
@@ -322,6 +318,33 @@ __global__ void __launch_bounds__(kThreads) k_step1f(const __grid_constant__ Tab
     for (int k = 0; k < Q; ++k) fe = fmaf(tb.Hs[i][k], dM[k], fe);
     const float om = kt * (U0 - (float)tb.s[i] * Ux);     // p.U / (p0 tau)
     store1<float>(s, fout, i, x, fmaf(om, fe - g[i], g[i]));
+  }
+}
+
+// CPT cells per thread, kThreads apart: every thread issues the pulls of
+// all its cells before it computes, so that more loads are in flight.  On
+// 2^24 cells two cells per thread were 2-5 % faster than one (orders 2-5),
+// four and eight slower; the step is bound by the compensated sums' issue
+// rather than by loads in flight.
+template <int N, int CPT>
+__global__ void __launch_bounds__(kThreads) k_step1f(const __grid_constant__ Tab<float> tb,
+                                                     const __grid_constant__ Sc s, const float* __restrict__ fin,
+                                                     float* __restrict__ fout, unsigned long long* status) {
+  constexpr int Q = 2 * N;
+  const int x0 = blockIdx.x * (kThreads * CPT) + threadIdx.x;
+  float g[CPT][Q];
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) {
+    const int x = x0 + c * kThreads;
+    if (x < s.nx) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) g[c][i] = __ldg(fin + (long long)i * s.P + x + 1 - tb.s[i]);   // pull
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) {
+    const int x = x0 + c * kThreads;
+    if (x < s.nx) cell1f<N>(tb, s, g[c], x, fout, status);
   }
 }
 
@@ -614,11 +637,12 @@ int rlbm1_step(rlbm1_handle* h, int nsteps) {
     if (h->elem == 4) {
       const float* in = (const float*)h->buf[h->cur];
       float* o = (float*)h->buf[h->cur ^ 1];
+      const dim3 gr((h->sc.nx + kThreads * kStep1CPT - 1) / (kThreads * kStep1CPT));
       switch (h->sc.N) {
-        case 2: k_step1f<2><<<grid1(h->sc.nx), kThreads, 0, h->stream>>>(*h->tf, h->sc, in, o, h->status); break;
-        case 3: k_step1f<3><<<grid1(h->sc.nx), kThreads, 0, h->stream>>>(*h->tf, h->sc, in, o, h->status); break;
-        case 4: k_step1f<4><<<grid1(h->sc.nx), kThreads, 0, h->stream>>>(*h->tf, h->sc, in, o, h->status); break;
-        default: k_step1f<5><<<grid1(h->sc.nx), kThreads, 0, h->stream>>>(*h->tf, h->sc, in, o, h->status); break;
+        case 2: k_step1f<2, kStep1CPT><<<gr, kThreads, 0, h->stream>>>(*h->tf, h->sc, in, o, h->status); break;
+        case 3: k_step1f<3, kStep1CPT><<<gr, kThreads, 0, h->stream>>>(*h->tf, h->sc, in, o, h->status); break;
+        case 4: k_step1f<4, kStep1CPT><<<gr, kThreads, 0, h->stream>>>(*h->tf, h->sc, in, o, h->status); break;
+        default: k_step1f<5, kStep1CPT><<<gr, kThreads, 0, h->stream>>>(*h->tf, h->sc, in, o, h->status); break;
       }
     } else
       k_step1<double><<<grid1(h->sc.nx), kThreads, 0, h->stream>>>(*h->td, h->sc, (const double*)h->buf[h->cur],
