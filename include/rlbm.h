@@ -468,7 +468,10 @@ int rlbm1_plan(int order, int* Q, int* nvec, double* p, double* w, double* H);
  * the cell's own T); precision RLBM_FP64 or RLBM_FP32_STORE (populations
  * stored as f - f_ref in FP32, f_ref the equilibrium of n = T = 1 at rest);
  * stream: the cudaStream_t work is issued on.  Allocates two population
- * buffers of 2 order (nx + 2) elements and field buffers.  Synchronous. */
+ * buffers of 2 order (nx + 2) elements and field buffers.  Synchronous.
+ * RLBM_ERR_QUADRATURE if the table lacks the direction symmetry the FP32
+ * step uses (each pair's second H row the first with the odd members'
+ * signs flipped; the built-in tables have it exactly). */
 int rlbm1_create(int nx, int order, double tau, int boundary, const double* wall_T, int precision,
                  void* stream, rlbm1_handle** out);
 void rlbm1_destroy(rlbm1_handle* h);

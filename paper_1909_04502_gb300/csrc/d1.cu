@@ -239,6 +239,27 @@ __device__ __forceinline__ void moments_dM_f32(float n, float dn, float T, float
   }
 }
 
+// Store the Q values of cell x, and for an end cell its halo image (as
+// store1), the image stores behind one branch that interior warps skip.
+template <int Q>
+__device__ __forceinline__ void store_cell1f(const Sc& s, float* out, int x, const float (&v)[Q]) {
+#pragma unroll
+  for (int i = 0; i < Q; ++i) out[(long long)i * s.P + x + 1] = v[i];
+  if (x == 0 || x == s.nx - 1) {
+    const bool per = s.boundary == RLBM_BC_PERIODIC;
+    if (x == 0) {
+      const int hx = per ? s.nx + 1 : 0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) out[(long long)i * s.P + hx] = v[i];
+    }
+    if (x == s.nx - 1) {
+      const int hx = per ? 0 : s.nx + 1;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) out[(long long)i * s.P + hx] = v[i];
+    }
+  }
+}
+
 // One cell of the FP32-storage step from its pulled populations g.
 template <int N>
 __device__ __forceinline__ void cell1f(const Tab<float>& tb, const Sc& s, const float (&g)[2 * N], int x,
@@ -248,27 +269,40 @@ __device__ __forceinline__ void cell1f(const Tab<float>& tb, const Sc& s, const 
   // (FMA), every addition exactly (two-sum), the errors and the lo parts of
   // p0^k summed in a second register.  Plain FP32 sums measured 2.5x the
   // error of exact ones against the oracle (their rounding is not a
-  // consistent change of the state)
-  float m[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+  // consistent change of the state).  Population i = 2j + b is shell j
+  // moving in direction +1 (b = 0) or -1 (b = 1) (build_tables), so the sums
+  // run separately over the two directions -- A: sum g p0, B: sum g p0^2 --
+  // and N^0 = A+ + A-, N^x = A+ - A-, T^00 = B+ + B-, T^0x = B+ - B- are
+  // formed at the end, each in one two-sum.
+  float m[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};   // A+, A-, B+, B-
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const float sg = tb.s[i] > 0 ? 1.f : -1.f;
+    const int b = i & 1;
     const float p1 = __fmul_rn(g[i], tb.w1h[i]);   // not contracted into the sums below
     const float p2 = __fmul_rn(g[i], tb.w2h[i]);
     const float r1 = fmaf(g[i], tb.w1l[i], fmaf(g[i], tb.w1h[i], -p1));   // p1's error + the lo part
     const float r2 = fmaf(g[i], tb.w2l[i], fmaf(g[i], tb.w2h[i], -p2));
-    const float p[4] = {p1, sg * p1, p2, sg * p2};
-    const float r[4] = {r1, sg * r1, r2, sg * r2};
+    const float p[2] = {p1, p2};
+    const float r[2] = {r1, r2};
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const float t = m[k] + p[k];
-      const float bb = t - m[k];
-      const float err = (m[k] - (t - bb)) + (p[k] - bb);
-      m[k] = t;
-      c[k] += err + r[k];
+    for (int k = 0; k < 2; ++k) {
+      const int a = 2 * k + b;
+      const float t = m[a] + p[k];
+      const float bb = t - m[a];
+      const float err = (m[a] - (t - bb)) + (p[k] - bb);
+      m[a] = t;
+      c[a] += err + r[k];
     }
   }
-  const float dN0 = m[0] + c[0], Nx = m[1] + c[1], dE = m[2] + c[2], T0x = m[3] + c[3];
+  // (hi_a + lo_a) + sgn (hi_b + lo_b), the hi parts added exactly
+  auto combine = [](float ha, float la, float hb, float lb) {
+    const float t = ha + hb;
+    const float bb = t - ha;
+    const float err = (ha - (t - bb)) + (hb - bb);
+    return t + (err + (la + lb));
+  };
+  const float dN0 = combine(m[0], c[0], m[1], c[1]), Nx = combine(m[0], c[0], -m[1], -c[1]);
+  const float dE = combine(m[2], c[2], m[3], c[3]), T0x = combine(m[2], c[2], -m[3], -c[3]);
   const float Er = s.f_Er, nr = s.f_n_ref, Tr = s.f_T_ref;
   const float E = Er + dE;
   const float q = (E - T0x) * (E + T0x);
@@ -287,11 +321,23 @@ __device__ __forceinline__ void cell1f(const Tab<float>& tb, const Sc& s, const 
                   isfinite(U0) && isfinite(dn);
   if (!ok) {
     atomicAdd(status, 1ULL);                                 // left unrelaxed (Omega = 0)
-#pragma unroll
-    for (int i = 0; i < Q; ++i) store1<float>(s, fout, i, x, g[i]);
+    store_cell1f<Q>(s, fout, x, g);
     return;
   }
-  float dM[Q];
+  // f^eq of the pair (shell j, +1), (shell j, -1) from the first row: the
+  // rows differ by the sign of the odd members (phi_{a,1} changes sign with
+  // the direction; exact in the table, checked on the host), so
+  // f^eq = E +- O with E, O the even- and odd-member partial sums
+  auto feq_pair = [&](int j, const float (&dM)[Q], float& fp, float& fm) {
+    float E = 0.f, O = 0.f;
+#pragma unroll
+    for (int k = 0; k < Q; k += 2) E = fmaf(tb.Hs[2 * j][k], dM[k], E);
+#pragma unroll
+    for (int k = 1; k < Q; k += 2) O = fmaf(tb.Hs[2 * j][k], dM[k], O);
+    fp = E + O;
+    fm = E - O;
+  };
+  float dM[Q], o[Q];
   const bool wall = s.boundary == RLBM_BC_EQWALL_X && (x == 0 || x == s.nx - 1);
   if (wall) {
     // f^eq(n, rest, T_w): theta = 0, T_w the prescribed wall temperature or the cell's own
@@ -300,25 +346,22 @@ __device__ __forceinline__ void cell1f(const Tab<float>& tb, const Sc& s, const 
     const float Tw = fix ? s.f_wall_T[side] : T, dTw = fix ? s.f_wall_dT[side] : dT;
     moments_dM_f32<N>(n, dn, Tw, dTw, 0.f, 1.f, nr, Tr, dM);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      float fe = 0.f;
-#pragma unroll
-      for (int k = 0; k < Q; ++k) fe = fmaf(tb.Hs[i][k], dM[k], fe);
-      store1<float>(s, fout, i, x, fe);
-    }
+    for (int j = 0; j < N; ++j) feq_pair(j, dM, o[2 * j], o[2 * j + 1]);
+    store_cell1f<Q>(s, fout, x, o);
     return;
   }
   const float Em1 = Ux + __fdividef(Ux * Ux, U0 + 1.f);     // e^theta - 1
   moments_dM_f32<N>(n, dn, T, dT, Em1, 1.f + Em1, nr, Tr, dM);
   const float kt = s.f_inv_tau;
+  const float omp = kt * (U0 - Ux), omm = kt * (U0 + Ux);   // p.U / (p0 tau), directions +1 and -1
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    float fe = 0.f;
-#pragma unroll
-    for (int k = 0; k < Q; ++k) fe = fmaf(tb.Hs[i][k], dM[k], fe);
-    const float om = kt * (U0 - (float)tb.s[i] * Ux);     // p.U / (p0 tau)
-    store1<float>(s, fout, i, x, fmaf(om, fe - g[i], g[i]));
+  for (int j = 0; j < N; ++j) {
+    float fp, fm;
+    feq_pair(j, dM, fp, fm);
+    o[2 * j] = fmaf(omp, fp - g[2 * j], g[2 * j]);
+    o[2 * j + 1] = fmaf(omm, fm - g[2 * j + 1], g[2 * j + 1]);
   }
+  store_cell1f<Q>(s, fout, x, o);
 }
 
 // CPT cells per thread, kThreads apart: every thread issues the pulls of
@@ -338,7 +381,7 @@ __global__ void __launch_bounds__(kThreads) k_step1f(const __grid_constant__ Tab
     const int x = x0 + c * kThreads;
     if (x < s.nx) {
 #pragma unroll
-      for (int i = 0; i < Q; ++i) g[c][i] = __ldg(fin + (long long)i * s.P + x + 1 - tb.s[i]);   // pull
+      for (int i = 0; i < Q; ++i) g[c][i] = __ldg(fin + (long long)i * s.P + x + 2 * (i & 1));   // pull from x - s
     }
   }
 #pragma unroll
@@ -395,6 +438,8 @@ bool build_tables(int order, std::vector<double>* p0, std::vector<int>* sgn, std
   p0->clear();
   sgn->clear();
   w->clear();
+  // population 2j + b: shell j, direction +1 (b = 0) or -1 (b = 1); the
+  // FP32-storage step takes this order as given
   for (int j = 0; j < order; ++j)
     for (int s : {1, -1}) {
       p0->push_back(t->p0[j]);
@@ -534,6 +579,13 @@ int rlbm1_create(int nx, int order, double tau, int boundary, const double* wall
   std::unique_ptr<rlbm1_handle> h(new rlbm1_handle());
   std::vector<double> H;
   if (!build_tables(order, &h->p0, &h->sgn, &h->w, &H)) return fail1(nullptr, RLBM_ERR_INVALID_ARG, "order must be 2 ... 5");
+  // the FP32-storage step takes each pair's second row as the first with the
+  // odd members' signs flipped, and the directions as +1, -1 alternating
+  for (int j = 0; j < order; ++j)
+    for (int k = 0; k < 2 * order; ++k)
+      if (h->sgn[2 * j] != 1 || h->sgn[2 * j + 1] != -1 ||
+          H[(size_t)(2 * j + 1) * 2 * order + k] != ((k & 1) ? -1.0 : 1.0) * H[(size_t)2 * j * 2 * order + k])
+        return fail1(nullptr, RLBM_ERR_QUADRATURE, "1-d equilibrium matrix without the direction symmetry");
   Sc& s = h->sc;
   s.N = order;
   s.Q = 2 * order;

@@ -38,6 +38,21 @@ def test_host_tables_reproduce_the_oracle_equilibrium(rl, order):
     assert np.abs(f_lib - f_orc).max() <= 1e-13 * np.abs(f_orc).max()
 
 
+@pytest.mark.parametrize("order", ORDERS)
+def test_host_tables_have_the_direction_symmetry_the_fp32_step_uses(rl, order):
+    """Populations alternate between the directions +1 and -1 shell by shell,
+    and the second row of each pair equals the first with the odd members'
+    signs flipped, exactly (phi_{a,1} changes sign with the direction): the
+    FP32-storage step evaluates each pair's equilibrium as E +- O from the
+    first row alone."""
+    d = rl.plan1(order)
+    Q, H = d["Q"], d["H"]
+    assert np.array_equal(d["n"], np.array([1, -1] * order))
+    flip = np.array([1.0 if k % 2 == 0 else -1.0 for k in range(Q)])
+    for j in range(order):
+        assert np.array_equal(H[2 * j + 1], flip * H[2 * j])
+
+
 def test_invalid_arguments_are_refused(rl):
     import ctypes
     h = ctypes.c_void_p()
