@@ -821,6 +821,9 @@ __device__ __forceinline__ void cell_update(const Tables<S>& tb, const Scalars& 
 // (not orbit-symmetric) on-lattice kernels, which carry the force and wall
 // terms, run six blocks at up to 80 registers instead of spilling 1.6 KB at
 // 64.
+// FP32 storage with more than 40 populations (order 3): five blocks per SM
+// (96 registers, no spills) for the orbit-symmetric kernels, four for the
+// generic ones, which spill kilobytes at 96.
 // FP64 storage with more than 56 populations: 256 threads per SM, so that a
 // cell's 64-72 doubles stay in registers (12 % faster at Q = 65); up to 56
 // populations the spills of 512 threads cost less than the lost warps (3 %).
@@ -830,7 +833,7 @@ __device__ __forceinline__ void cell_update(const Tables<S>& tb, const Scalars& 
 // generic kernels that otherwise carry them).
 template <typename S, int QT, int MODE, bool SYM, bool FW = false>
 constexpr int step_threads_per_sm() {
-  return sizeof(S) == 4 ? (QT <= 40 ? (MODE == kBilinear ? 896 : (SYM && !FW ? 1024 : 768)) : 512)
+  return sizeof(S) == 4 ? (QT <= 40 ? (MODE == kBilinear ? 896 : (SYM && !FW ? 1024 : 768)) : (SYM ? 640 : 512))
                         : (QT <= 56 ? 512 : 256);
 }
 
