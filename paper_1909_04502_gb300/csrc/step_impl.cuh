@@ -821,9 +821,11 @@ __device__ __forceinline__ void cell_update(const Tables<S>& tb, const Scalars& 
 // (not orbit-symmetric) on-lattice kernels, which carry the force and wall
 // terms, run six blocks at up to 80 registers instead of spilling 1.6 KB at
 // 64.
-// FP32 storage with more than 40 populations (order 3): five blocks per SM
-// (96 registers, no spills) for the orbit-symmetric kernels, four for the
-// generic ones, which spill kilobytes at 96.
+// FP32 storage with more than 40 populations (order 3): the orbit-symmetric
+// kernels run six blocks per SM up to 49 populations (80 registers, at most
+// 8 bytes spilled) and five above (96 registers, no spills), the generic
+// ones four (they spill kilobytes at 96).  Paper setup (Q = 49, 512^2):
+// 31.0 / 29.2 / 27.2 us at four / five / six blocks.
 // FP64 storage with more than 56 populations: 256 threads per SM, so that a
 // cell's 64-72 doubles stay in registers (12 % faster at Q = 65); up to 56
 // populations the spills of 512 threads cost less than the lost warps (3 %).
@@ -833,7 +835,8 @@ __device__ __forceinline__ void cell_update(const Tables<S>& tb, const Scalars& 
 // generic kernels that otherwise carry them).
 template <typename S, int QT, int MODE, bool SYM, bool FW = false>
 constexpr int step_threads_per_sm() {
-  return sizeof(S) == 4 ? (QT <= 40 ? (MODE == kBilinear ? 896 : (SYM && !FW ? 1024 : 768)) : (SYM ? 640 : 512))
+  return sizeof(S) == 4 ? (QT <= 40 ? (MODE == kBilinear ? 896 : (SYM && !FW ? 1024 : 768))
+                                    : (SYM ? (QT <= 49 ? 768 : 640) : 512))
                         : (QT <= 56 ? 512 : 256);
 }
 
