@@ -20,11 +20,11 @@ def rl():
     return rlbm
 
 
-def _pair(rl, nx, ny, m, g, boundary, precision, tau=0.9, seed=5, umax=0.2):
+def _pair(rl, nx, ny, m, g, boundary, precision, tau=0.9, seed=5, umax=0.2, order=2):
     fields = [np.ascontiguousarray(a) for a in inputs.random_smooth(nx, ny, seed=seed, umax=umax)]
-    lat = rl.Lattice(nx, ny, m=m, tau=tau, boundary=boundary, precision=precision, g=g)
-    d = rl.plan(nx=nx, ny=ny, m=m)
-    quad = oracle_quadrature(m, 2, d["n"], d["v0"])
+    lat = rl.Lattice(nx, ny, m=m, tau=tau, boundary=boundary, precision=precision, g=g, order=order)
+    d = rl.plan(nx=nx, ny=ny, m=m, order=order)
+    quad = oracle_quadrature(m, order, d["n"], d["v0"])
     idx = permutation(lat.n, lat.p, quad)
     sim = oracle_sim(quad, nx, ny, tau=tau, boundary=boundary, g=g)
     lat.init(*fields)
@@ -38,6 +38,22 @@ def test_forced_flow_between_equilibrium_walls_matches_oracle(rl, m, precision, 
     """40 x 24 (two tiles wide, ragged), walls at the first and last column,
     g with a component into the walls and one along them."""
     lat, sim, idx = _pair(rl, 40, 24, m, (2e-3, 5e-3), "eqwall_x", precision)
+    lat.step(steps)
+    sim.step(steps)
+    assert lat.sync_status()[0] == 0
+    assert rel_linf(lat.populations()[idx], sim.fs) <= tol
+    mo = lat.moments()
+    umax = max(np.abs(sim.fields.ux).max(), np.abs(sim.fields.uy).max())
+    assert np.abs(mo["uy"] - sim.fields.uy).max() <= tol * umax * 10
+    lat.close()
+
+
+@pytest.mark.parametrize("precision,steps,tol", [("fp64", 10, 1e-12), ("fp32", 20, 1e-5)])
+def test_order3_forced_flow_between_walls_on_the_generic_kernel(rl, precision, steps, tol):
+    """Order 3 (m~ = 5, Q = 49): the force and the walls run on the generic
+    (not orbit-symmetric) kernel, the order-2 cases above on the orbit-
+    symmetric one; 40 x 24 with walls at the first and last column."""
+    lat, sim, idx = _pair(rl, 40, 24, 5.0, (2e-3, 5e-3), "eqwall_x", precision, order=3)
     lat.step(steps)
     sim.step(steps)
     assert lat.sync_status()[0] == 0
