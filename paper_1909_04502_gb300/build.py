@@ -2,7 +2,8 @@
 
 Every ``.cu``/``.cpp`` under ``csrc/`` is compiled by nvcc in parallel, then
 linked into one shared library next to this file.  Rebuilds only when a
-source or header is newer than the library.
+source or header is newer than the library.  Each object's ptxas resource
+report (registers, spills per kernel) is kept beside it in ``_build/``.
 """
 from __future__ import annotations
 
@@ -34,6 +35,8 @@ def sources():
 def _stale():
     if not os.path.exists(LIB):
         return True
+    if any(not os.path.exists(os.path.join(BUILD, os.path.basename(src) + ".o.ptxas.txt")) for src in sources()):
+        return True
     t = os.path.getmtime(LIB)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
     deps.append(os.path.join(HERE, "..", "include", "rlbm.h"))
@@ -48,10 +51,13 @@ def build(force=False, verbose=False):
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, "-Xptxas", "-v", "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed on %s:\n%s" % (src, r.stderr))
+        # ptxas' resource report (registers, spills, shared memory per kernel)
+        with open(obj + ".ptxas.txt", "w") as fh:
+            fh.write(r.stderr)
         if verbose and r.stderr:
             print(r.stderr)
         return obj
